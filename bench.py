@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark: Wilson-Dirac hop (Dslash) GFLOP/s and its HBM roofline fraction
+on the 32^3 x 64 SU(3) workload, plus CG time-to-1e-10 of the mixed-precision
+solver against the plain FP64 solver on the same GPU.
+
+One step = the hopping term on the whole lattice in FP32 (both parity blocks,
+bsm_dslash EVEN then ODD, 1320 flop per site), L2 flushed between steps.
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): independent replicas, one lattice per GPU, no
+collective on the data path; the value is the whole-job rate (weak scaling).
+"""
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GFLOP/s (% of HBM roofline); CG time-to-1e-10 vs plain FP64 CG"
+WORKLOAD = dict(dims=(64, 32, 32, 32), N=3, m0=0.05, phase=(math.pi, 0.0, 0.0, 0.0), link_seed=3, eps=0.3,
+                src_seed=4)
+SAMPLE_DIMS = (32, 16, 16, 16)   # bounded CPU sample: same per-site work, 1/16 of the sites
+WORKLOAD_NAME = ("32^3x64 SU(3) fundamental, smooth links exp(i 0.3 H), m0=0.05, antiperiodic time: "
+                 "even-odd Wilson hop on both parity blocks, FP32 storage and arithmetic")
+
+
+def flops_per_site(d, real=False):
+    """Counting convention per output site of one hop: complex mul 6, add 2."""
+    return 64 * d * d + 56 * d if real else 128 * d * d + 56 * d
+
+
+def bytes_per_site(d, w, real=False):
+    """8 links + one input spinor (perfect neighbour reuse) + one output spinor."""
+    return (8 * d * d + 16 * d) * w if real else (16 * d * d + 16 * d) * w
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Polls SM clock and clock-event reasons through NVML (read-only) in a
+    background thread while the timed region runs."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x40: "sw_thermal_slowdown",
+               0x80: "hw_thermal_slowdown", 0x100: "hw_power_brake_slowdown", 0x2: "applications_clocks_setting"}
+
+    def __init__(self, uuid):
+        self.samples, self.reasons, self.max_mhz = [], set(), None
+        self.ok = False
+        try:
+            self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nv.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            if self.nv.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) != 0:
+                if self.nv.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(self.h)) != 0:
+                    return
+            m = ctypes.c_uint()
+            if self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(m)) == 0:
+                self.max_mhz = m.value
+            self.ok = True
+        except OSError:
+            pass
+
+    def sample(self):
+        c, r = ctypes.c_uint(), ctypes.c_ulonglong()
+        if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(c)) == 0:
+            self.samples.append(c.value)
+        if self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h, ctypes.byref(r)) == 0:
+            for bit, name in self.REASONS.items():
+                if r.value & bit:
+                    self.reasons.add(name)
+
+    def __enter__(self):
+        self.stop = threading.Event()
+        if self.ok:
+            def loop():
+                while not self.stop.is_set():
+                    self.sample()
+                    time.sleep(0.005)
+            self.t = threading.Thread(target=loop, daemon=True)
+            self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        if self.ok:
+            self.t.join()
+            if not self.samples:
+                self.sample()
+
+    def summary(self):
+        if not self.ok:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvml unavailable"]}
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples)}
+
+
+def time_oracle_hop(dims, min_seconds, max_reps=None):
+    """The oracle's full-lattice hop on a host-generated sample, repeated with
+    the doubling loop of the paper's timing method until min_seconds pass.
+    Returns (GFLOP/s, reps, seconds, threads)."""
+    import oracle as orc
+    from paper_1401_3733_gb300 import fields
+
+    w = WORKLOAD
+    lat = orc.Lattice(dims, w["N"], orc.FUND, w["m0"], w["phase"])
+    U = fields.gauge_field(dims, w["N"], "smooth", seed=w["link_seed"], eps=w["eps"])
+    R = orc.links_to_rep(lat, U)
+    psi = fields.gaussian_spinor(dims, lat.d, w["src_seed"])
+    orc.hop(lat, R, psi, orc.FULL)   # warm-up
+    reps, n, t0 = 0, 1, time.perf_counter()
+    while True:
+        for _ in range(n):
+            orc.hop(lat, R, psi, orc.FULL)
+        reps += n
+        el = time.perf_counter() - t0
+        if el >= min_seconds or (max_reps and reps >= max_reps):
+            break
+        n *= 2
+    gflops = reps * flops_per_site(lat.d) * lat.V / el / 1e9
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return gflops, reps, el, threads
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as orc
+    from paper_1401_3733_gb300 import fields
+    w = WORKLOAD
+    lat = orc.Lattice(SAMPLE_DIMS, w["N"], orc.FUND, w["m0"], w["phase"])
+    U = fields.gauge_field(SAMPLE_DIMS, w["N"], "smooth", seed=w["link_seed"], eps=w["eps"])
+    R = orc.links_to_rep(lat, U)
+    psi = fields.gaussian_spinor(SAMPLE_DIMS, lat.d, w["src_seed"])
+    for _ in range(args.warmup):
+        orc.hop(lat, R, psi, orc.FULL)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.hop(lat, R, psi, orc.FULL)
+    el = time.perf_counter() - t0
+    value = args.steps * flops_per_site(lat.d) * lat.V / el / 1e9
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"oracle hop (FP64 plain C, OpenMP over sites) on a {'x'.join(map(str, SAMPLE_DIMS))} lattice per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "sample": list(SAMPLE_DIMS)},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    from paper_1401_3733_gb300 import bsm, fields
+
+    w = WORKLOAD
+    dims, N = w["dims"], w["N"]
+    lat = bsm.lattice(dims, N, bsm.FUND, w["m0"], w["phase"])
+    d = bsm.bsm_rep_dim(N, bsm.FUND)
+    V = int(np.prod(dims))
+    Vh = V // 2
+    U = fields.gauge_field(dims, N, "smooth", seed=w["link_seed"] + rank, eps=w["eps"])
+    psi = fields.gaussian_spinor(dims, d, w["src_seed"] + rank)
+
+    stream = torch.cuda.current_stream()
+    Ud = torch.from_numpy(U).cuda()
+    links = {p: bsm.empty_field(lat, bsm.FIELD_LINKS, p) for p in (bsm.F64, bsm.F32)}
+    ev_l0, ev_l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev_l0.record()
+    bsm.bsm_links_to_rep(lat, Ud, links[bsm.F32], bsm.F32)
+    ev_l1.record()
+    bsm.bsm_links_to_rep(lat, Ud, links[bsm.F64], bsm.F64)
+    del Ud
+    psid = torch.from_numpy(psi).cuda()
+    src = {p: bsm.empty_field(lat, bsm.FIELD_SPINOR, p) for p in (bsm.F64, bsm.F32)}
+    dst = {p: bsm.empty_field(lat, bsm.FIELD_SPINOR, p) for p in (bsm.F64, bsm.F32)}
+    for p in (bsm.F64, bsm.F32):
+        bsm.bsm_pack_spinor(lat, psid, src[p], p)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+    torch.cuda.synchronize()
+    links_ms = ev_l0.elapsed_time(ev_l1)
+
+    def halves(t, prec):
+        n = bsm.bsm_field_bytes(lat, bsm.FIELD_HALF_SPINOR, prec)
+        return t[:n], t[n:]
+
+    def dslash_step(prec, evs=None):
+        se, so = halves(src[prec], prec)
+        de, do = halves(dst[prec], prec)
+        if evs:
+            evs[0].record()
+        bsm.bsm_dslash(lat, links[prec], so, de, bsm.EVEN, 0, prec)
+        if evs:
+            evs[1].record()
+        bsm.bsm_dslash(lat, links[prec], se, do, bsm.ODD, 0, prec)
+        if evs:
+            evs[2].record()
+
+    flop_step = flops_per_site(d) * V
+    for _ in range(args.warmup):
+        flush.zero_()
+        dslash_step(bsm.F32)
+    uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(uuid) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            dslash_step(bsm.F32, evs[k])
+        torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    launch_ms = [e[0].elapsed_time(e[1]) for e in evs] + [e[1].elapsed_time(e[2]) for e in evs]
+    ms_step = sum(launch_ms) / args.steps
+    ms_step_max = max_over_ranks(ms_step, world)
+    value = world * flop_step / (ms_step_max * 1e-3) / 1e9
+
+    peak, peak_src = load_peaks()
+    hop_bytes = bytes_per_site(d, 4) * Vh
+    avg_launch_ms = sum(launch_ms) / len(launch_ms)
+    achieved = hop_bytes / (avg_launch_ms * 1e-3) / 1e9
+
+    # FP64 Dslash on the same inputs (its own line; ALU-bound on this part)
+    ev64 = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(max(3, args.steps // 4))]
+    for e in ev64:
+        flush.zero_()
+        dslash_step(bsm.F64, e)
+    torch.cuda.synchronize()
+    ms64 = sum(e[0].elapsed_time(e[2]) for e in ev64) / len(ev64)
+
+    # end to end through the public API: pinned host canonical FP64 input ->
+    # pack -> hop on both parity blocks -> unpack -> pinned host output
+    h_in = torch.from_numpy(psi).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_in = torch.empty_like(psid)
+    d_out = torch.empty_like(psid)
+    n_e2e = max(3, min(args.steps, 10))
+
+    def e2e_step():
+        d_in.copy_(h_in, non_blocking=True)
+        bsm.bsm_pack_spinor(lat, d_in, src[bsm.F32], bsm.F32)
+        dslash_step(bsm.F32)
+        bsm.bsm_unpack_spinor(lat, dst[bsm.F32], d_out, bsm.F32)
+        h_out.copy_(d_out, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n_e2e):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / n_e2e, world)
+    e2e_value = world * flop_step / (e2e_ms * 1e-3) / 1e9
+    io_bytes = psi.nbytes
+
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step_max, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "lattice_TXYZ": list(dims), "sites": V, "flop_per_site": flops_per_site(d),
+                   "algorithmic_bytes_per_site": bytes_per_site(d, 4), "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}", "wall_s_timed_region": round(wall, 4)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
+                     "kernel": "hop_kernel<F32,3,complex>", "bytes_per_launch": hop_bytes,
+                     "avg_launch_us": round(avg_launch_ms * 1e3, 2), "frac_of_8TBs": round(achieved / 8000, 4)},
+        "dslash_fp64": {"gflops": round(flop_step / (ms64 * 1e-3) / 1e9, 2), "ms_per_step": round(ms64, 4),
+                        "hbm_frac": round(2 * bytes_per_site(d, 8) * Vh / (ms64 * 1e-3) / 1e9 / peak, 4)},
+        "links_to_rep_ms_f32": round(links_ms, 3),
+        "e2e": {"value": round(e2e_value, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": io_bytes,
+                "d2h_bytes_per_step": io_bytes, "ms_per_step": round(e2e_ms, 4)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+
+    if rank == 0 and not args.no_cg:
+        out["cg"] = run_cg(lat, links, src[bsm.F64], args.cg_max_iter)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        g, reps, el, th = time_oracle_hop(SAMPLE_DIMS, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": round(g, 3), "unit": "GFLOP/s", "cores": th, "kind": "oracle",
+                               "sample": f"oracle full-lattice hop on {'x'.join(map(str, SAMPLE_DIMS))} "
+                                         f"(same per-site work), {reps} reps in {el:.1f} s"}
+    barrier(world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_cg(lat, links, b, max_iter):
+    """Time-to-1e-10 (FP64 true residual of the normal equations) of the
+    mixed-precision solver and of plain FP64 CG, same source, same GPU."""
+    import torch
+    from paper_1401_3733_gb300 import bsm
+
+    res = {}
+    for name, prec in (("mixed", bsm.F32), ("fp64", bsm.F64)):
+        ws = torch.empty(bsm.bsm_workspace_bytes(lat, bsm.CALL_CG, prec), dtype=torch.uint8, device="cuda")
+        x = torch.zeros_like(b)
+        st, stats = bsm.bsm_cg_solve(lat, links[bsm.F64], links[bsm.F32], b, x,
+                                     bsm.cg_opts(tol=1e-10, max_iter=max_iter, prec_inner=prec), ws,
+                                     raise_on_error=False)
+        res[name] = {"status": bsm.bsm_strerror(st), "seconds": round(stats.seconds, 4), "iters": stats.iters,
+                     "reliable_updates": stats.reliable_updates, "true_res_normal": stats.true_res_normal,
+                     "true_res_full": stats.true_res_full}
+        del ws
+    if res["mixed"]["seconds"] > 0:
+        res["fp64_over_mixed_time"] = round(res["fp64"]["seconds"] / res["mixed"]["seconds"], 3)
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution part")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cg-max-iter", type=int, default=20000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * bsm.h -- C ABI of the GB300 (sm_103a) library for the BSMBench hot path:
+ * the even-odd preconditioned Wilson-Dirac operator and CG on its normal
+ * equations (Bennett et al., "BSMBench", HPCS 2016, Sec. II-A field content,
+ * Sec. II-B Dirac operator and CG, Sec. III benchmark tasks).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice (Sec. II-A): dims = {T, X, Y, Z}, mu = 0 is time, every extent even
+ * and >= 2, V = T*X*Y*Z sites, V_h = V/2 sites per parity.  Canonical site
+ * index s = ((t*X + x)*Y + y)*Z + z; parity(x) = (t+x+y+z) mod 2 (even = 0);
+ * within a parity a site's index is s >> 1 (valid because Z is even).
+ *
+ * Fields (Sec. II-A): a link is an N x N complex matrix U_mu(x) (link from x
+ * to x+mu).  The fermion at a site is 4 (spin) x d colour components in the
+ * d-dimensional representation R of SU(N): fundamental (d = N), adjoint
+ * (d = N^2-1, real), two-index symmetric (N(N+1)/2) or antisymmetric
+ * (N(N-1)/2).
+ *
+ * Operator (Sec. II-B "Dphi"; the paper does not print the formula, the
+ * standard Wilson form is used):
+ *   (H psi)(x) = sum_mu [ (1 - g_mu) U^R_mu(x) psi(x+mu)
+ *                       + (1 + g_mu) U^R_mu(x-mu)^+ psi(x-mu) ]
+ *   D = A - H/2,  A = 4 + m0,
+ * with U^R_mu(x) = R(U_mu(x)) times exp(i phi_mu) on the links that cross the
+ * boundary (x_mu = L_mu - 1), and the chiral gamma basis g_0 = [[0,1],[1,0]],
+ * g_k = [[0,-i s_k],[i s_k,0]], g_5 = diag(-1,-1,1,1).  The adjoint operator
+ * is H^+ = g_5 H g_5 (the projectors exchanged).  Even-odd (Schur) operator on
+ * the even sites: Dhat = A - 1/(4A) H_eo H_oe, Dhat^+ = A - 1/(4A) H^+_eo H^+_oe.
+ * Representation bases: generalised Gell-Mann generators for the adjoint
+ * (symmetric off-diagonal, antisymmetric off-diagonal, diagonal; Tr T^aT^b =
+ * delta/2); e_(ii) = E_ii, e_(ij) = (E_ij +- E_ji)/sqrt2 (i<j, lexicographic)
+ * for the two-index representations.
+ *
+ * Canonical host-order arrays (used only by pack/unpack and links_to_rep),
+ * complex numbers as interleaved (re, im) FP64:
+ *   fundamental links  [V][4][N][N]     spinors  [V][4][d]
+ *
+ * Device layouts (produced by this library; sizes from bsm_field_bytes):
+ *   half spinor (one parity), FP64: 4d planes of V_h double2 (re, im),
+ *       plane = spin*d + colour.
+ *   half spinor, FP32: 2d planes of V_h float4, plane = s*d + colour for
+ *       s = 0, 1, holding (psi[s][c], psi[s+2][c]) as (re, im, re, im).
+ *   full spinor: the even half followed by the odd half.
+ *   links, complex representation, for each output parity p (p = 0 block
+ *       first): FP64 -- 8 x d^2 planes of V_h double2, plane (2mu+f)*d^2 + c,
+ *       f = 0 forward link U^R_mu(x), f = 1 backward link U^R_mu(x-mu)^+,
+ *       c = row*d + col, x running over the sites of parity p;
+ *       FP32 -- 4 x d^2 planes of V_h float4, plane mu*d^2 + c holding
+ *       (forward[c], backward[c]).
+ *   links, real (adjoint) representation: 4 x d^2 planes per output parity of
+ *       V_h double2 (FP64) or float2 (FP32) holding (forward[c], backward[c]).
+ *   Every link is stored twice (as a forward link of its own site and as the
+ *   backward link of its neighbour), so each hop reads its 8 links per site
+ *   as aligned, coalesced 16-byte (8-byte for FP32 real) vectors.
+ *
+ * Ownership and execution: all pointers are device pointers unless stated;
+ * the caller allocates and frees every buffer (workspace included) and the
+ * library keeps no pointer past a call.  Buffers must be 16-byte aligned.
+ * `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * Every call is asynchronous on `stream` except bsm_cg_solve, which
+ * synchronises `stream` before it returns.  Calls on different streams may
+ * run concurrently if they share no output buffer.
+ *
+ * Errors: every call validates its arguments before it launches anything and
+ * returns a bsm_status; nothing aborts or exits.  A CUDA launch or runtime
+ * error returns BSM_ECUDA (bsm_last_cuda_error() gives its text).
+ */
+#ifndef BSM_GB300_H
+#define BSM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BSM_OK = 0,
+  BSM_EINVAL = -1,        /* bad argument: null/misaligned pointer, odd or zero extent, A == 0 */
+  BSM_EUNSUPPORTED = -2,  /* (N, representation, precision, phase) not instantiated */
+  BSM_ECUDA = -3,         /* CUDA launch or runtime error */
+  BSM_EWORKSPACE = -4,    /* workspace smaller than bsm_workspace_bytes() */
+  BSM_ENOCONV = -5,       /* CG reached max_iter before the tolerance */
+  BSM_EBREAKDOWN = -6,    /* CG breakdown: <p, M p> <= 0 */
+  BSM_ENAN = -7,          /* NaN or Inf met in a CG reduction */
+  BSM_ETIMEOUT = -8       /* a bounded device-side wait gave up */
+} bsm_status;
+
+typedef enum { BSM_FUND = 0, BSM_ADJ = 1, BSM_SYM = 2, BSM_ASYM = 3 } bsm_rep;
+typedef enum { BSM_F64 = 0, BSM_F32 = 1 } bsm_prec;
+typedef enum { BSM_EVEN = 0, BSM_ODD = 1, BSM_FULL = 2 } bsm_parity;
+typedef enum { BSM_OP_DHAT = 0, BSM_OP_DHAT_DAG = 1, BSM_OP_DHAT_DAG_DHAT = 2 } bsm_eo_op;
+typedef enum {
+  BSM_FIELD_LINKS = 0,        /* representation links, device layout, both parities */
+  BSM_FIELD_SPINOR = 1,       /* full-lattice spinor, device layout */
+  BSM_FIELD_HALF_SPINOR = 2,  /* one parity, device layout */
+  BSM_FIELD_FUND_CANON = 3,   /* canonical FP64 fundamental links [V][4][N][N] */
+  BSM_FIELD_SPINOR_CANON = 4  /* canonical FP64 spinor [V][4][d] */
+} bsm_field_kind;
+typedef enum { BSM_CALL_DIRAC_EO = 0, BSM_CALL_CG = 1 } bsm_call;
+
+typedef struct {
+  int32_t dims[4];      /* {T, X, Y, Z}; all even and >= 2 */
+  int32_t N;            /* gauge group SU(N) */
+  int32_t rep;          /* bsm_rep */
+  double m0;            /* Wilson bare mass; A = 4 + m0 must be nonzero */
+  double bc_phase[4];   /* phi_mu in radians (pi = antiperiodic); a real
+                           representation accepts only multiples of pi */
+} bsm_lattice;
+
+typedef struct {
+  double tol;           /* stop when |rhs - M x_e| <= tol |rhs| (FP64, recomputed) */
+  int32_t max_iter;     /* total CG iterations allowed */
+  int32_t prec_inner;   /* BSM_F64: plain FP64 CG; BSM_F32: mixed precision with
+                           FP64 reliable updates (needs U_rep32) */
+  double delta;         /* reliable-update trigger: |r| < delta * max|r| since the
+                           last update (0 selects 0.1) */
+  int32_t use_x0;       /* nonzero: x holds the initial guess on entry */
+  int32_t eo;           /* nonzero: even-odd Schur system (default path);
+                           zero: unpreconditioned D^+ D on the full lattice */
+  int32_t check_every;  /* iterations between host convergence checks (0 = 8) */
+} bsm_cg_opts;
+
+typedef struct {
+  int32_t iters;            /* CG iterations performed */
+  int32_t reliable_updates; /* FP64 residual recomputations (mixed precision) */
+  double true_res_normal;   /* |rhs - M x| / |rhs| recomputed in FP64 */
+  double true_res_full;     /* |D x - b| / |b| on the full lattice, FP64 */
+  double seconds;           /* wall time of the solve (host clock, synchronised) */
+} bsm_cg_stats;
+
+/* d_R of (N, rep), or a negative bsm_status when unsupported.  Pure host. */
+int bsm_rep_dim(int32_t N, int32_t rep);
+
+/* Bytes of a field of `kind` at precision `prec` (canonical kinds ignore
+ * prec).  0 when the lattice is invalid.  Pure host. */
+size_t bsm_field_bytes(const bsm_lattice *lat, int32_t kind, int32_t prec);
+
+/* Workspace bytes that bsm_dirac_eo (call = BSM_CALL_DIRAC_EO) or
+ * bsm_cg_solve (BSM_CALL_CG, prec = the inner precision) needs.  Pure host. */
+size_t bsm_workspace_bytes(const bsm_lattice *lat, int32_t call, int32_t prec);
+
+/* Canonical FP64 spinor [V][4][d] (device) -> full device-layout spinor at
+ * `prec`, and back (FP32 values are widened exactly on unpack). */
+int bsm_pack_spinor(const bsm_lattice *lat, const double *canon, void *dev,
+                    int32_t prec, void *stream);
+int bsm_unpack_spinor(const bsm_lattice *lat, const void *dev, double *canon,
+                      int32_t prec, void *stream);
+
+/* Representation links (Sec. II-A: the fermion transforms under a
+ * non-trivial representation of the gauge group).  U_fund: canonical FP64
+ * fundamental links on the device.  U_rep: device-layout links at `prec`
+ * (bsm_field_bytes(lat, BSM_FIELD_LINKS, prec) bytes), computed in FP64 and
+ * rounded once, with the boundary phases folded in. */
+int bsm_links_to_rep(const bsm_lattice *lat, const double *U_fund, void *U_rep,
+                     int32_t prec, void *stream);
+
+/* Dphi (Sec. II-B).  out_parity = BSM_EVEN / BSM_ODD: the hopping block
+ * out_p = H_{p,1-p} in_{1-p} (raw hop, no 1/2, no mass), `in` and `out` half
+ * spinors.  out_parity = BSM_FULL: out = D in on full spinors.  dagger != 0
+ * applies the adjoint (H^+ = g_5 H g_5, D^+).  U_rep at the same `prec`. */
+int bsm_dslash(const bsm_lattice *lat, const void *U_rep, const void *in,
+               void *out, int32_t out_parity, int32_t dagger, int32_t prec,
+               void *stream);
+
+/* Even-odd Schur operator on even half spinors: op = BSM_OP_DHAT (Dhat),
+ * BSM_OP_DHAT_DAG (Dhat^+) or BSM_OP_DHAT_DAG_DHAT (Dhat^+ Dhat).  workspace:
+ * at least bsm_workspace_bytes(lat, BSM_CALL_DIRAC_EO, prec) bytes. */
+int bsm_dirac_eo(const bsm_lattice *lat, const void *U_rep, const void *in_e,
+                 void *out_e, int32_t op, int32_t prec, void *workspace,
+                 size_t workspace_bytes, void *stream);
+
+/* Solve D x = b (Sec. II-B: inverting the Dirac operator by CG) through CG on
+ * the normal equations.  With opts->eo: Dhat^+ Dhat x_e = Dhat^+ bhat_e,
+ * bhat_e = b_e + 1/(2A) H_eo b_o, then x_o = (b_o + H_oe x_e / 2) / A.
+ * b, x: full FP64 device-layout spinors.  U_rep64: FP64 links; U_rep32: FP32
+ * links (required when opts->prec_inner == BSM_F32, else ignored).  stats is a
+ * host pointer (may be NULL).  Synchronises `stream`.  Returns BSM_ENOCONV,
+ * BSM_EBREAKDOWN or BSM_ENAN with x holding the last iterate. */
+int bsm_cg_solve(const bsm_lattice *lat, const void *U_rep64, const void *U_rep32,
+                 const void *b, void *x, const bsm_cg_opts *opts,
+                 bsm_cg_stats *stats, void *workspace, size_t workspace_bytes,
+                 void *stream);
+
+/* Static text for a bsm_status. */
+const char *bsm_strerror(int status);
+
+/* Text of the last CUDA error seen by this library on the calling thread
+ * ("" if none). */
+const char *bsm_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

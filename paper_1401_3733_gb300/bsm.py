@@ -1,0 +1,181 @@
+"""ctypes binding of the C ABI in include/bsm.h (libbsm_gb300.so).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are torch tensors (their data_ptr is passed), the
+stream defaults to torch's current stream.  Importing this module raises
+ImportError when the library has not been built, so there is no silent
+fallback.  Function names follow the C entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libbsm_gb300.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+# enums of bsm.h
+OK, EINVAL, EUNSUPPORTED, ECUDA, EWORKSPACE, ENOCONV, EBREAKDOWN, ENAN, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8
+FUND, ADJ, SYM, ASYM = 0, 1, 2, 3
+F64, F32 = 0, 1
+EVEN, ODD, FULL = 0, 1, 2
+OP_DHAT, OP_DHAT_DAG, OP_DHAT_DAG_DHAT = 0, 1, 2
+FIELD_LINKS, FIELD_SPINOR, FIELD_HALF_SPINOR, FIELD_FUND_CANON, FIELD_SPINOR_CANON = 0, 1, 2, 3, 4
+CALL_DIRAC_EO, CALL_CG = 0, 1
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 4), ("N", ctypes.c_int32), ("rep", ctypes.c_int32),
+                ("m0", ctypes.c_double), ("bc_phase", ctypes.c_double * 4)]
+
+
+class CgOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("prec_inner", ctypes.c_int32),
+                ("delta", ctypes.c_double), ("use_x0", ctypes.c_int32), ("eo", ctypes.c_int32),
+                ("check_every", ctypes.c_int32)]
+
+
+class CgStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("reliable_updates", ctypes.c_int32),
+                ("true_res_normal", ctypes.c_double), ("true_res_full", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BsmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = f"{what}: {bsm_strerror(status)} ({status})"
+        if status == ECUDA:
+            msg += f" [{bsm_last_cuda_error()}]"
+        super().__init__(msg)
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_LP = ctypes.POINTER(Lattice)
+_lib.bsm_rep_dim.argtypes = [ctypes.c_int32, ctypes.c_int32]
+_lib.bsm_rep_dim.restype = ctypes.c_int
+_lib.bsm_field_bytes.argtypes = [_LP, ctypes.c_int32, ctypes.c_int32]
+_lib.bsm_field_bytes.restype = ctypes.c_size_t
+_lib.bsm_workspace_bytes.argtypes = [_LP, ctypes.c_int32, ctypes.c_int32]
+_lib.bsm_workspace_bytes.restype = ctypes.c_size_t
+_lib.bsm_pack_spinor.argtypes = [_LP, _P, _P, ctypes.c_int32, _P]
+_lib.bsm_unpack_spinor.argtypes = [_LP, _P, _P, ctypes.c_int32, _P]
+_lib.bsm_links_to_rep.argtypes = [_LP, _P, _P, ctypes.c_int32, _P]
+_lib.bsm_dslash.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]
+_lib.bsm_dirac_eo.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P]
+_lib.bsm_cg_solve.argtypes = [_LP, _P, _P, _P, _P, ctypes.POINTER(CgOpts), ctypes.POINTER(CgStats), _P,
+                              ctypes.c_size_t, _P]
+_lib.bsm_strerror.argtypes = [ctypes.c_int]
+_lib.bsm_strerror.restype = ctypes.c_char_p
+_lib.bsm_last_cuda_error.argtypes = []
+_lib.bsm_last_cuda_error.restype = ctypes.c_char_p
+for _f in ("bsm_pack_spinor", "bsm_unpack_spinor", "bsm_links_to_rep", "bsm_dslash", "bsm_dirac_eo",
+           "bsm_cg_solve"):
+    getattr(_lib, _f).restype = ctypes.c_int
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lattice(dims, N, rep=FUND, m0=0.1, bc_phase=(0.0, 0.0, 0.0, 0.0)) -> Lattice:
+    return Lattice((ctypes.c_int32 * 4)(*dims), N, rep, float(m0), (ctypes.c_double * 4)(*bc_phase))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return stream
+
+
+def _check(status, what):
+    if status != OK:
+        raise BsmError(status, what)
+
+
+def bsm_strerror(status: int) -> str:
+    return _lib.bsm_strerror(status).decode()
+
+
+def bsm_last_cuda_error() -> str:
+    return _lib.bsm_last_cuda_error().decode()
+
+
+def bsm_rep_dim(N: int, rep: int) -> int:
+    return _lib.bsm_rep_dim(N, rep)
+
+
+def bsm_field_bytes(lat: Lattice, kind: int, prec: int = F64) -> int:
+    return _lib.bsm_field_bytes(ctypes.byref(lat), kind, prec)
+
+
+def bsm_workspace_bytes(lat: Lattice, call: int, prec: int) -> int:
+    return _lib.bsm_workspace_bytes(ctypes.byref(lat), call, prec)
+
+
+def empty_field(lat: Lattice, kind: int, prec: int = F64, device="cuda") -> torch.Tensor:
+    """Uninitialised byte tensor sized for a field of `kind` (torch device
+    allocations are at least 256-byte aligned)."""
+    n = bsm_field_bytes(lat, kind, prec)
+    if n == 0:
+        raise BsmError(EINVAL, "bsm_field_bytes")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def bsm_pack_spinor(lat, canon, dev, prec, stream=None):
+    _check(_lib.bsm_pack_spinor(ctypes.byref(lat), _ptr(canon), _ptr(dev), prec, _stream(stream)),
+           "bsm_pack_spinor")
+
+
+def bsm_unpack_spinor(lat, dev, canon, prec, stream=None):
+    _check(_lib.bsm_unpack_spinor(ctypes.byref(lat), _ptr(dev), _ptr(canon), prec, _stream(stream)),
+           "bsm_unpack_spinor")
+
+
+def bsm_links_to_rep(lat, U_fund, U_rep, prec, stream=None):
+    _check(_lib.bsm_links_to_rep(ctypes.byref(lat), _ptr(U_fund), _ptr(U_rep), prec, _stream(stream)),
+           "bsm_links_to_rep")
+
+
+def bsm_dslash(lat, U_rep, inp, out, out_parity, dagger, prec, stream=None):
+    _check(_lib.bsm_dslash(ctypes.byref(lat), _ptr(U_rep), _ptr(inp), _ptr(out), out_parity, int(dagger), prec,
+                           _stream(stream)), "bsm_dslash")
+
+
+def bsm_dirac_eo(lat, U_rep, in_e, out_e, op, prec, workspace, stream=None):
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(_lib.bsm_dirac_eo(ctypes.byref(lat), _ptr(U_rep), _ptr(in_e), _ptr(out_e), op, prec, _ptr(workspace),
+                             nbytes, _stream(stream)), "bsm_dirac_eo")
+
+
+def bsm_cg_solve(lat, U_rep64, U_rep32, b, x, opts: CgOpts, workspace, stream=None, raise_on_error=True):
+    """Returns (status, CgStats); raises BsmError on a nonzero status unless
+    raise_on_error is False."""
+    stats = CgStats()
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    st = _lib.bsm_cg_solve(ctypes.byref(lat), _ptr(U_rep64), _ptr(U_rep32), _ptr(b), _ptr(x), ctypes.byref(opts),
+                           ctypes.byref(stats), _ptr(workspace), nbytes, _stream(stream))
+    if raise_on_error:
+        _check(st, "bsm_cg_solve")
+    return st, stats
+
+
+def cg_opts(tol=1e-10, max_iter=10000, prec_inner=F64, delta=0.1, use_x0=False, eo=True, check_every=8) -> CgOpts:
+    return CgOpts(tol, max_iter, prec_inner, delta, int(use_x0), int(eo), check_every)

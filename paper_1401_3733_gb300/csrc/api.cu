@@ -1,0 +1,247 @@
+// api.cu -- the extern "C" entry points declared in include/bsm.h: argument
+// validation (before any launch), size queries, dispatch to the kernels, and
+// CUDA error mapping.
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "blas.cuh"
+#include "operators.cuh"
+
+namespace bsm {
+
+int links_to_rep_launch(const bsm_lattice& L, const double* U, void* out, int prec, cudaStream_t s);
+void pack_spinor_launch(const bsm_lattice& L, const double* canon, void* dev, int d, int prec, bool unpack,
+                        cudaStream_t s);
+size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo);
+int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* b, void* x,
+             const bsm_cg_opts& o, bsm_cg_stats* stats, void* ws, cudaStream_t s);
+
+RepInfo rep_info(int N, int rep) {
+  RepInfo r{-1, false};
+  switch (rep) {
+    case BSM_FUND:
+      if (N == 2 || N == 3 || N == 4 || N == 6 || N == 8) r.d = N;
+      break;
+    case BSM_ADJ:
+      if (N == 2 || N == 3) {
+        r.d = N * N - 1;
+        r.real = true;
+      }
+      break;
+    case BSM_SYM:
+      if (N == 2 || N == 3) r.d = N * (N + 1) / 2;
+      break;
+    case BSM_ASYM:
+      if (N == 3 || N == 4) r.d = N * (N - 1) / 2;
+      break;
+    default:
+      break;
+  }
+  return r;
+}
+
+namespace {
+thread_local char g_cuda_err[256] = "";
+}
+
+void set_cuda_error(cudaError_t e) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+namespace {
+
+// checks every field of the lattice; BSM_OK, BSM_EINVAL or BSM_EUNSUPPORTED
+int check_lattice(const bsm_lattice* L) {
+  if (L == nullptr) return BSM_EINVAL;
+  int64_t V = 1;
+  for (int m = 0; m < 4; ++m) {
+    if (L->dims[m] < 2 || (L->dims[m] & 1)) return BSM_EINVAL;
+    V *= L->dims[m];
+    if (!isfinite(L->bc_phase[m])) return BSM_EINVAL;
+  }
+  if (V > ((int64_t)1 << 30)) return BSM_EUNSUPPORTED;  // 32-bit site indexing with headroom
+  if (!isfinite(L->m0) || 4.0 + L->m0 == 0.0) return BSM_EINVAL;
+  const RepInfo ri = rep_info(L->N, L->rep);
+  if (ri.d < 0) return BSM_EUNSUPPORTED;
+  if (ri.real) {
+    // a real representation stays real only for phases that are multiples of pi
+    for (int m = 0; m < 4; ++m) {
+      const double k = L->bc_phase[m] / M_PI;
+      if (fabs(k - nearbyint(k)) > 1e-12) return BSM_EUNSUPPORTED;
+    }
+  }
+  return BSM_OK;
+}
+
+bool aligned(const void* p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+bool prec_ok(int prec) { return prec == BSM_F64 || prec == BSM_F32; }
+
+int finish(int rc) {
+  if (rc != BSM_OK) return rc;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return BSM_ECUDA;
+  }
+  return BSM_OK;
+}
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
+
+}  // namespace
+}  // namespace bsm
+
+using namespace bsm;
+
+extern "C" {
+
+int bsm_rep_dim(int32_t N, int32_t rep) {
+  const RepInfo r = rep_info(N, rep);
+  return r.d < 0 ? BSM_EUNSUPPORTED : r.d;
+}
+
+size_t bsm_field_bytes(const bsm_lattice* lat, int32_t kind, int32_t prec) {
+  if (check_lattice(lat) != BSM_OK) return 0;
+  const Geom g = make_geom(*lat);
+  const RepInfo ri = rep_info(lat->N, lat->rep);
+  const size_t V = 2 * (size_t)g.Vh;
+  switch (kind) {
+    case BSM_FIELD_FUND_CANON: return V * 4 * lat->N * lat->N * 16;
+    case BSM_FIELD_SPINOR_CANON: return V * 4 * ri.d * 16;
+    default: break;
+  }
+  if (!prec_ok(prec)) return 0;
+  switch (kind) {
+    case BSM_FIELD_LINKS: return 2 * link_block_bytes(g.Vh, ri.d, ri.real, prec);
+    case BSM_FIELD_SPINOR: return 2 * half_spinor_bytes(g.Vh, ri.d, prec);
+    case BSM_FIELD_HALF_SPINOR: return half_spinor_bytes(g.Vh, ri.d, prec);
+    default: return 0;
+  }
+}
+
+size_t bsm_workspace_bytes(const bsm_lattice* lat, int32_t call, int32_t prec) {
+  if (check_lattice(lat) != BSM_OK || !prec_ok(prec)) return 0;
+  const Geom g = make_geom(*lat);
+  const RepInfo ri = rep_info(lat->N, lat->rep);
+  if (call == BSM_CALL_DIRAC_EO) return 2 * half_spinor_bytes(g.Vh, ri.d, prec);
+  if (call == BSM_CALL_CG) {
+    // the larger of the even-odd and full-lattice layouts
+    const size_t a = cg_workspace_bytes(*lat, prec, 1), b = cg_workspace_bytes(*lat, prec, 0);
+    return a > b ? a : b;
+  }
+  return 0;
+}
+
+int bsm_pack_spinor(const bsm_lattice* lat, const double* canon, void* dev, int32_t prec, void* stream) {
+  int rc = check_lattice(lat);
+  if (rc != BSM_OK) return rc;
+  if (!prec_ok(prec)) return BSM_EUNSUPPORTED;
+  if (!aligned(canon) || !aligned(dev)) return BSM_EINVAL;
+  pack_spinor_launch(*lat, canon, dev, rep_info(lat->N, lat->rep).d, prec, false, (cudaStream_t)stream);
+  return finish(BSM_OK);
+}
+
+int bsm_unpack_spinor(const bsm_lattice* lat, const void* dev, double* canon, int32_t prec, void* stream) {
+  int rc = check_lattice(lat);
+  if (rc != BSM_OK) return rc;
+  if (!prec_ok(prec)) return BSM_EUNSUPPORTED;
+  if (!aligned(canon) || !aligned(dev)) return BSM_EINVAL;
+  pack_spinor_launch(*lat, canon, const_cast<void*>(dev), rep_info(lat->N, lat->rep).d, prec, true,
+                     (cudaStream_t)stream);
+  return finish(BSM_OK);
+}
+
+int bsm_links_to_rep(const bsm_lattice* lat, const double* U_fund, void* U_rep, int32_t prec, void* stream) {
+  int rc = check_lattice(lat);
+  if (rc != BSM_OK) return rc;
+  if (!prec_ok(prec)) return BSM_EUNSUPPORTED;
+  if (!aligned(U_fund) || !aligned(U_rep)) return BSM_EINVAL;
+  return finish(links_to_rep_launch(*lat, U_fund, U_rep, prec, (cudaStream_t)stream));
+}
+
+int bsm_dslash(const bsm_lattice* lat, const void* U_rep, const void* in, void* out, int32_t out_parity,
+               int32_t dagger, int32_t prec, void* stream) {
+  int rc = check_lattice(lat);
+  if (rc != BSM_OK) return rc;
+  if (!prec_ok(prec)) return BSM_EUNSUPPORTED;
+  if (!aligned(U_rep) || !aligned(in) || !aligned(out)) return BSM_EINVAL;
+  if (out_parity != BSM_EVEN && out_parity != BSM_ODD && out_parity != BSM_FULL) return BSM_EINVAL;
+  const OpCtx c = make_ctx(*lat, U_rep, prec, (cudaStream_t)stream);
+  const size_t n = out_parity == BSM_FULL ? 2 * c.half_bytes : c.half_bytes;
+  if (overlap(in, n, out, n)) return BSM_EINVAL;  // the stencil reads neighbours of what it writes
+  if (out_parity == BSM_FULL) rc = op_dirac(c, in, out, dagger != 0, nullptr, nullptr);
+  else rc = op_hop(c, out_parity, in, out, dagger != 0, nullptr, 0.0, 1.0, nullptr, nullptr);
+  return finish(rc < 0 ? rc : BSM_OK);
+}
+
+int bsm_dirac_eo(const bsm_lattice* lat, const void* U_rep, const void* in_e, void* out_e, int32_t op,
+                 int32_t prec, void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_lattice(lat);
+  if (rc != BSM_OK) return rc;
+  if (!prec_ok(prec)) return BSM_EUNSUPPORTED;
+  if (!aligned(U_rep) || !aligned(in_e) || !aligned(out_e) || !aligned(workspace)) return BSM_EINVAL;
+  if (op != BSM_OP_DHAT && op != BSM_OP_DHAT_DAG && op != BSM_OP_DHAT_DAG_DHAT) return BSM_EINVAL;
+  const OpCtx c = make_ctx(*lat, U_rep, prec, (cudaStream_t)stream);
+  if (workspace_bytes < 2 * c.half_bytes) return BSM_EWORKSPACE;
+  if (overlap(in_e, c.half_bytes, out_e, c.half_bytes)) return BSM_EINVAL;
+  char* t = reinterpret_cast<char*>(workspace);
+  char* u = t + c.half_bytes;
+  if (op == BSM_OP_DHAT_DAG_DHAT) {
+    rc = op_dhat(c, in_e, u, t, 0, nullptr, nullptr);
+    if (rc >= 0) rc = op_dhat(c, u, out_e, t, 1, nullptr, nullptr);
+  } else {
+    rc = op_dhat(c, in_e, out_e, t, op == BSM_OP_DHAT_DAG, nullptr, nullptr);
+  }
+  return finish(rc < 0 ? rc : BSM_OK);
+}
+
+int bsm_cg_solve(const bsm_lattice* lat, const void* U_rep64, const void* U_rep32, const void* b, void* x,
+                 const bsm_cg_opts* opts, bsm_cg_stats* stats, void* workspace, size_t workspace_bytes,
+                 void* stream) {
+  int rc = check_lattice(lat);
+  if (rc != BSM_OK) return rc;
+  if (opts == nullptr || !(opts->tol > 0.0) || opts->max_iter < 1 || opts->delta < 0.0 || opts->delta >= 1.0)
+    return BSM_EINVAL;
+  if (opts->prec_inner != BSM_F64 && opts->prec_inner != BSM_F32) return BSM_EUNSUPPORTED;
+  if (!aligned(U_rep64) || !aligned(b) || !aligned(x) || !aligned(workspace)) return BSM_EINVAL;
+  if (opts->prec_inner == BSM_F32 && !aligned(U_rep32)) return BSM_EINVAL;
+  if (workspace_bytes < cg_workspace_bytes(*lat, opts->prec_inner, opts->eo != 0)) return BSM_EWORKSPACE;
+  const size_t full = bsm_field_bytes(lat, BSM_FIELD_SPINOR, BSM_F64);
+  if (overlap(b, full, x, full)) return BSM_EINVAL;
+  const cudaError_t pre = cudaGetLastError();
+  if (pre != cudaSuccess) {
+    set_cuda_error(pre);
+    return BSM_ECUDA;
+  }
+  rc = cg_solve(*lat, U_rep64, U_rep32, b, x, *opts, stats, workspace, (cudaStream_t)stream);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return BSM_ECUDA;
+  }
+  return rc;
+}
+
+const char* bsm_strerror(int status) {
+  switch (status) {
+    case BSM_OK: return "ok";
+    case BSM_EINVAL: return "invalid argument";
+    case BSM_EUNSUPPORTED: return "unsupported configuration";
+    case BSM_ECUDA: return "CUDA error";
+    case BSM_EWORKSPACE: return "workspace too small";
+    case BSM_ENOCONV: return "CG did not converge within max_iter";
+    case BSM_EBREAKDOWN: return "CG breakdown (<p, M p> <= 0)";
+    case BSM_ENAN: return "NaN or Inf in a CG reduction";
+    case BSM_ETIMEOUT: return "bounded device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* bsm_last_cuda_error(void) { return g_cuda_err; }
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+// blas.cu -- vector kernels and deterministic reductions for CG.
+//
+// Reductions: each thread accumulates its grid-stride share in FP64 (for
+// FP32 vectors the four products of one 16-byte element are summed in FP32
+// first, then added in FP64), a fixed shuffle tree gives one partial per
+// block, and a single-block finalize kernel sums the partials in a fixed
+// order.  The result is therefore bit-reproducible for a given problem size.
+#include "blas.cuh"
+
+namespace bsm {
+
+namespace {
+
+__device__ __forceinline__ double edot(const double2& a, const double2& b) { return fma(a.x, b.x, a.y * b.y); }
+__device__ __forceinline__ double edot(const float4& a, const float4& b) {
+  return (double)fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+__device__ __forceinline__ double2 eaxpy(double a, const double2& x, const double2& y) {
+  return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
+}
+__device__ __forceinline__ float4 eaxpy(double a, const float4& x, const float4& y) {
+  const float f = (float)a;
+  return make_float4(fmaf(f, x.x, y.x), fmaf(f, x.y, y.y), fmaf(f, x.z, y.z), fmaf(f, x.w, y.w));
+}
+// x + b y
+__device__ __forceinline__ double2 expay(const double2& x, double b, const double2& y) {
+  return make_double2(fma(b, y.x, x.x), fma(b, y.y, x.y));
+}
+__device__ __forceinline__ float4 expay(const float4& x, double b, const float4& y) {
+  const float f = (float)b;
+  return make_float4(fmaf(f, y.x, x.x), fmaf(f, y.y, x.y), fmaf(f, y.z, x.z), fmaf(f, y.w, x.w));
+}
+
+template <typename E>
+struct ElemOf;
+template <>
+struct ElemOf<F64> {
+  using T = double2;
+};
+template <>
+struct ElemOf<F32> {
+  using T = float4;
+};
+
+__global__ void reduce_kernel(const double* __restrict__ partials, int n, double* out) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < n; k += kBlasThreads) s += partials[k];
+  __shared__ double buf[kBlasThreads];
+  buf[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kBlasThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) buf[threadIdx.x] += buf[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = buf[0];
+}
+
+__device__ double block_total(const double* __restrict__ partials, int n) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < n; k += kBlasThreads) s += partials[k];
+  __shared__ double buf[kBlasThreads];
+  buf[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kBlasThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) buf[threadIdx.x] += buf[threadIdx.x + o];
+    __syncthreads();
+  }
+  return buf[0];
+}
+
+// alpha = rr / <p, M p>
+__global__ void cg_alpha_kernel(CgState* st, const double* __restrict__ partials, int n) {
+  if (st->done) return;
+  const double pAp = block_total(partials, n);
+  if (threadIdx.x != 0) return;
+  st->pAp = pAp;
+  if (!isfinite(pAp)) {
+    st->done = kDoneNaN;
+    st->alpha = 0.0;
+  } else if (!(pAp > 0.0)) {
+    st->done = kDoneBreakdown;
+    st->alpha = 0.0;
+  } else {
+    st->alpha = st->rr / pAp;
+  }
+}
+
+// beta = |r_new|^2 / |r|^2, convergence and reliable-update flags
+__global__ void cg_beta_kernel(CgState* st, const double* __restrict__ partials, int n) {
+  if (st->done) return;
+  const double rr_new = block_total(partials, n);
+  if (threadIdx.x != 0) return;
+  st->iter += 1;
+  st->rr_prev = st->rr;
+  st->beta = rr_new / st->rr;
+  st->rr = rr_new;
+  if (!isfinite(rr_new)) {
+    st->done = kDoneNaN;
+    return;
+  }
+  if (rr_new > st->rr_max) st->rr_max = rr_new;
+  if (rr_new < st->delta2 * st->rr_max) st->want_update = 1;
+  if (rr_new <= st->stop2) st->done = kDoneConverged;
+  else if (st->iter >= st->max_iter) st->done = kDoneMaxIter;
+}
+
+// x += alpha p ; r -= alpha Ap ; partials of |r|^2
+template <typename P>
+__global__ void __launch_bounds__(kBlasThreads) cg_xr_kernel(typename ElemOf<P>::T* __restrict__ x,
+                                                             typename ElemOf<P>::T* __restrict__ r,
+                                                             const typename ElemOf<P>::T* __restrict__ p,
+                                                             const typename ElemOf<P>::T* __restrict__ Ap,
+                                                             size_t n, const CgState* st, double* partials) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  double acc = 0.0;
+  for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
+    x[k] = eaxpy(alpha, p[k], x[k]);
+    const auto rk = eaxpy(-alpha, Ap[k], r[k]);
+    r[k] = rk;
+    acc += edot(rk, rk);
+  }
+  block_sum_store<kBlasThreads>(acc, partials);
+}
+
+// p = r + beta p
+template <typename P>
+__global__ void __launch_bounds__(kBlasThreads) cg_p_kernel(typename ElemOf<P>::T* __restrict__ p,
+                                                            const typename ElemOf<P>::T* __restrict__ r, size_t n,
+                                                            const CgState* st) {
+  if (st->done) return;
+  const double beta = st->beta;
+  for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads)
+    p[k] = expay(r[k], beta, p[k]);
+}
+
+template <typename P>
+__global__ void __launch_bounds__(kBlasThreads) dot_kernel(const typename ElemOf<P>::T* __restrict__ a,
+                                                           const typename ElemOf<P>::T* __restrict__ b, size_t n,
+                                                           double* partials) {
+  double acc = 0.0;
+  for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads)
+    acc += edot(a[k], b[k]);
+  block_sum_store<kBlasThreads>(acc, partials);
+}
+
+__global__ void __launch_bounds__(kBlasThreads) axpby64_kernel(double a, const double2* __restrict__ x, double b,
+                                                               double2* __restrict__ y, size_t n,
+                                                               double* partials) {
+  double acc = 0.0;
+  for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
+    const double2 xv = x[k], yv = y[k];
+    const double2 v = make_double2(fma(a, xv.x, b * yv.x), fma(a, xv.y, b * yv.y));
+    y[k] = v;
+    acc += edot(v, v);
+  }
+  if (partials != nullptr) block_sum_store<kBlasThreads>(acc, partials);
+}
+
+// FP64 and FP32 half spinors pair their components differently: FP32 element
+// k of a half (float4) holds the spin-0/1 component at FP64 element k and the
+// spin-2/3 component at FP64 element k + n32, n32 = float4 elements per half.
+// y64 += widen(x32); x32 = 0
+__global__ void __launch_bounds__(kBlasThreads) acc32to64_kernel(double2* __restrict__ y, float4* __restrict__ x,
+                                                                 size_t n32, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
+    const size_t h = k / n32, kk = k - h * n32;
+    double2* yh = y + h * 2 * n32;
+    const float4 v = x[k];
+    double2 a = yh[kk], b = yh[kk + n32];
+    a.x += v.x;
+    a.y += v.y;
+    b.x += v.z;
+    b.y += v.w;
+    yh[kk] = a;
+    yh[kk + n32] = b;
+    x[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// y32 = round(x64)
+__global__ void __launch_bounds__(kBlasThreads) conv64to32_kernel(float4* __restrict__ y, const double2* __restrict__ x,
+                                                                  size_t n32, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
+    const size_t h = k / n32, kk = k - h * n32;
+    const double2* xh = x + h * 2 * n32;
+    const double2 a = xh[kk], b = xh[kk + n32];
+    y[k] = make_float4(__double2float_rn(a.x), __double2float_rn(a.y), __double2float_rn(b.x), __double2float_rn(b.y));
+  }
+}
+
+__global__ void __launch_bounds__(kBlasThreads) axpy_ratio32_kernel(float4* __restrict__ y,
+                                                                    const float4* __restrict__ x, size_t n,
+                                                                    const double* num, const double* den) {
+  const double c = -(*num) / (*den);
+  for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads)
+    y[k] = eaxpy(c, x[k], y[k]);
+}
+
+}  // namespace
+
+void reduce_launch(const double* partials, int n, double* out, cudaStream_t s) {
+  reduce_kernel<<<1, kBlasThreads, 0, s>>>(partials, n, out);
+}
+void cg_alpha_launch(CgState* st, const double* partials, int n, cudaStream_t s) {
+  cg_alpha_kernel<<<1, kBlasThreads, 0, s>>>(st, partials, n);
+}
+void cg_beta_launch(CgState* st, const double* partials, int n, cudaStream_t s) {
+  cg_beta_kernel<<<1, kBlasThreads, 0, s>>>(st, partials, n);
+}
+
+int cg_xr_update_launch(int prec, void* x, void* r, const void* p, const void* Ap, size_t n16, CgState* st,
+                        double* partials, cudaStream_t s) {
+  const int b = blas_blocks(n16);
+  if (prec == BSM_F64)
+    cg_xr_kernel<F64><<<b, kBlasThreads, 0, s>>>((double2*)x, (double2*)r, (const double2*)p, (const double2*)Ap,
+                                                  n16, st, partials);
+  else
+    cg_xr_kernel<F32><<<b, kBlasThreads, 0, s>>>((float4*)x, (float4*)r, (const float4*)p, (const float4*)Ap, n16,
+                                                  st, partials);
+  return b;
+}
+
+void cg_p_update_launch(int prec, void* p, const void* r, size_t n16, const CgState* st, cudaStream_t s) {
+  const int b = blas_blocks(n16);
+  if (prec == BSM_F64)
+    cg_p_kernel<F64><<<b, kBlasThreads, 0, s>>>((double2*)p, (const double2*)r, n16, st);
+  else
+    cg_p_kernel<F32><<<b, kBlasThreads, 0, s>>>((float4*)p, (const float4*)r, n16, st);
+}
+
+int dot_launch(int prec, const void* a, const void* b, size_t n16, double* partials, cudaStream_t s) {
+  const int nb = blas_blocks(n16);
+  if (prec == BSM_F64)
+    dot_kernel<F64><<<nb, kBlasThreads, 0, s>>>((const double2*)a, (const double2*)b, n16, partials);
+  else
+    dot_kernel<F32><<<nb, kBlasThreads, 0, s>>>((const float4*)a, (const float4*)b, n16, partials);
+  return nb;
+}
+
+int axpby64_launch(double a, const void* x, double b, void* y, size_t n16, double* partials, cudaStream_t s) {
+  const int nb = blas_blocks(n16);
+  axpby64_kernel<<<nb, kBlasThreads, 0, s>>>(a, (const double2*)x, b, (double2*)y, n16, partials);
+  return nb;
+}
+
+void accumulate32to64_launch(void* y64, void* x32, size_t n32_half, int halves, cudaStream_t s) {
+  const size_t n = n32_half * halves;
+  acc32to64_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>((double2*)y64, (float4*)x32, n32_half, n);
+}
+
+void convert64to32_launch(void* y32, const void* x64, size_t n32_half, int halves, cudaStream_t s) {
+  const size_t n = n32_half * halves;
+  conv64to32_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>((float4*)y32, (const double2*)x64, n32_half, n);
+}
+
+void axpy_ratio32_launch(void* y, const void* x, size_t n16, const double* num, const double* den, cudaStream_t s) {
+  axpy_ratio32_kernel<<<blas_blocks(n16), kBlasThreads, 0, s>>>((float4*)y, (const float4*)x, n16, num, den);
+}
+
+}  // namespace bsm

@@ -1,0 +1,270 @@
+// bsm_internal.cuh -- shared device-side building blocks of the GB300 library:
+// complex arithmetic, precision policies, the device field layouts declared
+// in include/bsm.h, and the even-odd lattice geometry (Sec. II-A).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bsm.h"
+
+namespace bsm {
+
+// ---------------------------------------------------------------------------
+// complex numbers
+// ---------------------------------------------------------------------------
+template <typename R>
+struct cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cx<R> cmake(R re, R im) {
+  cx<R> c;
+  c.re = re;
+  c.im = im;
+  return c;
+}
+
+// w += u * h (4 fused multiply-adds)
+template <typename R>
+__device__ __forceinline__ void cmac(cx<R>& w, const cx<R>& u, const cx<R>& h) {
+  w.re = fma(u.re, h.re, w.re);
+  w.re = fma(-u.im, h.im, w.re);
+  w.im = fma(u.re, h.im, w.im);
+  w.im = fma(u.im, h.re, w.im);
+}
+
+// w += u * h for a real u
+template <typename R>
+__device__ __forceinline__ void rmac(cx<R>& w, R u, const cx<R>& h) {
+  w.re = fma(u, h.re, w.re);
+  w.im = fma(u, h.im, w.im);
+}
+
+// ---------------------------------------------------------------------------
+// precision policies
+// ---------------------------------------------------------------------------
+struct F64 {
+  using R = double;
+  static constexpr int prec = BSM_F64;
+};
+struct F32 {
+  using R = float;
+  static constexpr int prec = BSM_F32;
+};
+
+// bytes of one parity block of a spinor with d colours
+inline size_t half_spinor_bytes(int64_t Vh, int d, int prec) {
+  return (size_t)Vh * 8 * d * (prec == BSM_F64 ? 8 : 4);
+}
+// bytes of the links of one output parity
+inline size_t link_block_bytes(int64_t Vh, int d, bool real, int prec) {
+  const size_t w = prec == BSM_F64 ? 8 : 4;
+  return (size_t)Vh * 8 * d * d * w * (real ? 1 : 2);
+}
+
+// ---------------------------------------------------------------------------
+// even-odd geometry: dims {T, X, Y, Z}, Z even; a site of parity p with index
+// i in its parity block has z = 2k + ((t+x+y+p) & 1), i = ((t*X+x)*Y+y)*Z/2 + k
+// ---------------------------------------------------------------------------
+struct Geom {
+  int T, X, Y, Zh;   // Zh = Z/2
+  int sy, sx, st;    // eo-index strides of a step in y, x, t
+  int Vh;
+};
+
+inline Geom make_geom(const bsm_lattice& L) {
+  Geom g;
+  g.T = L.dims[0];
+  g.X = L.dims[1];
+  g.Y = L.dims[2];
+  g.Zh = L.dims[3] / 2;
+  g.sy = g.Zh;
+  g.sx = g.Y * g.Zh;
+  g.st = g.X * g.Y * g.Zh;
+  g.Vh = g.T * g.st;
+  return g;
+}
+
+// indices (in the other parity block) of the 8 neighbours of eo site i of
+// parity p: nf[mu] = x + mu, nb[mu] = x - mu
+__device__ __forceinline__ void eo_neighbours(const Geom& g, int i, int p, int nf[4], int nb[4]) {
+  const int k = i % g.Zh;
+  const int row = i / g.Zh;
+  const int y = row % g.Y;
+  const int r2 = row / g.Y;
+  const int x = r2 % g.X;
+  const int t = r2 / g.X;
+  const int z = 2 * k + ((t + x + y + p) & 1);
+  nf[0] = (t == g.T - 1) ? i - (g.T - 1) * g.st : i + g.st;
+  nb[0] = (t == 0) ? i + (g.T - 1) * g.st : i - g.st;
+  nf[1] = (x == g.X - 1) ? i - (g.X - 1) * g.sx : i + g.sx;
+  nb[1] = (x == 0) ? i + (g.X - 1) * g.sx : i - g.sx;
+  nf[2] = (y == g.Y - 1) ? i - (g.Y - 1) * g.sy : i + g.sy;
+  nb[2] = (y == 0) ? i + (g.Y - 1) * g.sy : i - g.sy;
+  const int Z = 2 * g.Zh;
+  const int zf = (z == Z - 1) ? 0 : z + 1;
+  const int zb = (z == 0) ? Z - 1 : z - 1;
+  nf[3] = row * g.Zh + (zf >> 1);
+  nb[3] = row * g.Zh + (zb >> 1);
+}
+
+// ---------------------------------------------------------------------------
+// spinor layout access
+// ---------------------------------------------------------------------------
+template <typename P, int D>
+struct SpinorIO;
+
+template <int D>
+struct SpinorIO<F64, D> {
+  // 4D planes of double2, plane = spin*D + colour
+  __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, cx<double> (&s)[4][D]) {
+    const double2* b = reinterpret_cast<const double2*>(base);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const double2 v = __ldg(b + (size_t)(sp * D + a) * Vh + i);
+        s[sp][a] = cmake(v.x, v.y);
+      }
+  }
+  __device__ __forceinline__ static void store(void* base, size_t Vh, int i, const cx<double> (&s)[4][D]) {
+    double2* b = reinterpret_cast<double2*>(base);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int a = 0; a < D; ++a) b[(size_t)(sp * D + a) * Vh + i] = make_double2(s[sp][a].re, s[sp][a].im);
+  }
+};
+
+template <int D>
+struct SpinorIO<F32, D> {
+  // 2D planes of float4, plane = s*D + colour, (psi[s][c], psi[s+2][c])
+  __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, cx<float> (&s)[4][D]) {
+    const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const float4 v = __ldg(b + (size_t)(sp * D + a) * Vh + i);
+        s[sp][a] = cmake(v.x, v.y);
+        s[sp + 2][a] = cmake(v.z, v.w);
+      }
+  }
+  __device__ __forceinline__ static void store(void* base, size_t Vh, int i, const cx<float> (&s)[4][D]) {
+    float4* b = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        b[(size_t)(sp * D + a) * Vh + i] = make_float4(s[sp][a].re, s[sp][a].im, s[sp + 2][a].re, s[sp + 2][a].im);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// link layout access: forward link U(x) and backward link U(x-mu)^+ of
+// direction mu at eo site i of the output parity block `base`
+// ---------------------------------------------------------------------------
+template <typename P, int D, bool REAL>
+struct LinkIO;
+
+template <int D>
+struct LinkIO<F64, D, false> {
+  using elem = cx<double>;
+  __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, int mu, int c, elem& f, elem& b) {
+    const double2* p = reinterpret_cast<const double2*>(base);
+    const double2 vf = __ldcs(p + (size_t)((2 * mu) * D * D + c) * Vh + i);
+    const double2 vb = __ldcs(p + (size_t)((2 * mu + 1) * D * D + c) * Vh + i);
+    f = cmake(vf.x, vf.y);
+    b = cmake(vb.x, vb.y);
+  }
+};
+
+template <int D>
+struct LinkIO<F32, D, false> {
+  using elem = cx<float>;
+  __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, int mu, int c, elem& f, elem& b) {
+    const float4* p = reinterpret_cast<const float4*>(base);
+    const float4 v = __ldcs(p + (size_t)(mu * D * D + c) * Vh + i);
+    f = cmake(v.x, v.y);
+    b = cmake(v.z, v.w);
+  }
+};
+
+template <int D>
+struct LinkIO<F64, D, true> {
+  using elem = double;
+  __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, int mu, int c, elem& f, elem& b) {
+    const double2* p = reinterpret_cast<const double2*>(base);
+    const double2 v = __ldcs(p + (size_t)(mu * D * D + c) * Vh + i);
+    f = v.x;
+    b = v.y;
+  }
+};
+
+template <int D>
+struct LinkIO<F32, D, true> {
+  using elem = float;
+  __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, int mu, int c, elem& f, elem& b) {
+    const float2* p = reinterpret_cast<const float2*>(base);
+    const float2 v = __ldcs(p + (size_t)(mu * D * D + c) * Vh + i);
+    f = v.x;
+    b = v.y;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// block reduction of one double per thread -> one partial per block
+// (fixed shuffle tree, so the sum is deterministic for a fixed launch shape)
+// ---------------------------------------------------------------------------
+template <int THREADS>
+__device__ __forceinline__ void block_sum_store(double v, double* out) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __shared__ double warp_sums[THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) warp_sums[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double s = lane < THREADS / 32 ? warp_sums[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[blockIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host-side helpers shared by the translation units
+// ---------------------------------------------------------------------------
+struct RepInfo {
+  int d;
+  bool real;
+};
+// d and realness of a supported (N, rep); d < 0 if unsupported
+RepInfo rep_info(int N, int rep);
+
+// parameters of one hop launch (Sec. II-B hopping block H_{p,1-p})
+struct HopArgs {
+  const void* links;   // link block of output parity p
+  const void* in;      // half spinor of parity 1-p
+  void* out;           // half spinor of parity p
+  const void* x;       // optional same-parity input: out = a*x + b*H in
+  double a, b;
+  double* partials;    // optional per-block partial sums of |out|^2
+  const int* done;     // optional early-exit flag (CG): skip when *done != 0
+  Geom g;
+  int p;               // output parity
+  int dagger;          // apply H^+ = g5 H g5
+};
+
+// launch the hop for (prec, d, real); returns the number of blocks (the
+// number of partials written when args.partials != nullptr), or -1
+int launch_hop(int prec, int d, bool real, const HopArgs& args, cudaStream_t s);
+
+constexpr int kHopThreads = 128;
+inline int hop_blocks(int Vh) { return (Vh + kHopThreads - 1) / kHopThreads; }
+
+void set_cuda_error(cudaError_t e);
+
+}  // namespace bsm

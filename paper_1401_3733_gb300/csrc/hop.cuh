@@ -1,0 +1,169 @@
+// hop.cuh -- the Wilson hopping block H_{p,1-p} (Sec. II-B "Dphi"), one
+// thread per output site of parity p.
+//
+// For each direction mu the two neighbour spinors are spin-projected to two
+// colour vectors (chiral basis, g_mu = [[0, B_mu], [B_mu^+, 0]] with B_0 = 1,
+// B_k = -i sigma_k):
+//     (1 + sg g_mu) psi = ( h , sg B_mu^+ h ),   h = u + sg B_mu l,
+// where u, l are the upper and lower spin pairs and sg = -1 for the forward
+// term (1 - g_mu) U(x) psi(x+mu), sg = +1 for the backward term
+// (1 + g_mu) U(x-mu)^+ psi(x-mu); the adjoint H^+ = g5 H g5 flips sg.  The
+// link then multiplies the two colour vectors, one row at a time, and the
+// row is reconstructed into the four spin components of the accumulator.
+// The forward and backward links of mu share one 16-byte load (FP32) or sit
+// in neighbouring planes (FP64); links are read with the streaming cache hint
+// because each is used once per hop, neighbour spinors through the read-only
+// path because each is used by 8 output sites.
+#pragma once
+
+#include "bsm_internal.cuh"
+
+namespace bsm {
+
+// h = u + sg * B_mu l
+template <int MU, typename R, int D>
+__device__ __forceinline__ void spin_project(const cx<R> (&s)[4][D], R sg, cx<R> (&h)[2][D]) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const cx<R> u0 = s[0][a], u1 = s[1][a], l0 = s[2][a], l1 = s[3][a];
+    cx<R> b0, b1;  // B_mu l
+    if (MU == 0) {
+      b0 = l0;
+      b1 = l1;
+    } else if (MU == 1) {  // (-i l1, -i l0)
+      b0 = cmake(l1.im, -l1.re);
+      b1 = cmake(l0.im, -l0.re);
+    } else if (MU == 2) {  // (-l1, l0)
+      b0 = cmake(-l1.re, -l1.im);
+      b1 = l0;
+    } else {               // (-i l0, i l1)
+      b0 = cmake(l0.im, -l0.re);
+      b1 = cmake(-l1.im, l1.re);
+    }
+    h[0][a] = cmake(fma(sg, b0.re, u0.re), fma(sg, b0.im, u0.im));
+    h[1][a] = cmake(fma(sg, b1.re, u1.re), fma(sg, b1.im, u1.im));
+  }
+}
+
+// acc[0,1][a] += w ; acc[2,3][a] += sg * B_mu^+ w
+template <int MU, typename R, int D>
+__device__ __forceinline__ void spin_reconstruct(cx<R> (&acc)[4][D], int a, const cx<R>& w0,
+                                                 const cx<R>& w1, R sg) {
+  acc[0][a].re += w0.re;
+  acc[0][a].im += w0.im;
+  acc[1][a].re += w1.re;
+  acc[1][a].im += w1.im;
+  cx<R> c0, c1;  // B_mu^+ w
+  if (MU == 0) {
+    c0 = w0;
+    c1 = w1;
+  } else if (MU == 1) {  // (i w1, i w0)
+    c0 = cmake(-w1.im, w1.re);
+    c1 = cmake(-w0.im, w0.re);
+  } else if (MU == 2) {  // (w1, -w0)
+    c0 = w1;
+    c1 = cmake(-w0.re, -w0.im);
+  } else {               // (i w0, -i w1)
+    c0 = cmake(-w0.im, w0.re);
+    c1 = cmake(w1.im, -w1.re);
+  }
+  acc[2][a].re = fma(sg, c0.re, acc[2][a].re);
+  acc[2][a].im = fma(sg, c0.im, acc[2][a].im);
+  acc[3][a].re = fma(sg, c1.re, acc[3][a].re);
+  acc[3][a].im = fma(sg, c1.im, acc[3][a].im);
+}
+
+template <typename R>
+__device__ __forceinline__ void link_mac(cx<R>& w, const cx<R>& u, const cx<R>& h) { cmac(w, u, h); }
+template <typename R>
+__device__ __forceinline__ void link_mac(cx<R>& w, R u, const cx<R>& h) { rmac(w, u, h); }
+
+template <int MU, typename P, int D, bool REAL>
+__device__ __forceinline__ void hop_direction(const HopArgs& A, size_t Vh, int i, int nf, int nb,
+                                              typename P::R sgf, typename P::R sgb,
+                                              cx<typename P::R> (&acc)[4][D]) {
+  using R = typename P::R;
+  using L = LinkIO<P, D, REAL>;
+  cx<R> hf[2][D], hb[2][D];
+  {
+    cx<R> psi[4][D];
+    SpinorIO<P, D>::load(A.in, Vh, nf, psi);
+    spin_project<MU>(psi, sgf, hf);
+    SpinorIO<P, D>::load(A.in, Vh, nb, psi);
+    spin_project<MU>(psi, sgb, hb);
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    cx<R> wf0 = cmake(R(0), R(0)), wf1 = wf0, wb0 = wf0, wb1 = wf0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      typename L::elem uf, ub;
+      L::load(A.links, Vh, i, MU, a * D + b, uf, ub);
+      link_mac(wf0, uf, hf[0][b]);
+      link_mac(wf1, uf, hf[1][b]);
+      link_mac(wb0, ub, hb[0][b]);
+      link_mac(wb1, ub, hb[1][b]);
+    }
+    spin_reconstruct<MU>(acc, a, wf0, wf1, sgf);
+    spin_reconstruct<MU>(acc, a, wb0, wb1, sgb);
+  }
+}
+
+template <typename P, int D, bool REAL>
+__global__ void __launch_bounds__(kHopThreads) hop_kernel(const HopArgs A) {
+  using R = typename P::R;
+  if (A.done != nullptr && *A.done != 0) return;  // uniform over the grid
+  const int i = blockIdx.x * kHopThreads + threadIdx.x;
+  double nrm = 0.0;
+  if (i < A.g.Vh) {
+    const size_t Vh = (size_t)A.g.Vh;
+    int nf[4], nb[4];
+    eo_neighbours(A.g, i, A.p, nf, nb);
+    const R sg = A.dagger ? R(1) : R(-1);  // forward sign; backward is -sg
+    cx<R> acc[4][D];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[s][a] = cmake(R(0), R(0));
+    hop_direction<0, P, D, REAL>(A, Vh, i, nf[0], nb[0], sg, -sg, acc);
+    hop_direction<1, P, D, REAL>(A, Vh, i, nf[1], nb[1], sg, -sg, acc);
+    hop_direction<2, P, D, REAL>(A, Vh, i, nf[2], nb[2], sg, -sg, acc);
+    hop_direction<3, P, D, REAL>(A, Vh, i, nf[3], nb[3], sg, -sg, acc);
+
+    const R b = (R)A.b;
+    if (A.x != nullptr) {
+      const R a = (R)A.a;
+      cx<R> xs[4][D];
+      SpinorIO<P, D>::load(A.x, Vh, i, xs);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          acc[s][c] = cmake(fma(a, xs[s][c].re, b * acc[s][c].re), fma(a, xs[s][c].im, b * acc[s][c].im));
+    } else {
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc[s][c] = cmake(b * acc[s][c].re, b * acc[s][c].im);
+    }
+    SpinorIO<P, D>::store(A.out, Vh, i, acc);
+    if (A.partials != nullptr) {
+      R n = 0;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < D; ++c) n = fma(acc[s][c].re, acc[s][c].re, fma(acc[s][c].im, acc[s][c].im, n));
+      nrm = (double)n;
+    }
+  }
+  if (A.partials != nullptr) block_sum_store<kHopThreads>(nrm, A.partials);
+}
+
+template <typename P, int D, bool REAL>
+inline int launch_hop_t(const HopArgs& A, cudaStream_t s) {
+  const int blocks = hop_blocks(A.g.Vh);
+  hop_kernel<P, D, REAL><<<blocks, kHopThreads, 0, s>>>(A);
+  return blocks;
+}
+
+}  // namespace bsm

@@ -1,0 +1,287 @@
+// links.cu -- representation links (Sec. II-A: the fermion transforms under a
+// non-trivial representation R of SU(N)) and spinor packing between the
+// canonical host order and the device layout.
+//
+// R(U) is computed in FP64 from closed forms:
+//   adjoint     R_ab = 2 Tr(T^a W^b), W^b = U T^b U^+, evaluated entrywise
+//               from the sparse generators (2 Re W_ij, -2 Im W_ij, or the
+//               Cartan combination of the diagonal);
+//   two-index   R_(ij),(kl) = U_ik U_jl -+ U_il U_jk (the 2x2 minors /
+//               permanents of U), with factors sqrt2 and 1 on the diagonal
+//               pairs of the symmetric representation;
+// then multiplied by exp(i phi_mu) on links leaving the last slice of mu,
+// rounded once to the target precision and written twice: as the forward
+// link of x (block of parity(x)) and, daggered, as the backward link of x+mu
+// (block of the other parity).
+#include <math.h>
+
+#include "bsm_internal.cuh"
+
+namespace bsm {
+
+namespace {
+
+__host__ __device__ constexpr int rep_dim_c(int N, int REP) {
+  return REP == BSM_FUND ? N : REP == BSM_ADJ ? N * N - 1 : REP == BSM_SYM ? N * (N + 1) / 2 : N * (N - 1) / 2;
+}
+
+struct LinkGeom {
+  int dims[4];
+  int V;
+  int Vh;
+  double cph[4], sph[4];  // cos, sin of the boundary phases
+};
+
+__device__ __forceinline__ cx<double> cmul(cx<double> a, cx<double> b) {
+  return cmake(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+__device__ __forceinline__ cx<double> cmulc(cx<double> a, cx<double> b) {  // a * conj(b)
+  return cmake(a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im);
+}
+
+template <int N, int REP>
+__device__ void rep_of(const cx<double> (&U)[N][N], cx<double> (&R)[rep_dim_c(N, REP)][rep_dim_c(N, REP)]) {
+  constexpr int d = rep_dim_c(N, REP);
+  if (REP == BSM_FUND) {
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+      for (int b = 0; b < N; ++b) R[a][b] = U[a][b];
+  } else if (REP == BSM_ADJ) {
+    constexpr int noff = N * (N - 1) / 2;
+    for (int bcol = 0; bcol < d; ++bcol) {
+      // W = U T^b U^+ for generator bcol
+      cx<double> W[N][N];
+      if (bcol < 2 * noff) {
+        int q = bcol < noff ? bcol : bcol - noff, k = 0, l = 1;
+        for (int n = 0; n < q; ++n)
+          if (++l == N) { ++k; l = k + 1; }
+        const bool sym = bcol < noff;
+        for (int i = 0; i < N; ++i)
+          for (int j = 0; j < N; ++j) {
+            const cx<double> p1 = cmulc(U[i][k], U[j][l]);  // U_ik conj(U_jl)
+            const cx<double> p2 = cmulc(U[i][l], U[j][k]);  // U_il conj(U_jk)
+            if (sym) {
+              W[i][j] = cmake(0.5 * (p1.re + p2.re), 0.5 * (p1.im + p2.im));
+            } else {  // -i (p1 - p2) / 2
+              W[i][j] = cmake(0.5 * (p1.im - p2.im), -0.5 * (p1.re - p2.re));
+            }
+          }
+      } else {
+        const int l = bcol - 2 * noff + 1;
+        const double nrm = 1.0 / sqrt(2.0 * l * (l + 1));
+        for (int i = 0; i < N; ++i)
+          for (int j = 0; j < N; ++j) {
+            cx<double> s = cmake(0.0, 0.0);
+            for (int m = 0; m <= l; ++m) {
+              const double Dm = (m < l ? 1.0 : -(double)l) * nrm;
+              const cx<double> p = cmulc(U[i][m], U[j][m]);
+              s.re += Dm * p.re;
+              s.im += Dm * p.im;
+            }
+            W[i][j] = s;
+          }
+      }
+      // R_ab = 2 Tr(T^a W)
+      int a = 0;
+      for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j, ++a) {
+          R[a][bcol] = cmake(2.0 * W[i][j].re, 0.0);
+          R[a + noff][bcol] = cmake(-2.0 * W[i][j].im, 0.0);
+        }
+      for (int l = 1; l < N; ++l) {
+        const double nrm = 1.0 / sqrt(2.0 * l * (l + 1));
+        double s = 0.0;
+        for (int m = 0; m < l; ++m) s += W[m][m].re;
+        s -= l * W[l][l].re;
+        R[2 * noff + l - 1][bcol] = cmake(2.0 * nrm * s, 0.0);
+      }
+    }
+  } else {
+    constexpr bool sym = REP == BSM_SYM;
+    const double r2 = sqrt(2.0);
+    int A = 0;
+    for (int i = 0; i < N; ++i)
+      for (int j = sym ? i : i + 1; j < N; ++j, ++A) {
+        int B = 0;
+        for (int k = 0; k < N; ++k)
+          for (int l = sym ? k : k + 1; l < N; ++l, ++B) {
+            const cx<double> t1 = cmul(U[i][k], U[j][l]);
+            const cx<double> t2 = cmul(U[i][l], U[j][k]);
+            cx<double> v;
+            if (!sym) {
+              v = cmake(t1.re - t2.re, t1.im - t2.im);
+            } else if (i != j && k != l) {
+              v = cmake(t1.re + t2.re, t1.im + t2.im);
+            } else if (i != j || k != l) {  // one diagonal pair: sqrt2 U_ik U_jl
+              v = cmake(r2 * t1.re, r2 * t1.im);
+            } else {
+              v = t1;
+            }
+            R[A][B] = v;
+          }
+      }
+  }
+}
+
+template <int N, int REP>
+__global__ void links_to_rep_kernel(const double2* __restrict__ Uc, void* __restrict__ out, LinkGeom g,
+                                    int prec, size_t block_bytes) {
+  constexpr int d = rep_dim_c(N, REP);
+  constexpr bool real = REP == BSM_ADJ;
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= (int64_t)g.V * 4) return;
+  const int s = (int)(l >> 2), mu = (int)(l & 3);
+  int c[4];
+  {
+    int r = s;
+    c[3] = r % g.dims[3]; r /= g.dims[3];
+    c[2] = r % g.dims[2]; r /= g.dims[2];
+    c[1] = r % g.dims[1]; r /= g.dims[1];
+    c[0] = r;
+  }
+  const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
+  const int i = s >> 1;
+  int cn[4] = {c[0], c[1], c[2], c[3]};
+  cn[mu] = (cn[mu] + 1 == g.dims[mu]) ? 0 : cn[mu] + 1;
+  const int sn = ((cn[0] * g.dims[1] + cn[1]) * g.dims[2] + cn[2]) * g.dims[3] + cn[3];
+  const int j = sn >> 1;  // neighbour x+mu, parity 1-p
+
+  cx<double> U[N][N];
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      const double2 v = Uc[(size_t)l * N * N + a * N + b];
+      U[a][b] = cmake(v.x, v.y);
+    }
+  cx<double> R[d][d];
+  rep_of<N, REP>(U, R);
+  if (c[mu] == g.dims[mu] - 1) {  // boundary phase exp(i phi_mu)
+    const cx<double> ph = cmake(g.cph[mu], g.sph[mu]);
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) R[a][b] = cmul(ph, R[a][b]);
+  }
+
+  char* blk_f = reinterpret_cast<char*>(out) + (size_t)p * block_bytes;
+  char* blk_b = reinterpret_cast<char*>(out) + (size_t)(1 - p) * block_bytes;
+  const size_t Vh = (size_t)g.Vh;
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) {
+      const int cc = a * d + b;
+      const cx<double> f = R[a][b];
+      const cx<double> bw = cmake(R[b][a].re, -R[b][a].im);  // (R^+)_ab
+      if (!real && prec == BSM_F64) {
+        double2* P = reinterpret_cast<double2*>(blk_f);
+        double2* Q = reinterpret_cast<double2*>(blk_b);
+        P[(size_t)((2 * mu) * d * d + cc) * Vh + i] = make_double2(f.re, f.im);
+        Q[(size_t)((2 * mu + 1) * d * d + cc) * Vh + j] = make_double2(bw.re, bw.im);
+      } else if (!real) {
+        float2* P = reinterpret_cast<float2*>(blk_f);
+        float2* Q = reinterpret_cast<float2*>(blk_b);
+        P[2 * ((size_t)(mu * d * d + cc) * Vh + i)] = make_float2(__double2float_rn(f.re), __double2float_rn(f.im));
+        Q[2 * ((size_t)(mu * d * d + cc) * Vh + j) + 1] =
+            make_float2(__double2float_rn(bw.re), __double2float_rn(bw.im));
+      } else if (prec == BSM_F64) {
+        double* P = reinterpret_cast<double*>(blk_f);
+        double* Q = reinterpret_cast<double*>(blk_b);
+        P[2 * ((size_t)(mu * d * d + cc) * Vh + i)] = f.re;
+        Q[2 * ((size_t)(mu * d * d + cc) * Vh + j) + 1] = bw.re;
+      } else {
+        float* P = reinterpret_cast<float*>(blk_f);
+        float* Q = reinterpret_cast<float*>(blk_b);
+        P[2 * ((size_t)(mu * d * d + cc) * Vh + i)] = __double2float_rn(f.re);
+        Q[2 * ((size_t)(mu * d * d + cc) * Vh + j) + 1] = __double2float_rn(bw.re);
+      }
+    }
+}
+
+// canonical [V][4][d] FP64 <-> device layout, one thread per site
+__global__ void pack_spinor_kernel(const double2* __restrict__ canon, void* __restrict__ dev, int4 dims, int d,
+                                   int prec, int unpack) {
+  const int V = dims.x * dims.y * dims.z * dims.w;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  int r = s;
+  const int z = r % dims.w; r /= dims.w;
+  const int y = r % dims.z; r /= dims.z;
+  const int x = r % dims.y;
+  const int t = r / dims.y;
+  const int p = (t + x + y + z) & 1;
+  const int i = s >> 1;
+  const size_t Vh = (size_t)V / 2;
+  double2* cs = const_cast<double2*>(canon) + (size_t)s * 4 * d;
+  if (prec == BSM_F64) {
+    double2* blk = reinterpret_cast<double2*>(dev) + (size_t)p * 4 * d * Vh;
+    for (int q = 0; q < 4 * d; ++q) {
+      if (unpack) cs[q] = blk[q * Vh + i];
+      else blk[q * Vh + i] = cs[q];
+    }
+  } else {
+    float4* blk = reinterpret_cast<float4*>(dev) + (size_t)p * 2 * d * Vh;
+    for (int sp = 0; sp < 2; ++sp)
+      for (int a = 0; a < d; ++a) {
+        const int q = sp * d + a;
+        if (unpack) {
+          const float4 v = blk[q * Vh + i];
+          cs[sp * d + a] = make_double2(v.x, v.y);
+          cs[(sp + 2) * d + a] = make_double2(v.z, v.w);
+        } else {
+          const double2 u = cs[sp * d + a], w = cs[(sp + 2) * d + a];
+          blk[q * Vh + i] = make_float4(__double2float_rn(u.x), __double2float_rn(u.y), __double2float_rn(w.x),
+                                        __double2float_rn(w.y));
+        }
+      }
+  }
+}
+
+template <int N, int REP>
+void launch_links(const double* U, void* out, const LinkGeom& g, int prec, size_t block_bytes, cudaStream_t s) {
+  const int threads = 128;
+  const int64_t n = (int64_t)g.V * 4;
+  const int blocks = (int)((n + threads - 1) / threads);
+  links_to_rep_kernel<N, REP><<<blocks, threads, 0, s>>>(reinterpret_cast<const double2*>(U), out, g, prec,
+                                                          block_bytes);
+}
+
+}  // namespace
+
+int links_to_rep_launch(const bsm_lattice& L, const double* U, void* out, int prec, cudaStream_t s) {
+  const RepInfo ri = rep_info(L.N, L.rep);
+  if (ri.d < 0) return BSM_EUNSUPPORTED;
+  LinkGeom g;
+  for (int m = 0; m < 4; ++m) {
+    g.dims[m] = L.dims[m];
+    g.cph[m] = cos(L.bc_phase[m]);
+    g.sph[m] = sin(L.bc_phase[m]);
+  }
+  g.V = L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3];
+  g.Vh = g.V / 2;
+  if (ri.real)
+    for (int m = 0; m < 4; ++m) g.sph[m] = 0.0;  // phases are multiples of pi here
+  const size_t bb = link_block_bytes(g.Vh, ri.d, ri.real, prec);
+#define BSM_LINKS_CASE(NN, RR) \
+  if (L.N == NN && L.rep == RR) { launch_links<NN, RR>(U, out, g, prec, bb, s); return BSM_OK; }
+  BSM_LINKS_CASE(2, BSM_FUND)
+  BSM_LINKS_CASE(3, BSM_FUND)
+  BSM_LINKS_CASE(4, BSM_FUND)
+  BSM_LINKS_CASE(6, BSM_FUND)
+  BSM_LINKS_CASE(8, BSM_FUND)
+  BSM_LINKS_CASE(2, BSM_ADJ)
+  BSM_LINKS_CASE(3, BSM_ADJ)
+  BSM_LINKS_CASE(2, BSM_SYM)
+  BSM_LINKS_CASE(3, BSM_SYM)
+  BSM_LINKS_CASE(3, BSM_ASYM)
+  BSM_LINKS_CASE(4, BSM_ASYM)
+#undef BSM_LINKS_CASE
+  return BSM_EUNSUPPORTED;
+}
+
+void pack_spinor_launch(const bsm_lattice& L, const double* canon, void* dev, int d, int prec, bool unpack,
+                        cudaStream_t s) {
+  const int4 dims = make_int4(L.dims[0], L.dims[1], L.dims[2], L.dims[3]);
+  const int V = L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3];
+  const int threads = 128;
+  pack_spinor_kernel<<<(V + threads - 1) / threads, threads, 0, s>>>(reinterpret_cast<const double2*>(canon), dev,
+                                                                     dims, d, prec, unpack ? 1 : 0);
+}
+
+}  // namespace bsm

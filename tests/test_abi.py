@@ -1,0 +1,122 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every symbol
+that include/bsm.h declares, answers size queries, and rejects bad arguments
+on the host before any launch (fake device addresses are passed where the
+call must return before touching them)."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bsm():
+    from paper_1401_3733_gb300 import build
+    build.build()
+    from paper_1401_3733_gb300 import bsm as mod
+    return mod
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "bsm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bsm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(bsm):
+    names = declared_functions()
+    assert len(names) >= 11
+    lib = ctypes.CDLL(bsm.library_path())
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_rep_dims(bsm):
+    want = {(2, bsm.FUND): 2, (3, bsm.FUND): 3, (4, bsm.FUND): 4, (6, bsm.FUND): 6, (8, bsm.FUND): 8,
+            (2, bsm.ADJ): 3, (3, bsm.ADJ): 8, (2, bsm.SYM): 3, (3, bsm.SYM): 6, (3, bsm.ASYM): 3, (4, bsm.ASYM): 6}
+    for (N, r), d in want.items():
+        assert bsm.bsm_rep_dim(N, r) == d
+    for N, r in [(5, bsm.FUND), (2, bsm.ASYM), (4, bsm.ADJ), (1, bsm.FUND), (3, 9)]:
+        assert bsm.bsm_rep_dim(N, r) == bsm.EUNSUPPORTED
+
+
+def test_field_and_workspace_sizes(bsm):
+    lat = bsm.lattice((64, 32, 32, 32), 3)
+    V, Vh, d = 64 * 32 ** 3, 64 * 32 ** 3 // 2, 3
+    assert bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR, bsm.F64) == V * 4 * d * 16
+    assert bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR, bsm.F32) == V * 4 * d * 8
+    assert bsm.bsm_field_bytes(lat, bsm.FIELD_HALF_SPINOR, bsm.F32) == Vh * 4 * d * 8
+    # every link stored twice (forward of its site, backward of its neighbour)
+    assert bsm.bsm_field_bytes(lat, bsm.FIELD_LINKS, bsm.F64) == 2 * 4 * V * d * d * 16
+    assert bsm.bsm_field_bytes(lat, bsm.FIELD_LINKS, bsm.F32) == 2 * 4 * V * d * d * 8
+    adj = bsm.lattice((4, 4, 4, 4), 2, bsm.ADJ)
+    assert bsm.bsm_field_bytes(adj, bsm.FIELD_LINKS, bsm.F32) == 2 * 4 * 256 * 9 * 4
+    assert bsm.bsm_field_bytes(lat, bsm.FIELD_FUND_CANON) == V * 4 * 9 * 16
+    assert bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR_CANON) == V * 4 * d * 16
+    assert bsm.bsm_workspace_bytes(lat, bsm.CALL_DIRAC_EO, bsm.F32) == 2 * Vh * 4 * d * 8
+    ws64 = bsm.bsm_workspace_bytes(lat, bsm.CALL_CG, bsm.F64)
+    ws32 = bsm.bsm_workspace_bytes(lat, bsm.CALL_CG, bsm.F32)
+    assert ws64 >= 6 * Vh * 4 * d * 16 and ws32 > ws64
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 3), (0, 4, 4, 4), (4, 4, 1, 4), (-2, 4, 4, 4)])
+def test_bad_extents_rejected(bsm, dims):
+    lat = bsm.lattice(dims, 3)
+    assert bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR, bsm.F64) == 0
+    assert bsm._lib.bsm_dslash(ctypes.byref(lat), 256, 512, 1024, bsm.EVEN, 0, bsm.F64, 0) == bsm.EINVAL
+
+
+def test_host_validation_paths(bsm):
+    L = ctypes.byref
+    good = bsm.lattice((4, 4, 4, 4), 3, bsm.FUND, 0.1, (math.pi, 0, 0, 0))
+    A = 1 << 20  # fake, 16-byte aligned device addresses: never dereferenced
+    # unsupported (N, rep), real representation with a generic phase, A == 0
+    assert bsm._lib.bsm_dslash(L(bsm.lattice((4, 4, 4, 4), 5)), A, 2 * A, 3 * A, 0, 0, 0, 0) == bsm.EUNSUPPORTED
+    adj = bsm.lattice((4, 4, 4, 4), 2, bsm.ADJ, 0.1, (0.3, 0, 0, 0))
+    assert bsm._lib.bsm_links_to_rep(L(adj), A, 2 * A, bsm.F64, 0) == bsm.EUNSUPPORTED
+    assert bsm._lib.bsm_dslash(L(bsm.lattice((4, 4, 4, 4), 3, bsm.FUND, -4.0)), A, 2 * A, 3 * A, 0, 0, 0, 0) \
+        == bsm.EINVAL
+    # null and misaligned pointers, bad enums, aliasing input and output
+    assert bsm._lib.bsm_dslash(L(good), None, 2 * A, 3 * A, 0, 0, 0, 0) == bsm.EINVAL
+    assert bsm._lib.bsm_dslash(L(good), A, 2 * A + 8, 3 * A, 0, 0, 0, 0) == bsm.EINVAL
+    assert bsm._lib.bsm_dslash(L(good), A, 2 * A, 3 * A, 7, 0, 0, 0) == bsm.EINVAL
+    assert bsm._lib.bsm_dslash(L(good), A, 2 * A, 3 * A, 0, 0, 5, 0) == bsm.EUNSUPPORTED
+    assert bsm._lib.bsm_dslash(L(good), A, 2 * A, 2 * A + 256, 0, 0, 0, 0) == bsm.EINVAL
+    assert bsm._lib.bsm_pack_spinor(L(good), None, A, 0, 0) == bsm.EINVAL
+    # dirac_eo: bad op, short workspace
+    assert bsm._lib.bsm_dirac_eo(L(good), A, 2 * A, 3 * A, 9, 0, 4 * A, 1 << 30, 0) == bsm.EINVAL
+    assert bsm._lib.bsm_dirac_eo(L(good), A, 2 * A, 3 * A, 0, 0, 4 * A, 16, 0) == bsm.EWORKSPACE
+
+
+def test_cg_option_validation(bsm):
+    L = ctypes.byref
+    good = bsm.lattice((4, 4, 4, 4), 2, bsm.FUND, 0.1, (math.pi, 0, 0, 0))
+    A = 1 << 24
+    big = 1 << 40
+
+    def call(opts, ws_bytes=big, U32=None):
+        st = bsm.CgStats()
+        return bsm._lib.bsm_cg_solve(L(good), A, U32, 2 * A, 3 * A, L(opts), L(st), 4 * A, ws_bytes, 0)
+
+    assert call(bsm.cg_opts(tol=0.0)) == bsm.EINVAL
+    assert call(bsm.cg_opts(tol=-1.0)) == bsm.EINVAL
+    assert call(bsm.cg_opts(max_iter=0)) == bsm.EINVAL
+    assert call(bsm.cg_opts(delta=1.5)) == bsm.EINVAL
+    assert call(bsm.cg_opts(prec_inner=9)) == bsm.EUNSUPPORTED
+    assert call(bsm.cg_opts(prec_inner=bsm.F32)) == bsm.EINVAL        # mixed precision needs FP32 links
+    assert call(bsm.cg_opts(), ws_bytes=4096) == bsm.EWORKSPACE
+
+
+def test_too_large_lattice_is_unsupported(bsm):
+    lat = bsm.lattice((2048, 1024, 1024, 2), 3)
+    assert bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR, bsm.F32) == 0
+    assert bsm._lib.bsm_dslash(ctypes.byref(lat), 256, 512, 1024, 0, 0, 0, 0) == bsm.EUNSUPPORTED
+
+
+def test_strerror_covers_every_status(bsm):
+    for s in range(0, -9, -1):
+        assert bsm.bsm_strerror(s) not in ("", "unknown status")
+    assert bsm.bsm_strerror(-99) == "unknown status"

@@ -1,0 +1,184 @@
+"""GPU parity of the representation links, the hopping block, the full Wilson
+operator and the even-odd Schur operator against the FP64 oracle, element by
+element on the same seeded inputs, through the C ABI.  Bars: relative L2
+<= 1e-13 in FP64 and <= 2e-6 in FP32.  Also physics invariants evaluated on
+the GPU output itself (closed-form free field, gamma5-hermiticity, gauge
+covariance), so that a convention shared by both sides cannot hide."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_1401_3733_gb300 import bsm, fields
+from tests.gpu_helpers import (REP_CASES, REP_IDS, TOL, gpu_links, gpu_spinor, half, rel, to_canon,
+                               zeros_field)
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [bsm.F64, bsm.F32]
+PREC_IDS = ["f64", "f32"]
+
+
+def setup(dims, N, rep, m0, phase, seed, kind="haar", eps=0.3):
+    olat = orc.Lattice(dims, N, rep, m0, phase)
+    blat = bsm.lattice(dims, N, rep, m0, phase)
+    U = fields.gauge_field(dims, N, kind, seed=seed, eps=eps)
+    R = orc.links_to_rep(olat, U)
+    psi = fields.gaussian_spinor(dims, olat.d, seed + 1000)
+    return olat, blat, U, R, psi
+
+
+def gpu_hop_parity(blat, U, psi, p, dagger, prec):
+    Ud = gpu_links(blat, U, prec)
+    inp = gpu_spinor(blat, psi, prec)
+    out = zeros_field(blat, bsm.FIELD_SPINOR, prec)
+    bsm.bsm_dslash(blat, Ud, half(blat, inp, 1 - p, prec), half(blat, out, p, prec), p, dagger, prec)
+    return to_canon(blat, out, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_pack_unpack_roundtrip(prec):
+    dims = (4, 2, 6, 4)
+    lat = bsm.lattice(dims, 3)
+    psi = fields.gaussian_spinor(dims, 3, 5)
+    back = to_canon(lat, gpu_spinor(lat, psi, prec), prec)
+    want = psi if prec == bsm.F64 else psi.astype(np.complex64).astype(np.complex128)
+    assert np.array_equal(back, want)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+@pytest.mark.parametrize("N,rep", REP_CASES, ids=REP_IDS)
+def test_hop_parity_blocks_all_reps(N, rep, prec):
+    dims = (4, 4, 4, 4)
+    phase = (np.pi, 0, 0, 0) if rep == bsm.ADJ else (np.pi, 0.4, -1.3, 0.0)
+    olat, blat, U, R, psi = setup(dims, N, rep, 0.1, phase, seed=100 + 7 * N + rep)
+    for p in (0, 1):
+        for dagger in (False, True):
+            got = gpu_hop_parity(blat, U, psi, p, dagger, prec)
+            want = orc.hop(olat, R, psi, out_parity=p, dagger=dagger)
+            assert rel(got, want) <= TOL[prec], (p, dagger, rel(got, want))
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 2, 2, 6), (6, 4, 2, 10), (4, 6, 8, 2), (8, 4, 4, 6)],
+                         ids=["2^4", "ragged24", "ragged240", "nonc-z2", "8x4x4x6"])
+def test_full_dirac_shapes(dims, prec):
+    """Full D and D^+ on small, non-cubic and ragged lattices (V_h not a
+    multiple of the block size; Z = 2 and L = 2, where both neighbours of a
+    site coincide)."""
+    olat, blat, U, R, psi = setup(dims, 3, bsm.FUND, 0.05, (np.pi, 0.3, 0, 1.1), seed=200)
+    Ud = gpu_links(blat, U, prec)
+    inp = gpu_spinor(blat, psi, prec)
+    out = zeros_field(blat, bsm.FIELD_SPINOR, prec)
+    for dagger in (False, True):
+        bsm.bsm_dslash(blat, Ud, inp, out, bsm.FULL, dagger, prec)
+        got = to_canon(blat, out, prec)
+        want = orc.dirac(olat, R, psi, dagger=dagger)
+        assert rel(got, want) <= TOL[prec], (dagger, rel(got, want))
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+@pytest.mark.parametrize("N,rep", [(2, bsm.FUND), (3, bsm.FUND), (2, bsm.ADJ), (4, bsm.ASYM), (3, bsm.SYM)],
+                         ids=["SU2-F", "SU3-F", "SU2-ADJ", "SU4-AS", "SU3-S"])
+def test_dirac_eo_ops(N, rep, prec):
+    dims = (4, 4, 2, 6)
+    olat, blat, U, R, psi = setup(dims, N, rep, 0.1, (np.pi, 0, 0, 0), seed=300 + N)
+    odd = orc.parity_mask(dims)
+    psi[odd] = 0
+    Ud = gpu_links(blat, U, prec)
+    inp = gpu_spinor(blat, psi, prec)
+    ws = torch.empty(bsm.bsm_workspace_bytes(blat, bsm.CALL_DIRAC_EO, prec), dtype=torch.uint8, device="cuda")
+    for op in (bsm.OP_DHAT, bsm.OP_DHAT_DAG, bsm.OP_DHAT_DAG_DHAT):
+        out = zeros_field(blat, bsm.FIELD_SPINOR, prec)
+        bsm.bsm_dirac_eo(blat, Ud, half(blat, inp, 0, prec), half(blat, out, 0, prec), op, prec, ws)
+        got = to_canon(blat, out, prec)
+        want = orc.dhat(olat, R, psi, op)
+        assert rel(got, want) <= TOL[prec], (op, rel(got, want))
+
+
+# ----------------------------------------------------------------------------
+# invariants on the GPU output itself
+# ----------------------------------------------------------------------------
+
+def free_symbol(m0, p):
+    D = (m0 + np.sum(1 - np.cos(p))) * np.eye(4, dtype=np.complex128)
+    for mu in range(4):
+        D = D + 1j * np.sin(p[mu]) * orc.gamma(mu)
+    return D
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_gpu_free_field_plane_wave(prec):
+    dims, phase, m0 = (8, 4, 6, 4), (np.pi, 0.5, 0, -0.8), 0.07
+    blat = bsm.lattice(dims, 3, bsm.FUND, m0, phase)
+    Ud = gpu_links(blat, fields.gauge_field(dims, 3, "unit"), prec)
+    xs = fields.site_coords(dims)
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        n = np.array([rng.integers(0, L) for L in dims])
+        p = (2 * np.pi * n + np.array(phase)) / np.array(dims)
+        chi = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+        wave = np.exp(1j * xs @ p)
+        out = zeros_field(blat, bsm.FIELD_SPINOR, prec)
+        bsm.bsm_dslash(blat, Ud, gpu_spinor(blat, wave[:, None, None] * chi[None], prec), out, bsm.FULL, 0, prec)
+        want = wave[:, None, None] * (free_symbol(m0, p) @ chi)[None]
+        assert rel(to_canon(blat, out, prec), want) <= TOL[prec]
+
+
+@pytest.mark.parametrize("N,rep", [(3, bsm.FUND), (2, bsm.ADJ), (4, bsm.ASYM)], ids=["SU3-F", "SU2-ADJ", "SU4-AS"])
+def test_gpu_gamma5_hermiticity_and_gauge_covariance(N, rep):
+    prec = bsm.F64
+    dims = (4, 4, 2, 4)
+    olat, blat, U, R, psi = setup(dims, N, rep, 0.1, (np.pi, 0, 0, 0), seed=400)
+    phi = fields.gaussian_spinor(dims, olat.d, 401)
+    Ud = gpu_links(blat, U, prec)
+
+    def D(links, f, dagger=False):
+        out = zeros_field(blat, bsm.FIELD_SPINOR, prec)
+        bsm.bsm_dslash(blat, links, gpu_spinor(blat, f, prec), out, bsm.FULL, dagger, prec)
+        return to_canon(blat, out, prec)
+
+    G5 = lambda f: np.einsum("ab,sbc->sac", np.diag([-1.0, -1.0, 1.0, 1.0]), f)
+    lhs = np.vdot(phi.reshape(-1), G5(D(Ud, G5(psi))).reshape(-1))
+    rhs = np.vdot(D(Ud, phi).reshape(-1), psi.reshape(-1))
+    assert abs(lhs - rhs) / abs(rhs) < 1e-13
+    assert rel(D(Ud, psi, dagger=True), G5(D(Ud, G5(psi)))) < 1e-13
+
+    g = fields.gauge_transform(dims, N, 402)
+    xs = fields.site_coords(dims)
+    T, X, Y, Z = dims
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        c = xs.copy()
+        c[:, mu] = (c[:, mu] + 1) % dims[mu]
+        fwd = ((c[:, 0] * X + c[:, 1]) * Y + c[:, 2]) * Z + c[:, 3]
+        Ug[:, mu] = g @ U[:, mu] @ np.conj(np.transpose(g[fwd], (0, 2, 1)))
+    Rg = orc.links_to_rep(olat, np.repeat(g[:, None], 4, axis=1))[:, 0]
+    rot = lambda f: np.einsum("sab,sib->sia", Rg, f)
+    assert rel(D(gpu_links(blat, Ug, prec), rot(psi)), rot(D(Ud, psi))) < 1e-13
+
+
+# ----------------------------------------------------------------------------
+# the 32^3 x 64 SU(3) workload at full size, in the benchmark's launch shape
+# ----------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def big_case():
+    dims = (64, 32, 32, 32)
+    olat, blat, U, R, psi = setup(dims, 3, bsm.FUND, 0.05, (np.pi, 0, 0, 0), seed=3, kind="smooth", eps=0.3)
+    return olat, blat, U, R, psi
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_full_size_32c64_hop(big_case, prec):
+    """Both parity blocks of the hop on the whole 32^3 x 64 lattice, every
+    output element compared with the oracle."""
+    olat, blat, U, R, psi = big_case
+    Ud = gpu_links(blat, U, prec)
+    inp = gpu_spinor(blat, psi, prec)
+    out = zeros_field(blat, bsm.FIELD_SPINOR, prec)
+    bsm.bsm_dslash(blat, Ud, half(blat, inp, 1, prec), half(blat, out, 0, prec), bsm.EVEN, 0, prec)
+    bsm.bsm_dslash(blat, Ud, half(blat, inp, 0, prec), half(blat, out, 1, prec), bsm.ODD, 0, prec)
+    got = to_canon(blat, out, prec)
+    want = orc.hop(olat, R, psi, out_parity=orc.FULL)
+    assert rel(got, want) <= TOL[prec]

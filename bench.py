@@ -30,6 +30,11 @@ METRIC = "Dslash GFLOP/s (% of HBM roofline); CG time-to-1e-10 vs plain FP64 CG"
 WORKLOAD = dict(dims=(64, 32, 32, 32), N=3, m0=0.05, phase=(math.pi, 0.0, 0.0, 0.0), link_seed=3, eps=0.3,
                 src_seed=4)
 SAMPLE_DIMS = (32, 16, 16, 16)   # bounded CPU sample: same per-site work, 1/16 of the sites
+# DRAM bytes per output site (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the FP32 SU(3) hop kernel as it stands, from one ncu capture on the 24^3 x 48
+# case, scaled by sites (the capture is summarised under profiles/).  Set to None
+# whenever the kernel changes until it is captured again.
+HOP_F32_TRAFFIC_PER_SITE = 686.3
 WORKLOAD_NAME = ("32^3x64 SU(3) fundamental, smooth links exp(i 0.3 H), m0=0.05, antiperiodic time: "
                  "even-odd Wilson hop on both parity blocks, FP32 storage and arithmetic")
 
@@ -324,7 +329,9 @@ def run_ours(args):
                    "algorithmic_bytes_per_site": bytes_per_site(d, 4), "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world}", "wall_s_timed_region": round(wall, 4)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
+                     "frac": round(achieved / peak, 4),
+                     "traffic": None if HOP_F32_TRAFFIC_PER_SITE is None else round(HOP_F32_TRAFFIC_PER_SITE * Vh),
+                     "peak_source": peak_src,
                      "kernel": "hop_kernel<F32,3,complex>", "bytes_per_launch": hop_bytes,
                      "avg_launch_us": round(avg_launch_ms * 1e3, 2), "frac_of_8TBs": round(achieved / 8000, 4)},
         "dslash_fp64": {"gflops": round(flop_step / (ms64 * 1e-3) / 1e9, 2), "ms_per_step": round(ms64, 4),

@@ -172,6 +172,31 @@ int bsm_dirac_eo(const bsm_lattice *lat, const void *U_rep, const void *in_e,
                  void *out_e, int32_t op, int32_t prec, void *workspace,
                  size_t workspace_bytes, void *stream);
 
+/* Size of the library-owned scratch array of bsm_dirac_eo_noalloc: 64 MiB. */
+#define BSM_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* bsm_dirac_eo without a caller workspace.  The paper has no counterpart:
+ * this entry point serves callers that cannot allocate device memory
+ * themselves -- a host that has handed all device memory to its own pool
+ * allocator, a plugin or sandbox that exposes no allocation call, or a loop
+ * that cannot afford the device-wide synchronisation that cudaMalloc and
+ * cudaFree imply.  It takes the arguments of bsm_dirac_eo minus the
+ * workspace and computes the same result with the same kernels.
+ * Its two scratch half spinors live in one BSM_NOALLOC_SCRATCH_BYTES array
+ * that the library declares as device memory; a GPU on which this entry
+ * point has run keeps that array until the process exits.  A lattice whose
+ * scratch, 2 * bsm_field_bytes(lat, BSM_FIELD_HALF_SPINOR, prec), exceeds
+ * the array returns BSM_EWORKSPACE before any launch.  The call allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine).  Its
+ * first call on a device looks up the array's device address with that
+ * device current and remembers it: make that first call before any stream
+ * capture.  All calls on a device share the one array and the scratch is
+ * fully rewritten by each call, so nothing needs clearing between calls,
+ * but calls that overlap on the GPU (e.g. on two streams) race on it:
+ * serialise them. */
+int bsm_dirac_eo_noalloc(const bsm_lattice *lat, const void *U_rep, const void *in_e,
+                         void *out_e, int32_t op, int32_t prec, void *stream);
+
 /* Solve D x = b (Sec. II-B: inverting the Dirac operator by CG) through CG on
  * the normal equations.  With opts->eo: Dhat^+ Dhat x_e = Dhat^+ bhat_e,
  * bhat_e = b_e + 1/(2A) H_eo b_o, then x_o = (b_o + H_oe x_e / 2) / A.

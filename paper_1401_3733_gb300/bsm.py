@@ -70,6 +70,7 @@ _lib.bsm_unpack_spinor.argtypes = [_LP, _P, _P, ctypes.c_int32, _P]
 _lib.bsm_links_to_rep.argtypes = [_LP, _P, _P, ctypes.c_int32, _P]
 _lib.bsm_dslash.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]
 _lib.bsm_dirac_eo.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P]
+_lib.bsm_dirac_eo_noalloc.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]
 _lib.bsm_cg_solve.argtypes = [_LP, _P, _P, _P, _P, ctypes.POINTER(CgOpts), ctypes.POINTER(CgStats), _P,
                               ctypes.c_size_t, _P]
 _lib.bsm_strerror.argtypes = [ctypes.c_int]
@@ -77,7 +78,7 @@ _lib.bsm_strerror.restype = ctypes.c_char_p
 _lib.bsm_last_cuda_error.argtypes = []
 _lib.bsm_last_cuda_error.restype = ctypes.c_char_p
 for _f in ("bsm_pack_spinor", "bsm_unpack_spinor", "bsm_links_to_rep", "bsm_dslash", "bsm_dirac_eo",
-           "bsm_cg_solve"):
+           "bsm_dirac_eo_noalloc", "bsm_cg_solve"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -163,6 +164,16 @@ def bsm_dirac_eo(lat, U_rep, in_e, out_e, op, prec, workspace, stream=None):
     nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(_lib.bsm_dirac_eo(ctypes.byref(lat), _ptr(U_rep), _ptr(in_e), _ptr(out_e), op, prec, _ptr(workspace),
                              nbytes, _stream(stream)), "bsm_dirac_eo")
+
+
+def bsm_dirac_eo_noalloc(lat, U_rep, in_e, out_e, op, prec, stream=None):
+    """bsm_dirac_eo with the library's own fixed scratch array instead of a
+    workspace, for callers that cannot allocate device memory."""
+    _check(_lib.bsm_dirac_eo_noalloc(ctypes.byref(lat), _ptr(U_rep), _ptr(in_e), _ptr(out_e), op, prec,
+                                     _stream(stream)), "bsm_dirac_eo_noalloc")
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 def bsm_cg_solve(lat, U_rep64, U_rep32, b, x, opts: CgOpts, workspace, stream=None, raise_on_error=True):

@@ -42,14 +42,17 @@
  *   half spinor, FP32: 2d planes of V_h float4, plane = s*d + colour for
  *       s = 0, 1, holding (psi[s][c], psi[s+2][c]) as (re, im, re, im).
  *   full spinor: the even half followed by the odd half.
- *   links, complex representation, for each output parity p (p = 0 block
- *       first): FP64 -- 8 x d^2 planes of V_h double2, plane (2mu+f)*d^2 + c,
- *       f = 0 forward link U^R_mu(x), f = 1 backward link U^R_mu(x-mu)^+,
- *       c = row*d + col, x running over the sites of parity p;
- *       FP32 -- 4 x d^2 planes of V_h float4, plane mu*d^2 + c holding
- *       (forward[c], backward[c]).
- *   links, real (adjoint) representation: 4 x d^2 planes per output parity of
- *       V_h double2 (FP64) or float2 (FP32) holding (forward[c], backward[c]).
+ *   links: for each output parity p (p = 0 block first) the 8 links that a
+ *       site x of parity p needs, forward U^R_mu(x) and backward
+ *       U^R_mu(x-mu)^+, grouped in planes.  Complex representation, FP64:
+ *       8 d^2 planes of double2, plane (2mu+f)*d^2 + c (f = 0 forward, 1
+ *       backward, c = row*d + col); FP32: 4 d^2 planes of float4, plane
+ *       mu*d^2 + c holding (forward[c], backward[c]).  Real (adjoint)
+ *       representation: 4 d^2 planes of double2 (FP64) or float2 (FP32)
+ *       holding (forward[c], backward[c]).  The planes are tiled by 32 sites:
+ *       element (plane, site i) sits at ((i/32)*planes + plane)*32 + i%32,
+ *       with V_h rounded up to a multiple of 32, so the links of a warp's 32
+ *       sites are one contiguous region.
  *   Every link is stored twice (as a forward link of its own site and as the
  *   backward link of its neighbour), so each hop reads its 8 links per site
  *   as aligned, coalesced 16-byte (8-byte for FP32 real) vectors.

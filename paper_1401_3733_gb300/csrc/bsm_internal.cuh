@@ -58,10 +58,20 @@ struct F32 {
 inline size_t half_spinor_bytes(int64_t Vh, int d, int prec) {
   return (size_t)Vh * 8 * d * (prec == BSM_F64 ? 8 : 4);
 }
+// Links are tiled: the sites of one parity are grouped in tiles of
+// kLinkTile consecutive eo indices, and a tile stores all its link planes
+// contiguously ([tile][plane][kLinkTile]), so a warp reads its 8 links per
+// site from one contiguous region.  V_h is padded up to a whole tile.
+constexpr int kLinkTile = 32;
+inline size_t padded_sites(int64_t Vh) { return (size_t)((Vh + kLinkTile - 1) / kLinkTile) * kLinkTile; }
 // bytes of the links of one output parity
 inline size_t link_block_bytes(int64_t Vh, int d, bool real, int prec) {
   const size_t w = prec == BSM_F64 ? 8 : 4;
-  return (size_t)Vh * 8 * d * d * w * (real ? 1 : 2);
+  return padded_sites(Vh) * 8 * d * d * w * (real ? 1 : 2);
+}
+// element offset of (plane, site i) in a tiled link block of `planes` planes
+__host__ __device__ __forceinline__ size_t link_index(int planes, int plane, int i) {
+  return ((size_t)(i / kLinkTile) * planes + plane) * kLinkTile + (i % kLinkTile);
 }
 
 // ---------------------------------------------------------------------------
@@ -164,7 +174,8 @@ struct SpinorIO<F32, D> {
 
 // ---------------------------------------------------------------------------
 // link layout access: forward link U(x) and backward link U(x-mu)^+ of
-// direction mu at eo site i of the output parity block `base`
+// direction mu, element c, for the thread's site.  `tile` points at the
+// site's column of its tile (tile_ptr); planes are kLinkTile elements apart.
 // ---------------------------------------------------------------------------
 template <typename P, int D, bool REAL>
 struct LinkIO;
@@ -172,10 +183,14 @@ struct LinkIO;
 template <int D>
 struct LinkIO<F64, D, false> {
   using elem = cx<double>;
-  __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, int mu, int c, elem& f, elem& b) {
-    const double2* p = reinterpret_cast<const double2*>(base);
-    const double2 vf = __ldcs(p + (size_t)((2 * mu) * D * D + c) * Vh + i);
-    const double2 vb = __ldcs(p + (size_t)((2 * mu + 1) * D * D + c) * Vh + i);
+  using vec = double2;
+  static constexpr int planes = 8 * D * D;
+  __device__ __forceinline__ static const vec* tile_ptr(const void* base, int i) {
+    return reinterpret_cast<const vec*>(base) + link_index(planes, 0, i);
+  }
+  __device__ __forceinline__ static void load(const vec* t, int mu, int c, elem& f, elem& b) {
+    const double2 vf = __ldcs(t + ((2 * mu) * D * D + c) * kLinkTile);
+    const double2 vb = __ldcs(t + ((2 * mu + 1) * D * D + c) * kLinkTile);
     f = cmake(vf.x, vf.y);
     b = cmake(vb.x, vb.y);
   }
@@ -184,9 +199,13 @@ struct LinkIO<F64, D, false> {
 template <int D>
 struct LinkIO<F32, D, false> {
   using elem = cx<float>;
-  __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, int mu, int c, elem& f, elem& b) {
-    const float4* p = reinterpret_cast<const float4*>(base);
-    const float4 v = __ldcs(p + (size_t)(mu * D * D + c) * Vh + i);
+  using vec = float4;
+  static constexpr int planes = 4 * D * D;
+  __device__ __forceinline__ static const vec* tile_ptr(const void* base, int i) {
+    return reinterpret_cast<const vec*>(base) + link_index(planes, 0, i);
+  }
+  __device__ __forceinline__ static void load(const vec* t, int mu, int c, elem& f, elem& b) {
+    const float4 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
     f = cmake(v.x, v.y);
     b = cmake(v.z, v.w);
   }
@@ -195,9 +214,13 @@ struct LinkIO<F32, D, false> {
 template <int D>
 struct LinkIO<F64, D, true> {
   using elem = double;
-  __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, int mu, int c, elem& f, elem& b) {
-    const double2* p = reinterpret_cast<const double2*>(base);
-    const double2 v = __ldcs(p + (size_t)(mu * D * D + c) * Vh + i);
+  using vec = double2;
+  static constexpr int planes = 4 * D * D;
+  __device__ __forceinline__ static const vec* tile_ptr(const void* base, int i) {
+    return reinterpret_cast<const vec*>(base) + link_index(planes, 0, i);
+  }
+  __device__ __forceinline__ static void load(const vec* t, int mu, int c, elem& f, elem& b) {
+    const double2 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
     f = v.x;
     b = v.y;
   }
@@ -206,9 +229,13 @@ struct LinkIO<F64, D, true> {
 template <int D>
 struct LinkIO<F32, D, true> {
   using elem = float;
-  __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, int mu, int c, elem& f, elem& b) {
-    const float2* p = reinterpret_cast<const float2*>(base);
-    const float2 v = __ldcs(p + (size_t)(mu * D * D + c) * Vh + i);
+  using vec = float2;
+  static constexpr int planes = 4 * D * D;
+  __device__ __forceinline__ static const vec* tile_ptr(const void* base, int i) {
+    return reinterpret_cast<const vec*>(base) + link_index(planes, 0, i);
+  }
+  __device__ __forceinline__ static void load(const vec* t, int mu, int c, elem& f, elem& b) {
+    const float2 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
     f = v.x;
     b = v.y;
   }

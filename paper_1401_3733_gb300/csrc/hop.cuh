@@ -11,7 +11,8 @@
 // link then multiplies the two colour vectors, one row at a time, and the
 // row is reconstructed into the four spin components of the accumulator.
 // The forward and backward links of mu share one 16-byte load (FP32) or sit
-// in neighbouring planes (FP64); links are read with the streaming cache hint
+// in neighbouring planes (FP64) of the site's link tile, so a warp reads its
+// links from one contiguous region; links are read with the streaming cache hint
 // because each is used once per hop, neighbour spinors through the read-only
 // path because each is used by 8 output sites.
 #pragma once
@@ -79,8 +80,8 @@ template <typename R>
 __device__ __forceinline__ void link_mac(cx<R>& w, R u, const cx<R>& h) { rmac(w, u, h); }
 
 template <int MU, typename P, int D, bool REAL>
-__device__ __forceinline__ void hop_direction(const HopArgs& A, size_t Vh, int i, int nf, int nb,
-                                              typename P::R sgf, typename P::R sgb,
+__device__ __forceinline__ void hop_direction(const HopArgs& A, size_t Vh, const typename LinkIO<P, D, REAL>::vec* lt,
+                                              int nf, int nb, typename P::R sgf, typename P::R sgb,
                                               cx<typename P::R> (&acc)[4][D]) {
   using R = typename P::R;
   using L = LinkIO<P, D, REAL>;
@@ -98,7 +99,7 @@ __device__ __forceinline__ void hop_direction(const HopArgs& A, size_t Vh, int i
 #pragma unroll
     for (int b = 0; b < D; ++b) {
       typename L::elem uf, ub;
-      L::load(A.links, Vh, i, MU, a * D + b, uf, ub);
+      L::load(lt, MU, a * D + b, uf, ub);
       link_mac(wf0, uf, hf[0][b]);
       link_mac(wf1, uf, hf[1][b]);
       link_mac(wb0, ub, hb[0][b]);
@@ -109,8 +110,17 @@ __device__ __forceinline__ void hop_direction(const HopArgs& A, size_t Vh, int i
   }
 }
 
+// Minimum resident blocks per SM (register budget) of each instantiation: the
+// FP32 kernels are bound by memory latency and want about 128 registers so
+// that each thread keeps a direction's loads in flight; larger d need more.
+template <typename P, int D>
+struct HopOccupancy {
+  static constexpr int min_blocks = P::prec == BSM_F32 ? (D <= 3 ? 4 : D == 4 ? 3 : D == 6 ? 2 : 1)
+                                                         : (D <= 2 ? 4 : D == 3 ? 2 : 1);
+};
+
 template <typename P, int D, bool REAL>
-__global__ void __launch_bounds__(kHopThreads) hop_kernel(const HopArgs A) {
+__global__ void __launch_bounds__(kHopThreads, HopOccupancy<P, D>::min_blocks) hop_kernel(const HopArgs A) {
   using R = typename P::R;
   if (A.done != nullptr && *A.done != 0) return;  // uniform over the grid
   const int i = blockIdx.x * kHopThreads + threadIdx.x;
@@ -119,16 +129,17 @@ __global__ void __launch_bounds__(kHopThreads) hop_kernel(const HopArgs A) {
     const size_t Vh = (size_t)A.g.Vh;
     int nf[4], nb[4];
     eo_neighbours(A.g, i, A.p, nf, nb);
+    const auto* lt = LinkIO<P, D, REAL>::tile_ptr(A.links, i);
     const R sg = A.dagger ? R(1) : R(-1);  // forward sign; backward is -sg
     cx<R> acc[4][D];
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
       for (int a = 0; a < D; ++a) acc[s][a] = cmake(R(0), R(0));
-    hop_direction<0, P, D, REAL>(A, Vh, i, nf[0], nb[0], sg, -sg, acc);
-    hop_direction<1, P, D, REAL>(A, Vh, i, nf[1], nb[1], sg, -sg, acc);
-    hop_direction<2, P, D, REAL>(A, Vh, i, nf[2], nb[2], sg, -sg, acc);
-    hop_direction<3, P, D, REAL>(A, Vh, i, nf[3], nb[3], sg, -sg, acc);
+    hop_direction<0, P, D, REAL>(A, Vh, lt, nf[0], nb[0], sg, -sg, acc);
+    hop_direction<1, P, D, REAL>(A, Vh, lt, nf[1], nb[1], sg, -sg, acc);
+    hop_direction<2, P, D, REAL>(A, Vh, lt, nf[2], nb[2], sg, -sg, acc);
+    hop_direction<3, P, D, REAL>(A, Vh, lt, nf[3], nb[3], sg, -sg, acc);
 
     const R b = (R)A.b;
     if (A.x != nullptr) {

@@ -163,7 +163,6 @@ __global__ void links_to_rep_kernel(const double2* __restrict__ Uc, void* __rest
 
   char* blk_f = reinterpret_cast<char*>(out) + (size_t)p * block_bytes;
   char* blk_b = reinterpret_cast<char*>(out) + (size_t)(1 - p) * block_bytes;
-  const size_t Vh = (size_t)g.Vh;
   for (int a = 0; a < d; ++a)
     for (int b = 0; b < d; ++b) {
       const int cc = a * d + b;
@@ -172,24 +171,26 @@ __global__ void links_to_rep_kernel(const double2* __restrict__ Uc, void* __rest
       if (!real && prec == BSM_F64) {
         double2* P = reinterpret_cast<double2*>(blk_f);
         double2* Q = reinterpret_cast<double2*>(blk_b);
-        P[(size_t)((2 * mu) * d * d + cc) * Vh + i] = make_double2(f.re, f.im);
-        Q[(size_t)((2 * mu + 1) * d * d + cc) * Vh + j] = make_double2(bw.re, bw.im);
+        P[link_index(8 * d * d, (2 * mu) * d * d + cc, i)] = make_double2(f.re, f.im);
+        Q[link_index(8 * d * d, (2 * mu + 1) * d * d + cc, j)] = make_double2(bw.re, bw.im);
       } else if (!real) {
+        // float4 element (plane, site) = float2 pair (forward, backward)
         float2* P = reinterpret_cast<float2*>(blk_f);
         float2* Q = reinterpret_cast<float2*>(blk_b);
-        P[2 * ((size_t)(mu * d * d + cc) * Vh + i)] = make_float2(__double2float_rn(f.re), __double2float_rn(f.im));
-        Q[2 * ((size_t)(mu * d * d + cc) * Vh + j) + 1] =
+        P[2 * link_index(4 * d * d, mu * d * d + cc, i)] =
+            make_float2(__double2float_rn(f.re), __double2float_rn(f.im));
+        Q[2 * link_index(4 * d * d, mu * d * d + cc, j) + 1] =
             make_float2(__double2float_rn(bw.re), __double2float_rn(bw.im));
       } else if (prec == BSM_F64) {
         double* P = reinterpret_cast<double*>(blk_f);
         double* Q = reinterpret_cast<double*>(blk_b);
-        P[2 * ((size_t)(mu * d * d + cc) * Vh + i)] = f.re;
-        Q[2 * ((size_t)(mu * d * d + cc) * Vh + j) + 1] = bw.re;
+        P[2 * link_index(4 * d * d, mu * d * d + cc, i)] = f.re;
+        Q[2 * link_index(4 * d * d, mu * d * d + cc, j) + 1] = bw.re;
       } else {
         float* P = reinterpret_cast<float*>(blk_f);
         float* Q = reinterpret_cast<float*>(blk_b);
-        P[2 * ((size_t)(mu * d * d + cc) * Vh + i)] = __double2float_rn(f.re);
-        Q[2 * ((size_t)(mu * d * d + cc) * Vh + j) + 1] = __double2float_rn(bw.re);
+        P[2 * link_index(4 * d * d, mu * d * d + cc, i)] = __double2float_rn(f.re);
+        Q[2 * link_index(4 * d * d, mu * d * d + cc, j) + 1] = __double2float_rn(bw.re);
       }
     }
 }

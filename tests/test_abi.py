@@ -52,6 +52,9 @@ def test_field_and_workspace_sizes(bsm):
     # every link stored twice (forward of its site, backward of its neighbour)
     assert bsm.bsm_field_bytes(lat, bsm.FIELD_LINKS, bsm.F64) == 2 * 4 * V * d * d * 16
     assert bsm.bsm_field_bytes(lat, bsm.FIELD_LINKS, bsm.F32) == 2 * 4 * V * d * d * 8
+    # links are tiled by 32 sites: a 2^4 lattice (V_h = 8) pads to one tile
+    tiny = bsm.lattice((2, 2, 2, 2), 3)
+    assert bsm.bsm_field_bytes(tiny, bsm.FIELD_LINKS, bsm.F32) == 2 * 32 * 8 * 9 * 4 * 2
     adj = bsm.lattice((4, 4, 4, 4), 2, bsm.ADJ)
     assert bsm.bsm_field_bytes(adj, bsm.FIELD_LINKS, bsm.F32) == 2 * 4 * 256 * 9 * 4
     assert bsm.bsm_field_bytes(lat, bsm.FIELD_FUND_CANON) == V * 4 * 9 * 16

@@ -41,6 +41,8 @@
  *       plane = spin*d + colour.
  *   half spinor, FP32: 2d planes of V_h float4, plane = s*d + colour for
  *       s = 0, 1, holding (psi[s][c], psi[s+2][c]) as (re, im, re, im).
+ *   half spinor, DF64: as FP64 with each double2 replaced by a float4
+ *       (re.hi, re.lo, im.hi, im.lo).
  *   full spinor: the even half followed by the odd half.
  *   links: for each output parity p (p = 0 block first) the 8 links that a
  *       site x of parity p needs, forward U^R_mu(x) and backward
@@ -49,7 +51,10 @@
  *       backward, c = row*d + col); FP32: 4 d^2 planes of float4, plane
  *       mu*d^2 + c holding (forward[c], backward[c]).  Real (adjoint)
  *       representation: 4 d^2 planes of double2 (FP64) or float2 (FP32)
- *       holding (forward[c], backward[c]).  The planes are tiled by 32 sites:
+ *       holding (forward[c], backward[c]).  DF64 stores what FP64 stores
+ *       with every double split into (hi, lo) floats: complex planes of
+ *       float4 (re.hi, re.lo, im.hi, im.lo), real planes of float4
+ *       (forward.hi, forward.lo, backward.hi, backward.lo).  The planes are tiled by 32 sites:
  *       element (plane, site i) sits at ((i/32)*planes + plane)*32 + i%32,
  *       with V_h rounded up to a multiple of 32, so the links of a warp's 32
  *       sites are one contiguous region.
@@ -92,7 +97,11 @@ typedef enum {
 } bsm_status;
 
 typedef enum { BSM_FUND = 0, BSM_ADJ = 1, BSM_SYM = 2, BSM_ASYM = 3 } bsm_rep;
-typedef enum { BSM_F64 = 0, BSM_F32 = 1 } bsm_prec;
+/* BSM_DF64: FP64-accurate "double-float" storage and arithmetic -- every real
+ * is an unevaluated sum hi + lo of two FP32 numbers (about 48 significand
+ * bits), computed with error-free transformations on the FP32 units; same
+ * bytes as FP64, several times the speed on GB300, whose FP64 units are slow. */
+typedef enum { BSM_F64 = 0, BSM_F32 = 1, BSM_DF64 = 2 } bsm_prec;
 typedef enum { BSM_EVEN = 0, BSM_ODD = 1, BSM_FULL = 2 } bsm_parity;
 typedef enum { BSM_OP_DHAT = 0, BSM_OP_DHAT_DAG = 1, BSM_OP_DHAT_DAG_DHAT = 2 } bsm_eo_op;
 typedef enum {
@@ -116,14 +125,19 @@ typedef struct {
 typedef struct {
   double tol;           /* stop when |rhs - M x_e| <= tol |rhs| (FP64, recomputed) */
   int32_t max_iter;     /* total CG iterations allowed */
-  int32_t prec_inner;   /* BSM_F64: plain FP64 CG; BSM_F32: mixed precision with
-                           FP64 reliable updates (needs U_rep32) */
+  int32_t prec_inner;   /* equal to prec_outer: plain CG at that precision;
+                           BSM_F32: mixed precision with reliable updates at
+                           prec_outer (needs U_rep32) */
   double delta;         /* reliable-update trigger: |r| < delta * max|r| since the
                            last update (0 selects 0.1) */
   int32_t use_x0;       /* nonzero: x holds the initial guess on entry */
   int32_t eo;           /* nonzero: even-odd Schur system (default path);
                            zero: unpreconditioned D^+ D on the full lattice */
   int32_t check_every;  /* iterations between host convergence checks (0 = 8) */
+  int32_t prec_outer;   /* precision of U_rep64, of the source preparation, the
+                           reliable updates, the true residuals and (plain CG)
+                           of the whole iteration: BSM_F64 or BSM_DF64.  b and
+                           x are FP64 device-layout spinors either way. */
 } bsm_cg_opts;
 
 typedef struct {
@@ -142,7 +156,8 @@ int bsm_rep_dim(int32_t N, int32_t rep);
 size_t bsm_field_bytes(const bsm_lattice *lat, int32_t kind, int32_t prec);
 
 /* Workspace bytes that bsm_dirac_eo (call = BSM_CALL_DIRAC_EO) or
- * bsm_cg_solve (BSM_CALL_CG, prec = the inner precision) needs.  Pure host. */
+ * bsm_cg_solve (BSM_CALL_CG, prec = the inner precision; enough for either
+ * outer precision) needs.  Pure host. */
 size_t bsm_workspace_bytes(const bsm_lattice *lat, int32_t call, int32_t prec);
 
 /* Canonical FP64 spinor [V][4][d] (device) -> full device-layout spinor at
@@ -203,8 +218,9 @@ int bsm_dirac_eo_noalloc(const bsm_lattice *lat, const void *U_rep, const void *
 /* Solve D x = b (Sec. II-B: inverting the Dirac operator by CG) through CG on
  * the normal equations.  With opts->eo: Dhat^+ Dhat x_e = Dhat^+ bhat_e,
  * bhat_e = b_e + 1/(2A) H_eo b_o, then x_o = (b_o + H_oe x_e / 2) / A.
- * b, x: full FP64 device-layout spinors.  U_rep64: FP64 links; U_rep32: FP32
- * links (required when opts->prec_inner == BSM_F32, else ignored).  stats is a
+ * b, x: full FP64 device-layout spinors.  U_rep64: links at opts->prec_outer
+ * (FP64 or DF64); U_rep32: FP32 links (required when opts->prec_inner ==
+ * BSM_F32, else ignored).  stats is a
  * host pointer (may be NULL).  Synchronises `stream`.  Returns BSM_ENOCONV,
  * BSM_EBREAKDOWN or BSM_ENAN with x holding the last iterate. */
 int bsm_cg_solve(const bsm_lattice *lat, const void *U_rep64, const void *U_rep32,

@@ -21,7 +21,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 # enums of bsm.h
 OK, EINVAL, EUNSUPPORTED, ECUDA, EWORKSPACE, ENOCONV, EBREAKDOWN, ENAN, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8
 FUND, ADJ, SYM, ASYM = 0, 1, 2, 3
-F64, F32 = 0, 1
+F64, F32, DF64 = 0, 1, 2
 EVEN, ODD, FULL = 0, 1, 2
 OP_DHAT, OP_DHAT_DAG, OP_DHAT_DAG_DHAT = 0, 1, 2
 FIELD_LINKS, FIELD_SPINOR, FIELD_HALF_SPINOR, FIELD_FUND_CANON, FIELD_SPINOR_CANON = 0, 1, 2, 3, 4
@@ -36,7 +36,7 @@ class Lattice(ctypes.Structure):
 class CgOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("prec_inner", ctypes.c_int32),
                 ("delta", ctypes.c_double), ("use_x0", ctypes.c_int32), ("eo", ctypes.c_int32),
-                ("check_every", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("prec_outer", ctypes.c_int32)]
 
 
 class CgStats(ctypes.Structure):
@@ -188,5 +188,6 @@ def bsm_cg_solve(lat, U_rep64, U_rep32, b, x, opts: CgOpts, workspace, stream=No
     return st, stats
 
 
-def cg_opts(tol=1e-10, max_iter=10000, prec_inner=F64, delta=0.1, use_x0=False, eo=True, check_every=8) -> CgOpts:
-    return CgOpts(tol, max_iter, prec_inner, delta, int(use_x0), int(eo), check_every)
+def cg_opts(tol=1e-10, max_iter=10000, prec_inner=F64, delta=0.1, use_x0=False, eo=True, check_every=8,
+            prec_outer=F64) -> CgOpts:
+    return CgOpts(tol, max_iter, prec_inner, delta, int(use_x0), int(eo), check_every, prec_outer)

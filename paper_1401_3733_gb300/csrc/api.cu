@@ -14,7 +14,7 @@ namespace bsm {
 int links_to_rep_launch(const bsm_lattice& L, const double* U, void* out, int prec, cudaStream_t s);
 void pack_spinor_launch(const bsm_lattice& L, const double* canon, void* dev, int d, int prec, bool unpack,
                         cudaStream_t s);
-size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo);
+size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo, int prec_outer);
 int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* b, void* x,
              const bsm_cg_opts& o, bsm_cg_stats* stats, void* ws, cudaStream_t s);
 
@@ -76,7 +76,7 @@ int check_lattice(const bsm_lattice* L) {
 }
 
 bool aligned(const void* p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
-bool prec_ok(int prec) { return prec == BSM_F64 || prec == BSM_F32; }
+bool prec_ok(int prec) { return prec == BSM_F64 || prec == BSM_F32 || prec == BSM_DF64; }
 
 int finish(int rc) {
   if (rc != BSM_OK) return rc;
@@ -130,9 +130,16 @@ size_t bsm_workspace_bytes(const bsm_lattice* lat, int32_t call, int32_t prec) {
   const RepInfo ri = rep_info(lat->N, lat->rep);
   if (call == BSM_CALL_DIRAC_EO) return 2 * half_spinor_bytes(g.Vh, ri.d, prec);
   if (call == BSM_CALL_CG) {
-    // the larger of the even-odd and full-lattice layouts
-    const size_t a = cg_workspace_bytes(*lat, prec, 1), b = cg_workspace_bytes(*lat, prec, 0);
-    return a > b ? a : b;
+    // the largest layout over even-odd/full and, for a mixed inner
+    // precision, over both outer precisions
+    size_t m = 0;
+    const int outers[2] = {prec == BSM_F32 ? BSM_F64 : prec, prec == BSM_F32 ? BSM_DF64 : prec};
+    for (int k = 0; k < 2; ++k)
+      for (int eo = 0; eo < 2; ++eo) {
+        const size_t v = cg_workspace_bytes(*lat, prec, eo, outers[k]);
+        m = v > m ? v : m;
+      }
+    return m;
   }
   return 0;
 }
@@ -207,10 +214,12 @@ int bsm_cg_solve(const bsm_lattice* lat, const void* U_rep64, const void* U_rep3
   if (rc != BSM_OK) return rc;
   if (opts == nullptr || !(opts->tol > 0.0) || opts->max_iter < 1 || opts->delta < 0.0 || opts->delta >= 1.0)
     return BSM_EINVAL;
-  if (opts->prec_inner != BSM_F64 && opts->prec_inner != BSM_F32) return BSM_EUNSUPPORTED;
+  if (opts->prec_outer != BSM_F64 && opts->prec_outer != BSM_DF64) return BSM_EUNSUPPORTED;
+  if (opts->prec_inner != BSM_F32 && opts->prec_inner != opts->prec_outer) return BSM_EUNSUPPORTED;
   if (!aligned(U_rep64) || !aligned(b) || !aligned(x) || !aligned(workspace)) return BSM_EINVAL;
   if (opts->prec_inner == BSM_F32 && !aligned(U_rep32)) return BSM_EINVAL;
-  if (workspace_bytes < cg_workspace_bytes(*lat, opts->prec_inner, opts->eo != 0)) return BSM_EWORKSPACE;
+  if (workspace_bytes < cg_workspace_bytes(*lat, opts->prec_inner, opts->eo != 0, opts->prec_outer))
+    return BSM_EWORKSPACE;
   const size_t full = bsm_field_bytes(lat, BSM_FIELD_SPINOR, BSM_F64);
   if (overlap(b, full, x, full)) return BSM_EINVAL;
   const cudaError_t pre = cudaGetLastError();

@@ -2,9 +2,11 @@
 //
 // Reductions: each thread accumulates its grid-stride share in FP64 (for
 // FP32 vectors the four products of one 16-byte element are summed in FP32
-// first, then added in FP64), a fixed shuffle tree gives one partial per
-// block, and a single-block finalize kernel sums the partials in a fixed
+// first, for DF64 vectors the two products of one complex element in
+// double-float, then added in FP64), a fixed shuffle tree gives one partial
+// per block, and a single-block finalize kernel sums the partials in a fixed
 // order.  The result is therefore bit-reproducible for a given problem size.
+// DF64 vector updates run in double-float arithmetic on the FP32 units.
 #include "blas.cuh"
 
 namespace bsm {
@@ -31,6 +33,39 @@ __device__ __forceinline__ float4 expay(const float4& x, double b, const float4&
   return make_float4(fmaf(f, y.x, x.x), fmaf(f, y.y, x.y), fmaf(f, y.z, x.z), fmaf(f, y.w, x.w));
 }
 
+// DF64 element: one complex number as (re.hi, re.lo, im.hi, im.lo)
+struct dfc {
+  float4 v;
+};
+__device__ __forceinline__ df dre(const dfc& a) { return df(a.v.x, a.v.y); }
+__device__ __forceinline__ df dim(const dfc& a) { return df(a.v.z, a.v.w); }
+__device__ __forceinline__ dfc dmake(df re, df im) {
+  re = df_norm(re);
+  im = df_norm(im);
+  dfc c;
+  c.v = make_float4(re.hi, re.lo, im.hi, im.lo);
+  return c;
+}
+__device__ __forceinline__ double edot(const dfc& a, const dfc& b) {
+  return (double)fma(dim(a), dim(b), dre(a) * dre(b));
+}
+__device__ __forceinline__ dfc eaxpy(double a, const dfc& x, const dfc& y) {
+  const df al(a);
+  return dmake(fma(al, dre(x), dre(y)), fma(al, dim(x), dim(y)));
+}
+__device__ __forceinline__ dfc expay(const dfc& x, double b, const dfc& y) {
+  const df be(b);
+  return dmake(fma(be, dre(y), dre(x)), fma(be, dim(y), dim(x)));
+}
+// a x + b y
+__device__ __forceinline__ double2 eaxpby(double a, const double2& x, double b, const double2& y) {
+  return make_double2(fma(a, x.x, b * y.x), fma(a, x.y, b * y.y));
+}
+__device__ __forceinline__ dfc eaxpby(double a, const dfc& x, double b, const dfc& y) {
+  const df al(a), be(b);
+  return dmake(fma(al, dre(x), be * dre(y)), fma(al, dim(x), be * dim(y)));
+}
+
 template <typename E>
 struct ElemOf;
 template <>
@@ -40,6 +75,10 @@ struct ElemOf<F64> {
 template <>
 struct ElemOf<F32> {
   using T = float4;
+};
+template <>
+struct ElemOf<DF64> {
+  using T = dfc;
 };
 
 __global__ void reduce_kernel(const double* __restrict__ partials, int n, double* out) {
@@ -144,49 +183,81 @@ __global__ void __launch_bounds__(kBlasThreads) dot_kernel(const typename ElemOf
   block_sum_store<kBlasThreads>(acc, partials);
 }
 
-__global__ void __launch_bounds__(kBlasThreads) axpby64_kernel(double a, const double2* __restrict__ x, double b,
-                                                               double2* __restrict__ y, size_t n,
-                                                               double* partials) {
+template <typename P>
+__global__ void __launch_bounds__(kBlasThreads) axpby_kernel(double a, const typename ElemOf<P>::T* __restrict__ x,
+                                                             double b, typename ElemOf<P>::T* __restrict__ y,
+                                                             size_t n, double* partials) {
   double acc = 0.0;
   for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
-    const double2 xv = x[k], yv = y[k];
-    const double2 v = make_double2(fma(a, xv.x, b * yv.x), fma(a, xv.y, b * yv.y));
+    const auto v = eaxpby(a, x[k], b, y[k]);
     y[k] = v;
     acc += edot(v, v);
   }
   if (partials != nullptr) block_sum_store<kBlasThreads>(acc, partials);
 }
 
-// FP64 and FP32 half spinors pair their components differently: FP32 element
-// k of a half (float4) holds the spin-0/1 component at FP64 element k and the
-// spin-2/3 component at FP64 element k + n32, n32 = float4 elements per half.
-// y64 += widen(x32); x32 = 0
-__global__ void __launch_bounds__(kBlasThreads) acc32to64_kernel(double2* __restrict__ y, float4* __restrict__ x,
-                                                                 size_t n32, size_t n) {
+// FP64/DF64 and FP32 half spinors pair their components differently: FP32
+// element k of a half (float4) holds the spin-0/1 complex component at outer
+// element k and the spin-2/3 component at outer element k + n32, n32 = float4
+// elements per half.
+__device__ __forceinline__ void add_float2(double2& y, float re, float im) {
+  y.x += re;
+  y.y += im;
+}
+__device__ __forceinline__ void add_float2(dfc& y, float re, float im) {
+  y = dmake(dre(y) + df(re, 0.f), dim(y) + df(im, 0.f));
+}
+__device__ __forceinline__ float2 round_float2(const double2& x) {
+  return make_float2(__double2float_rn(x.x), __double2float_rn(x.y));
+}
+__device__ __forceinline__ float2 round_float2(const dfc& x) {
+  return make_float2(__fadd_rn(x.v.x, x.v.y), __fadd_rn(x.v.z, x.v.w));  // nearest float to hi + lo
+}
+
+// y_outer += widen(x32); x32 = 0
+template <typename P>
+__global__ void __launch_bounds__(kBlasThreads) acc32_kernel(typename ElemOf<P>::T* __restrict__ y,
+                                                             float4* __restrict__ x, size_t n32, size_t n) {
   for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
     const size_t h = k / n32, kk = k - h * n32;
-    double2* yh = y + h * 2 * n32;
+    auto* yh = y + h * 2 * n32;
     const float4 v = x[k];
-    double2 a = yh[kk], b = yh[kk + n32];
-    a.x += v.x;
-    a.y += v.y;
-    b.x += v.z;
-    b.y += v.w;
+    auto a = yh[kk], b = yh[kk + n32];
+    add_float2(a, v.x, v.y);
+    add_float2(b, v.z, v.w);
     yh[kk] = a;
     yh[kk + n32] = b;
     x[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
-// y32 = round(x64)
-__global__ void __launch_bounds__(kBlasThreads) conv64to32_kernel(float4* __restrict__ y, const double2* __restrict__ x,
-                                                                  size_t n32, size_t n) {
+// y32 = nearest FP32 of x_outer
+template <typename P>
+__global__ void __launch_bounds__(kBlasThreads) conv32_kernel(float4* __restrict__ y,
+                                                              const typename ElemOf<P>::T* __restrict__ x,
+                                                              size_t n32, size_t n) {
   for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
     const size_t h = k / n32, kk = k - h * n32;
-    const double2* xh = x + h * 2 * n32;
-    const double2 a = xh[kk], b = xh[kk + n32];
-    y[k] = make_float4(__double2float_rn(a.x), __double2float_rn(a.y), __double2float_rn(b.x), __double2float_rn(b.y));
+    const auto* xh = x + h * 2 * n32;
+    const float2 a = round_float2(xh[kk]), b = round_float2(xh[kk + n32]);
+    y[k] = make_float4(a.x, a.y, b.x, b.y);
   }
+}
+
+// FP64 <-> DF64, elementwise (same component order)
+__global__ void __launch_bounds__(kBlasThreads) f64_to_df64_kernel(dfc* __restrict__ y, const double2* __restrict__ x,
+                                                                   size_t n) {
+  for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
+    const df re(x[k].x), im(x[k].y);
+    dfc c;
+    c.v = make_float4(re.hi, re.lo, im.hi, im.lo);
+    y[k] = c;
+  }
+}
+__global__ void __launch_bounds__(kBlasThreads) df64_to_f64_kernel(double2* __restrict__ y, const dfc* __restrict__ x,
+                                                                   size_t n) {
+  for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads)
+    y[k] = make_double2((double)dre(x[k]), (double)dim(x[k]));
 }
 
 __global__ void __launch_bounds__(kBlasThreads) axpy_ratio32_kernel(float4* __restrict__ y,
@@ -209,49 +280,88 @@ void cg_beta_launch(CgState* st, const double* partials, int n, cudaStream_t s) 
   cg_beta_kernel<<<1, kBlasThreads, 0, s>>>(st, partials, n);
 }
 
+template <typename P>
+using E = typename ElemOf<P>::T;
+
 int cg_xr_update_launch(int prec, void* x, void* r, const void* p, const void* Ap, size_t n16, CgState* st,
                         double* partials, cudaStream_t s) {
   const int b = blas_blocks(n16);
-  if (prec == BSM_F64)
-    cg_xr_kernel<F64><<<b, kBlasThreads, 0, s>>>((double2*)x, (double2*)r, (const double2*)p, (const double2*)Ap,
-                                                  n16, st, partials);
-  else
-    cg_xr_kernel<F32><<<b, kBlasThreads, 0, s>>>((float4*)x, (float4*)r, (const float4*)p, (const float4*)Ap, n16,
-                                                  st, partials);
+  switch (prec) {
+    case BSM_F64:
+      cg_xr_kernel<F64><<<b, kBlasThreads, 0, s>>>((E<F64>*)x, (E<F64>*)r, (const E<F64>*)p, (const E<F64>*)Ap, n16,
+                                                    st, partials);
+      break;
+    case BSM_F32:
+      cg_xr_kernel<F32><<<b, kBlasThreads, 0, s>>>((E<F32>*)x, (E<F32>*)r, (const E<F32>*)p, (const E<F32>*)Ap, n16,
+                                                    st, partials);
+      break;
+    default:
+      cg_xr_kernel<DF64><<<b, kBlasThreads, 0, s>>>((E<DF64>*)x, (E<DF64>*)r, (const E<DF64>*)p,
+                                                     (const E<DF64>*)Ap, n16, st, partials);
+      break;
+  }
   return b;
 }
 
 void cg_p_update_launch(int prec, void* p, const void* r, size_t n16, const CgState* st, cudaStream_t s) {
   const int b = blas_blocks(n16);
-  if (prec == BSM_F64)
-    cg_p_kernel<F64><<<b, kBlasThreads, 0, s>>>((double2*)p, (const double2*)r, n16, st);
-  else
-    cg_p_kernel<F32><<<b, kBlasThreads, 0, s>>>((float4*)p, (const float4*)r, n16, st);
+  switch (prec) {
+    case BSM_F64: cg_p_kernel<F64><<<b, kBlasThreads, 0, s>>>((E<F64>*)p, (const E<F64>*)r, n16, st); break;
+    case BSM_F32: cg_p_kernel<F32><<<b, kBlasThreads, 0, s>>>((E<F32>*)p, (const E<F32>*)r, n16, st); break;
+    default: cg_p_kernel<DF64><<<b, kBlasThreads, 0, s>>>((E<DF64>*)p, (const E<DF64>*)r, n16, st); break;
+  }
 }
 
 int dot_launch(int prec, const void* a, const void* b, size_t n16, double* partials, cudaStream_t s) {
   const int nb = blas_blocks(n16);
-  if (prec == BSM_F64)
-    dot_kernel<F64><<<nb, kBlasThreads, 0, s>>>((const double2*)a, (const double2*)b, n16, partials);
-  else
-    dot_kernel<F32><<<nb, kBlasThreads, 0, s>>>((const float4*)a, (const float4*)b, n16, partials);
+  switch (prec) {
+    case BSM_F64:
+      dot_kernel<F64><<<nb, kBlasThreads, 0, s>>>((const E<F64>*)a, (const E<F64>*)b, n16, partials);
+      break;
+    case BSM_F32:
+      dot_kernel<F32><<<nb, kBlasThreads, 0, s>>>((const E<F32>*)a, (const E<F32>*)b, n16, partials);
+      break;
+    default:
+      dot_kernel<DF64><<<nb, kBlasThreads, 0, s>>>((const E<DF64>*)a, (const E<DF64>*)b, n16, partials);
+      break;
+  }
   return nb;
 }
 
-int axpby64_launch(double a, const void* x, double b, void* y, size_t n16, double* partials, cudaStream_t s) {
+int axpby_launch(int prec, double a, const void* x, double b, void* y, size_t n16, double* partials, cudaStream_t s) {
   const int nb = blas_blocks(n16);
-  axpby64_kernel<<<nb, kBlasThreads, 0, s>>>(a, (const double2*)x, b, (double2*)y, n16, partials);
+  switch (prec) {
+    case BSM_F64:
+      axpby_kernel<F64><<<nb, kBlasThreads, 0, s>>>(a, (const E<F64>*)x, b, (E<F64>*)y, n16, partials);
+      break;
+    default:
+      axpby_kernel<DF64><<<nb, kBlasThreads, 0, s>>>(a, (const E<DF64>*)x, b, (E<DF64>*)y, n16, partials);
+      break;
+  }
   return nb;
 }
 
-void accumulate32to64_launch(void* y64, void* x32, size_t n32_half, int halves, cudaStream_t s) {
+void accumulate32_launch(int prec_outer, void* y, void* x32, size_t n32_half, int halves, cudaStream_t s) {
   const size_t n = n32_half * halves;
-  acc32to64_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>((double2*)y64, (float4*)x32, n32_half, n);
+  if (prec_outer == BSM_F64)
+    acc32_kernel<F64><<<blas_blocks(n), kBlasThreads, 0, s>>>((E<F64>*)y, (float4*)x32, n32_half, n);
+  else
+    acc32_kernel<DF64><<<blas_blocks(n), kBlasThreads, 0, s>>>((E<DF64>*)y, (float4*)x32, n32_half, n);
 }
 
-void convert64to32_launch(void* y32, const void* x64, size_t n32_half, int halves, cudaStream_t s) {
+void convert_to32_launch(int prec_outer, void* y32, const void* x, size_t n32_half, int halves, cudaStream_t s) {
   const size_t n = n32_half * halves;
-  conv64to32_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>((float4*)y32, (const double2*)x64, n32_half, n);
+  if (prec_outer == BSM_F64)
+    conv32_kernel<F64><<<blas_blocks(n), kBlasThreads, 0, s>>>((float4*)y32, (const E<F64>*)x, n32_half, n);
+  else
+    conv32_kernel<DF64><<<blas_blocks(n), kBlasThreads, 0, s>>>((float4*)y32, (const E<DF64>*)x, n32_half, n);
+}
+
+void f64_df64_launch(void* dst, const void* src, size_t n16, bool to_df64, cudaStream_t s) {
+  if (to_df64)
+    f64_to_df64_kernel<<<blas_blocks(n16), kBlasThreads, 0, s>>>((dfc*)dst, (const double2*)src, n16);
+  else
+    df64_to_f64_kernel<<<blas_blocks(n16), kBlasThreads, 0, s>>>((double2*)dst, (const dfc*)src, n16);
 }
 
 void axpy_ratio32_launch(void* y, const void* x, size_t n16, const double* num, const double* den, cudaStream_t s) {

@@ -42,13 +42,17 @@ int cg_xr_update_launch(int prec, void* x, void* r, const void* p, const void* A
 void cg_p_update_launch(int prec, void* p, const void* r, size_t n16, const CgState* st, cudaStream_t s);
 // generic: partials of Re<a, b> (a == b gives |a|^2); returns block count
 int dot_launch(int prec, const void* a, const void* b, size_t n16, double* partials, cudaStream_t s);
-// y = a*x + b*y elementwise on FP64 vectors; returns blocks; optional |y|^2 partials
-int axpby64_launch(double a, const void* x, double b, void* y, size_t n16, double* partials, cudaStream_t s);
-// y64 += x32 (widened), then x32 = 0, over `halves` half spinors of n32_half
-// float4 elements each (the FP64/FP32 component pairing is handled here)
-void accumulate32to64_launch(void* y64, void* x32, size_t n32_half, int halves, cudaStream_t s);
-// y32 = round-to-nearest(x64), same shape convention
-void convert64to32_launch(void* y32, const void* x64, size_t n32_half, int halves, cudaStream_t s);
+// y = a*x + b*y elementwise on FP64 or DF64 vectors; returns blocks;
+// optional |y|^2 partials
+int axpby_launch(int prec, double a, const void* x, double b, void* y, size_t n16, double* partials, cudaStream_t s);
+// y_outer += x32 (widened), then x32 = 0, over `halves` half spinors of
+// n32_half float4 elements each (the outer/FP32 component pairing is handled
+// here); prec_outer is BSM_F64 or BSM_DF64
+void accumulate32_launch(int prec_outer, void* y, void* x32, size_t n32_half, int halves, cudaStream_t s);
+// y32 = nearest FP32 of x_outer, same shape convention
+void convert_to32_launch(int prec_outer, void* y32, const void* x, size_t n32_half, int halves, cudaStream_t s);
+// FP64 <-> DF64 vectors (n16 complex elements)
+void f64_df64_launch(void* dst, const void* src, size_t n16, bool to_df64, cudaStream_t s);
 // y -= (*num / *den) * x   (FP32 vectors, device scalars)
 void axpy_ratio32_launch(void* y, const void* x, size_t n16, const double* num, const double* den, cudaStream_t s);
 

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "bsm.h"
+#include "df64.cuh"
 
 namespace bsm {
 
@@ -53,11 +54,16 @@ struct F32 {
   using R = float;
   static constexpr int prec = BSM_F32;
 };
+struct DF64 {
+  using R = df;
+  static constexpr int prec = BSM_DF64;
+};
+
+// bytes per real number of a precision (DF64 stores two floats)
+inline size_t real_bytes(int prec) { return prec == BSM_F32 ? 4 : 8; }
 
 // bytes of one parity block of a spinor with d colours
-inline size_t half_spinor_bytes(int64_t Vh, int d, int prec) {
-  return (size_t)Vh * 8 * d * (prec == BSM_F64 ? 8 : 4);
-}
+inline size_t half_spinor_bytes(int64_t Vh, int d, int prec) { return (size_t)Vh * 8 * d * real_bytes(prec); }
 // Links are tiled: the sites of one parity are grouped in tiles of
 // kLinkTile consecutive eo indices, and a tile stores all its link planes
 // contiguously ([tile][plane][kLinkTile]), so a warp reads its 8 links per
@@ -66,8 +72,7 @@ constexpr int kLinkTile = 32;
 inline size_t padded_sites(int64_t Vh) { return (size_t)((Vh + kLinkTile - 1) / kLinkTile) * kLinkTile; }
 // bytes of the links of one output parity
 inline size_t link_block_bytes(int64_t Vh, int d, bool real, int prec) {
-  const size_t w = prec == BSM_F64 ? 8 : 4;
-  return padded_sites(Vh) * 8 * d * d * w * (real ? 1 : 2);
+  return padded_sites(Vh) * 8 * d * d * real_bytes(prec) * (real ? 1 : 2);
 }
 // element offset of (plane, site i) in a tiled link block of `planes` planes
 __host__ __device__ __forceinline__ size_t link_index(int planes, int plane, int i) {
@@ -172,6 +177,31 @@ struct SpinorIO<F32, D> {
   }
 };
 
+template <int D>
+struct SpinorIO<DF64, D> {
+  // 4D planes of float4 (re.hi, re.lo, im.hi, im.lo), plane = spin*D + colour
+  __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, cx<df> (&s)[4][D]) {
+    const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const float4 v = __ldg(b + (size_t)(sp * D + a) * Vh + i);
+        s[sp][a] = cmake(df(v.x, v.y), df(v.z, v.w));
+      }
+  }
+  __device__ __forceinline__ static void store(void* base, size_t Vh, int i, const cx<df> (&s)[4][D]) {
+    float4* b = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const df re = df_norm(s[sp][a].re), im = df_norm(s[sp][a].im);
+        b[(size_t)(sp * D + a) * Vh + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // link layout access: forward link U(x) and backward link U(x-mu)^+ of
 // direction mu, element c, for the thread's site.  `tile` points at the
@@ -238,6 +268,37 @@ struct LinkIO<F32, D, true> {
     const float2 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
     f = v.x;
     b = v.y;
+  }
+};
+
+template <int D>
+struct LinkIO<DF64, D, false> {
+  using elem = cx<df>;
+  using vec = float4;
+  static constexpr int planes = 8 * D * D;
+  __device__ __forceinline__ static const vec* tile_ptr(const void* base, int i) {
+    return reinterpret_cast<const vec*>(base) + link_index(planes, 0, i);
+  }
+  __device__ __forceinline__ static void load(const vec* t, int mu, int c, elem& f, elem& b) {
+    const float4 vf = __ldcs(t + ((2 * mu) * D * D + c) * kLinkTile);
+    const float4 vb = __ldcs(t + ((2 * mu + 1) * D * D + c) * kLinkTile);
+    f = cmake(df(vf.x, vf.y), df(vf.z, vf.w));
+    b = cmake(df(vb.x, vb.y), df(vb.z, vb.w));
+  }
+};
+
+template <int D>
+struct LinkIO<DF64, D, true> {
+  using elem = df;
+  using vec = float4;
+  static constexpr int planes = 4 * D * D;
+  __device__ __forceinline__ static const vec* tile_ptr(const void* base, int i) {
+    return reinterpret_cast<const vec*>(base) + link_index(planes, 0, i);
+  }
+  __device__ __forceinline__ static void load(const vec* t, int mu, int c, elem& f, elem& b) {
+    const float4 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
+    f = df(v.x, v.y);
+    b = df(v.z, v.w);
   }
 };
 

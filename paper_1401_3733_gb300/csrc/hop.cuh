@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kHopThreads, HopOccupancy<P, D>::min_blocks) h
     }
     SpinorIO<P, D>::store(A.out, Vh, i, acc);
     if (A.partials != nullptr) {
-      R n = 0;
+      R n = R(0);
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll

@@ -10,7 +10,8 @@
 //               permanents of U), with factors sqrt2 and 1 on the diagonal
 //               pairs of the symmetric representation;
 // then multiplied by exp(i phi_mu) on links leaving the last slice of mu,
-// rounded once to the target precision and written twice: as the forward
+// rounded once to the target precision (FP32; FP64; or split exactly into a
+// DF64 hi/lo pair) and written twice: as the forward
 // link of x (block of parity(x)) and, daggered, as the backward link of x+mu
 // (block of the other parity).
 #include <math.h>
@@ -173,6 +174,12 @@ __global__ void links_to_rep_kernel(const double2* __restrict__ Uc, void* __rest
         double2* Q = reinterpret_cast<double2*>(blk_b);
         P[link_index(8 * d * d, (2 * mu) * d * d + cc, i)] = make_double2(f.re, f.im);
         Q[link_index(8 * d * d, (2 * mu + 1) * d * d + cc, j)] = make_double2(bw.re, bw.im);
+      } else if (!real && prec == BSM_DF64) {
+        float4* P = reinterpret_cast<float4*>(blk_f);
+        float4* Q = reinterpret_cast<float4*>(blk_b);
+        const df fr(f.re), fi(f.im), br(bw.re), bi(bw.im);
+        P[link_index(8 * d * d, (2 * mu) * d * d + cc, i)] = make_float4(fr.hi, fr.lo, fi.hi, fi.lo);
+        Q[link_index(8 * d * d, (2 * mu + 1) * d * d + cc, j)] = make_float4(br.hi, br.lo, bi.hi, bi.lo);
       } else if (!real) {
         // float4 element (plane, site) = float2 pair (forward, backward)
         float2* P = reinterpret_cast<float2*>(blk_f);
@@ -186,6 +193,13 @@ __global__ void links_to_rep_kernel(const double2* __restrict__ Uc, void* __rest
         double* Q = reinterpret_cast<double*>(blk_b);
         P[2 * link_index(4 * d * d, mu * d * d + cc, i)] = f.re;
         Q[2 * link_index(4 * d * d, mu * d * d + cc, j) + 1] = bw.re;
+      } else if (prec == BSM_DF64) {
+        // float4 element (plane, site) = (forward.hi, forward.lo, backward.hi, backward.lo)
+        float2* P = reinterpret_cast<float2*>(blk_f);
+        float2* Q = reinterpret_cast<float2*>(blk_b);
+        const df a(f.re), b(bw.re);
+        P[2 * link_index(4 * d * d, mu * d * d + cc, i)] = make_float2(a.hi, a.lo);
+        Q[2 * link_index(4 * d * d, mu * d * d + cc, j) + 1] = make_float2(b.hi, b.lo);
       } else {
         float* P = reinterpret_cast<float*>(blk_f);
         float* Q = reinterpret_cast<float*>(blk_b);
@@ -215,6 +229,17 @@ __global__ void pack_spinor_kernel(const double2* __restrict__ canon, void* __re
     for (int q = 0; q < 4 * d; ++q) {
       if (unpack) cs[q] = blk[q * Vh + i];
       else blk[q * Vh + i] = cs[q];
+    }
+  } else if (prec == BSM_DF64) {
+    float4* blk = reinterpret_cast<float4*>(dev) + (size_t)p * 4 * d * Vh;
+    for (int q = 0; q < 4 * d; ++q) {
+      if (unpack) {
+        const float4 v = blk[q * Vh + i];
+        cs[q] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+      } else {
+        const df re(cs[q].x), im(cs[q].y);
+        blk[q * Vh + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      }
     }
   } else {
     float4* blk = reinterpret_cast<float4*>(dev) + (size_t)p * 2 * d * Vh;

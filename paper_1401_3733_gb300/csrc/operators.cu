@@ -5,9 +5,15 @@ namespace bsm {
 
 int launch_hop_f64(int d, bool real, const HopArgs& A, cudaStream_t s);
 int launch_hop_f32(int d, bool real, const HopArgs& A, cudaStream_t s);
+int launch_hop_df64(int d, bool real, const HopArgs& A, cudaStream_t s);
 
 int launch_hop(int prec, int d, bool real, const HopArgs& A, cudaStream_t s) {
-  return prec == BSM_F64 ? launch_hop_f64(d, real, A, s) : launch_hop_f32(d, real, A, s);
+  switch (prec) {
+    case BSM_F64: return launch_hop_f64(d, real, A, s);
+    case BSM_F32: return launch_hop_f32(d, real, A, s);
+    case BSM_DF64: return launch_hop_df64(d, real, A, s);
+    default: return -1;
+  }
 }
 
 OpCtx make_ctx(const bsm_lattice& L, const void* links, int prec, cudaStream_t s) {

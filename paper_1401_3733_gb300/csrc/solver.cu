@@ -1,18 +1,19 @@
 // solver.cu -- CG on the normal equations of the Wilson operator (Sec. II-B:
-// the Dirac operator is inverted by CG), plain FP64 or mixed precision.
+// the Dirac operator is inverted by CG), plain or mixed precision.
 //
 // Plain: Hestenes-Stiefel CG on M = Dhat^+ Dhat (even-odd, default) or
-// M = D^+ D (full lattice), all vectors FP64.
+// M = D^+ D (full lattice), every vector at the outer precision (FP64, or
+// FP64-accurate double-float DF64).
 //
 // Mixed: the same iteration with FP32 hops and FP32 vectors (alpha and beta
-// from FP64-accumulated reductions), restarted from FP64 "reliable updates"
-// (Clark, Babich, Barros, Brower, Rebbi 2010): when the iterated residual
-// has dropped by delta since the last update, or has reached the tolerance,
-// the FP32 correction is added into the FP64 solution, the residual is
-// recomputed as rhs - M x in FP64, copied back to FP32, the search direction
-// is re-orthogonalised against it and beta is recomputed from the true
-// residual.  The solve ends only when the recomputed FP64 residual meets the
-// tolerance.
+// from FP64-accumulated reductions), restarted from "reliable updates" at the
+// outer precision (Clark, Babich, Barros, Brower, Rebbi 2010): when the
+// iterated residual has dropped by delta since the last update, or has reached
+// the tolerance, the FP32 correction is added into the outer solution, the
+// residual is recomputed as rhs - M x at the outer precision, copied back to
+// FP32, the search direction is re-orthogonalised against it and beta is
+// recomputed from the true residual.  The solve ends only when the recomputed
+// residual meets the tolerance.
 //
 // Iteration order (one kernel each, scalars stay on the device):
 //   p = r + beta p ; Ap = M p with |Dhat p|^2 fused ; alpha = rr/pAp ;
@@ -38,18 +39,19 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct CgLayout {
   size_t state, partA, partB;
-  size_t bp, r, p, Ap, u, t;              // FP64 vectors
+  size_t bp, r, p, Ap, u, t;              // outer-precision vectors
   size_t r32, p32, Ap32, u32, t32, x32;   // FP32 vectors (mixed precision)
+  size_t bdf, xdf;                        // DF64 copies of b and x (DF64 outer)
   size_t vec64, vec32;                    // bytes of one CG vector
   int npart;
   size_t total;
 };
 
-CgLayout cg_layout(const bsm_lattice& L, int prec_inner, int eo) {
+CgLayout cg_layout(const bsm_lattice& L, int prec_inner, int eo, int prec_outer) {
   CgLayout y;
   const Geom g = make_geom(L);
   const RepInfo ri = rep_info(L.N, L.rep);
-  const size_t h64 = half_spinor_bytes(g.Vh, ri.d, BSM_F64);
+  const size_t h64 = half_spinor_bytes(g.Vh, ri.d, BSM_F64);  // = DF64 bytes
   const size_t h32 = half_spinor_bytes(g.Vh, ri.d, BSM_F32);
   y.vec64 = eo ? h64 : 2 * h64;
   y.vec32 = eo ? h32 : 2 * h32;
@@ -62,7 +64,7 @@ CgLayout cg_layout(const bsm_lattice& L, int prec_inner, int eo) {
   y.r = o; o = align_up(o + y.vec64);
   y.p = o; o = align_up(o + y.vec64);
   y.Ap = o; o = align_up(o + y.vec64);
-  // u and t adjacent: together they hold a full FP64 spinor at the end
+  // u and t adjacent: together they hold a full outer spinor at the end
   y.u = o; o = align_up(o + (eo ? h64 : 0));
   y.t = o; o = align_up(o + (eo ? h64 : 2 * h64));
   y.r32 = y.p32 = y.Ap32 = y.u32 = y.t32 = y.x32 = 0;
@@ -74,13 +76,17 @@ CgLayout cg_layout(const bsm_lattice& L, int prec_inner, int eo) {
     y.t32 = o; o = align_up(o + (eo ? h32 : 2 * h32));
     y.x32 = o; o = align_up(o + y.vec32);
   }
+  y.bdf = y.xdf = 0;
+  if (prec_outer == BSM_DF64) {
+    y.bdf = o; o = align_up(o + 2 * h64);
+    y.xdf = o; o = align_up(o + 2 * h64);
+  }
   y.total = o;
   return y;
 }
 
 struct Solver {
-  const bsm_lattice& L;
-  OpCtx c64, c32;
+  OpCtx co, ci;   // outer and inner operator contexts
   CgLayout y;
   char* ws;
   cudaStream_t s;
@@ -90,12 +96,12 @@ struct Solver {
   double* partA;
   double* partB;
 
-  Solver(const bsm_lattice& L_, const void* U64, const void* U32, int prec_inner, int eo_, void* ws_,
+  Solver(const bsm_lattice& L, const void* Uo, const void* U32, int prec_outer, int prec_inner, int eo_, void* ws_,
          cudaStream_t s_)
-      : L(L_), s(s_), eo(eo_) {
-    c64 = make_ctx(L, U64, BSM_F64, s);
-    c32 = make_ctx(L, U32, BSM_F32, s);
-    y = cg_layout(L, prec_inner, eo);
+      : s(s_), eo(eo_) {
+    co = make_ctx(L, Uo, prec_outer, s);
+    ci = prec_inner == BSM_F32 ? make_ctx(L, U32, BSM_F32, s) : co;
+    y = cg_layout(L, prec_inner, eo, prec_outer);
     ws = reinterpret_cast<char*>(ws_);
     st = reinterpret_cast<CgState*>(ws + y.state);
     done = reinterpret_cast<const int*>(ws + y.state + offsetof(CgState, done));
@@ -121,16 +127,13 @@ struct Solver {
     }
     return n;
   }
-  int apply_normal64(const void* in, void* out) const {
-    return apply_normal(c64, in, out, at(y.u), at(y.t), nullptr, nullptr);
-  }
 
-  // r = bp - M x (FP64); |r|^2 into st->aux[0]
+  // r = bp - M x at the outer precision; |r|^2 into st->aux[0]
   int true_residual(const void* x) const {
-    const int e = apply_normal64(x, at(y.Ap));
+    const int e = apply_normal(co, x, at(y.Ap), at(y.u), at(y.t), nullptr, nullptr);
     if (e < 0) return e;
     cudaMemcpyAsync(at(y.r), at(y.bp), y.vec64, cudaMemcpyDeviceToDevice, s);
-    const int nb = axpby64_launch(-1.0, at(y.Ap), 1.0, at(y.r), y.vec64 / 16, partA, s);
+    const int nb = axpby_launch(co.prec, -1.0, at(y.Ap), 1.0, at(y.r), y.vec64 / 16, partA, s);
     reduce_launch(partA, nb, &st->aux[0], s);
     return 0;
   }
@@ -146,14 +149,13 @@ struct Solver {
   }
   void write_state(const CgState& h) const { cudaMemcpyAsync(st, &h, sizeof(CgState), cudaMemcpyHostToDevice, s); }
 
-  // one CG iteration at the inner precision
+  // one CG iteration at the precision of context c
   int iterate(const OpCtx& c, void* x, void* r, void* p, void* Ap, void* u, void* t, size_t vec) const {
-    const int prec = c.prec;
-    cg_p_update_launch(prec, p, r, vec / 16, st, s);
+    cg_p_update_launch(c.prec, p, r, vec / 16, st, s);
     const int np = apply_normal(c, p, Ap, u, t, partA, done);
     if (np < 0) return np;
     cg_alpha_launch(st, partA, np, s);
-    const int nb = cg_xr_update_launch(prec, x, r, p, Ap, vec / 16, st, partB, s);
+    const int nb = cg_xr_update_launch(c.prec, x, r, p, Ap, vec / 16, st, partB, s);
     cg_beta_launch(st, partB, nb, s);
     return 0;
   }
@@ -161,7 +163,9 @@ struct Solver {
 
 }  // namespace
 
-size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo) { return cg_layout(L, prec_inner, eo).total; }
+size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo, int prec_outer) {
+  return cg_layout(L, prec_inner, eo, prec_outer).total;
+}
 
 int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* b, void* x,
              const bsm_cg_opts& o, bsm_cg_stats* stats, void* ws, cudaStream_t s) {
@@ -169,30 +173,41 @@ int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void*
   const int eo = o.eo != 0;
   const int check = o.check_every > 0 ? o.check_every : 8;
   const double delta = o.delta > 0 ? o.delta : 0.1;
-  Solver S(L, U64, U32, o.prec_inner, eo, ws, s);
-  const OpCtx& c64 = S.c64;
+  const int po = o.prec_outer;
+  Solver S(L, U64, U32, po, o.prec_inner, eo, ws, s);
+  const OpCtx& co = S.co;
   const CgLayout& y = S.y;
-  const size_t h64 = c64.half_bytes;
-  const char* bc = reinterpret_cast<const char*>(b);
-  char* xc = reinterpret_cast<char*>(x);
+  const size_t h64 = co.half_bytes;
   int rc;
 
   if (cudaStreamSynchronize(s) != cudaSuccess) return BSM_ECUDA;
   const auto t0 = std::chrono::steady_clock::now();
 
+  // the outer-precision copies of b and x (DF64 keeps its own)
+  const void* bo = b;
+  void* xo = x;
+  if (po == BSM_DF64) {
+    f64_df64_launch(S.at(y.bdf), b, 2 * h64 / 16, true, s);
+    if (o.use_x0) f64_df64_launch(S.at(y.xdf), x, 2 * h64 / 16, true, s);
+    bo = S.at(y.bdf);
+    xo = S.at(y.xdf);
+  }
+  const char* bc = reinterpret_cast<const char*>(bo);
+  char* xc = reinterpret_cast<char*>(xo);
+
   // right-hand side bp of the normal equations, |bp|^2 -> aux[0], |b|^2 -> aux[1]
   int np;
   if (eo) {
     // bhat_e = b_e + 1/(2A) H_eo b_o  (into u), bp = Dhat^+ bhat_e
-    rc = op_hop(c64, 0, bc + h64, S.at(y.u), 0, bc, 1.0, 1.0 / (2.0 * c64.A), nullptr, nullptr);
+    rc = op_hop(co, 0, bc + h64, S.at(y.u), 0, bc, 1.0, 1.0 / (2.0 * co.A), nullptr, nullptr);
     if (rc < 0) return rc;
-    np = op_dhat(c64, S.at(y.u), S.at(y.bp), S.at(y.t), 1, S.partA, nullptr);
+    np = op_dhat(co, S.at(y.u), S.at(y.bp), S.at(y.t), 1, S.partA, nullptr);
   } else {
-    np = op_dirac(c64, b, S.at(y.bp), 1, S.partA, nullptr);
+    np = op_dirac(co, bo, S.at(y.bp), 1, S.partA, nullptr);
   }
   if (np < 0) return np;
   reduce_launch(S.partA, np, &S.st->aux[0], s);
-  const int nbb = dot_launch(BSM_F64, b, b, 2 * h64 / 16, S.partB, s);
+  const int nbb = dot_launch(po, bo, bo, 2 * h64 / 16, S.partB, s);
   reduce_launch(S.partB, nbb, &S.st->aux[1], s);
   CgState h;
   memset(&h, 0, sizeof(h));
@@ -200,9 +215,10 @@ int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void*
   const double rhs2 = h.aux[0], b2 = h.aux[1];
   if (!isfinite(rhs2) || !isfinite(b2)) return BSM_ENAN;
 
-  void* xs = x;  // even half (eo) or full x: the FP64 solution vector
+  void* xs = xo;  // even half (eo) or the full solution vector
   int status = BSM_OK;
   int updates = 0;
+  bool residual_fresh = false;  // st->aux[0] already holds |bp - M x|^2 for the final x
   CgState hs;
   memset(&hs, 0, sizeof(hs));
   hs.stop2 = o.tol * o.tol * rhs2;
@@ -210,7 +226,7 @@ int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void*
   hs.delta2 = delta * delta;
 
   if (rhs2 == 0.0) {
-    cudaMemsetAsync(x, 0, 2 * h64, s);
+    cudaMemsetAsync(xo, 0, 2 * h64, s);
   } else {
     // initial residual
     double rr0 = rhs2;
@@ -226,12 +242,12 @@ int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void*
     hs.rr_prev = rr0;
     hs.beta = 0.0;
     hs.done = rr0 <= hs.stop2 ? kDoneConverged : kDoneRunning;
-    const size_t n32 = S.c32.half_bytes / 16;  // float4 elements per FP32 half
+    const size_t n32 = S.ci.half_bytes / 16;  // float4 elements per FP32 half (mixed)
     const int halves = eo ? 1 : 2;
     if (mixed) {
       cudaMemsetAsync(S.at(y.x32), 0, y.vec32, s);
       cudaMemsetAsync(S.at(y.p32), 0, y.vec32, s);
-      convert64to32_launch(S.at(y.r32), S.at(y.r), n32, halves, s);
+      convert_to32_launch(po, S.at(y.r32), S.at(y.r), n32, halves, s);
     } else {
       cudaMemsetAsync(S.at(y.p), 0, y.vec64, s);
     }
@@ -241,9 +257,9 @@ int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void*
     while (hs.done != kDoneConverged || mixed) {
       if (hs.done == kDoneRunning) {
         for (int k = 0; k < check; ++k) {
-          rc = mixed ? S.iterate(S.c32, S.at(y.x32), S.at(y.r32), S.at(y.p32), S.at(y.Ap32), S.at(y.u32),
+          rc = mixed ? S.iterate(S.ci, S.at(y.x32), S.at(y.r32), S.at(y.p32), S.at(y.Ap32), S.at(y.u32),
                                  S.at(y.t32), y.vec32)
-                     : S.iterate(c64, xs, S.at(y.r), S.at(y.p), S.at(y.Ap), S.at(y.u), S.at(y.t), y.vec64);
+                     : S.iterate(co, xs, S.at(y.r), S.at(y.p), S.at(y.Ap), S.at(y.u), S.at(y.t), y.vec64);
           if (rc < 0) return rc;
         }
         if ((rc = S.read_state(hs)) != 0) return rc;
@@ -258,21 +274,24 @@ int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void*
       // mixed precision: reliable update when due
       if (hs.done == kDoneNaN) { status = BSM_ENAN; break; }
       if (hs.done == kDoneRunning && !hs.want_update) continue;
-      accumulate32to64_launch(xs, S.at(y.x32), n32, halves, s);
+      accumulate32_launch(po, xs, S.at(y.x32), n32, halves, s);
       if ((rc = S.true_residual(xs)) != 0) return rc;
       if ((rc = S.read_state(h)) != 0) return rc;
       ++updates;
       const double rr_true = h.aux[0];
       if (!isfinite(rr_true)) { status = BSM_ENAN; break; }
-      if (rr_true <= hs.stop2) break;
+      if (rr_true <= hs.stop2) {
+        residual_fresh = true;
+        break;
+      }
       if (hs.done == kDoneMaxIter || hs.iter >= o.max_iter) { status = BSM_ENOCONV; break; }
       if (hs.done == kDoneBreakdown) {
         if (++breakdowns > 2) { status = BSM_EBREAKDOWN; break; }
       } else {
         breakdowns = 0;
       }
-      // restart the FP32 iteration from the FP64 residual
-      convert64to32_launch(S.at(y.r32), S.at(y.r), n32, halves, s);
+      // restart the FP32 iteration from the outer residual
+      convert_to32_launch(po, S.at(y.r32), S.at(y.r), n32, halves, s);
       const int n1 = dot_launch(BSM_F32, S.at(y.r32), S.at(y.p32), y.vec32 / 16, S.partA, s);
       reduce_launch(S.partA, n1, &S.st->aux[1], s);
       const int n2 = dot_launch(BSM_F32, S.at(y.r32), S.at(y.r32), y.vec32 / 16, S.partB, s);
@@ -287,17 +306,19 @@ int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void*
     }
   }
 
-  // true FP64 residual of the normal equations, odd-site reconstruction and
-  // the full-system residual |D x - b| / |b|
-  if ((rc = S.true_residual(xs)) != 0) return rc;
+  // true residual of the normal equations (unless the last reliable update
+  // has just computed it for this x), odd-site reconstruction and the
+  // full-system residual |D x - b| / |b|, all at the outer precision
+  if (!residual_fresh && (rc = S.true_residual(xs)) != 0) return rc;
   if (eo) {
-    rc = op_hop(c64, 1, xs, xc + h64, 0, bc + h64, 1.0 / c64.A, 1.0 / (2.0 * c64.A), nullptr, nullptr);
+    rc = op_hop(co, 1, xs, xc + h64, 0, bc + h64, 1.0 / co.A, 1.0 / (2.0 * co.A), nullptr, nullptr);
     if (rc < 0) return rc;
   }
   void* full_tmp = eo ? S.at(y.u) : S.at(y.t);
-  if ((rc = op_dirac(c64, x, full_tmp, 0, nullptr, nullptr)) < 0) return rc;
-  const int nf = axpby64_launch(-1.0, b, 1.0, full_tmp, 2 * h64 / 16, S.partB, s);
+  if ((rc = op_dirac(co, xo, full_tmp, 0, nullptr, nullptr)) < 0) return rc;
+  const int nf = axpby_launch(po, -1.0, bo, 1.0, full_tmp, 2 * h64 / 16, S.partB, s);
   reduce_launch(S.partB, nf, &S.st->aux[1], s);
+  if (po == BSM_DF64) f64_df64_launch(x, xo, 2 * h64 / 16, false, s);
   if ((rc = S.read_state(h)) != 0) return rc;
   const auto t1 = std::chrono::steady_clock::now();
   if (stats) {

@@ -8,7 +8,7 @@ from paper_1401_3733_gb300 import bsm
 REP_CASES = [(2, bsm.FUND), (3, bsm.FUND), (4, bsm.FUND), (6, bsm.FUND), (8, bsm.FUND),
              (2, bsm.ADJ), (3, bsm.ADJ), (2, bsm.SYM), (3, bsm.SYM), (3, bsm.ASYM), (4, bsm.ASYM)]
 REP_IDS = [f"SU{N}-{['F', 'ADJ', 'S', 'AS'][r]}" for N, r in REP_CASES]
-TOL = {bsm.F64: 1e-13, bsm.F32: 2e-6}   # relative L2 bars for the Dslash
+TOL = {bsm.F64: 1e-13, bsm.F32: 2e-6, bsm.DF64: 1e-13}   # relative L2 bars for the Dslash
 
 
 def rel(a, b):

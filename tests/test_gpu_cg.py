@@ -32,14 +32,17 @@ def cfg1():
     return olat, blat, U, b
 
 
+@pytest.mark.parametrize("outer", [bsm.F64, bsm.DF64], ids=["f64", "df64"])
 @pytest.mark.parametrize("eo", [True, False], ids=["eo", "full"])
-def test_fp64_cg_matches_oracle_cg(eo):
+def test_plain_cg_matches_oracle_cg(eo, outer):
+    """Plain CG in FP64, and in FP64-accurate double-float (DF64)."""
     olat, blat, U, b = cfg1()
     R = orc.links_to_rep(olat, U)
     x_ref, it_ref, _ = orc.cg(olat, R, b, eo=eo, tol=1e-10, max_iter=5000)
     assert it_ref > 0
-    U64 = gpu_links(blat, U, bsm.F64)
-    st, stats, x = solve(blat, U64, None, gpu_spinor(blat, b, bsm.F64), bsm.cg_opts(tol=1e-10, eo=eo, check_every=4))
+    U64 = gpu_links(blat, U, outer)
+    st, stats, x = solve(blat, U64, None, gpu_spinor(blat, b, bsm.F64),
+                         bsm.cg_opts(tol=1e-10, eo=eo, check_every=4, prec_inner=outer, prec_outer=outer))
     assert st == bsm.OK
     assert stats.true_res_normal <= 1e-10
     assert abs(stats.iters - it_ref) <= 3, (stats.iters, it_ref)
@@ -63,18 +66,21 @@ def test_fp64_cg_initial_guess_restart():
     assert rel(to_canon(blat, x2, bsm.F64), to_canon(blat, x3, bsm.F64)) < 1e-8
 
 
+@pytest.mark.parametrize("outer", [bsm.F64, bsm.DF64], ids=["f64", "df64"])
 @pytest.mark.parametrize("dims,N,rep,eps", [((8, 8, 8, 8), 3, bsm.FUND, 0.3), ((8, 4, 4, 8), 2, bsm.ADJ, 0.4),
                                             ((6, 6, 4, 4), 4, bsm.ASYM, 0.4)], ids=["SU3-F", "SU2-ADJ", "SU4-AS"])
-def test_mixed_precision_cg_reaches_fp64_residual(dims, N, rep, eps):
+def test_mixed_precision_cg_reaches_fp64_residual(dims, N, rep, eps, outer):
+    """FP32 inner iteration with reliable updates in FP64 or DF64, against
+    plain FP64 CG."""
     m0 = 0.05
     blat = bsm.lattice(dims, N, rep, m0, (np.pi, 0, 0, 0))
     U = fields.gauge_field(dims, N, "smooth", seed=3, eps=eps)
     d = bsm.bsm_rep_dim(N, rep)
     b = fields.gaussian_spinor(dims, d, 4)
-    U64, U32 = gpu_links(blat, U, bsm.F64), gpu_links(blat, U, bsm.F32)
+    U64, U32, Uo = gpu_links(blat, U, bsm.F64), gpu_links(blat, U, bsm.F32), gpu_links(blat, U, outer)
     bd = gpu_spinor(blat, b, bsm.F64)
     st64, s64, x64 = solve(blat, U64, None, bd, bsm.cg_opts(tol=1e-10))
-    stm, sm, xm = solve(blat, U64, U32, bd, bsm.cg_opts(tol=1e-10, prec_inner=bsm.F32))
+    stm, sm, xm = solve(blat, Uo, U32, bd, bsm.cg_opts(tol=1e-10, prec_inner=bsm.F32, prec_outer=outer))
     assert st64 == bsm.OK and stm == bsm.OK
     assert s64.true_res_normal <= 1e-10 and sm.true_res_normal <= 1e-10
     assert sm.reliable_updates >= 1

@@ -224,6 +224,11 @@ struct LinkIO<F64, D, false> {
     f = cmake(vf.x, vf.y);
     b = cmake(vb.x, vb.y);
   }
+  template <int FB>
+  __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
+    const double2 v = __ldcs(t + ((2 * mu + FB) * D * D + c) * kLinkTile);
+    return cmake(v.x, v.y);
+  }
 };
 
 template <int D>
@@ -238,6 +243,11 @@ struct LinkIO<F32, D, false> {
     const float4 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
     f = cmake(v.x, v.y);
     b = cmake(v.z, v.w);
+  }
+  template <int FB>
+  __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
+    const float4 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
+    return FB == 0 ? cmake(v.x, v.y) : cmake(v.z, v.w);
   }
 };
 
@@ -254,6 +264,11 @@ struct LinkIO<F64, D, true> {
     f = v.x;
     b = v.y;
   }
+  template <int FB>
+  __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
+    const double2 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
+    return FB == 0 ? v.x : v.y;
+  }
 };
 
 template <int D>
@@ -268,6 +283,11 @@ struct LinkIO<F32, D, true> {
     const float2 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
     f = v.x;
     b = v.y;
+  }
+  template <int FB>
+  __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
+    const float2 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
+    return FB == 0 ? v.x : v.y;
   }
 };
 
@@ -285,6 +305,11 @@ struct LinkIO<DF64, D, false> {
     f = cmake(df(vf.x, vf.y), df(vf.z, vf.w));
     b = cmake(df(vb.x, vb.y), df(vb.z, vb.w));
   }
+  template <int FB>
+  __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
+    const float4 v = __ldcs(t + ((2 * mu + FB) * D * D + c) * kLinkTile);
+    return cmake(df(v.x, v.y), df(v.z, v.w));
+  }
 };
 
 template <int D>
@@ -299,6 +324,11 @@ struct LinkIO<DF64, D, true> {
     const float4 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
     f = df(v.x, v.y);
     b = df(v.z, v.w);
+  }
+  template <int FB>
+  __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
+    const float4 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
+    return FB == 0 ? df(v.x, v.y) : df(v.z, v.w);
   }
 };
 

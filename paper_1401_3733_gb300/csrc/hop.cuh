@@ -74,10 +74,101 @@ __device__ __forceinline__ void spin_reconstruct(cx<R> (&acc)[4][D], int a, cons
   acc[3][a].im = fma(sg, c1.im, acc[3][a].im);
 }
 
+// Double-float specialisations: the projector and reconstruction signs are
+// exactly +-1, so they are folded into the operands (a sign flip) instead of
+// costing a double-float multiply-add.
+__device__ __forceinline__ df signed_df(float s, df x) { return df(s * x.hi, s * x.lo); }
+
+template <int MU, int D>
+__device__ __forceinline__ void spin_project(const cx<df> (&s)[4][D], df sgd, cx<df> (&h)[2][D]) {
+  const float sg = sgd.hi;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const cx<df> u0 = s[0][a], u1 = s[1][a], l0 = s[2][a], l1 = s[3][a];
+    cx<df> b0, b1;
+    if (MU == 0) {
+      b0 = l0;
+      b1 = l1;
+    } else if (MU == 1) {
+      b0 = cmake(l1.im, -l1.re);
+      b1 = cmake(l0.im, -l0.re);
+    } else if (MU == 2) {
+      b0 = cmake(-l1.re, -l1.im);
+      b1 = l0;
+    } else {
+      b0 = cmake(l0.im, -l0.re);
+      b1 = cmake(-l1.im, l1.re);
+    }
+    h[0][a] = cmake(u0.re + signed_df(sg, b0.re), u0.im + signed_df(sg, b0.im));
+    h[1][a] = cmake(u1.re + signed_df(sg, b1.re), u1.im + signed_df(sg, b1.im));
+  }
+}
+
+template <int MU, int D>
+__device__ __forceinline__ void spin_reconstruct(cx<df> (&acc)[4][D], int a, const cx<df>& w0, const cx<df>& w1,
+                                                 df sgd) {
+  const float sg = sgd.hi;
+  acc[0][a].re += w0.re;
+  acc[0][a].im += w0.im;
+  acc[1][a].re += w1.re;
+  acc[1][a].im += w1.im;
+  cx<df> c0, c1;
+  if (MU == 0) {
+    c0 = w0;
+    c1 = w1;
+  } else if (MU == 1) {
+    c0 = cmake(-w1.im, w1.re);
+    c1 = cmake(-w0.im, w0.re);
+  } else if (MU == 2) {
+    c0 = w1;
+    c1 = cmake(-w0.re, -w0.im);
+  } else {
+    c0 = cmake(-w0.im, w0.re);
+    c1 = cmake(w1.im, -w1.re);
+  }
+  acc[2][a].re += signed_df(sg, c0.re);
+  acc[2][a].im += signed_df(sg, c0.im);
+  acc[3][a].re += signed_df(sg, c1.re);
+  acc[3][a].im += signed_df(sg, c1.im);
+}
+
 template <typename R>
 __device__ __forceinline__ void link_mac(cx<R>& w, const cx<R>& u, const cx<R>& h) { cmac(w, u, h); }
 template <typename R>
 __device__ __forceinline__ void link_mac(cx<R>& w, R u, const cx<R>& h) { rmac(w, u, h); }
+
+// One sense (FB = 0 forward, 1 backward) of direction mu: used where the two
+// senses are processed one after the other to halve the live registers
+// (double-float, whose dependent chains need occupancy more than load
+// batching).
+template <int MU, int FB, typename P, int D, bool REAL>
+__device__ __forceinline__ void hop_sense(const HopArgs& A, size_t Vh, const typename LinkIO<P, D, REAL>::vec* lt,
+                                          int n, typename P::R sg, cx<typename P::R> (&acc)[4][D]) {
+  using R = typename P::R;
+  using L = LinkIO<P, D, REAL>;
+  cx<R> h[2][D];
+  {
+    cx<R> psi[4][D];
+    SpinorIO<P, D>::load(A.in, Vh, n, psi);
+    spin_project<MU>(psi, sg, h);
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    cx<R> w0 = cmake(R(0), R(0)), w1 = w0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const typename L::elem u = L::template load_one<FB>(lt, MU, a * D + b);
+      link_mac(w0, u, h[0][b]);
+      link_mac(w1, u, h[1][b]);
+    }
+    spin_reconstruct<MU>(acc, a, w0, w1, sg);
+  }
+}
+
+template <typename P>
+struct HopSplitSenses {
+  static constexpr bool value = P::prec == BSM_DF64;
+};
 
 template <int MU, typename P, int D, bool REAL>
 __device__ __forceinline__ void hop_direction(const HopArgs& A, size_t Vh, const typename LinkIO<P, D, REAL>::vec* lt,
@@ -85,6 +176,11 @@ __device__ __forceinline__ void hop_direction(const HopArgs& A, size_t Vh, const
                                               cx<typename P::R> (&acc)[4][D]) {
   using R = typename P::R;
   using L = LinkIO<P, D, REAL>;
+  if constexpr (HopSplitSenses<P>::value) {
+    hop_sense<MU, 0, P, D, REAL>(A, Vh, lt, nf, sgf, acc);
+    hop_sense<MU, 1, P, D, REAL>(A, Vh, lt, nb, sgb, acc);
+    return;
+  }
   cx<R> hf[2][D], hb[2][D];
   {
     cx<R> psi[4][D];
@@ -112,11 +208,13 @@ __device__ __forceinline__ void hop_direction(const HopArgs& A, size_t Vh, const
 
 // Minimum resident blocks per SM (register budget) of each instantiation: the
 // FP32 kernels are bound by memory latency and want about 128 registers so
-// that each thread keeps a direction's loads in flight; larger d need more.
+// that each thread keeps a direction's loads in flight; the double-float
+// kernels are bound by dependent FP32 chains and want occupancy; larger d
+// need more registers.
 template <typename P, int D>
 struct HopOccupancy {
-  static constexpr int min_blocks = P::prec == BSM_F32 ? (D <= 3 ? 4 : D == 4 ? 3 : D == 6 ? 2 : 1)
-                                                         : (D <= 2 ? 4 : D == 3 ? 2 : 1);
+  static constexpr int min_blocks = P::prec == BSM_F64 ? (D <= 2 ? 4 : D == 3 ? 2 : 1)
+                                                       : (D <= 3 ? 4 : D == 4 ? 3 : D == 6 ? 2 : 1);
 };
 
 template <typename P, int D, bool REAL>
@@ -151,7 +249,7 @@ __global__ void __launch_bounds__(kHopThreads, HopOccupancy<P, D>::min_blocks) h
 #pragma unroll
         for (int c = 0; c < D; ++c)
           acc[s][c] = cmake(fma(a, xs[s][c].re, b * acc[s][c].re), fma(a, xs[s][c].im, b * acc[s][c].im));
-    } else {
+    } else if (A.b != 1.0) {
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll

@@ -358,6 +358,8 @@ def run_ours(args):
 
     if rank == 0 and not args.no_cg:
         out["cg"] = run_cg(lat, links, src[bsm.F64], args.cg_max_iter)
+    if rank == 0 and not args.no_mrhs:
+        out["mrhs"] = run_mrhs(max(3, min(args.steps, 20)), flush, peak)
     if rank == 0 and world == 1 and not args.no_cpu:
         g, reps, el, th = time_oracle_hop(SAMPLE_DIMS, args.cpu_seconds)
         out["cpu_baseline"] = {"value": round(g, 3), "unit": "GFLOP/s", "cores": th, "kind": "oracle",
@@ -369,6 +371,59 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+MRHS_THEORIES = (("SU(2) adjoint", 2, 1, 5), ("SU(4) two-index antisymmetric", 4, 3, 6),
+                 ("SU(6) fundamental", 6, 0, 7))   # (name, N, bsm_rep, link seed)
+MRHS_DIMS, MRHS_NRHS, MRHS_EPS = (24, 24, 24, 24), 12, 0.4
+
+
+def run_mrhs(steps, flush, peak):
+    """Batched multi-RHS Dslash on 24^4 lattices in three theories, 12
+    Gaussian RHS each, FP32 and BF16 storage (FP32 arithmetic): the full
+    operator D on every RHS per step, L2 flushed between steps."""
+    import torch
+    from paper_1401_3733_gb300 import bsm, fields
+
+    out = {"lattice_TXYZ": list(MRHS_DIMS), "nrhs": MRHS_NRHS, "eps": MRHS_EPS, "theories": {}}
+    V = int(np.prod(MRHS_DIMS))
+    for name, N, rep, seed in MRHS_THEORIES:
+        lat = bsm.lattice(MRHS_DIMS, N, rep, 0.1, (math.pi, 0, 0, 0))
+        d = bsm.bsm_rep_dim(N, rep)
+        real = rep == bsm.ADJ
+        Ud = torch.from_numpy(fields.gauge_field(MRHS_DIMS, N, "smooth", seed=seed, eps=MRHS_EPS)).cuda()
+        src = torch.from_numpy(np.stack([fields.gaussian_spinor(MRHS_DIMS, d, 100 * seed + r)
+                                         for r in range(MRHS_NRHS)])).cuda()
+        res = {"d": d, "real_rep": real}
+        for pname, prec, w in (("f32", bsm.F32, 4), ("bf16", bsm.BF16, 2)):
+            links = bsm.empty_field(lat, bsm.FIELD_LINKS, prec)
+            bsm.bsm_links_to_rep(lat, Ud, links, prec)
+            nbytes = bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR, prec) * MRHS_NRHS
+            inp = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            outp = torch.empty_like(inp)
+            bsm.bsm_pack_spinor_mrhs(lat, src, inp, MRHS_NRHS, prec)
+            bsm.bsm_dslash_mrhs(lat, links, inp, outp, MRHS_NRHS, bsm.FULL, 0, prec)   # tunes the RHS block
+            for _ in range(3):
+                bsm.bsm_dslash_mrhs(lat, links, inp, outp, MRHS_NRHS, bsm.FULL, 0, prec)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for e0, e1 in evs:
+                flush.zero_()
+                e0.record()
+                bsm.bsm_dslash_mrhs(lat, links, inp, outp, MRHS_NRHS, bsm.FULL, 0, prec)
+                e1.record()
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+            flop = flops_per_site(d, real) * V * MRHS_NRHS
+            # hop bytes per output site: links once + n_rhs input and output spinors,
+            # plus the same-site read of the A*psi term of D
+            byt = ((8 * d * d if real else 16 * d * d) + MRHS_NRHS * 16 * d) * w * V + MRHS_NRHS * 8 * d * w * V
+            res[pname] = {"gflops": round(flop / (ms * 1e-3) / 1e9, 1), "ms_per_D": round(ms, 4),
+                          "hbm_frac": round(byt / (ms * 1e-3) / 1e9 / peak, 4),
+                          "rhs_block": bsm.bsm_dslash_mrhs_block(lat, MRHS_NRHS, prec)}
+            del links, inp, outp
+        out["theories"][name] = res
+        del Ud, src
+    return out
 
 
 def run_cg(lat, links, b, max_iter):
@@ -413,6 +468,7 @@ def main():
                     help="override the lattice (profiling of a smaller case); default 64 32 32 32")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 Dslash line")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
+    ap.add_argument("--no-mrhs", action="store_true", help="skip the multi-RHS 24^4 three-theory lines")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -43,6 +43,8 @@
  *       s = 0, 1, holding (psi[s][c], psi[s+2][c]) as (re, im, re, im).
  *   half spinor, DF64: as FP64 with each double2 replaced by a float4
  *       (re.hi, re.lo, im.hi, im.lo).
+ *   half spinor, BF16: as FP32 with each float replaced by a bfloat16 (2d
+ *       planes of 8-byte (re, im, re, im) quadruples).
  *   full spinor: the even half followed by the odd half.
  *   links: for each output parity p (p = 0 block first) the 8 links that a
  *       site x of parity p needs, forward U^R_mu(x) and backward
@@ -54,7 +56,8 @@
  *       holding (forward[c], backward[c]).  DF64 stores what FP64 stores
  *       with every double split into (hi, lo) floats: complex planes of
  *       float4 (re.hi, re.lo, im.hi, im.lo), real planes of float4
- *       (forward.hi, forward.lo, backward.hi, backward.lo).  The planes are tiled by 32 sites:
+ *       (forward.hi, forward.lo, backward.hi, backward.lo).  BF16 stores what
+ *       FP32 stores with every float replaced by a bfloat16.  The planes are tiled by 32 sites:
  *       element (plane, site i) sits at ((i/32)*planes + plane)*32 + i%32,
  *       with V_h rounded up to a multiple of 32, so the links of a warp's 32
  *       sites are one contiguous region.
@@ -101,7 +104,9 @@ typedef enum { BSM_FUND = 0, BSM_ADJ = 1, BSM_SYM = 2, BSM_ASYM = 3 } bsm_rep;
  * is an unevaluated sum hi + lo of two FP32 numbers (about 48 significand
  * bits), computed with error-free transformations on the FP32 units; same
  * bytes as FP64, several times the speed on GB300, whose FP64 units are slow. */
-typedef enum { BSM_F64 = 0, BSM_F32 = 1, BSM_DF64 = 2 } bsm_prec;
+/* BSM_BF16: bfloat16 storage of links and spinors with FP32 arithmetic
+ * (Dslash only: error about 2^-9 relative per stored value). */
+typedef enum { BSM_F64 = 0, BSM_F32 = 1, BSM_DF64 = 2, BSM_BF16 = 3 } bsm_prec;
 typedef enum { BSM_EVEN = 0, BSM_ODD = 1, BSM_FULL = 2 } bsm_parity;
 typedef enum { BSM_OP_DHAT = 0, BSM_OP_DHAT_DAG = 1, BSM_OP_DHAT_DAG_DHAT = 2 } bsm_eo_op;
 typedef enum {
@@ -167,6 +172,16 @@ int bsm_pack_spinor(const bsm_lattice *lat, const double *canon, void *dev,
 int bsm_unpack_spinor(const bsm_lattice *lat, const void *dev, double *canon,
                       int32_t prec, void *stream);
 
+/* Multi-RHS pack/unpack: canonical FP64 spinors [nrhs][V][4][d] (device) <->
+ * the multi-RHS device layout at `prec` (BSM_F32 or BSM_BF16): the
+ * single-RHS layout with the RHS index innermost, element (plane, site, rhs)
+ * at (plane*V_h + site)*nrhs + rhs within each parity; nrhs times
+ * bsm_field_bytes(lat, BSM_FIELD_SPINOR, prec) bytes.  V*nrhs <= 2^30. */
+int bsm_pack_spinor_mrhs(const bsm_lattice *lat, const double *canon, void *dev,
+                         int32_t nrhs, int32_t prec, void *stream);
+int bsm_unpack_spinor_mrhs(const bsm_lattice *lat, const void *dev, double *canon,
+                           int32_t nrhs, int32_t prec, void *stream);
+
 /* Representation links (Sec. II-A: the fermion transforms under a
  * non-trivial representation of the gauge group).  U_fund: canonical FP64
  * fundamental links on the device.  U_rep: device-layout links at `prec`
@@ -182,6 +197,24 @@ int bsm_links_to_rep(const bsm_lattice *lat, const double *U_fund, void *U_rep,
 int bsm_dslash(const bsm_lattice *lat, const void *U_rep, const void *in,
                void *out, int32_t out_parity, int32_t dagger, int32_t prec,
                void *stream);
+
+/* Dphi on nrhs right-hand sides at once (Sec. II-A: N_f fermion flavours in
+ * one gauge field), the same operator as bsm_dslash applied to every RHS:
+ * out_parity EVEN/ODD gives the hopping block on multi-RHS half spinors,
+ * FULL gives D on full ones.  prec: BSM_F32 or BSM_BF16 (FP32 arithmetic).
+ * Each link is read once per site and applied to all RHS; a thread owns a
+ * site and a block of RHS whose size is tuned on the first call for each
+ * (precision, d, nrhs, lattice) shape: that call times the candidates on
+ * `stream` and synchronises it (set BSM_MRHS_TUNE=0 to take a fixed block
+ * instead); later calls are asynchronous. */
+int bsm_dslash_mrhs(const bsm_lattice *lat, const void *U_rep, const void *in, void *out,
+                    int32_t nrhs, int32_t out_parity, int32_t dagger, int32_t prec,
+                    void *stream);
+
+/* The RHS block (RHS per thread) that bsm_dslash_mrhs uses for this
+ * (lattice, nrhs, prec): 0 before the first call has tuned it, else 1..4;
+ * or a negative bsm_status.  Pure host. */
+int bsm_dslash_mrhs_block(const bsm_lattice *lat, int32_t nrhs, int32_t prec);
 
 /* Even-odd Schur operator on even half spinors: op = BSM_OP_DHAT (Dhat),
  * BSM_OP_DHAT_DAG (Dhat^+) or BSM_OP_DHAT_DAG_DHAT (Dhat^+ Dhat).  workspace:

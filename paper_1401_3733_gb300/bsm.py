@@ -21,7 +21,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 # enums of bsm.h
 OK, EINVAL, EUNSUPPORTED, ECUDA, EWORKSPACE, ENOCONV, EBREAKDOWN, ENAN, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8
 FUND, ADJ, SYM, ASYM = 0, 1, 2, 3
-F64, F32, DF64 = 0, 1, 2
+F64, F32, DF64, BF16 = 0, 1, 2, 3
 EVEN, ODD, FULL = 0, 1, 2
 OP_DHAT, OP_DHAT_DAG, OP_DHAT_DAG_DHAT = 0, 1, 2
 FIELD_LINKS, FIELD_SPINOR, FIELD_HALF_SPINOR, FIELD_FUND_CANON, FIELD_SPINOR_CANON = 0, 1, 2, 3, 4
@@ -68,6 +68,11 @@ _lib.bsm_workspace_bytes.restype = ctypes.c_size_t
 _lib.bsm_pack_spinor.argtypes = [_LP, _P, _P, ctypes.c_int32, _P]
 _lib.bsm_unpack_spinor.argtypes = [_LP, _P, _P, ctypes.c_int32, _P]
 _lib.bsm_links_to_rep.argtypes = [_LP, _P, _P, ctypes.c_int32, _P]
+_lib.bsm_pack_spinor_mrhs.argtypes = [_LP, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]
+_lib.bsm_unpack_spinor_mrhs.argtypes = [_LP, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]
+_lib.bsm_dslash_mrhs_block.argtypes = [_LP, ctypes.c_int32, ctypes.c_int32]
+_lib.bsm_dslash_mrhs_block.restype = ctypes.c_int
+_lib.bsm_dslash_mrhs.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]
 _lib.bsm_dslash.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]
 _lib.bsm_dirac_eo.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P]
 _lib.bsm_dirac_eo_noalloc.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]
@@ -78,7 +83,8 @@ _lib.bsm_strerror.restype = ctypes.c_char_p
 _lib.bsm_last_cuda_error.argtypes = []
 _lib.bsm_last_cuda_error.restype = ctypes.c_char_p
 for _f in ("bsm_pack_spinor", "bsm_unpack_spinor", "bsm_links_to_rep", "bsm_dslash", "bsm_dirac_eo",
-           "bsm_dirac_eo_noalloc", "bsm_cg_solve"):
+           "bsm_dirac_eo_noalloc", "bsm_cg_solve", "bsm_pack_spinor_mrhs", "bsm_unpack_spinor_mrhs",
+           "bsm_dslash_mrhs"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -148,6 +154,25 @@ def bsm_pack_spinor(lat, canon, dev, prec, stream=None):
 def bsm_unpack_spinor(lat, dev, canon, prec, stream=None):
     _check(_lib.bsm_unpack_spinor(ctypes.byref(lat), _ptr(dev), _ptr(canon), prec, _stream(stream)),
            "bsm_unpack_spinor")
+
+
+def bsm_pack_spinor_mrhs(lat, canon, dev, nrhs, prec, stream=None):
+    _check(_lib.bsm_pack_spinor_mrhs(ctypes.byref(lat), _ptr(canon), _ptr(dev), nrhs, prec, _stream(stream)),
+           "bsm_pack_spinor_mrhs")
+
+
+def bsm_unpack_spinor_mrhs(lat, dev, canon, nrhs, prec, stream=None):
+    _check(_lib.bsm_unpack_spinor_mrhs(ctypes.byref(lat), _ptr(dev), _ptr(canon), nrhs, prec, _stream(stream)),
+           "bsm_unpack_spinor_mrhs")
+
+
+def bsm_dslash_mrhs(lat, U_rep, inp, out, nrhs, out_parity, dagger, prec, stream=None):
+    _check(_lib.bsm_dslash_mrhs(ctypes.byref(lat), _ptr(U_rep), _ptr(inp), _ptr(out), nrhs, out_parity, int(dagger),
+                                prec, _stream(stream)), "bsm_dslash_mrhs")
+
+
+def bsm_dslash_mrhs_block(lat, nrhs, prec) -> int:
+    return _lib.bsm_dslash_mrhs_block(ctypes.byref(lat), nrhs, prec)
 
 
 def bsm_links_to_rep(lat, U_fund, U_rep, prec, stream=None):

@@ -7,13 +7,16 @@
 #include <string.h>
 
 #include "blas.cuh"
+#include "mrhs.cuh"
 #include "operators.cuh"
 
 namespace bsm {
 
 int links_to_rep_launch(const bsm_lattice& L, const double* U, void* out, int prec, cudaStream_t s);
 void pack_spinor_launch(const bsm_lattice& L, const double* canon, void* dev, int d, int prec, bool unpack,
-                        cudaStream_t s);
+                        int nrhs, cudaStream_t s);
+int launch_mrhs(int prec, int d, bool real, const MrhsArgs& A, cudaStream_t s);
+int mrhs_tuned_block(int prec, int d, bool real, int nrhs, int Vh);
 size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo, int prec_outer);
 int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* b, void* x,
              const bsm_cg_opts& o, bsm_cg_stats* stats, void* ws, cudaStream_t s);
@@ -76,7 +79,7 @@ int check_lattice(const bsm_lattice* L) {
 }
 
 bool aligned(const void* p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
-bool prec_ok(int prec) { return prec == BSM_F64 || prec == BSM_F32 || prec == BSM_DF64; }
+bool prec_ok(int prec) { return prec == BSM_F64 || prec == BSM_F32 || prec == BSM_DF64 || prec == BSM_BF16; }
 
 int finish(int rc) {
   if (rc != BSM_OK) return rc;
@@ -85,6 +88,15 @@ int finish(int rc) {
     set_cuda_error(e);
     return BSM_ECUDA;
   }
+  return BSM_OK;
+}
+
+// multi-RHS: supported precisions and the 32-bit (site, rhs) index bound
+int check_mrhs(const bsm_lattice* L, int nrhs, int prec) {
+  if (nrhs < 1) return BSM_EINVAL;
+  if (prec != BSM_F32 && prec != BSM_BF16) return BSM_EUNSUPPORTED;
+  const int64_t V = (int64_t)L->dims[0] * L->dims[1] * L->dims[2] * L->dims[3];
+  if (V * nrhs > ((int64_t)1 << 30)) return BSM_EUNSUPPORTED;
   return BSM_OK;
 }
 
@@ -149,7 +161,7 @@ int bsm_pack_spinor(const bsm_lattice* lat, const double* canon, void* dev, int3
   if (rc != BSM_OK) return rc;
   if (!prec_ok(prec)) return BSM_EUNSUPPORTED;
   if (!aligned(canon) || !aligned(dev)) return BSM_EINVAL;
-  pack_spinor_launch(*lat, canon, dev, rep_info(lat->N, lat->rep).d, prec, false, (cudaStream_t)stream);
+  pack_spinor_launch(*lat, canon, dev, rep_info(lat->N, lat->rep).d, prec, false, 1, (cudaStream_t)stream);
   return finish(BSM_OK);
 }
 
@@ -158,7 +170,7 @@ int bsm_unpack_spinor(const bsm_lattice* lat, const void* dev, double* canon, in
   if (rc != BSM_OK) return rc;
   if (!prec_ok(prec)) return BSM_EUNSUPPORTED;
   if (!aligned(canon) || !aligned(dev)) return BSM_EINVAL;
-  pack_spinor_launch(*lat, canon, const_cast<void*>(dev), rep_info(lat->N, lat->rep).d, prec, true,
+  pack_spinor_launch(*lat, canon, const_cast<void*>(dev), rep_info(lat->N, lat->rep).d, prec, true, 1,
                      (cudaStream_t)stream);
   return finish(BSM_OK);
 }
@@ -184,6 +196,74 @@ int bsm_dslash(const bsm_lattice* lat, const void* U_rep, const void* in, void* 
   if (out_parity == BSM_FULL) rc = op_dirac(c, in, out, dagger != 0, nullptr, nullptr);
   else rc = op_hop(c, out_parity, in, out, dagger != 0, nullptr, 0.0, 1.0, nullptr, nullptr);
   return finish(rc < 0 ? rc : BSM_OK);
+}
+
+int bsm_pack_spinor_mrhs(const bsm_lattice* lat, const double* canon, void* dev, int32_t nrhs, int32_t prec,
+                         void* stream) {
+  int rc = check_lattice(lat);
+  if (rc != BSM_OK) return rc;
+  if ((rc = check_mrhs(lat, nrhs, prec)) != BSM_OK) return rc;
+  if (!aligned(canon) || !aligned(dev)) return BSM_EINVAL;
+  pack_spinor_launch(*lat, canon, dev, rep_info(lat->N, lat->rep).d, prec, false, nrhs, (cudaStream_t)stream);
+  return finish(BSM_OK);
+}
+
+int bsm_unpack_spinor_mrhs(const bsm_lattice* lat, const void* dev, double* canon, int32_t nrhs, int32_t prec,
+                           void* stream) {
+  int rc = check_lattice(lat);
+  if (rc != BSM_OK) return rc;
+  if ((rc = check_mrhs(lat, nrhs, prec)) != BSM_OK) return rc;
+  if (!aligned(canon) || !aligned(dev)) return BSM_EINVAL;
+  pack_spinor_launch(*lat, canon, const_cast<void*>(dev), rep_info(lat->N, lat->rep).d, prec, true, nrhs,
+                     (cudaStream_t)stream);
+  return finish(BSM_OK);
+}
+
+int bsm_dslash_mrhs(const bsm_lattice* lat, const void* U_rep, const void* in, void* out, int32_t nrhs,
+                    int32_t out_parity, int32_t dagger, int32_t prec, void* stream) {
+  int rc = check_lattice(lat);
+  if (rc != BSM_OK) return rc;
+  if ((rc = check_mrhs(lat, nrhs, prec)) != BSM_OK) return rc;
+  if (!aligned(U_rep) || !aligned(in) || !aligned(out)) return BSM_EINVAL;
+  if (out_parity != BSM_EVEN && out_parity != BSM_ODD && out_parity != BSM_FULL) return BSM_EINVAL;
+  const OpCtx c = make_ctx(*lat, U_rep, prec, (cudaStream_t)stream);
+  const size_t half = c.half_bytes * nrhs;
+  const size_t n = out_parity == BSM_FULL ? 2 * half : half;
+  if (overlap(in, n, out, n)) return BSM_EINVAL;
+  MrhsArgs A;
+  A.g = c.g;
+  A.dagger = dagger != 0;
+  A.nrhs = nrhs;
+  const char* ic = reinterpret_cast<const char*>(in);
+  char* oc = reinterpret_cast<char*>(out);
+  const int first = out_parity == BSM_ODD ? 1 : 0, last = out_parity == BSM_EVEN ? 0 : 1;
+  for (int p = first; p <= last; ++p) {
+    A.links = c.links + (size_t)p * c.link_block;
+    A.p = p;
+    if (out_parity == BSM_FULL) {  // out_p = A in_p - 1/2 H in_{1-p}
+      A.in = ic + (size_t)(1 - p) * half;
+      A.out = oc + (size_t)p * half;
+      A.x = ic + (size_t)p * half;
+      A.a = c.A;
+      A.b = -0.5;
+    } else {  // the raw hopping block on half spinors
+      A.in = in;
+      A.out = out;
+      A.x = nullptr;
+      A.a = 0.0;
+      A.b = 1.0;
+    }
+    if ((rc = launch_mrhs(prec, c.d, c.real, A, (cudaStream_t)stream)) != 0) return rc;
+  }
+  return finish(BSM_OK);
+}
+
+int bsm_dslash_mrhs_block(const bsm_lattice* lat, int32_t nrhs, int32_t prec) {
+  int rc = check_lattice(lat);
+  if (rc != BSM_OK) return rc;
+  if ((rc = check_mrhs(lat, nrhs, prec)) != BSM_OK) return rc;
+  const RepInfo ri = rep_info(lat->N, lat->rep);
+  return mrhs_tuned_block(prec, ri.d, ri.real, nrhs, make_geom(*lat).Vh);
 }
 
 int bsm_dirac_eo(const bsm_lattice* lat, const void* U_rep, const void* in_e, void* out_e, int32_t op,

@@ -3,6 +3,7 @@
 // in include/bsm.h, and the even-odd lattice geometry (Sec. II-A).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -58,9 +59,32 @@ struct DF64 {
   using R = df;
   static constexpr int prec = BSM_DF64;
 };
+// bfloat16 storage, FP32 arithmetic
+struct BF16 {
+  using R = float;
+  static constexpr int prec = BSM_BF16;
+};
 
 // bytes per real number of a precision (DF64 stores two floats)
-inline size_t real_bytes(int prec) { return prec == BSM_F32 ? 4 : 8; }
+inline size_t real_bytes(int prec) { return prec == BSM_F32 ? 4 : prec == BSM_BF16 ? 2 : 8; }
+
+// load through L1 (data shared by several threads) or with the streaming hint
+template <bool L1, typename T>
+__device__ __forceinline__ T ldx(const T* p) {
+  if constexpr (L1) return __ldg(p);
+  else return __ldcs(p);
+}
+__device__ __forceinline__ float2 bf2_to_f2(unsigned int v) {
+  __nv_bfloat162 b;
+  memcpy(&b, &v, 4);
+  return __bfloat1622float2(b);
+}
+__device__ __forceinline__ unsigned int f2_to_bf2(float x, float y) {
+  const __nv_bfloat162 b = __floats2bfloat162_rn(x, y);
+  unsigned int v;
+  memcpy(&v, &b, 4);
+  return v;
+}
 
 // bytes of one parity block of a spinor with d colours
 inline size_t half_spinor_bytes(int64_t Vh, int d, int prec) { return (size_t)Vh * 8 * d * real_bytes(prec); }
@@ -178,6 +202,32 @@ struct SpinorIO<F32, D> {
 };
 
 template <int D>
+struct SpinorIO<BF16, D> {
+  // as FP32 with bfloat16 values: 2D planes of uint2 = (psi[s][c], psi[s+2][c])
+  __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, cx<float> (&s)[4][D]) {
+    const uint2* b = reinterpret_cast<const uint2*>(base);
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const uint2 v = __ldg(b + (size_t)(sp * D + a) * Vh + i);
+        const float2 u = bf2_to_f2(v.x), l = bf2_to_f2(v.y);
+        s[sp][a] = cmake(u.x, u.y);
+        s[sp + 2][a] = cmake(l.x, l.y);
+      }
+  }
+  __device__ __forceinline__ static void store(void* base, size_t Vh, int i, const cx<float> (&s)[4][D]) {
+    uint2* b = reinterpret_cast<uint2*>(base);
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        b[(size_t)(sp * D + a) * Vh + i] =
+            make_uint2(f2_to_bf2(s[sp][a].re, s[sp][a].im), f2_to_bf2(s[sp + 2][a].re, s[sp + 2][a].im));
+  }
+};
+
+template <int D>
 struct SpinorIO<DF64, D> {
   // 4D planes of float4 (re.hi, re.lo, im.hi, im.lo), plane = spin*D + colour
   __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, cx<df> (&s)[4][D]) {
@@ -224,9 +274,9 @@ struct LinkIO<F64, D, false> {
     f = cmake(vf.x, vf.y);
     b = cmake(vb.x, vb.y);
   }
-  template <int FB>
+  template <int FB, bool L1 = false>
   __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
-    const double2 v = __ldcs(t + ((2 * mu + FB) * D * D + c) * kLinkTile);
+    const double2 v = ldx<L1>(t + ((2 * mu + FB) * D * D + c) * kLinkTile);
     return cmake(v.x, v.y);
   }
 };
@@ -244,9 +294,9 @@ struct LinkIO<F32, D, false> {
     f = cmake(v.x, v.y);
     b = cmake(v.z, v.w);
   }
-  template <int FB>
+  template <int FB, bool L1 = false>
   __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
-    const float4 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
+    const float4 v = ldx<L1>(t + (mu * D * D + c) * kLinkTile);
     return FB == 0 ? cmake(v.x, v.y) : cmake(v.z, v.w);
   }
 };
@@ -264,9 +314,9 @@ struct LinkIO<F64, D, true> {
     f = v.x;
     b = v.y;
   }
-  template <int FB>
+  template <int FB, bool L1 = false>
   __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
-    const double2 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
+    const double2 v = ldx<L1>(t + (mu * D * D + c) * kLinkTile);
     return FB == 0 ? v.x : v.y;
   }
 };
@@ -284,9 +334,9 @@ struct LinkIO<F32, D, true> {
     f = v.x;
     b = v.y;
   }
-  template <int FB>
+  template <int FB, bool L1 = false>
   __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
-    const float2 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
+    const float2 v = ldx<L1>(t + (mu * D * D + c) * kLinkTile);
     return FB == 0 ? v.x : v.y;
   }
 };
@@ -305,9 +355,9 @@ struct LinkIO<DF64, D, false> {
     f = cmake(df(vf.x, vf.y), df(vf.z, vf.w));
     b = cmake(df(vb.x, vb.y), df(vb.z, vb.w));
   }
-  template <int FB>
+  template <int FB, bool L1 = false>
   __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
-    const float4 v = __ldcs(t + ((2 * mu + FB) * D * D + c) * kLinkTile);
+    const float4 v = ldx<L1>(t + ((2 * mu + FB) * D * D + c) * kLinkTile);
     return cmake(df(v.x, v.y), df(v.z, v.w));
   }
 };
@@ -325,10 +375,52 @@ struct LinkIO<DF64, D, true> {
     f = df(v.x, v.y);
     b = df(v.z, v.w);
   }
-  template <int FB>
+  template <int FB, bool L1 = false>
   __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
-    const float4 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
+    const float4 v = ldx<L1>(t + (mu * D * D + c) * kLinkTile);
     return FB == 0 ? df(v.x, v.y) : df(v.z, v.w);
+  }
+};
+
+template <int D>
+struct LinkIO<BF16, D, false> {
+  using elem = cx<float>;
+  using vec = uint2;  // (forward re/im, backward re/im) as two bfloat16 pairs
+  static constexpr int planes = 4 * D * D;
+  __device__ __forceinline__ static const vec* tile_ptr(const void* base, int i) {
+    return reinterpret_cast<const vec*>(base) + link_index(planes, 0, i);
+  }
+  __device__ __forceinline__ static void load(const vec* t, int mu, int c, elem& f, elem& b) {
+    const uint2 v = __ldcs(t + (mu * D * D + c) * kLinkTile);
+    const float2 x = bf2_to_f2(v.x), y = bf2_to_f2(v.y);
+    f = cmake(x.x, x.y);
+    b = cmake(y.x, y.y);
+  }
+  template <int FB, bool L1 = false>
+  __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
+    const uint2 v = ldx<L1>(t + (mu * D * D + c) * kLinkTile);
+    const float2 x = bf2_to_f2(FB == 0 ? v.x : v.y);
+    return cmake(x.x, x.y);
+  }
+};
+
+template <int D>
+struct LinkIO<BF16, D, true> {
+  using elem = float;
+  using vec = unsigned int;  // (forward, backward) bfloat16 pair
+  static constexpr int planes = 4 * D * D;
+  __device__ __forceinline__ static const vec* tile_ptr(const void* base, int i) {
+    return reinterpret_cast<const vec*>(base) + link_index(planes, 0, i);
+  }
+  __device__ __forceinline__ static void load(const vec* t, int mu, int c, elem& f, elem& b) {
+    const float2 x = bf2_to_f2(__ldcs(t + (mu * D * D + c) * kLinkTile));
+    f = x.x;
+    b = x.y;
+  }
+  template <int FB, bool L1 = false>
+  __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
+    const float2 x = bf2_to_f2(ldx<L1>(t + (mu * D * D + c) * kLinkTile));
+    return FB == 0 ? x.x : x.y;
   }
 };
 

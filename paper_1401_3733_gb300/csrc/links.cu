@@ -180,6 +180,17 @@ __global__ void links_to_rep_kernel(const double2* __restrict__ Uc, void* __rest
         const df fr(f.re), fi(f.im), br(bw.re), bi(bw.im);
         P[link_index(8 * d * d, (2 * mu) * d * d + cc, i)] = make_float4(fr.hi, fr.lo, fi.hi, fi.lo);
         Q[link_index(8 * d * d, (2 * mu + 1) * d * d + cc, j)] = make_float4(br.hi, br.lo, bi.hi, bi.lo);
+      } else if (!real && prec == BSM_BF16) {
+        // uint2 element (plane, site) = bfloat16 pairs (forward, backward)
+        unsigned int* P = reinterpret_cast<unsigned int*>(blk_f);
+        unsigned int* Q = reinterpret_cast<unsigned int*>(blk_b);
+        P[2 * link_index(4 * d * d, mu * d * d + cc, i)] = f2_to_bf2((float)f.re, (float)f.im);
+        Q[2 * link_index(4 * d * d, mu * d * d + cc, j) + 1] = f2_to_bf2((float)bw.re, (float)bw.im);
+      } else if (real && prec == BSM_BF16) {
+        __nv_bfloat16* P = reinterpret_cast<__nv_bfloat16*>(blk_f);
+        __nv_bfloat16* Q = reinterpret_cast<__nv_bfloat16*>(blk_b);
+        P[2 * link_index(4 * d * d, mu * d * d + cc, i)] = __double2bfloat16(f.re);
+        Q[2 * link_index(4 * d * d, mu * d * d + cc, j) + 1] = __double2bfloat16(bw.re);
       } else if (!real) {
         // float4 element (plane, site) = float2 pair (forward, backward)
         float2* P = reinterpret_cast<float2*>(blk_f);
@@ -209,21 +220,25 @@ __global__ void links_to_rep_kernel(const double2* __restrict__ Uc, void* __rest
     }
 }
 
-// canonical [V][4][d] FP64 <-> device layout, one thread per site
+// canonical [nrhs][V][4][d] FP64 <-> device layout (RHS index innermost), one
+// thread per (RHS, site)
 __global__ void pack_spinor_kernel(const double2* __restrict__ canon, void* __restrict__ dev, int4 dims, int d,
-                                   int prec, int unpack) {
+                                   int prec, int unpack, int nrhs) {
   const int V = dims.x * dims.y * dims.z * dims.w;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= V) return;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)V * nrhs) return;
+  const int rhs = (int)(tid / V);
+  const int s = (int)(tid - (long long)rhs * V);
   int r = s;
   const int z = r % dims.w; r /= dims.w;
   const int y = r % dims.z; r /= dims.z;
   const int x = r % dims.y;
   const int t = r / dims.y;
   const int p = (t + x + y + z) & 1;
-  const int i = s >> 1;
-  const size_t Vh = (size_t)V / 2;
-  double2* cs = const_cast<double2*>(canon) + (size_t)s * 4 * d;
+  // element (plane q, eo site, rhs) sits at q * Vh * nrhs + (eo site * nrhs + rhs)
+  const size_t i = (size_t)(s >> 1) * nrhs + rhs;
+  const size_t Vh = (size_t)V / 2 * nrhs;
+  double2* cs = const_cast<double2*>(canon) + ((size_t)rhs * V + s) * 4 * d;
   if (prec == BSM_F64) {
     double2* blk = reinterpret_cast<double2*>(dev) + (size_t)p * 4 * d * Vh;
     for (int q = 0; q < 4 * d; ++q) {
@@ -241,6 +256,21 @@ __global__ void pack_spinor_kernel(const double2* __restrict__ canon, void* __re
         blk[q * Vh + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
       }
     }
+  } else if (prec == BSM_BF16) {
+    uint2* blk = reinterpret_cast<uint2*>(dev) + (size_t)p * 2 * d * Vh;
+    for (int sp = 0; sp < 2; ++sp)
+      for (int a = 0; a < d; ++a) {
+        const int q = sp * d + a;
+        if (unpack) {
+          const uint2 v = blk[q * Vh + i];
+          const float2 u = bf2_to_f2(v.x), l = bf2_to_f2(v.y);
+          cs[sp * d + a] = make_double2(u.x, u.y);
+          cs[(sp + 2) * d + a] = make_double2(l.x, l.y);
+        } else {
+          const double2 u = cs[sp * d + a], w = cs[(sp + 2) * d + a];
+          blk[q * Vh + i] = make_uint2(f2_to_bf2((float)u.x, (float)u.y), f2_to_bf2((float)w.x, (float)w.y));
+        }
+      }
   } else {
     float4* blk = reinterpret_cast<float4*>(dev) + (size_t)p * 2 * d * Vh;
     for (int sp = 0; sp < 2; ++sp)
@@ -302,12 +332,12 @@ int links_to_rep_launch(const bsm_lattice& L, const double* U, void* out, int pr
 }
 
 void pack_spinor_launch(const bsm_lattice& L, const double* canon, void* dev, int d, int prec, bool unpack,
-                        cudaStream_t s) {
+                        int nrhs, cudaStream_t s) {
   const int4 dims = make_int4(L.dims[0], L.dims[1], L.dims[2], L.dims[3]);
-  const int V = L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3];
+  const long long n = (long long)L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3] * nrhs;
   const int threads = 128;
-  pack_spinor_kernel<<<(V + threads - 1) / threads, threads, 0, s>>>(reinterpret_cast<const double2*>(canon), dev,
-                                                                     dims, d, prec, unpack ? 1 : 0);
+  pack_spinor_kernel<<<(int)((n + threads - 1) / threads), threads, 0, s>>>(reinterpret_cast<const double2*>(canon),
+                                                                            dev, dims, d, prec, unpack ? 1 : 0, nrhs);
 }
 
 }  // namespace bsm

@@ -1,0 +1,150 @@
+// mrhs.cuh -- the hopping block for many right-hand sides at once (the N_f
+// fermion flavours of Sec. II-A share one gauge field): every link is read
+// from memory once per site and applied to all RHS, which raises the
+// arithmetic intensity from ~1 to ~n_rhs/2 flop per byte.
+//
+// Multi-RHS spinor layout: the single-RHS layout with the RHS index
+// innermost, element (plane, site, rhs) at (plane*V_h + site)*n_rhs + rhs, so
+// SpinorIO addresses it as a field of V_h*n_rhs "sites".  One thread owns one
+// output site and a block of RB consecutive RHS; the RB spinors live in
+// registers and each link element, loaded once through L1 (the other RHS
+// blocks of the same site reuse it from there), multiplies all of them.
+#pragma once
+
+#include "hop.cuh"
+
+namespace bsm {
+
+struct MrhsArgs {
+  const void* links;  // link block of output parity p
+  const void* in;     // multi-RHS half spinor of parity 1-p
+  void* out;          // multi-RHS half spinor of parity p
+  const void* x;      // optional same-parity input: out = a*x + b*H in
+  double a, b;
+  Geom g;
+  int p;
+  int dagger;
+  int nrhs;
+};
+
+template <int MU, int FB, typename P, int D, bool REAL, int RB>
+__device__ __forceinline__ void mrhs_sense(const MrhsArgs& A, const typename LinkIO<P, D, REAL>::vec* lt, int n,
+                                           int r0, typename P::R sg, cx<typename P::R> (&acc)[RB][4][D]) {
+  using R = typename P::R;
+  using L = LinkIO<P, D, REAL>;
+  const size_t nr = (size_t)A.nrhs;
+  const size_t Vn = (size_t)A.g.Vh * nr;
+  cx<R> h[RB][2][D];
+#pragma unroll
+  for (int j = 0; j < RB; ++j) {
+    cx<R> psi[4][D];
+    SpinorIO<P, D>::load(A.in, Vn, (int)((size_t)n * nr + r0 + j), psi);
+    spin_project<MU>(psi, sg, h[j]);
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    cx<R> w[RB][2];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) w[j][0] = w[j][1] = cmake(R(0), R(0));
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const typename L::elem u = L::template load_one<FB, true>(lt, MU, a * D + b);
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        link_mac(w[j][0], u, h[j][0][b]);
+        link_mac(w[j][1], u, h[j][1][b]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < RB; ++j) spin_reconstruct<MU>(acc[j], a, w[j][0], w[j][1], sg);
+  }
+}
+
+template <int MU, typename P, int D, bool REAL, int RB>
+__device__ __forceinline__ void mrhs_direction(const MrhsArgs& A, const typename LinkIO<P, D, REAL>::vec* lt,
+                                               int nf, int nb, int r0, typename P::R sg,
+                                               cx<typename P::R> (&acc)[RB][4][D]) {
+  mrhs_sense<MU, 0, P, D, REAL, RB>(A, lt, nf, r0, sg, acc);
+  mrhs_sense<MU, 1, P, D, REAL, RB>(A, lt, nb, r0, -sg, acc);
+}
+
+template <typename P, int D, bool REAL, int RB>
+__global__ void __launch_bounds__(kHopThreads) hop_mrhs_kernel(const MrhsArgs A) {
+  using R = typename P::R;
+  const int nblk = A.nrhs / RB;
+  const long long t = blockIdx.x * (long long)kHopThreads + threadIdx.x;
+  if (t >= (long long)A.g.Vh * nblk) return;
+  const int i = (int)(t / nblk);
+  const int r0 = (int)(t - (long long)i * nblk) * RB;
+  int nf[4], nb[4];
+  eo_neighbours(A.g, i, A.p, nf, nb);
+  const auto* lt = LinkIO<P, D, REAL>::tile_ptr(A.links, i);
+  const R sg = A.dagger ? R(1) : R(-1);  // forward sign; backward is -sg
+  cx<R> acc[RB][4][D];
+#pragma unroll
+  for (int j = 0; j < RB; ++j)
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[j][s][a] = cmake(R(0), R(0));
+  mrhs_direction<0, P, D, REAL, RB>(A, lt, nf[0], nb[0], r0, sg, acc);
+  mrhs_direction<1, P, D, REAL, RB>(A, lt, nf[1], nb[1], r0, sg, acc);
+  mrhs_direction<2, P, D, REAL, RB>(A, lt, nf[2], nb[2], r0, sg, acc);
+  mrhs_direction<3, P, D, REAL, RB>(A, lt, nf[3], nb[3], r0, sg, acc);
+
+  const size_t nr = (size_t)A.nrhs;
+  const size_t Vn = (size_t)A.g.Vh * nr;
+  const R b = (R)A.b;
+#pragma unroll
+  for (int j = 0; j < RB; ++j) {
+    const int e = (int)((size_t)i * nr + r0 + j);
+    if (A.x != nullptr) {
+      const R a = (R)A.a;
+      cx<R> xs[4][D];
+      SpinorIO<P, D>::load(A.x, Vn, e, xs);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          acc[j][s][c] = cmake(fma(a, xs[s][c].re, b * acc[j][s][c].re), fma(a, xs[s][c].im, b * acc[j][s][c].im));
+    } else if (A.b != 1.0) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc[j][s][c] = cmake(b * acc[j][s][c].re, b * acc[j][s][c].im);
+    }
+    SpinorIO<P, D>::store(A.out, Vn, e, acc[j]);
+  }
+}
+
+// RHS blocks compiled for colour dimension D (register budget: the RB
+// accumulators hold 8*D*RB reals)
+template <int D>
+struct MrhsBlocks {
+  static constexpr int max_rb = D <= 3 ? 4 : 2;
+};
+
+template <typename P, int D, bool REAL, int RB>
+inline void launch_mrhs_t(const MrhsArgs& A, cudaStream_t s) {
+  const long long n = (long long)A.g.Vh * (A.nrhs / RB);
+  const int blocks = (int)((n + kHopThreads - 1) / kHopThreads);
+  hop_mrhs_kernel<P, D, REAL, RB><<<blocks, kHopThreads, 0, s>>>(A);
+}
+
+// dispatch on RB for one (P, D, REAL); false if RB is not compiled for D
+template <typename P, int D, bool REAL>
+inline bool launch_mrhs_rb(int rb, const MrhsArgs& A, cudaStream_t s) {
+  switch (rb) {
+    case 1: launch_mrhs_t<P, D, REAL, 1>(A, s); return true;
+    case 2: launch_mrhs_t<P, D, REAL, 2>(A, s); return true;
+    case 3:
+      if constexpr (MrhsBlocks<D>::max_rb >= 3) { launch_mrhs_t<P, D, REAL, 3>(A, s); return true; }
+      return false;
+    case 4:
+      if constexpr (MrhsBlocks<D>::max_rb >= 4) { launch_mrhs_t<P, D, REAL, 4>(A, s); return true; }
+      return false;
+    default: return false;
+  }
+}
+
+}  // namespace bsm

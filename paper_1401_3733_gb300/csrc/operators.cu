@@ -6,12 +6,14 @@ namespace bsm {
 int launch_hop_f64(int d, bool real, const HopArgs& A, cudaStream_t s);
 int launch_hop_f32(int d, bool real, const HopArgs& A, cudaStream_t s);
 int launch_hop_df64(int d, bool real, const HopArgs& A, cudaStream_t s);
+int launch_hop_bf16(int d, bool real, const HopArgs& A, cudaStream_t s);
 
 int launch_hop(int prec, int d, bool real, const HopArgs& A, cudaStream_t s) {
   switch (prec) {
     case BSM_F64: return launch_hop_f64(d, real, A, s);
     case BSM_F32: return launch_hop_f32(d, real, A, s);
     case BSM_DF64: return launch_hop_df64(d, real, A, s);
+    case BSM_BF16: return launch_hop_bf16(d, real, A, s);
     default: return -1;
   }
 }

@@ -113,6 +113,21 @@ def test_cg_option_validation(bsm):
     assert call(bsm.cg_opts(), ws_bytes=4096) == bsm.EWORKSPACE
 
 
+def test_mrhs_validation(bsm):
+    L = ctypes.byref
+    good = bsm.lattice((4, 4, 4, 4), 3)
+    A = 1 << 20
+    assert bsm._lib.bsm_dslash_mrhs(L(good), A, 2 * A, 3 * A, 0, bsm.FULL, 0, bsm.F32, 0) == bsm.EINVAL
+    assert bsm._lib.bsm_dslash_mrhs(L(good), A, 2 * A, 3 * A, 4, bsm.FULL, 0, bsm.F64, 0) == bsm.EUNSUPPORTED
+    assert bsm._lib.bsm_dslash_mrhs(L(good), A, 2 * A, 3 * A, 4, 9, 0, bsm.F32, 0) == bsm.EINVAL
+    assert bsm._lib.bsm_dslash_mrhs(L(good), A, 2 * A, 2 * A + 64, 4, bsm.EVEN, 0, bsm.F32, 0) == bsm.EINVAL
+    big = bsm.lattice((64, 64, 64, 64), 3)   # V * nrhs beyond 2^30
+    assert bsm._lib.bsm_dslash_mrhs(L(big), A, 2 * A, 3 * A, 128, bsm.FULL, 0, bsm.F32, 0) == bsm.EUNSUPPORTED
+    assert bsm._lib.bsm_pack_spinor_mrhs(L(good), None, A, 4, bsm.F32, 0) == bsm.EINVAL
+    assert bsm.bsm_dslash_mrhs_block(good, 12, bsm.F32) == 0        # nothing tuned yet
+    assert bsm.bsm_dslash_mrhs_block(good, 12, bsm.F64) == bsm.EUNSUPPORTED
+
+
 def test_too_large_lattice_is_unsupported(bsm):
     lat = bsm.lattice((2048, 1024, 1024, 2), 3)
     assert bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR, bsm.F32) == 0

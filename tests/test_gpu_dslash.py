@@ -15,8 +15,8 @@ from tests.gpu_helpers import (REP_CASES, REP_IDS, TOL, gpu_links, gpu_spinor, h
 
 pytestmark = pytest.mark.gpu
 
-PRECS = [bsm.F64, bsm.F32, bsm.DF64]
-PREC_IDS = ["f64", "f32", "df64"]
+PRECS = [bsm.F64, bsm.F32, bsm.DF64, bsm.BF16]
+PREC_IDS = ["f64", "f32", "df64", "bf16"]
 
 
 def setup(dims, N, rep, m0, phase, seed, kind="haar", eps=0.3):
@@ -42,11 +42,12 @@ def test_pack_unpack_roundtrip(prec):
     lat = bsm.lattice(dims, 3)
     psi = fields.gaussian_spinor(dims, 3, 5)
     back = to_canon(lat, gpu_spinor(lat, psi, prec), prec)
-    if prec == bsm.DF64:
-        # hi + lo carries 48 significand bits: |error| <= 2^-48 |x| per real
+    if prec in (bsm.DF64, bsm.BF16):
+        # DF64: hi + lo carries 48 significand bits, |error| <= 2^-48 |x|;
+        # BF16: 8 significand bits, |error| <= 2^-8 |x| (round to nearest)
         err = np.maximum(np.abs(back.real - psi.real) / np.abs(psi.real),
                          np.abs(back.imag - psi.imag) / np.abs(psi.imag))
-        assert err.max() <= 2.0 ** -48
+        assert err.max() <= (2.0 ** -48 if prec == bsm.DF64 else 2.0 ** -8)
         return
     want = psi if prec == bsm.F64 else psi.astype(np.complex64).astype(np.complex128)
     assert np.array_equal(back, want)

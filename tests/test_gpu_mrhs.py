@@ -1,0 +1,116 @@
+"""Multi-RHS hopping block (bsm_dslash_mrhs): every right-hand side of a
+batch equals the oracle's operator applied to that RHS alone, for every
+representation, both parity blocks and the full operator, the adjoint, FP32
+and BF16 storage, and batch sizes that exercise every compiled RHS block
+(including an odd count and a ragged lattice)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_1401_3733_gb300 import bsm, fields
+from tests.gpu_helpers import REP_CASES, REP_IDS, TOL, dev_c128, gpu_links, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def mrhs_field(lat, nrhs, prec):
+    n = bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR, prec) * nrhs
+    return torch.zeros(n, dtype=torch.uint8, device="cuda")
+
+
+def pack(lat, psis, prec):
+    out = mrhs_field(lat, len(psis), prec)
+    bsm.bsm_pack_spinor_mrhs(lat, dev_c128(np.stack(psis)), out, len(psis), prec)
+    return out
+
+
+def unpack(lat, dev, nrhs, prec):
+    V = int(np.prod(list(lat.dims)))
+    d = bsm.bsm_rep_dim(lat.N, lat.rep)
+    c = torch.empty((nrhs, V, 4, d), dtype=torch.complex128, device="cuda")
+    bsm.bsm_unpack_spinor_mrhs(lat, dev, c, nrhs, prec)
+    torch.cuda.synchronize()
+    return c.cpu().numpy()
+
+
+def setup(dims, N, rep, nrhs, seed):
+    phase = (np.pi, 0, 0, 0) if rep == bsm.ADJ else (np.pi, 0.3, 0, -0.7)
+    olat = orc.Lattice(dims, N, rep, 0.1, phase)
+    blat = bsm.lattice(dims, N, rep, 0.1, phase)
+    U = fields.gauge_field(dims, N, "haar", seed=seed)
+    R = orc.links_to_rep(olat, U)
+    psis = [fields.gaussian_spinor(dims, olat.d, seed + 10 + r) for r in range(nrhs)]
+    return olat, blat, U, R, psis
+
+
+@pytest.mark.parametrize("prec", [bsm.F32, bsm.BF16], ids=["f32", "bf16"])
+def test_mrhs_pack_roundtrip(prec):
+    dims = (4, 2, 2, 6)
+    lat = bsm.lattice(dims, 3)
+    psis = [fields.gaussian_spinor(dims, 3, 40 + r) for r in range(5)]
+    back = unpack(lat, pack(lat, psis, prec), 5, prec)
+    want = np.stack(psis)
+    bound = 2.0 ** -24 if prec == bsm.F32 else 2.0 ** -8
+    for part in (np.real, np.imag):
+        assert (np.abs(part(back) - part(want)) <= bound * np.abs(part(want))).all()
+
+
+@pytest.mark.parametrize("prec", [bsm.F32, bsm.BF16], ids=["f32", "bf16"])
+@pytest.mark.parametrize("N,rep", REP_CASES, ids=REP_IDS)
+def test_mrhs_all_reps(N, rep, prec):
+    dims, nrhs = (4, 4, 4, 4), 4
+    olat, blat, U, R, psis = setup(dims, N, rep, nrhs, 500 + 3 * N + rep)
+    Ud = gpu_links(blat, U, prec)
+    inp = pack(blat, psis, prec)
+    for out_parity in (bsm.EVEN, bsm.ODD, bsm.FULL):
+        for dagger in (False, True):
+            out = mrhs_field(blat, nrhs, prec)
+            half = bsm.bsm_field_bytes(blat, bsm.FIELD_HALF_SPINOR, prec) * nrhs
+            if out_parity == bsm.FULL:
+                bsm.bsm_dslash_mrhs(blat, Ud, inp, out, nrhs, bsm.FULL, dagger, prec)
+            else:
+                p = out_parity
+                bsm.bsm_dslash_mrhs(blat, Ud, inp[(1 - p) * half:(2 - p) * half], out[p * half:(p + 1) * half],
+                                    nrhs, p, dagger, prec)
+            got = unpack(blat, out, nrhs, prec)
+            for r in range(nrhs):
+                if out_parity == bsm.FULL:
+                    want = orc.dirac(olat, R, psis[r], dagger=dagger)
+                else:
+                    want = orc.hop(olat, R, psis[r], out_parity=out_parity, dagger=dagger)
+                assert rel(got[r], want) <= TOL[prec], (out_parity, dagger, r, rel(got[r], want))
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 5, 12])
+@pytest.mark.parametrize("N,rep", [(3, bsm.FUND), (4, bsm.ASYM), (2, bsm.ADJ)], ids=["SU3-F", "SU4-AS", "SU2-ADJ"])
+def test_mrhs_batch_sizes_ragged(N, rep, nrhs):
+    """RHS counts that select every compiled RHS block (1..4 for d <= 3, 1..2
+    for d = 6) on a lattice whose V_h (120) fills no whole thread block."""
+    dims = (2, 6, 4, 10)
+    olat, blat, U, R, psis = setup(dims, N, rep, nrhs, 600 + nrhs)
+    Ud = gpu_links(blat, U, bsm.F32)
+    out = mrhs_field(blat, nrhs, bsm.F32)
+    bsm.bsm_dslash_mrhs(blat, Ud, pack(blat, psis, bsm.F32), out, nrhs, bsm.FULL, 0, bsm.F32)
+    got = unpack(blat, out, nrhs, bsm.F32)
+    for r in range(nrhs):
+        assert rel(got[r], orc.dirac(olat, R, psis[r])) <= TOL[bsm.F32]
+
+
+def test_mrhs_matches_single_rhs_calls():
+    """The batch result equals bsm_dslash applied to each RHS (same
+    arithmetic per RHS, so equal to rounding-order differences only)."""
+    dims, nrhs, prec = (8, 4, 4, 8), 6, bsm.F32
+    olat, blat, U, R, psis = setup(dims, 3, bsm.FUND, nrhs, 700)
+    Ud = gpu_links(blat, U, prec)
+    out = mrhs_field(blat, nrhs, prec)
+    bsm.bsm_dslash_mrhs(blat, Ud, pack(blat, psis, prec), out, nrhs, bsm.FULL, 0, prec)
+    got = unpack(blat, out, nrhs, prec)
+    for r in range(nrhs):
+        one = bsm.empty_field(blat, bsm.FIELD_SPINOR, prec)
+        res = bsm.empty_field(blat, bsm.FIELD_SPINOR, prec)
+        bsm.bsm_pack_spinor(blat, dev_c128(psis[r]), one, prec)
+        bsm.bsm_dslash(blat, Ud, one, res, bsm.FULL, 0, prec)
+        c = torch.empty_like(dev_c128(psis[r]))
+        bsm.bsm_unpack_spinor(blat, res, c, prec)
+        assert rel(got[r], c.cpu().numpy()) < 1e-6

@@ -212,9 +212,18 @@ int bsm_dslash_mrhs(const bsm_lattice *lat, const void *U_rep, const void *in, v
                     void *stream);
 
 /* The RHS block (RHS per thread) that bsm_dslash_mrhs uses for this
- * (lattice, nrhs, prec): 0 before the first call has tuned it, else 1..4;
- * or a negative bsm_status.  Pure host. */
+ * (lattice, nrhs, prec): 0 before the first call has tuned it, 1..4 for the
+ * SIMT kernel, 16 for the tensor-core kernel (BF16, complex d = 4, 6, 8,
+ * nrhs = 4, 8, 12, 16: one warp per site, the link x spinor block products
+ * as mma.sync m16n8k16 with FP32 accumulation); or a negative bsm_status.
+ * Pure host. */
 int bsm_dslash_mrhs_block(const bsm_lattice *lat, int32_t nrhs, int32_t prec);
+
+/* Pins the RHS block bsm_dslash_mrhs uses for (lattice, nrhs, prec) instead
+ * of tuning it (block = 0 forgets the choice; the next call tunes again).
+ * BSM_EUNSUPPORTED if that block does not exist for the shape.  Pure host;
+ * the choice is process-wide. */
+int bsm_dslash_mrhs_set_block(const bsm_lattice *lat, int32_t nrhs, int32_t prec, int32_t block);
 
 /* Even-odd Schur operator on even half spinors: op = BSM_OP_DHAT (Dhat),
  * BSM_OP_DHAT_DAG (Dhat^+) or BSM_OP_DHAT_DAG_DHAT (Dhat^+ Dhat).  workspace:

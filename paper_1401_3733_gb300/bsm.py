@@ -72,6 +72,8 @@ _lib.bsm_pack_spinor_mrhs.argtypes = [_LP, _P, _P, ctypes.c_int32, ctypes.c_int3
 _lib.bsm_unpack_spinor_mrhs.argtypes = [_LP, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]
 _lib.bsm_dslash_mrhs_block.argtypes = [_LP, ctypes.c_int32, ctypes.c_int32]
 _lib.bsm_dslash_mrhs_block.restype = ctypes.c_int
+_lib.bsm_dslash_mrhs_set_block.argtypes = [_LP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+_lib.bsm_dslash_mrhs_set_block.restype = ctypes.c_int
 _lib.bsm_dslash_mrhs.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]
 _lib.bsm_dslash.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]
 _lib.bsm_dirac_eo.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P]
@@ -173,6 +175,13 @@ def bsm_dslash_mrhs(lat, U_rep, inp, out, nrhs, out_parity, dagger, prec, stream
 
 def bsm_dslash_mrhs_block(lat, nrhs, prec) -> int:
     return _lib.bsm_dslash_mrhs_block(ctypes.byref(lat), nrhs, prec)
+
+
+MRHS_TENSOR_CORE_BLOCK = 16
+
+
+def bsm_dslash_mrhs_set_block(lat, nrhs, prec, block):
+    _check(_lib.bsm_dslash_mrhs_set_block(ctypes.byref(lat), nrhs, prec, block), "bsm_dslash_mrhs_set_block")
 
 
 def bsm_links_to_rep(lat, U_fund, U_rep, prec, stream=None):

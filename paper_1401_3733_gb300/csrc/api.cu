@@ -17,6 +17,7 @@ void pack_spinor_launch(const bsm_lattice& L, const double* canon, void* dev, in
                         int nrhs, cudaStream_t s);
 int launch_mrhs(int prec, int d, bool real, const MrhsArgs& A, cudaStream_t s);
 int mrhs_tuned_block(int prec, int d, bool real, int nrhs, int Vh);
+bool mrhs_set_block(int prec, int d, bool real, int nrhs, int Vh, int block);
 size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo, int prec_outer);
 int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* b, void* x,
              const bsm_cg_opts& o, bsm_cg_stats* stats, void* ws, cudaStream_t s);
@@ -264,6 +265,14 @@ int bsm_dslash_mrhs_block(const bsm_lattice* lat, int32_t nrhs, int32_t prec) {
   if ((rc = check_mrhs(lat, nrhs, prec)) != BSM_OK) return rc;
   const RepInfo ri = rep_info(lat->N, lat->rep);
   return mrhs_tuned_block(prec, ri.d, ri.real, nrhs, make_geom(*lat).Vh);
+}
+
+int bsm_dslash_mrhs_set_block(const bsm_lattice* lat, int32_t nrhs, int32_t prec, int32_t block) {
+  int rc = check_lattice(lat);
+  if (rc != BSM_OK) return rc;
+  if ((rc = check_mrhs(lat, nrhs, prec)) != BSM_OK) return rc;
+  const RepInfo ri = rep_info(lat->N, lat->rep);
+  return mrhs_set_block(prec, ri.d, ri.real, nrhs, make_geom(*lat).Vh, block) ? BSM_OK : BSM_EUNSUPPORTED;
 }
 
 int bsm_dirac_eo(const bsm_lattice* lat, const void* U_rep, const void* in_e, void* out_e, int32_t op,

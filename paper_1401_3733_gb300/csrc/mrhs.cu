@@ -1,7 +1,8 @@
 // mrhs.cu -- launch of the multi-RHS hopping block with an autotuned RHS
 // block: the first launch for a (precision, d, n_rhs, V_h) shape times every
-// compiled block size RB that divides n_rhs on the caller's stream and keeps
-// the fastest for the rest of the process.
+// compiled block size RB that divides n_rhs, and the tensor-core kernel where
+// it applies (BF16, d = 4, 6, 8), on the caller's stream and keeps the
+// fastest for the rest of the process.
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -14,6 +15,10 @@ namespace bsm {
 
 bool launch_mrhs_f32(int d, bool real, int rb, const MrhsArgs& A, cudaStream_t s);
 bool launch_mrhs_bf16(int d, bool real, int rb, const MrhsArgs& A, cudaStream_t s);
+bool launch_mrhs_tc(int prec, int d, bool real, const MrhsArgs& A, cudaStream_t s);
+
+// RHS-block code of the tensor-core kernel (one warp per site, all RHS)
+constexpr int kTensorCoreBlock = 16;
 
 namespace {
 
@@ -22,6 +27,7 @@ std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tuned;
 
 bool launch_rb(int prec, int d, bool real, int rb, const MrhsArgs& A, cudaStream_t s) {
+  if (rb == kTensorCoreBlock) return launch_mrhs_tc(prec, d, real, A, s);
   if (prec == BSM_F32) return launch_mrhs_f32(d, real, rb, A, s);
   if (prec == BSM_BF16) return launch_mrhs_bf16(d, real, rb, A, s);
   return false;
@@ -43,6 +49,24 @@ float time_rb(int prec, int d, bool real, int rb, const MrhsArgs& A, cudaStream_
 }
 
 }  // namespace
+
+// pins the block of a shape (0 forgets it, so the next launch tunes again);
+// false if that block is not available for the shape
+bool mrhs_set_block(int prec, int d, bool real, int nrhs, int Vh, int block) {
+  const TuneKey key(prec, d, real, nrhs, Vh);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (block == 0) {
+    g_tuned.erase(key);
+    return true;
+  }
+  if (block == kTensorCoreBlock) {
+    if (prec != BSM_BF16 || real || !(d == 4 || d == 6 || d == 8) || nrhs % 4 != 0 || nrhs > 16) return false;
+  } else if (block < 1 || block > max_rb(d) || nrhs % block != 0) {
+    return false;
+  }
+  g_tuned[key] = block;
+  return true;
+}
 
 int mrhs_tuned_block(int prec, int d, bool real, int nrhs, int Vh) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -71,8 +95,9 @@ int launch_mrhs(int prec, int d, bool real, const MrhsArgs& A, cudaStream_t s) {
         return BSM_ECUDA;
       }
       float best_ms = -1.f;
-      for (int c = 1; c <= max_rb(d); ++c) {
-        if (A.nrhs % c != 0) continue;
+      for (int c = 1; c <= kTensorCoreBlock; ++c) {
+        if (c > max_rb(d) && c != kTensorCoreBlock) continue;
+        if (c != kTensorCoreBlock && A.nrhs % c != 0) continue;
         const float ms = time_rb(prec, d, real, c, A, s, e0, e1);
         if (ms > 0.f && (best_ms < 0.f || ms < best_ms)) {
           best_ms = ms;

@@ -68,8 +68,17 @@ __device__ __forceinline__ void mrhs_direction(const MrhsArgs& A, const typename
   mrhs_sense<MU, 1, P, D, REAL, RB>(A, lt, nb, r0, -sg, acc);
 }
 
+// Minimum resident blocks (register budget) per RHS block: measured on the
+// 24^4, 12-RHS workload, one RHS per thread wants about 168 registers (3
+// blocks per SM), two RHS per thread at d = 6 about 255 (2 blocks per SM);
+// tighter budgets spill.
+template <int D, int RB>
+struct MrhsOccupancy {
+  static constexpr int min_blocks = D <= 2 ? 1 : RB == 1 ? 3 : (RB == 2 && D >= 6) ? 2 : 1;
+};
+
 template <typename P, int D, bool REAL, int RB>
-__global__ void __launch_bounds__(kHopThreads) hop_mrhs_kernel(const MrhsArgs A) {
+__global__ void __launch_bounds__(kHopThreads, MrhsOccupancy<D, RB>::min_blocks) hop_mrhs_kernel(const MrhsArgs A) {
   using R = typename P::R;
   const int nblk = A.nrhs / RB;
   const long long t = blockIdx.x * (long long)kHopThreads + threadIdx.x;

@@ -114,3 +114,41 @@ def test_mrhs_matches_single_rhs_calls():
         c = torch.empty_like(dev_c128(psis[r]))
         bsm.bsm_unpack_spinor(blat, res, c, prec)
         assert rel(got[r], c.cpu().numpy()) < 1e-6
+
+
+@pytest.mark.parametrize("nrhs", [4, 12])
+@pytest.mark.parametrize("N,rep", [(4, bsm.FUND), (6, bsm.FUND), (4, bsm.ASYM), (3, bsm.SYM), (8, bsm.FUND)],
+                         ids=["SU4-F", "SU6-F", "SU4-AS", "SU3-S", "SU8-F"])
+def test_mrhs_tensor_core_path(N, rep, nrhs):
+    """The tensor-core kernel (BF16 mma.sync block products, FP32
+    accumulation), pinned, against the oracle per RHS and against the SIMT
+    kernel on the same BF16 inputs, for the full operator and the adjoint
+    parity blocks."""
+    dims, prec = (4, 4, 2, 6), bsm.BF16
+    olat, blat, U, R, psis = setup(dims, N, rep, nrhs, 800 + N + nrhs)
+    Ud = gpu_links(blat, U, prec)
+    inp = pack(blat, psis, prec)
+    half = bsm.bsm_field_bytes(blat, bsm.FIELD_HALF_SPINOR, prec) * nrhs
+    results = {}
+    for block in (bsm.MRHS_TENSOR_CORE_BLOCK, 1):
+        bsm.bsm_dslash_mrhs_set_block(blat, nrhs, prec, block)
+        assert bsm.bsm_dslash_mrhs_block(blat, nrhs, prec) == block
+        full = mrhs_field(blat, nrhs, prec)
+        bsm.bsm_dslash_mrhs(blat, Ud, inp, full, nrhs, bsm.FULL, 0, prec)
+        odd = mrhs_field(blat, nrhs, prec)
+        bsm.bsm_dslash_mrhs(blat, Ud, inp[:half], odd[half:], nrhs, bsm.ODD, 1, prec)
+        results[block] = (unpack(blat, full, nrhs, prec), unpack(blat, odd, nrhs, prec))
+    bsm.bsm_dslash_mrhs_set_block(blat, nrhs, prec, 0)
+    tc, simt = results[bsm.MRHS_TENSOR_CORE_BLOCK], results[1]
+    for r in range(nrhs):
+        assert rel(tc[0][r], orc.dirac(olat, R, psis[r])) <= TOL[prec]
+        assert rel(tc[1][r], orc.hop(olat, R, psis[r], out_parity=orc.ODD, dagger=True)) <= TOL[prec]
+        assert rel(tc[0][r], simt[0][r]) <= TOL[prec]
+
+
+def test_mrhs_set_block_rejects_unavailable_blocks():
+    lat = bsm.lattice((4, 4, 4, 4), 3)
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_dslash_mrhs_set_block(lat, 12, bsm.F32, bsm.MRHS_TENSOR_CORE_BLOCK)   # FP32, d = 3
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_dslash_mrhs_set_block(lat, 12, bsm.F32, 5)

@@ -166,13 +166,22 @@ def barrier(world):
 
 
 def max_over_ranks(v, world):
+    """Largest value over the ranks (the slowest rank's time); works on the
+    NCCL (CUDA tensor) and gloo (CPU tensor) backends."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank, seconds_per_rank, world):
+    """Whole-job throughput of `world` replicas: every rank processes the same
+    units, the job takes as long as its slowest rank."""
+    return world * units_per_rank / max_over_ranks(seconds_per_rank, world)
 
 
 def run_reference(args):
@@ -279,7 +288,7 @@ def run_ours(args):
     launch_ms = [e[0].elapsed_time(e[1]) for e in evs] + [e[1].elapsed_time(e[2]) for e in evs]
     ms_step = sum(launch_ms) / args.steps
     ms_step_max = max_over_ranks(ms_step, world)
-    value = world * flop_step / (ms_step_max * 1e-3) / 1e9
+    value = world * flop_step / (ms_step_max * 1e-3) / 1e9   # = whole_job_rate over ranks
 
     peak, peak_src = load_peaks()
     hop_bytes = bytes_per_site(d, 4) * Vh

@@ -143,6 +143,11 @@ typedef struct {
                            reliable updates, the true residuals and (plain CG)
                            of the whole iteration: BSM_F64 or BSM_DF64.  b and
                            x are FP64 device-layout spinors either way. */
+  int32_t use_graph;    /* nonzero: capture the check_every iterations between
+                           host checks once as a CUDA graph and replay it
+                           (fewer launch gaps on small lattices).  Ignored on
+                           the legacy default stream and on a stream that is
+                           already capturing. */
 } bsm_cg_opts;
 
 typedef struct {
@@ -256,6 +261,35 @@ int bsm_dirac_eo(const bsm_lattice *lat, const void *U_rep, const void *in_e,
  * serialise them. */
 int bsm_dirac_eo_noalloc(const bsm_lattice *lat, const void *U_rep, const void *in_e,
                          void *out_e, int32_t op, int32_t prec, void *stream);
+
+/* A batch of lattices of uneven size in one persistent launch (several
+ * gauge configurations or theories at once).  Each item is an SU(2) or SU(3)
+ * fundamental lattice with FP32 links and its own nrhs multi-RHS FP32
+ * spinors (bsm_pack_spinor_mrhs layout).  op BSM_BATCH_D: out = D in on full
+ * spinors; BSM_BATCH_DHAT: out_e = Dhat in_e on even halves (two phases:
+ * odd temporaries in the workspace, a grid barrier between them).  Blocks of a
+ * cooperative grid take (lattice, parity, chunk) work items from a device
+ * queue.  The barrier wait is bounded by timeout_s (0 selects 1 s): past it
+ * the kernel raises an error flag and returns, and the call returns
+ * BSM_ETIMEOUT.  barrier_extra > 0 adds arrivals that never come (a test of
+ * that path).  items is a host array; the call synchronises `stream`. */
+typedef enum { BSM_BATCH_D = 0, BSM_BATCH_DHAT = 1 } bsm_batch_op;
+typedef struct {
+  bsm_lattice lat;
+  const void *U_rep;
+  const void *in;
+  void *out;
+  int32_t nrhs;
+} bsm_batch_item;
+typedef struct {
+  int32_t op;            /* bsm_batch_op */
+  int32_t prec;          /* BSM_F32 */
+  double timeout_s;      /* limit of the grid-barrier wait */
+  int32_t barrier_extra; /* 0 in normal use */
+} bsm_batch_opts;
+size_t bsm_batch_workspace_bytes(const bsm_batch_item *items, int32_t count, const bsm_batch_opts *opts);
+int bsm_dslash_batch(const bsm_batch_item *items, int32_t count, const bsm_batch_opts *opts,
+                     void *workspace, size_t workspace_bytes, void *stream);
 
 /* Solve D x = b (Sec. II-B: inverting the Dirac operator by CG) through CG on
  * the normal equations.  With opts->eo: Dhat^+ Dhat x_e = Dhat^+ bhat_e,

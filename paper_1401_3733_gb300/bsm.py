@@ -36,7 +36,7 @@ class Lattice(ctypes.Structure):
 class CgOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("prec_inner", ctypes.c_int32),
                 ("delta", ctypes.c_double), ("use_x0", ctypes.c_int32), ("eo", ctypes.c_int32),
-                ("check_every", ctypes.c_int32), ("prec_outer", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("prec_outer", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
 
 
 class CgStats(ctypes.Structure):
@@ -46,6 +46,19 @@ class CgStats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("lat", Lattice), ("U_rep", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("nrhs", ctypes.c_int32)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("prec", ctypes.c_int32), ("timeout_s", ctypes.c_double),
+                ("barrier_extra", ctypes.c_int32)]
+
+
+BATCH_D, BATCH_DHAT = 0, 1
 
 
 class BsmError(RuntimeError):
@@ -80,6 +93,11 @@ _lib.bsm_dirac_eo.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _
 _lib.bsm_dirac_eo_noalloc.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]
 _lib.bsm_cg_solve.argtypes = [_LP, _P, _P, _P, _P, ctypes.POINTER(CgOpts), ctypes.POINTER(CgStats), _P,
                               ctypes.c_size_t, _P]
+_lib.bsm_batch_workspace_bytes.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_int32, ctypes.POINTER(BatchOpts)]
+_lib.bsm_batch_workspace_bytes.restype = ctypes.c_size_t
+_lib.bsm_dslash_batch.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_int32, ctypes.POINTER(BatchOpts), _P,
+                                  ctypes.c_size_t, _P]
+_lib.bsm_dslash_batch.restype = ctypes.c_int
 _lib.bsm_strerror.argtypes = [ctypes.c_int]
 _lib.bsm_strerror.restype = ctypes.c_char_p
 _lib.bsm_last_cuda_error.argtypes = []
@@ -210,6 +228,27 @@ def bsm_dirac_eo_noalloc(lat, U_rep, in_e, out_e, op, prec, stream=None):
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
+def batch_items(entries):
+    """entries: iterable of (lattice, U_rep, in, out, nrhs) -> ctypes array."""
+    entries = list(entries)
+    arr = (BatchItem * len(entries))()
+    for k, (lat, U, i, o, n) in enumerate(entries):
+        arr[k] = BatchItem(lat, _ptr(U), _ptr(i), _ptr(o), n)
+    return arr
+
+
+def bsm_batch_workspace_bytes(items, opts: BatchOpts) -> int:
+    return _lib.bsm_batch_workspace_bytes(items, len(items), ctypes.byref(opts))
+
+
+def bsm_dslash_batch(items, opts: BatchOpts, workspace, stream=None, raise_on_error=True) -> int:
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    st = _lib.bsm_dslash_batch(items, len(items), ctypes.byref(opts), _ptr(workspace), nbytes, _stream(stream))
+    if raise_on_error:
+        _check(st, "bsm_dslash_batch")
+    return st
+
+
 def bsm_cg_solve(lat, U_rep64, U_rep32, b, x, opts: CgOpts, workspace, stream=None, raise_on_error=True):
     """Returns (status, CgStats); raises BsmError on a nonzero status unless
     raise_on_error is False."""
@@ -223,5 +262,5 @@ def bsm_cg_solve(lat, U_rep64, U_rep32, b, x, opts: CgOpts, workspace, stream=No
 
 
 def cg_opts(tol=1e-10, max_iter=10000, prec_inner=F64, delta=0.1, use_x0=False, eo=True, check_every=8,
-            prec_outer=F64) -> CgOpts:
-    return CgOpts(tol, max_iter, prec_inner, delta, int(use_x0), int(eo), check_every, prec_outer)
+            prec_outer=F64, use_graph=False) -> CgOpts:
+    return CgOpts(tol, max_iter, prec_inner, delta, int(use_x0), int(eo), check_every, prec_outer, int(use_graph))

@@ -17,6 +17,8 @@ void pack_spinor_launch(const bsm_lattice& L, const double* canon, void* dev, in
                         int nrhs, cudaStream_t s);
 int launch_mrhs(int prec, int d, bool real, const MrhsArgs& A, cudaStream_t s);
 int mrhs_tuned_block(int prec, int d, bool real, int nrhs, int Vh);
+size_t batch_workspace_bytes(const bsm_batch_item* items, int count, int op);
+int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o, void* ws, cudaStream_t s);
 bool mrhs_set_block(int prec, int d, bool real, int nrhs, int Vh, int block);
 size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo, int prec_outer);
 int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* b, void* x,
@@ -98,6 +100,28 @@ int check_mrhs(const bsm_lattice* L, int nrhs, int prec) {
   if (prec != BSM_F32 && prec != BSM_BF16) return BSM_EUNSUPPORTED;
   const int64_t V = (int64_t)L->dims[0] * L->dims[1] * L->dims[2] * L->dims[3];
   if (V * nrhs > ((int64_t)1 << 30)) return BSM_EUNSUPPORTED;
+  return BSM_OK;
+}
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb);
+
+// batch: SU(2)/SU(3) fundamental items, FP32, sane options
+int check_batch(const bsm_batch_item* items, int count, const bsm_batch_opts* o) {
+  if (items == nullptr || o == nullptr || count < 1 || count > 4096) return BSM_EINVAL;
+  if (o->op != BSM_BATCH_D && o->op != BSM_BATCH_DHAT) return BSM_EINVAL;
+  if (o->prec != BSM_F32) return BSM_EUNSUPPORTED;
+  if (!(o->timeout_s >= 0.0) || o->timeout_s > 60.0) return BSM_EINVAL;
+  for (int k = 0; k < count; ++k) {
+    const bsm_batch_item& it = items[k];
+    int rc = check_lattice(&it.lat);
+    if (rc != BSM_OK) return rc;
+    if (it.lat.rep != BSM_FUND || (it.lat.N != 2 && it.lat.N != 3)) return BSM_EUNSUPPORTED;
+    if ((rc = check_mrhs(&it.lat, it.nrhs, o->prec)) != BSM_OK) return rc;
+    if (!aligned(it.U_rep) || !aligned(it.in) || !aligned(it.out)) return BSM_EINVAL;
+    const Geom g = make_geom(it.lat);
+    const size_t n = half_spinor_bytes(g.Vh, it.lat.N, BSM_F32) * it.nrhs * (o->op == BSM_BATCH_D ? 2 : 1);
+    if (overlap(it.in, n, it.out, n)) return BSM_EINVAL;
+  }
   return BSM_OK;
 }
 
@@ -273,6 +297,25 @@ int bsm_dslash_mrhs_set_block(const bsm_lattice* lat, int32_t nrhs, int32_t prec
   if ((rc = check_mrhs(lat, nrhs, prec)) != BSM_OK) return rc;
   const RepInfo ri = rep_info(lat->N, lat->rep);
   return mrhs_set_block(prec, ri.d, ri.real, nrhs, make_geom(*lat).Vh, block) ? BSM_OK : BSM_EUNSUPPORTED;
+}
+
+size_t bsm_batch_workspace_bytes(const bsm_batch_item* items, int32_t count, const bsm_batch_opts* opts) {
+  if (check_batch(items, count, opts) != BSM_OK) return 0;
+  return batch_workspace_bytes(items, count, opts->op);
+}
+
+int bsm_dslash_batch(const bsm_batch_item* items, int32_t count, const bsm_batch_opts* opts, void* workspace,
+                     size_t workspace_bytes, void* stream) {
+  const int rc = check_batch(items, count, opts);
+  if (rc != BSM_OK) return rc;
+  if (!aligned(workspace)) return BSM_EINVAL;
+  if (workspace_bytes < batch_workspace_bytes(items, count, opts->op)) return BSM_EWORKSPACE;
+  const cudaError_t pre = cudaGetLastError();
+  if (pre != cudaSuccess) {
+    set_cuda_error(pre);
+    return BSM_ECUDA;
+  }
+  return batch_launch(items, count, *opts, workspace, (cudaStream_t)stream);
 }
 
 int bsm_dirac_eo(const bsm_lattice* lat, const void* U_rep, const void* in_e, void* out_e, int32_t op,

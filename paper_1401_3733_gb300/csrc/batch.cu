@@ -1,0 +1,229 @@
+// batch.cu -- several lattices of uneven size (SU(2) and SU(3) fundamental,
+// each with its own number of right-hand sides) in one persistent launch.
+//
+// The host turns the batch into a task table in the workspace: one task per
+// (lattice, output parity, phase), each covering V_h * n_rhs thread slots cut
+// into chunks of one block.  Blocks of a cooperative grid (every block
+// resident) take chunks from a device work queue (an atomic counter per
+// phase), so small and large lattices share the GPU without one launch per
+// lattice.  The full operator D needs one phase; the even-odd operator
+// Dhat = A - H_eo H_oe / (4A) needs two (the odd temporaries of phase 0 feed
+// phase 1), separated by a grid barrier.  The barrier wait is bounded by the
+// global timer: a block that waits longer than the limit raises an error flag
+// and returns, and the call reports BSM_ETIMEOUT instead of hanging.
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+#include "mrhs.cuh"
+#include "operators.cuh"
+
+namespace bsm {
+
+namespace {
+
+struct BatchTask {
+  MrhsArgs args;       // geometry, links of the output parity, in / out / x, a, b, nrhs
+  int d;               // 2 or 3
+  int phase;
+  long long chunk0;    // first chunk of this task within its phase
+  long long chunks;
+};
+
+struct BatchControl {
+  unsigned long long next[2];     // work-queue counters, one per phase
+  unsigned int arrived;           // blocks that finished phase 0
+  int error;                      // 1: a barrier wait timed out
+};
+
+struct BatchMeta {
+  int ntasks;
+  int nphases;
+  long long phase_chunks[2];
+  unsigned int barrier_target;    // arrivals the barrier waits for
+  unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void __launch_bounds__(kHopThreads) batch_kernel(const BatchTask* __restrict__ tasks, BatchControl* ctl,
+                                                            const BatchMeta meta) {
+  __shared__ long long s_chunk;
+  __shared__ int s_abort;
+  for (int phase = 0; phase < meta.nphases; ++phase) {
+    for (;;) {
+      if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(&ctl->next[phase], 1ull);
+      __syncthreads();
+      const long long c = s_chunk;
+      __syncthreads();
+      if (c >= meta.phase_chunks[phase]) break;
+      int k = 0;  // the task of chunk c (tasks are few: linear search)
+      while (k + 1 < meta.ntasks && !(tasks[k].phase == phase && c >= tasks[k].chunk0 &&
+                                      c < tasks[k].chunk0 + tasks[k].chunks))
+        ++k;
+      const BatchTask& tk = tasks[k];
+      const long long u = (c - tk.chunk0) * kHopThreads + threadIdx.x;
+      if (u < (long long)tk.args.g.Vh * tk.args.nrhs) {
+        const int i = (int)(u / tk.args.nrhs), r = (int)(u - (long long)i * tk.args.nrhs);
+        // phase 1 reads the odd temporaries written in phase 0: through L2 only
+        if (phase == 0) {
+          if (tk.d == 2) mrhs_site<F32, 2, false, 1>(tk.args, i, r);
+          else mrhs_site<F32, 3, false, 1>(tk.args, i, r);
+        } else {
+          if (tk.d == 2) mrhs_site<F32, 2, false, 1, true>(tk.args, i, r);
+          else mrhs_site<F32, 3, false, 1, true>(tk.args, i, r);
+        }
+      }
+    }
+    if (phase + 1 < meta.nphases) {
+      // grid barrier: every block of the cooperative grid arrives once, after
+      // all its threads have made their phase writes visible device-wide
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&ctl->arrived, 1u);
+        const unsigned long long t0 = global_ns();
+        int abort = 0;
+        // two independent bounds: the global timer and an iteration count
+        // (2^24 polls of >= 256 ns), so the wait ends even if the timer stalls
+        for (unsigned it = 0; *(volatile unsigned int*)&ctl->arrived < meta.barrier_target; ++it) {
+          if (*(volatile int*)&ctl->error != 0 || global_ns() - t0 > meta.timeout_ns || it > (1u << 24)) {
+            atomicExch(&ctl->error, 1);
+            abort = 1;
+            break;
+          }
+          __nanosleep(256);
+        }
+        __threadfence();
+        s_abort = abort;
+      }
+      __syncthreads();
+      if (s_abort) return;
+    }
+  }
+}
+
+}  // namespace
+
+// validated by the caller: SU(2)/SU(3) fundamental, FP32, nrhs >= 1
+size_t batch_workspace_bytes(const bsm_batch_item* items, int count, int op) {
+  size_t bytes = 0;
+  const auto align = [](size_t v) { return (v + 255) / 256 * 256; };
+  bytes += align(sizeof(BatchControl));
+  const int ntasks = count * 2;
+  bytes += align(sizeof(BatchTask) * ntasks);
+  if (op == BSM_BATCH_DHAT)
+    for (int k = 0; k < count; ++k) {
+      const Geom g = make_geom(items[k].lat);
+      bytes += align(half_spinor_bytes(g.Vh, items[k].lat.N, BSM_F32) * items[k].nrhs);
+    }
+  return bytes;
+}
+
+int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o, void* ws, cudaStream_t s) {
+  const auto align = [](size_t v) { return (v + 255) / 256 * 256; };
+  char* w = reinterpret_cast<char*>(ws);
+  BatchControl* ctl = reinterpret_cast<BatchControl*>(w);
+  w += align(sizeof(BatchControl));
+  BatchTask* dtasks = reinterpret_cast<BatchTask*>(w);
+  w += align(sizeof(BatchTask) * count * 2);
+
+  std::vector<BatchTask> tasks;
+  BatchMeta meta;
+  memset(&meta, 0, sizeof(meta));
+  meta.nphases = o.op == BSM_BATCH_DHAT ? 2 : 1;
+  for (int k = 0; k < count; ++k) {
+    const bsm_batch_item& it = items[k];
+    const OpCtx c = make_ctx(it.lat, it.U_rep, BSM_F32, s);
+    const size_t half = c.half_bytes * it.nrhs;
+    const char* in = reinterpret_cast<const char*>(it.in);
+    char* out = reinterpret_cast<char*>(it.out);
+    const long long chunks = ((long long)c.g.Vh * it.nrhs + kHopThreads - 1) / kHopThreads;
+    BatchTask t;
+    memset(&t, 0, sizeof(t));
+    t.d = c.d;
+    t.args.g = c.g;
+    t.args.nrhs = it.nrhs;
+    t.args.dagger = 0;
+    t.chunks = chunks;
+    if (o.op == BSM_BATCH_D) {  // out_p = A in_p - 1/2 H in_{1-p}, both parities in phase 0
+      for (int p = 0; p < 2; ++p) {
+        t.args.links = c.links + (size_t)p * c.link_block;
+        t.args.p = p;
+        t.args.in = in + (size_t)(1 - p) * half;
+        t.args.out = out + (size_t)p * half;
+        t.args.x = in + (size_t)p * half;
+        t.args.a = c.A;
+        t.args.b = -0.5;
+        t.phase = 0;
+        t.chunk0 = meta.phase_chunks[0];
+        meta.phase_chunks[0] += chunks;
+        tasks.push_back(t);
+      }
+    } else {  // phase 0: tmp_o = H_oe in_e ; phase 1: out_e = A in_e - 1/(4A) H_eo tmp_o
+      char* tmp = w;
+      w += align(half);
+      t.args.links = c.links + c.link_block;
+      t.args.p = 1;
+      t.args.in = in;
+      t.args.out = tmp;
+      t.args.x = nullptr;
+      t.args.a = 0.0;
+      t.args.b = 1.0;
+      t.phase = 0;
+      t.chunk0 = meta.phase_chunks[0];
+      meta.phase_chunks[0] += chunks;
+      tasks.push_back(t);
+      t.args.links = c.links;
+      t.args.p = 0;
+      t.args.in = tmp;
+      t.args.out = out;
+      t.args.x = in;
+      t.args.a = c.A;
+      t.args.b = -1.0 / (4.0 * c.A);
+      t.phase = 1;
+      t.chunk0 = meta.phase_chunks[1];
+      meta.phase_chunks[1] += chunks;
+      tasks.push_back(t);
+    }
+  }
+  meta.ntasks = (int)tasks.size();
+
+  // a cooperative grid: every block resident, so the barrier can complete
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kHopThreads, 0) != cudaSuccess ||
+      per_sm < 1)
+    return BSM_ECUDA;
+  long long want = meta.phase_chunks[0] > meta.phase_chunks[1] ? meta.phase_chunks[0] : meta.phase_chunks[1];
+  int grid = sms * per_sm;
+  if (want < grid) grid = (int)(want > 0 ? want : 1);
+  meta.barrier_target = (unsigned)grid + (unsigned)(o.barrier_extra > 0 ? o.barrier_extra : 0);
+  meta.timeout_ns = (unsigned long long)((o.timeout_s > 0 ? o.timeout_s : 1.0) * 1e9);
+
+  cudaMemsetAsync(ctl, 0, sizeof(BatchControl), s);
+  cudaMemcpyAsync(dtasks, tasks.data(), sizeof(BatchTask) * tasks.size(), cudaMemcpyHostToDevice, s);
+  void* kargs[] = {(void*)&dtasks, (void*)&ctl, (void*)&meta};
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)batch_kernel, grid, kHopThreads, kargs, 0, s);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return BSM_ECUDA;
+  }
+  int err = 0;
+  cudaMemcpyAsync(&err, &ctl->error, sizeof(int), cudaMemcpyDeviceToHost, s);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return BSM_ECUDA;
+  }
+  return err ? BSM_ETIMEOUT : BSM_OK;
+}
+
+}  // namespace bsm

@@ -179,14 +179,17 @@ struct SpinorIO<F64, D> {
 
 template <int D>
 struct SpinorIO<F32, D> {
-  // 2D planes of float4, plane = s*D + colour, (psi[s][c], psi[s+2][c])
+  // 2D planes of float4, plane = s*D + colour, (psi[s][c], psi[s+2][c]).
+  // L2ONLY loads bypass L1 (for data written earlier in the same kernel).
+  template <bool L2ONLY = false>
   __device__ __forceinline__ static void load(const void* base, size_t Vh, int i, cx<float> (&s)[4][D]) {
     const float4* b = reinterpret_cast<const float4*>(base);
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        const float4 v = __ldg(b + (size_t)(sp * D + a) * Vh + i);
+        const float4* q = b + (size_t)(sp * D + a) * Vh + i;
+        const float4 v = L2ONLY ? __ldcg(q) : __ldg(q);
         s[sp][a] = cmake(v.x, v.y);
         s[sp + 2][a] = cmake(v.z, v.w);
       }

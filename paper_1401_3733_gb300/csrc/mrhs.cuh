@@ -27,7 +27,7 @@ struct MrhsArgs {
   int nrhs;
 };
 
-template <int MU, int FB, typename P, int D, bool REAL, int RB>
+template <int MU, int FB, typename P, int D, bool REAL, int RB, bool L2IN = false>
 __device__ __forceinline__ void mrhs_sense(const MrhsArgs& A, const typename LinkIO<P, D, REAL>::vec* lt, int n,
                                            int r0, typename P::R sg, cx<typename P::R> (&acc)[RB][4][D]) {
   using R = typename P::R;
@@ -38,7 +38,8 @@ __device__ __forceinline__ void mrhs_sense(const MrhsArgs& A, const typename Lin
 #pragma unroll
   for (int j = 0; j < RB; ++j) {
     cx<R> psi[4][D];
-    SpinorIO<P, D>::load(A.in, Vn, (int)((size_t)n * nr + r0 + j), psi);
+    if constexpr (L2IN) SpinorIO<P, D>::template load<true>(A.in, Vn, (int)((size_t)n * nr + r0 + j), psi);
+    else SpinorIO<P, D>::load(A.in, Vn, (int)((size_t)n * nr + r0 + j), psi);
     spin_project<MU>(psi, sg, h[j]);
   }
 #pragma unroll
@@ -60,12 +61,12 @@ __device__ __forceinline__ void mrhs_sense(const MrhsArgs& A, const typename Lin
   }
 }
 
-template <int MU, typename P, int D, bool REAL, int RB>
+template <int MU, typename P, int D, bool REAL, int RB, bool L2IN = false>
 __device__ __forceinline__ void mrhs_direction(const MrhsArgs& A, const typename LinkIO<P, D, REAL>::vec* lt,
                                                int nf, int nb, int r0, typename P::R sg,
                                                cx<typename P::R> (&acc)[RB][4][D]) {
-  mrhs_sense<MU, 0, P, D, REAL, RB>(A, lt, nf, r0, sg, acc);
-  mrhs_sense<MU, 1, P, D, REAL, RB>(A, lt, nb, r0, -sg, acc);
+  mrhs_sense<MU, 0, P, D, REAL, RB, L2IN>(A, lt, nf, r0, sg, acc);
+  mrhs_sense<MU, 1, P, D, REAL, RB, L2IN>(A, lt, nb, r0, -sg, acc);
 }
 
 // Minimum resident blocks (register budget) per RHS block: measured on the
@@ -77,14 +78,11 @@ struct MrhsOccupancy {
   static constexpr int min_blocks = D <= 2 ? 1 : RB == 1 ? 3 : (RB == 2 && D >= 6) ? 2 : 1;
 };
 
-template <typename P, int D, bool REAL, int RB>
-__global__ void __launch_bounds__(kHopThreads, MrhsOccupancy<D, RB>::min_blocks) hop_mrhs_kernel(const MrhsArgs A) {
+// the output of site i, RHS r0 .. r0+RB-1 (one thread); L2IN reads the
+// input spinor through L2 only (it was written earlier in the same kernel)
+template <typename P, int D, bool REAL, int RB, bool L2IN = false>
+__device__ __forceinline__ void mrhs_site(const MrhsArgs& A, int i, int r0) {
   using R = typename P::R;
-  const int nblk = A.nrhs / RB;
-  const long long t = blockIdx.x * (long long)kHopThreads + threadIdx.x;
-  if (t >= (long long)A.g.Vh * nblk) return;
-  const int i = (int)(t / nblk);
-  const int r0 = (int)(t - (long long)i * nblk) * RB;
   int nf[4], nb[4];
   eo_neighbours(A.g, i, A.p, nf, nb);
   const auto* lt = LinkIO<P, D, REAL>::tile_ptr(A.links, i);
@@ -96,10 +94,10 @@ __global__ void __launch_bounds__(kHopThreads, MrhsOccupancy<D, RB>::min_blocks)
     for (int s = 0; s < 4; ++s)
 #pragma unroll
       for (int a = 0; a < D; ++a) acc[j][s][a] = cmake(R(0), R(0));
-  mrhs_direction<0, P, D, REAL, RB>(A, lt, nf[0], nb[0], r0, sg, acc);
-  mrhs_direction<1, P, D, REAL, RB>(A, lt, nf[1], nb[1], r0, sg, acc);
-  mrhs_direction<2, P, D, REAL, RB>(A, lt, nf[2], nb[2], r0, sg, acc);
-  mrhs_direction<3, P, D, REAL, RB>(A, lt, nf[3], nb[3], r0, sg, acc);
+  mrhs_direction<0, P, D, REAL, RB, L2IN>(A, lt, nf[0], nb[0], r0, sg, acc);
+  mrhs_direction<1, P, D, REAL, RB, L2IN>(A, lt, nf[1], nb[1], r0, sg, acc);
+  mrhs_direction<2, P, D, REAL, RB, L2IN>(A, lt, nf[2], nb[2], r0, sg, acc);
+  mrhs_direction<3, P, D, REAL, RB, L2IN>(A, lt, nf[3], nb[3], r0, sg, acc);
 
   const size_t nr = (size_t)A.nrhs;
   const size_t Vn = (size_t)A.g.Vh * nr;
@@ -124,6 +122,15 @@ __global__ void __launch_bounds__(kHopThreads, MrhsOccupancy<D, RB>::min_blocks)
     }
     SpinorIO<P, D>::store(A.out, Vn, e, acc[j]);
   }
+}
+
+template <typename P, int D, bool REAL, int RB>
+__global__ void __launch_bounds__(kHopThreads, MrhsOccupancy<D, RB>::min_blocks) hop_mrhs_kernel(const MrhsArgs A) {
+  const int nblk = A.nrhs / RB;
+  const long long t = blockIdx.x * (long long)kHopThreads + threadIdx.x;
+  if (t >= (long long)A.g.Vh * nblk) return;
+  const int i = (int)(t / nblk);
+  mrhs_site<P, D, REAL, RB>(A, i, (int)(t - (long long)i * nblk) * RB);
 }
 
 // RHS blocks compiled for colour dimension D (register budget: the RB

@@ -20,6 +20,8 @@
 //   x += alpha p, r -= alpha Ap with |r|^2 fused ; beta = rr_new/rr.
 // The host reads the CG state every `check_every` iterations; once the
 // device flags completion the remaining queued kernels return immediately.
+// Optionally the check_every iterations are captured once as a CUDA graph and
+// replayed (all pointers and the device-side scalars are fixed for a solve).
 #include <math.h>
 #include <stddef.h>
 #include <string.h>
@@ -149,6 +151,42 @@ struct Solver {
   }
   void write_state(const CgState& h) const { cudaMemcpyAsync(st, &h, sizeof(CgState), cudaMemcpyHostToDevice, s); }
 
+  // `count` CG iterations; with a graph, the first call captures them on the
+  // stream and later calls replay the instantiated graph
+  cudaGraphExec_t graph_exec = nullptr;
+  int iterate_batch(int count, bool use_graph, const OpCtx& c, void* x, void* r, void* p, void* Ap, void* u,
+                    void* t, size_t vec) {
+    if (graph_exec != nullptr) return cudaGraphLaunch(graph_exec, s) == cudaSuccess ? 0 : BSM_ECUDA;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool can_capture = use_graph && s != nullptr && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+                             cs == cudaStreamCaptureStatusNone;
+    if (can_capture && cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      int rc = 0;
+      for (int k = 0; k < count && rc == 0; ++k) rc = iterate(c, x, r, p, Ap, u, t, vec);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(s, &graph);
+      if (rc != 0) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      if (e == cudaSuccess && cudaGraphInstantiate(&graph_exec, graph, 0) == cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cudaGraphLaunch(graph_exec, s) == cudaSuccess ? 0 : BSM_ECUDA;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      graph_exec = nullptr;
+      cudaGetLastError();  // capture unavailable: fall back to direct launches
+    }
+    for (int k = 0; k < count; ++k) {
+      const int rc = iterate(c, x, r, p, Ap, u, t, vec);
+      if (rc != 0) return rc;
+    }
+    return 0;
+  }
+  ~Solver() {
+    if (graph_exec != nullptr) cudaGraphExecDestroy(graph_exec);
+  }
+
   // one CG iteration at the precision of context c
   int iterate(const OpCtx& c, void* x, void* r, void* p, void* Ap, void* u, void* t, size_t vec) const {
     cg_p_update_launch(c.prec, p, r, vec / 16, st, s);
@@ -256,12 +294,11 @@ int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void*
     int breakdowns = 0;
     while (hs.done != kDoneConverged || mixed) {
       if (hs.done == kDoneRunning) {
-        for (int k = 0; k < check; ++k) {
-          rc = mixed ? S.iterate(S.ci, S.at(y.x32), S.at(y.r32), S.at(y.p32), S.at(y.Ap32), S.at(y.u32),
-                                 S.at(y.t32), y.vec32)
-                     : S.iterate(co, xs, S.at(y.r), S.at(y.p), S.at(y.Ap), S.at(y.u), S.at(y.t), y.vec64);
-          if (rc < 0) return rc;
-        }
+        rc = mixed ? S.iterate_batch(check, o.use_graph != 0, S.ci, S.at(y.x32), S.at(y.r32), S.at(y.p32),
+                                     S.at(y.Ap32), S.at(y.u32), S.at(y.t32), y.vec32)
+                   : S.iterate_batch(check, o.use_graph != 0, co, xs, S.at(y.r), S.at(y.p), S.at(y.Ap), S.at(y.u),
+                                     S.at(y.t), y.vec64);
+        if (rc < 0) return rc;
         if ((rc = S.read_state(hs)) != 0) return rc;
       }
       if (!mixed) {

@@ -128,6 +128,22 @@ def test_mrhs_validation(bsm):
     assert bsm.bsm_dslash_mrhs_block(good, 12, bsm.F64) == bsm.EUNSUPPORTED
 
 
+def test_batch_validation(bsm):
+    A = 1 << 20
+    good = bsm.lattice((4, 4, 4, 4), 3)
+    items = bsm.batch_items([(good, A, 2 * A, 3 * A, 2), (bsm.lattice((2, 4, 6, 8), 2), 4 * A, 5 * A, 6 * A, 1)])
+    ok = bsm.BatchOpts(bsm.BATCH_D, bsm.F32, 0.0, 0)
+    assert bsm.bsm_batch_workspace_bytes(items, ok) > 0
+    assert bsm._lib.bsm_dslash_batch(items, 0, ctypes.byref(ok), 7 * A, 1 << 30, 0) == bsm.EINVAL
+    assert bsm._lib.bsm_dslash_batch(items, 2, ctypes.byref(bsm.BatchOpts(9, bsm.F32, 0, 0)), 7 * A, 1 << 30, 0) \
+        == bsm.EINVAL
+    assert bsm._lib.bsm_dslash_batch(items, 2, ctypes.byref(bsm.BatchOpts(0, bsm.F64, 0, 0)), 7 * A, 1 << 30, 0) \
+        == bsm.EUNSUPPORTED
+    assert bsm._lib.bsm_dslash_batch(items, 2, ctypes.byref(ok), 7 * A, 16, 0) == bsm.EWORKSPACE
+    su4 = bsm.batch_items([(bsm.lattice((4, 4, 4, 4), 4), A, 2 * A, 3 * A, 1)])
+    assert bsm._lib.bsm_dslash_batch(su4, 1, ctypes.byref(ok), 7 * A, 1 << 30, 0) == bsm.EUNSUPPORTED
+
+
 def test_too_large_lattice_is_unsupported(bsm):
     lat = bsm.lattice((2048, 1024, 1024, 2), 3)
     assert bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR, bsm.F32) == 0

@@ -1,0 +1,82 @@
+"""bsm_dslash_batch: uneven SU(2)/SU(3) lattices, each with its own number
+of right-hand sides, in one persistent cooperative launch fed by a device
+work queue.  Every RHS of every lattice equals the oracle's operator; the
+two-phase even-odd operator crosses a grid barrier whose bounded wait is
+also driven to time out (an arrival that never comes) to check that the call
+returns BSM_ETIMEOUT and leaves the GPU usable."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_1401_3733_gb300 import bsm, fields
+from tests.gpu_helpers import TOL, dev_c128, gpu_links, rel
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [((4, 4, 4, 4), 3, 2), ((2, 4, 6, 8), 2, 3), ((6, 6, 4, 4), 3, 1), ((8, 4, 2, 4), 2, 2),
+          ((4, 2, 2, 2), 3, 3)]   # (dims, N, nrhs)
+
+
+def make_batch(op, seed=900):
+    items, refs = [], []
+    for k, (dims, N, nrhs) in enumerate(SHAPES):
+        phase = (np.pi, 0, 0, 0)
+        olat = orc.Lattice(dims, N, orc.FUND, 0.1 + 0.05 * k, phase)
+        blat = bsm.lattice(dims, N, bsm.FUND, 0.1 + 0.05 * k, phase)
+        U = fields.gauge_field(dims, N, "haar", seed=seed + k)
+        R = orc.links_to_rep(olat, U)
+        psis = [fields.gaussian_spinor(dims, N, seed + 100 * k + r) for r in range(nrhs)]
+        if op == bsm.BATCH_DHAT:
+            odd = orc.parity_mask(dims)
+            for p in psis:
+                p[odd] = 0
+        full = bsm.bsm_field_bytes(blat, bsm.FIELD_SPINOR, bsm.F32) * nrhs
+        inp = torch.zeros(full, dtype=torch.uint8, device="cuda")
+        out = torch.zeros(full, dtype=torch.uint8, device="cuda")
+        bsm.bsm_pack_spinor_mrhs(blat, dev_c128(np.stack(psis)), inp, nrhs, bsm.F32)
+        Ud = gpu_links(blat, U, bsm.F32)
+        if op == bsm.BATCH_DHAT:   # even halves
+            half = full // 2
+            items.append((blat, Ud, inp[:half], out[:half], nrhs))
+        else:
+            items.append((blat, Ud, inp, out, nrhs))
+        refs.append((olat, R, psis, blat, out, nrhs))
+    return items, refs
+
+
+def unpack(blat, dev, nrhs):
+    V = int(np.prod(list(blat.dims)))
+    c = torch.empty((nrhs, V, 4, blat.N), dtype=torch.complex128, device="cuda")
+    bsm.bsm_unpack_spinor_mrhs(blat, dev, c, nrhs, bsm.F32)
+    torch.cuda.synchronize()
+    return c.cpu().numpy()
+
+
+@pytest.mark.parametrize("op", [bsm.BATCH_D, bsm.BATCH_DHAT], ids=["D", "Dhat"])
+def test_batch_matches_oracle(op):
+    items, refs = make_batch(op)
+    arr = bsm.batch_items(items)
+    opts = bsm.BatchOpts(op, bsm.F32, 0.0, 0)
+    ws = torch.empty(bsm.bsm_batch_workspace_bytes(arr, opts), dtype=torch.uint8, device="cuda")
+    assert bsm.bsm_dslash_batch(arr, opts, ws) == bsm.OK
+    for olat, R, psis, blat, out, nrhs in refs:
+        got = unpack(blat, out, nrhs)
+        for r in range(nrhs):
+            want = orc.dirac(olat, R, psis[r]) if op == bsm.BATCH_D else orc.dhat(olat, R, psis[r], orc.DHAT)
+            assert rel(got[r], want) <= TOL[bsm.F32], (blat.dims[:], r, rel(got[r], want))
+
+
+def test_barrier_timeout_returns_etimeout_and_gpu_stays_usable():
+    items, refs = make_batch(bsm.BATCH_DHAT, seed=950)
+    arr = bsm.batch_items(items)
+    ws_opts = bsm.BatchOpts(bsm.BATCH_DHAT, bsm.F32, 0.05, 0)
+    ws = torch.empty(bsm.bsm_batch_workspace_bytes(arr, ws_opts), dtype=torch.uint8, device="cuda")
+    # one phantom arrival that never comes: every block's bounded wait expires
+    st = bsm.bsm_dslash_batch(arr, bsm.BatchOpts(bsm.BATCH_DHAT, bsm.F32, 0.05, 1), ws, raise_on_error=False)
+    assert st == bsm.ETIMEOUT
+    # the context is intact: the same batch now completes and is correct
+    assert bsm.bsm_dslash_batch(arr, ws_opts, ws) == bsm.OK
+    olat, R, psis, blat, out, nrhs = refs[0]
+    got = unpack(blat, out, nrhs)
+    assert rel(got[0], orc.dhat(olat, R, psis[0], orc.DHAT)) <= TOL[bsm.F32]

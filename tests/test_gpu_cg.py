@@ -114,3 +114,28 @@ def test_zero_source_gives_zero_solution():
     st, stats, x = solve(blat, U64, None, gpu_spinor(blat, np.zeros_like(b), bsm.F64), bsm.cg_opts())
     assert st == bsm.OK and stats.iters == 0
     assert np.abs(to_canon(blat, x, bsm.F64)).max() == 0
+
+
+@pytest.mark.parametrize("inner,outer", [(bsm.F64, bsm.F64), (bsm.F32, bsm.DF64)], ids=["plain-f64", "mixed-df64"])
+def test_graph_replay_is_bit_identical(inner, outer):
+    """Capturing the iterations between host checks as a CUDA graph replays
+    the same kernels in the same order: the solution is bit-identical."""
+    dims, N = (8, 8, 4, 8), 3
+    blat = bsm.lattice(dims, N, bsm.FUND, 0.05, (np.pi, 0, 0, 0))
+    U = fields.gauge_field(dims, N, "smooth", seed=5, eps=0.3)
+    b = fields.gaussian_spinor(dims, 3, 6)
+    Uo, U32 = gpu_links(blat, U, outer), gpu_links(blat, U, bsm.F32)
+    bd = gpu_spinor(blat, b, bsm.F64)
+    stream = torch.cuda.Stream()
+    xs = []
+    for graph in (False, True):
+        x = zeros_field(blat, bsm.FIELD_SPINOR, bsm.F64)
+        ws = torch.empty(bsm.bsm_workspace_bytes(blat, bsm.CALL_CG, inner), dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        st, stats = bsm.bsm_cg_solve(blat, Uo, U32, bd, x,
+                                     bsm.cg_opts(tol=1e-10, prec_inner=inner, prec_outer=outer, use_graph=graph),
+                                     ws, stream=stream, raise_on_error=False)
+        assert st == bsm.OK and stats.true_res_normal <= 1e-10
+        xs.append((x.clone(), stats.iters))
+    assert xs[0][1] == xs[1][1]
+    assert torch.equal(xs[0][0], xs[1][0])

@@ -369,6 +369,10 @@ def run_ours(args):
         out["cg"] = run_cg(lat, links, src[bsm.F64], args.cg_max_iter)
     if rank == 0 and not args.no_mrhs:
         out["mrhs"] = run_mrhs(max(3, min(args.steps, 20)), flush, peak)
+    if rank == 0 and not args.no_batch:
+        out["batch"] = run_batch(max(3, min(args.steps, 20)), flush)
+        out["batch_small"] = run_batch(max(3, min(args.steps, 20)), flush, BATCH_SMALL)
+        out["cg_small_graph"] = run_cg_graph(args.cg_max_iter)
     if rank == 0 and world == 1 and not args.no_cpu:
         g, reps, el, th = time_oracle_hop(SAMPLE_DIMS, args.cpu_seconds)
         out["cpu_baseline"] = {"value": round(g, 3), "unit": "GFLOP/s", "cores": th, "kind": "oracle",
@@ -435,6 +439,103 @@ def run_mrhs(steps, flush, peak):
     return out
 
 
+BATCH_SHAPES = [((8, 8, 8, 8), 2), ((16, 8, 8, 8), 3), ((12, 12, 12, 12), 2), ((24, 12, 12, 12), 3),
+                ((16, 16, 16, 16), 2), ((32, 16, 16, 16), 3), ((20, 20, 20, 20), 2), ((24, 16, 16, 16), 3),
+                ((12, 8, 8, 8), 3), ((8, 12, 12, 12), 2), ((16, 12, 12, 12), 3), ((24, 24, 24, 24), 2),
+                ((32, 24, 24, 24), 3), ((48, 24, 24, 24), 2), ((40, 24, 24, 24), 3), ((48, 24, 24, 24), 3)]
+BATCH_NRHS = 8
+BATCH_SMALL = [((8, 8, 8, 8) if k % 2 else (16, 8, 8, 8), 2 + k % 2) for k in range(32)]
+
+
+def run_batch(steps, flush, shapes=BATCH_SHAPES):
+    """A batch of lattices with 8 Gaussian RHS each (default: 16 uneven
+    lattices 8^4 .. 24^3 x 48, SU(2) and SU(3) fundamental, smooth links eps =
+    0.3; BATCH_SMALL: 32 lattices of 8^4 and 16 x 8^3): the full operator D on
+    every RHS of every lattice as one persistent launch, against one multi-RHS
+    launch per lattice."""
+    import torch
+    from paper_1401_3733_gb300 import bsm, fields
+
+    entries, flop = [], 0
+    for k, (dims, N) in enumerate(shapes):
+        lat = bsm.lattice(dims, N, bsm.FUND, 0.1, (math.pi, 0, 0, 0))
+        V = int(np.prod(dims))
+        Ud = torch.from_numpy(fields.gauge_field(dims, N, "smooth", seed=20 + k, eps=0.3)).cuda()
+        links = bsm.empty_field(lat, bsm.FIELD_LINKS, bsm.F32)
+        bsm.bsm_links_to_rep(lat, Ud, links, bsm.F32)
+        del Ud
+        src = fields.device_gaussian_spinors(dims, N, BATCH_NRHS, seed=40 + k)
+        nbytes = bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR, bsm.F32) * BATCH_NRHS
+        inp = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        out = torch.empty_like(inp)
+        bsm.bsm_pack_spinor_mrhs(lat, src, inp, BATCH_NRHS, bsm.F32)
+        del src
+        entries.append((lat, links, inp, out, BATCH_NRHS))
+        flop += flops_per_site(N) * V * BATCH_NRHS
+    items = bsm.batch_items(entries)
+    opts = bsm.BatchOpts(bsm.BATCH_D, bsm.F32, 0.0, 0)
+    ws = torch.empty(bsm.bsm_batch_workspace_bytes(items, opts), dtype=torch.uint8, device="cuda")
+
+    def one_launch():
+        bsm.bsm_dslash_batch(items, opts, ws)
+
+    def per_lattice():
+        for lat, links, inp, out, n in entries:
+            bsm.bsm_dslash_mrhs(lat, links, inp, out, n, bsm.FULL, 0, bsm.F32)
+
+    res = {"lattices": len(entries), "nrhs": BATCH_NRHS, "sites": int(sum(np.prod(d) for d, _ in shapes)),
+           "gflop_per_step": round(flop / 1e9, 3)}
+    for name, fn in (("one_persistent_launch", one_launch), ("launch_per_lattice", per_lattice)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        ms = total / steps
+        res[name] = {"ms": round(ms, 4), "gflops": round(flop / (ms * 1e-3) / 1e9, 1)}
+    return res
+
+
+def run_cg_graph(max_iter):
+    """Mixed-precision CG (DF64 reliable updates) to 1e-10 on a small 8^3 x 16
+    SU(3) lattice, where launch gaps matter: iterations replayed from a CUDA
+    graph against direct launches, on a non-default stream."""
+    import torch
+    from paper_1401_3733_gb300 import bsm, fields
+
+    dims = (16, 8, 8, 8)
+    lat = bsm.lattice(dims, 3, bsm.FUND, 0.05, (math.pi, 0, 0, 0))
+    U = torch.from_numpy(fields.gauge_field(dims, 3, "smooth", seed=3, eps=0.3)).cuda()
+    links = {p: bsm.empty_field(lat, bsm.FIELD_LINKS, p) for p in (bsm.F32, bsm.DF64)}
+    for p, t in links.items():
+        bsm.bsm_links_to_rep(lat, U, t, p)
+    b = bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F64)
+    bsm.bsm_pack_spinor(lat, torch.from_numpy(fields.gaussian_spinor(dims, 3, 4)).cuda(), b, bsm.F64)
+    stream = torch.cuda.Stream()
+    ws = torch.empty(bsm.bsm_workspace_bytes(lat, bsm.CALL_CG, bsm.F32), dtype=torch.uint8, device="cuda")
+    res = {"lattice_TXYZ": list(dims)}
+    for name, graph in (("direct", False), ("graph", True)):
+        secs = []
+        for _ in range(3):
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            st, stats = bsm.bsm_cg_solve(lat, links[bsm.DF64], links[bsm.F32], b, x,
+                                         bsm.cg_opts(tol=1e-10, max_iter=max_iter, prec_inner=bsm.F32,
+                                                     prec_outer=bsm.DF64, use_graph=graph, check_every=16),
+                                         ws, stream=stream, raise_on_error=False)
+            secs.append(stats.seconds)
+        res[name] = {"status": bsm.bsm_strerror(st), "seconds": round(min(secs), 5), "iters": stats.iters,
+                     "true_res_normal": stats.true_res_normal}
+    return res
+
+
 def run_cg(lat, links, b, max_iter):
     """Time-to-1e-10 (true residual of the normal equations, recomputed at the
     outer precision) of the mixed-precision solver (FP32 inner iteration,
@@ -478,6 +579,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 Dslash line")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-mrhs", action="store_true", help="skip the multi-RHS 24^4 three-theory lines")
+    ap.add_argument("--no-batch", action="store_true", help="skip the uneven-lattice batch and small-lattice CG lines")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

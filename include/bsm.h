@@ -272,7 +272,8 @@ int bsm_dirac_eo_noalloc(const bsm_lattice *lat, const void *U_rep, const void *
  * queue.  The barrier wait is bounded by timeout_s (0 selects 1 s): past it
  * the kernel raises an error flag and returns, and the call returns
  * BSM_ETIMEOUT.  barrier_extra > 0 adds arrivals that never come (a test of
- * that path).  items is a host array; the call synchronises `stream`. */
+ * that path).  items is a host array of 1..32 lattices; the call
+ * synchronises `stream`. */
 typedef enum { BSM_BATCH_D = 0, BSM_BATCH_DHAT = 1 } bsm_batch_op;
 typedef struct {
   bsm_lattice lat;

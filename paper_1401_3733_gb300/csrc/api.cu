@@ -107,7 +107,7 @@ bool overlap(const void* a, size_t na, const void* b, size_t nb);
 
 // batch: SU(2)/SU(3) fundamental items, FP32, sane options
 int check_batch(const bsm_batch_item* items, int count, const bsm_batch_opts* o) {
-  if (items == nullptr || o == nullptr || count < 1 || count > 4096) return BSM_EINVAL;
+  if (items == nullptr || o == nullptr || count < 1 || count > 32) return BSM_EINVAL;
   if (o->op != BSM_BATCH_D && o->op != BSM_BATCH_DHAT) return BSM_EINVAL;
   if (o->prec != BSM_F32) return BSM_EUNSUPPORTED;
   if (!(o->timeout_s >= 0.0) || o->timeout_s > 60.0) return BSM_EINVAL;

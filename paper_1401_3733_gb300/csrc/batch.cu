@@ -51,32 +51,43 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__global__ void __launch_bounds__(kHopThreads) batch_kernel(const BatchTask* __restrict__ tasks, BatchControl* ctl,
-                                                            const BatchMeta meta) {
+constexpr int kMaxBatchTasks = 64;     // 2 tasks per lattice: up to 32 lattices per launch
+constexpr int kChunksPerGrab = 4;      // work-queue grabs cover 4 blocks' worth of thread slots
+
+__global__ void __launch_bounds__(kHopThreads, 3) batch_kernel(const BatchTask* __restrict__ tasks,
+                                                                BatchControl* ctl, const BatchMeta meta) {
+  __shared__ BatchTask s_tasks[kMaxBatchTasks];
   __shared__ long long s_chunk;
   __shared__ int s_abort;
+  for (int k = threadIdx.x; k < meta.ntasks; k += kHopThreads) s_tasks[k] = tasks[k];
+  __syncthreads();
   for (int phase = 0; phase < meta.nphases; ++phase) {
+    // this phase's tasks occupy a contiguous range of the table
+    int first = 0;
+    while (first < meta.ntasks && s_tasks[first].phase != phase) ++first;
     for (;;) {
-      if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(&ctl->next[phase], 1ull);
+      if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(&ctl->next[phase], 1ull) * kChunksPerGrab;
       __syncthreads();
-      const long long c = s_chunk;
+      const long long c0 = s_chunk;
       __syncthreads();
-      if (c >= meta.phase_chunks[phase]) break;
-      int k = 0;  // the task of chunk c (tasks are few: linear search)
-      while (k + 1 < meta.ntasks && !(tasks[k].phase == phase && c >= tasks[k].chunk0 &&
-                                      c < tasks[k].chunk0 + tasks[k].chunks))
-        ++k;
-      const BatchTask& tk = tasks[k];
-      const long long u = (c - tk.chunk0) * kHopThreads + threadIdx.x;
-      if (u < (long long)tk.args.g.Vh * tk.args.nrhs) {
-        const int i = (int)(u / tk.args.nrhs), r = (int)(u - (long long)i * tk.args.nrhs);
-        // phase 1 reads the odd temporaries written in phase 0: through L2 only
-        if (phase == 0) {
-          if (tk.d == 2) mrhs_site<F32, 2, false, 1>(tk.args, i, r);
-          else mrhs_site<F32, 3, false, 1>(tk.args, i, r);
-        } else {
-          if (tk.d == 2) mrhs_site<F32, 2, false, 1, true>(tk.args, i, r);
-          else mrhs_site<F32, 3, false, 1, true>(tk.args, i, r);
+      if (c0 >= meta.phase_chunks[phase]) break;
+      int k = first;
+      for (int sub = 0; sub < kChunksPerGrab; ++sub) {
+        const long long c = c0 + sub;
+        if (c >= meta.phase_chunks[phase]) break;
+        while (c >= s_tasks[k].chunk0 + s_tasks[k].chunks) ++k;  // chunks ascend with k
+        const BatchTask& tk = s_tasks[k];
+        const long long u = (c - tk.chunk0) * kHopThreads + threadIdx.x;
+        if (u < (long long)tk.args.g.Vh * tk.args.nrhs) {
+          const int i = (int)(u / tk.args.nrhs), r = (int)(u - (long long)i * tk.args.nrhs);
+          // phase 1 reads the odd temporaries written in phase 0: through L2 only
+          if (phase == 0) {
+            if (tk.d == 2) mrhs_site<F32, 2, false, 1>(tk.args, i, r);
+            else mrhs_site<F32, 3, false, 1>(tk.args, i, r);
+          } else {
+            if (tk.d == 2) mrhs_site<F32, 2, false, 1, true>(tk.args, i, r);
+            else mrhs_site<F32, 3, false, 1, true>(tk.args, i, r);
+          }
         }
       }
     }
@@ -134,7 +145,7 @@ int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o
   BatchTask* dtasks = reinterpret_cast<BatchTask*>(w);
   w += align(sizeof(BatchTask) * count * 2);
 
-  std::vector<BatchTask> tasks;
+  std::vector<BatchTask> tasks, tasks1;  // phase 0 and phase 1 (the kernel wants them by phase)
   BatchMeta meta;
   memset(&meta, 0, sizeof(meta));
   meta.nphases = o.op == BSM_BATCH_DHAT ? 2 : 1;
@@ -190,9 +201,10 @@ int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o
       t.phase = 1;
       t.chunk0 = meta.phase_chunks[1];
       meta.phase_chunks[1] += chunks;
-      tasks.push_back(t);
+      tasks1.push_back(t);
     }
   }
+  tasks.insert(tasks.end(), tasks1.begin(), tasks1.end());
   meta.ntasks = (int)tasks.size();
 
   // a cooperative grid: every block resident, so the barrier can complete
@@ -203,6 +215,7 @@ int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o
       per_sm < 1)
     return BSM_ECUDA;
   long long want = meta.phase_chunks[0] > meta.phase_chunks[1] ? meta.phase_chunks[0] : meta.phase_chunks[1];
+  want = (want + kChunksPerGrab - 1) / kChunksPerGrab;
   int grid = sms * per_sm;
   if (want < grid) grid = (int)(want > 0 ? want : 1);
   meta.barrier_target = (unsigned)grid + (unsigned)(o.barrier_extra > 0 ? o.barrier_extra : 0);

@@ -132,6 +132,19 @@ def gaussian_spinor(dims, d: int, seed: int) -> np.ndarray:
     return complex_gaussians(seed, (volume(dims), 4, d))
 
 
+def device_gaussian_spinors(dims, d: int, nrhs: int, seed: int, device="cuda"):
+    """nrhs Gaussian sources (nrhs, V, 4, d) complex128 drawn on the device
+    with torch's seeded Philox generator: for timing-only inputs too large to
+    draw quickly on the host (every real component N(0, 1))."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    shape = (nrhs, volume(dims), 4, d, 2)
+    v = torch.randn(shape, generator=g, device=device, dtype=torch.float64)
+    return torch.view_as_complex(v)
+
+
 def gauge_transform(dims, N: int, seed: int) -> np.ndarray:
     """Haar-random g(x) in SU(N) for every site, (V, N, N)."""
     return haar_su(seed, volume(dims), N)

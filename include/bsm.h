@@ -305,6 +305,88 @@ int bsm_cg_solve(const bsm_lattice *lat, const void *U_rep64, const void *U_rep3
                  bsm_cg_stats *stats, void *workspace, size_t workspace_bytes,
                  void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned preconditioner for the inversion of Sec. II-B (the paper itself
+ * solves with plain CG; this is an extension).  A two-layer linear
+ * parallel-transport convolution network M ~ D^{-1}, 1 -> C -> 1 channels:
+ *
+ *   layer(phi)_o(x)[s'] = sum_{k, i, s} (T_k phi_i)(x)[s] W[(k, i, s), (o, s')]
+ *   T_0 = 1, T_{1+2mu} phi(x) = U_mu(x) phi(x+mu),
+ *   T_{2+2mu} phi(x) = U_mu(x-mu)^+ phi(x-mu)
+ *
+ * with the representation links of the Dirac operator (boundary phases
+ * included); the weights mix channels and spins only, so M commutes with
+ * gauge transformations.  Supported: complex representations with d = 2, 3
+ * (SU(2), SU(3) fundamental; SU(2) symmetric; SU(3) antisymmetric); others
+ * give BSM_EUNSUPPORTED.  U_rep32: the FP32 links of bsm_links_to_rep.
+ *
+ * PTC field (device, complex FP32 = float2): rows (sample b, parity p, eo site
+ * i, colour c) in that order, row index ((b*2 + p)*V_h + i)*d + c, each row
+ * holding C channels x 4 spins, element [row][ch*4 + s].  A one-channel field
+ * of nbatch samples is nbatch*V*d*4 float2.
+ * Weights (device, complex FP32, row-major): W1 is 36 x 4C, W2 is 36C x 4,
+ * row (k*C_in + i)*4 + s, column o*4 + s'.
+ * --------------------------------------------------------------------------- */
+
+/* FP64 full device-layout spinor (bsm_pack_spinor, prec BSM_F64) -> one-
+ * channel PTC field of one sample (rounded to FP32), and back (widened). */
+int bsm_ptc_pack(const bsm_lattice *lat, const void *psi, void *field, void *stream);
+int bsm_ptc_unpack(const bsm_lattice *lat, const void *field, void *psi, void *stream);
+
+/* Workspace bytes of bsm_ptc_apply (train = 0) or bsm_ptc_loss_grad
+ * (train = 1) for `channels` hidden channels and nbatch samples; 0 for an
+ * unsupported lattice or channels outside 1..64.  Pure host. */
+size_t bsm_ptc_workspace_bytes(const bsm_lattice *lat, int32_t channels, int32_t nbatch, int32_t train);
+
+/* out = M(in) for nbatch one-channel PTC fields.  prec BSM_F32: complex FP32
+ * GEMMs; BSM_BF16: transported fields and weights rounded to BF16, products
+ * accumulated in FP32 (inference).  Asynchronous on `stream`. */
+int bsm_ptc_apply(const bsm_lattice *lat, const void *U_rep32, const void *W1, const void *W2,
+                  int32_t channels, const void *in, void *out, int32_t nbatch, int32_t prec,
+                  void *workspace, size_t workspace_bytes, void *stream);
+
+/* Training loss and gradients, FP32:
+ *   loss = sum_b |M(r_b) - e_b|^2 / |e_b|^2
+ * G_W1, G_W2 (device, shaped like W1, W2) receive dloss/dRe W + i dloss/dIm W.
+ * r, e: nbatch one-channel PTC fields.  *loss (host) is written.  Synchronises
+ * `stream`. */
+int bsm_ptc_loss_grad(const bsm_lattice *lat, const void *U_rep32, const void *W1, const void *W2,
+                      int32_t channels, const void *r, const void *e, int32_t nbatch, void *G_W1,
+                      void *G_W2, double *loss, void *workspace, size_t workspace_bytes, void *stream);
+
+/* One Adam step (Kingma and Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8) on n
+ * floats: W -= lr * mhat / (sqrt(vhat) + eps); m, v start at zero, step
+ * counts from 1.  Asynchronous. */
+int bsm_ptc_adam_step(void *W, const void *G, void *m, void *v, int64_t n, double lr, int32_t step,
+                      void *stream);
+
+/* Flexible GCR on the full operator, D x = b (FP64), with M = identity
+ * (precond BSM_FGCR_NONE) or the network above (BSM_FGCR_PTC, in
+ * ptc_prec BSM_F32 or BSM_BF16). */
+typedef enum { BSM_FGCR_NONE = 0, BSM_FGCR_PTC = 1 } bsm_fgcr_precond;
+typedef struct {
+  double tol;        /* stop when |r| <= tol |b| (iterated residual) */
+  int32_t max_iter;
+  int32_t restart;   /* directions kept, 1..64 */
+  int32_t precond;   /* bsm_fgcr_precond */
+  int32_t ptc_prec;  /* BSM_F32 or BSM_BF16 */
+  int32_t channels;  /* hidden channels C of W1, W2 */
+} bsm_fgcr_opts;
+typedef struct {
+  int32_t iters;
+  double true_res;   /* |b - D x| / |b|, recomputed at the end */
+  double seconds;
+} bsm_fgcr_stats;
+size_t bsm_fgcr_workspace_bytes(const bsm_lattice *lat, const bsm_fgcr_opts *opts);
+/* b, x: full FP64 device-layout spinors (x is overwritten, start x = 0);
+ * U_rep64: FP64 links; U_rep32, W1, W2: used with BSM_FGCR_PTC only (may be
+ * NULL otherwise).  Synchronises `stream` every iteration.  Returns
+ * BSM_ENOCONV (max_iter reached) or BSM_ENAN with x holding the last iterate. */
+int bsm_fgcr_solve(const bsm_lattice *lat, const void *U_rep64, const void *U_rep32,
+                   const void *W1, const void *W2, const void *b, void *x,
+                   const bsm_fgcr_opts *opts, bsm_fgcr_stats *stats, void *workspace,
+                   size_t workspace_bytes, void *stream);
+
 /* Static text for a bsm_status. */
 const char *bsm_strerror(int status);
 

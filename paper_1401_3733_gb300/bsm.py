@@ -59,6 +59,19 @@ class BatchOpts(ctypes.Structure):
 
 
 BATCH_D, BATCH_DHAT = 0, 1
+FGCR_NONE, FGCR_PTC = 0, 1
+
+
+class FgcrOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("precond", ctypes.c_int32), ("ptc_prec", ctypes.c_int32), ("channels", ctypes.c_int32)]
+
+
+class FgcrStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("true_res", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class BsmError(RuntimeError):
@@ -98,13 +111,27 @@ _lib.bsm_batch_workspace_bytes.restype = ctypes.c_size_t
 _lib.bsm_dslash_batch.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_int32, ctypes.POINTER(BatchOpts), _P,
                                   ctypes.c_size_t, _P]
 _lib.bsm_dslash_batch.restype = ctypes.c_int
+_lib.bsm_ptc_pack.argtypes = [_LP, _P, _P, _P]
+_lib.bsm_ptc_unpack.argtypes = [_LP, _P, _P, _P]
+_lib.bsm_ptc_workspace_bytes.argtypes = [_LP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+_lib.bsm_ptc_workspace_bytes.restype = ctypes.c_size_t
+_lib.bsm_ptc_apply.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
+                               ctypes.c_size_t, _P]
+_lib.bsm_ptc_loss_grad.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P,
+                                   ctypes.POINTER(ctypes.c_double), _P, ctypes.c_size_t, _P]
+_lib.bsm_ptc_adam_step.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_int32, _P]
+_lib.bsm_fgcr_workspace_bytes.argtypes = [_LP, ctypes.POINTER(FgcrOpts)]
+_lib.bsm_fgcr_workspace_bytes.restype = ctypes.c_size_t
+_lib.bsm_fgcr_solve.argtypes = [_LP, _P, _P, _P, _P, _P, _P, ctypes.POINTER(FgcrOpts), ctypes.POINTER(FgcrStats),
+                                _P, ctypes.c_size_t, _P]
 _lib.bsm_strerror.argtypes = [ctypes.c_int]
 _lib.bsm_strerror.restype = ctypes.c_char_p
 _lib.bsm_last_cuda_error.argtypes = []
 _lib.bsm_last_cuda_error.restype = ctypes.c_char_p
 for _f in ("bsm_pack_spinor", "bsm_unpack_spinor", "bsm_links_to_rep", "bsm_dslash", "bsm_dirac_eo",
            "bsm_dirac_eo_noalloc", "bsm_cg_solve", "bsm_pack_spinor_mrhs", "bsm_unpack_spinor_mrhs",
-           "bsm_dslash_mrhs"):
+           "bsm_dslash_mrhs", "bsm_ptc_pack", "bsm_ptc_unpack", "bsm_ptc_apply", "bsm_ptc_loss_grad",
+           "bsm_ptc_adam_step", "bsm_fgcr_solve"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -264,3 +291,63 @@ def bsm_cg_solve(lat, U_rep64, U_rep32, b, x, opts: CgOpts, workspace, stream=No
 def cg_opts(tol=1e-10, max_iter=10000, prec_inner=F64, delta=0.1, use_x0=False, eo=True, check_every=8,
             prec_outer=F64, use_graph=False) -> CgOpts:
     return CgOpts(tol, max_iter, prec_inner, delta, int(use_x0), int(eo), check_every, prec_outer, int(use_graph))
+
+
+# --- learned preconditioner (parallel-transport convolutions) and FGCR -------
+
+def ptc_shapes(channels: int):
+    """Shapes (complex entries) of W1 and W2 for `channels` hidden channels."""
+    return (36, 4 * channels), (36 * channels, 4)
+
+
+def bsm_ptc_pack(lat, psi, field, stream=None):
+    _check(_lib.bsm_ptc_pack(ctypes.byref(lat), _ptr(psi), _ptr(field), _stream(stream)), "bsm_ptc_pack")
+
+
+def bsm_ptc_unpack(lat, field, psi, stream=None):
+    _check(_lib.bsm_ptc_unpack(ctypes.byref(lat), _ptr(field), _ptr(psi), _stream(stream)), "bsm_ptc_unpack")
+
+
+def bsm_ptc_workspace_bytes(lat, channels, nbatch, train) -> int:
+    return _lib.bsm_ptc_workspace_bytes(ctypes.byref(lat), channels, nbatch, int(train))
+
+
+def bsm_ptc_apply(lat, U_rep32, W1, W2, channels, inp, out, nbatch, prec, workspace, stream=None):
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(_lib.bsm_ptc_apply(ctypes.byref(lat), _ptr(U_rep32), _ptr(W1), _ptr(W2), channels, _ptr(inp), _ptr(out),
+                              nbatch, prec, _ptr(workspace), nbytes, _stream(stream)), "bsm_ptc_apply")
+
+
+def bsm_ptc_loss_grad(lat, U_rep32, W1, W2, channels, r, e, nbatch, G_W1, G_W2, workspace, stream=None) -> float:
+    loss = ctypes.c_double(0.0)
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(_lib.bsm_ptc_loss_grad(ctypes.byref(lat), _ptr(U_rep32), _ptr(W1), _ptr(W2), channels, _ptr(r), _ptr(e),
+                                  nbatch, _ptr(G_W1), _ptr(G_W2), ctypes.byref(loss), _ptr(workspace), nbytes,
+                                  _stream(stream)), "bsm_ptc_loss_grad")
+    return loss.value
+
+
+def bsm_ptc_adam_step(W, G, m, v, lr, step, stream=None):
+    n = W.numel() * W.element_size() // 4
+    _check(_lib.bsm_ptc_adam_step(_ptr(W), _ptr(G), _ptr(m), _ptr(v), n, float(lr), step, _stream(stream)),
+           "bsm_ptc_adam_step")
+
+
+def fgcr_opts(tol=1e-10, max_iter=1000, restart=16, precond=FGCR_NONE, ptc_prec=F32, channels=1) -> FgcrOpts:
+    return FgcrOpts(tol, max_iter, restart, precond, ptc_prec, channels)
+
+
+def bsm_fgcr_workspace_bytes(lat, opts: FgcrOpts) -> int:
+    return _lib.bsm_fgcr_workspace_bytes(ctypes.byref(lat), ctypes.byref(opts))
+
+
+def bsm_fgcr_solve(lat, U_rep64, U_rep32, W1, W2, b, x, opts: FgcrOpts, workspace, stream=None,
+                   raise_on_error=True):
+    """Returns (status, FgcrStats)."""
+    stats = FgcrStats()
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    st = _lib.bsm_fgcr_solve(ctypes.byref(lat), _ptr(U_rep64), _ptr(U_rep32), _ptr(W1), _ptr(W2), _ptr(b), _ptr(x),
+                             ctypes.byref(opts), ctypes.byref(stats), _ptr(workspace), nbytes, _stream(stream))
+    if raise_on_error:
+        _check(st, "bsm_fgcr_solve")
+    return st, stats

@@ -23,6 +23,16 @@ bool mrhs_set_block(int prec, int d, bool real, int nrhs, int Vh, int block);
 size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo, int prec_outer);
 int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* b, void* x,
              const bsm_cg_opts& o, bsm_cg_stats* stats, void* ws, cudaStream_t s);
+size_t ptc_workspace_bytes(const bsm_lattice& L, int C, int nb, bool train);
+int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, cudaStream_t s);
+int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* in,
+              void* out, int nb, int prec, void* ws, cudaStream_t s);
+int ptc_loss_grad(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* r,
+                  const void* e, int nb, void* GW1, void* GW2, double* loss, void* ws, cudaStream_t s);
+int ptc_adam(void* W, const void* G, void* m, void* v, long long nfloat, double lr, int step, cudaStream_t s);
+size_t fgcr_workspace_bytes(const bsm_lattice& L, const bsm_fgcr_opts& o);
+int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* W1, const void* W2,
+               const void* b, void* x, const bsm_fgcr_opts& o, bsm_fgcr_stats* stats, void* ws, cudaStream_t s);
 
 RepInfo rep_info(int N, int rep) {
   RepInfo r{-1, false};
@@ -128,6 +138,18 @@ int check_batch(const bsm_batch_item* items, int count, const bsm_batch_opts* o)
 bool overlap(const void* a, size_t na, const void* b, size_t nb) {
   const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
   return x < y + nb && y < x + na;
+}
+
+// learned preconditioner: complex d = 2, 3; channels 1..64; 32-bit GEMM rows
+int check_ptc(const bsm_lattice* L, int C, int nb) {
+  const int rc = check_lattice(L);
+  if (rc != BSM_OK) return rc;
+  if (C < 1 || C > 64 || nb < 1) return BSM_EINVAL;
+  const RepInfo ri = rep_info(L->N, L->rep);
+  if (ri.real || (ri.d != 2 && ri.d != 3)) return BSM_EUNSUPPORTED;
+  const int64_t V = (int64_t)L->dims[0] * L->dims[1] * L->dims[2] * L->dims[3];
+  if (V * ri.d * nb > ((int64_t)1 << 28)) return BSM_EUNSUPPORTED;
+  return BSM_OK;
 }
 
 }  // namespace
@@ -368,6 +390,97 @@ int bsm_cg_solve(const bsm_lattice* lat, const void* U_rep64, const void* U_rep3
   return rc;
 }
 
+int bsm_ptc_pack(const bsm_lattice* lat, const void* psi, void* field, void* stream) {
+  int rc = check_ptc(lat, 1, 1);
+  if (rc != BSM_OK) return rc;
+  if (!aligned(psi) || !aligned(field)) return BSM_EINVAL;
+  return finish(ptc_pack(*lat, reinterpret_cast<const double*>(psi), field, false, (cudaStream_t)stream));
+}
+
+int bsm_ptc_unpack(const bsm_lattice* lat, const void* field, void* psi, void* stream) {
+  int rc = check_ptc(lat, 1, 1);
+  if (rc != BSM_OK) return rc;
+  if (!aligned(psi) || !aligned(field)) return BSM_EINVAL;
+  return finish(ptc_pack(*lat, reinterpret_cast<const double*>(psi), const_cast<void*>(field), true,
+                         (cudaStream_t)stream));
+}
+
+size_t bsm_ptc_workspace_bytes(const bsm_lattice* lat, int32_t channels, int32_t nbatch, int32_t train) {
+  if (check_ptc(lat, channels, nbatch) != BSM_OK) return 0;
+  return ptc_workspace_bytes(*lat, channels, nbatch, train != 0);
+}
+
+int bsm_ptc_apply(const bsm_lattice* lat, const void* U_rep32, const void* W1, const void* W2, int32_t channels,
+                  const void* in, void* out, int32_t nbatch, int32_t prec, void* workspace, size_t workspace_bytes,
+                  void* stream) {
+  int rc = check_ptc(lat, channels, nbatch);
+  if (rc != BSM_OK) return rc;
+  if (prec != BSM_F32 && prec != BSM_BF16) return BSM_EUNSUPPORTED;
+  if (!aligned(U_rep32) || !aligned(W1) || !aligned(W2) || !aligned(in) || !aligned(out) || !aligned(workspace))
+    return BSM_EINVAL;
+  if (workspace_bytes < ptc_workspace_bytes(*lat, channels, nbatch, false)) return BSM_EWORKSPACE;
+  const int64_t V = (int64_t)lat->dims[0] * lat->dims[1] * lat->dims[2] * lat->dims[3];
+  const size_t fb = (size_t)V * nbatch * rep_info(lat->N, lat->rep).d * 4 * 8;
+  if (overlap(in, fb, out, fb)) return BSM_EINVAL;
+  return finish(ptc_apply(*lat, U_rep32, W1, W2, channels, in, out, nbatch, prec, workspace, (cudaStream_t)stream));
+}
+
+int bsm_ptc_loss_grad(const bsm_lattice* lat, const void* U_rep32, const void* W1, const void* W2, int32_t channels,
+                      const void* r, const void* e, int32_t nbatch, void* G_W1, void* G_W2, double* loss,
+                      void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_ptc(lat, channels, nbatch);
+  if (rc != BSM_OK) return rc;
+  if (!aligned(U_rep32) || !aligned(W1) || !aligned(W2) || !aligned(r) || !aligned(e) || !aligned(G_W1) ||
+      !aligned(G_W2) || !aligned(workspace) || loss == nullptr)
+    return BSM_EINVAL;
+  if (workspace_bytes < ptc_workspace_bytes(*lat, channels, nbatch, true)) return BSM_EWORKSPACE;
+  return finish(ptc_loss_grad(*lat, U_rep32, W1, W2, channels, r, e, nbatch, G_W1, G_W2, loss, workspace,
+                              (cudaStream_t)stream));
+}
+
+int bsm_ptc_adam_step(void* W, const void* G, void* m, void* v, int64_t n, double lr, int32_t step, void* stream) {
+  if (!aligned(W) || !aligned(G) || !aligned(m) || !aligned(v) || n < 1 || step < 1 || !(lr > 0.0))
+    return BSM_EINVAL;
+  return finish(ptc_adam(W, G, m, v, n, lr, step, (cudaStream_t)stream));
+}
+
+size_t bsm_fgcr_workspace_bytes(const bsm_lattice* lat, const bsm_fgcr_opts* opts) {
+  if (opts == nullptr || check_lattice(lat) != BSM_OK || opts->restart < 1 || opts->restart > 64) return 0;
+  if (opts->precond == BSM_FGCR_PTC && check_ptc(lat, opts->channels, 1) != BSM_OK) return 0;
+  return fgcr_workspace_bytes(*lat, *opts);
+}
+
+int bsm_fgcr_solve(const bsm_lattice* lat, const void* U_rep64, const void* U_rep32, const void* W1, const void* W2,
+                   const void* b, void* x, const bsm_fgcr_opts* opts, bsm_fgcr_stats* stats, void* workspace,
+                   size_t workspace_bytes, void* stream) {
+  int rc = check_lattice(lat);
+  if (rc != BSM_OK) return rc;
+  if (opts == nullptr || !(opts->tol > 0.0) || opts->max_iter < 1 || opts->restart < 1 || opts->restart > 64)
+    return BSM_EINVAL;
+  if (opts->precond != BSM_FGCR_NONE && opts->precond != BSM_FGCR_PTC) return BSM_EINVAL;
+  if (opts->precond == BSM_FGCR_PTC) {
+    if ((rc = check_ptc(lat, opts->channels, 1)) != BSM_OK) return rc;
+    if (opts->ptc_prec != BSM_F32 && opts->ptc_prec != BSM_BF16) return BSM_EUNSUPPORTED;
+    if (!aligned(U_rep32) || !aligned(W1) || !aligned(W2)) return BSM_EINVAL;
+  }
+  if (!aligned(U_rep64) || !aligned(b) || !aligned(x) || !aligned(workspace)) return BSM_EINVAL;
+  if (workspace_bytes < fgcr_workspace_bytes(*lat, *opts)) return BSM_EWORKSPACE;
+  const size_t full = bsm_field_bytes(lat, BSM_FIELD_SPINOR, BSM_F64);
+  if (overlap(b, full, x, full)) return BSM_EINVAL;
+  const cudaError_t pre = cudaGetLastError();
+  if (pre != cudaSuccess) {
+    set_cuda_error(pre);
+    return BSM_ECUDA;
+  }
+  rc = fgcr_solve(*lat, U_rep64, U_rep32, W1, W2, b, x, *opts, stats, workspace, (cudaStream_t)stream);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return BSM_ECUDA;
+  }
+  return rc;
+}
+
 const char* bsm_strerror(int status) {
   switch (status) {
     case BSM_OK: return "ok";
@@ -375,9 +488,9 @@ const char* bsm_strerror(int status) {
     case BSM_EUNSUPPORTED: return "unsupported configuration";
     case BSM_ECUDA: return "CUDA error";
     case BSM_EWORKSPACE: return "workspace too small";
-    case BSM_ENOCONV: return "CG did not converge within max_iter";
+    case BSM_ENOCONV: return "solver did not converge within max_iter";
     case BSM_EBREAKDOWN: return "CG breakdown (<p, M p> <= 0)";
-    case BSM_ENAN: return "NaN or Inf in a CG reduction";
+    case BSM_ENAN: return "NaN or Inf in a solver reduction";
     case BSM_ETIMEOUT: return "bounded device wait timed out";
     default: return "unknown status";
   }

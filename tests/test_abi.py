@@ -154,3 +154,45 @@ def test_strerror_covers_every_status(bsm):
     for s in range(0, -9, -1):
         assert bsm.bsm_strerror(s) not in ("", "unknown status")
     assert bsm.bsm_strerror(-99) == "unknown status"
+
+
+def test_ptc_and_fgcr_validation(bsm):
+    L = ctypes.byref
+    A = 1 << 20
+    big = 1 << 40
+    good = bsm.lattice((4, 4, 4, 4), 3)
+    adj = bsm.lattice((4, 4, 4, 4), 2, bsm.ADJ)
+    su4 = bsm.lattice((4, 4, 4, 4), 4)
+    assert bsm.bsm_ptc_workspace_bytes(good, 12, 2, 1) > bsm.bsm_ptc_workspace_bytes(good, 12, 2, 0) > 0
+    for lat, C, nb in [(adj, 4, 1), (su4, 4, 1), (good, 0, 1), (good, 65, 1), (good, 4, 0)]:
+        assert bsm.bsm_ptc_workspace_bytes(lat, C, nb, 0) == 0
+    apply = bsm._lib.bsm_ptc_apply
+    assert apply(L(adj), A, 2 * A, 3 * A, 4, 4 * A, 5 * A, 1, bsm.F32, 6 * A, big, 0) == bsm.EUNSUPPORTED
+    assert apply(L(good), A, 2 * A, 3 * A, 4, 4 * A, 5 * A, 1, bsm.F64, 6 * A, big, 0) == bsm.EUNSUPPORTED
+    assert apply(L(good), A, 2 * A, 3 * A, 0, 4 * A, 5 * A, 1, bsm.F32, 6 * A, big, 0) == bsm.EINVAL
+    assert apply(L(good), A, 2 * A + 4, 3 * A, 4, 4 * A, 5 * A, 1, bsm.F32, 6 * A, big, 0) == bsm.EINVAL
+    assert apply(L(good), A, 2 * A, 3 * A, 4, 4 * A, 4 * A + 64, 1, bsm.F32, 6 * A, big, 0) == bsm.EINVAL
+    assert apply(L(good), A, 2 * A, 3 * A, 4, 4 * A, 5 * A, 1, bsm.F32, 6 * A, 1024, 0) == bsm.EWORKSPACE
+    loss = ctypes.c_double()
+    assert bsm._lib.bsm_ptc_loss_grad(L(good), A, 2 * A, 3 * A, 4, 4 * A, 5 * A, 1, 6 * A, 7 * A, None, 8 * A, big,
+                                      0) == bsm.EINVAL
+    assert bsm._lib.bsm_ptc_loss_grad(L(good), A, 2 * A, 3 * A, 4, 4 * A, 5 * A, 1, 6 * A, 7 * A, L(loss), 8 * A,
+                                      1024, 0) == bsm.EWORKSPACE
+    assert bsm._lib.bsm_ptc_adam_step(A, 2 * A, 3 * A, 4 * A, 0, 1e-3, 1, 0) == bsm.EINVAL
+    assert bsm._lib.bsm_ptc_adam_step(A, 2 * A, 3 * A, 4 * A, 16, 1e-3, 0, 0) == bsm.EINVAL
+    assert bsm._lib.bsm_ptc_pack(L(adj), A, 2 * A, 0) == bsm.EUNSUPPORTED
+    assert bsm._lib.bsm_ptc_unpack(L(good), None, 2 * A, 0) == bsm.EINVAL
+
+    def solve(opts, ws_bytes=big, W=A):
+        st = bsm.FgcrStats()
+        return bsm._lib.bsm_fgcr_solve(L(good), A, 2 * A, W, W, 3 * A, 4 * A, L(opts), L(st), 5 * A, ws_bytes, 0)
+
+    assert bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(restart=0)) == 0
+    assert bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(restart=8, precond=bsm.FGCR_PTC, channels=4)) > \
+        bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(restart=8)) > 0
+    assert solve(bsm.fgcr_opts(tol=0.0)) == bsm.EINVAL
+    assert solve(bsm.fgcr_opts(restart=65)) == bsm.EINVAL
+    assert solve(bsm.fgcr_opts(precond=7)) == bsm.EINVAL
+    assert solve(bsm.fgcr_opts(precond=bsm.FGCR_PTC, channels=4, ptc_prec=bsm.F64)) == bsm.EUNSUPPORTED
+    assert solve(bsm.fgcr_opts(precond=bsm.FGCR_PTC, channels=4), W=None) == bsm.EINVAL
+    assert solve(bsm.fgcr_opts(), ws_bytes=4096) == bsm.EWORKSPACE

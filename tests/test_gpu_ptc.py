@@ -1,0 +1,293 @@
+"""GPU learned preconditioner and flexible GCR through the C ABI:
+- the two-layer parallel-transport network against the oracle's layers
+  (FP32 and BF16 inference), and against the degree-2 Neumann polynomial of
+  the Wilson operator that it represents exactly with hand-set weights
+  (checked with the oracle's D alone);
+- the training gradient against central differences of the oracle's loss
+  (exact for a loss quadratic along the direction), one Adam step against
+  its formula, and a short training run that lowers the loss;
+- FGCR without preconditioner against the oracle's FGCR, FGCR with the
+  network converging to the same solution in fewer iterations, and the
+  error statuses."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from oracle import ptc
+from paper_1401_3733_gb300 import bsm, fields
+from tests.gpu_helpers import gpu_links, gpu_spinor, rel, to_canon, zeros_field
+
+pytestmark = pytest.mark.gpu
+
+CASES = [((4, 4, 2, 6), 3, bsm.FUND, (np.pi, 0.4, 0, -1.0)), ((4, 2, 4, 4), 2, bsm.FUND, (np.pi, 0, 0, 0)),
+         ((2, 4, 4, 2), 2, bsm.SYM, (0.3, 0, 0, 0)), ((4, 4, 4, 2), 3, bsm.ASYM, (np.pi, 0, 0.7, 0))]
+CASE_IDS = ["SU3-F", "SU2-F", "SU2-S", "SU3-AS"]
+
+
+def lats(dims, N, rep, phase, m0=0.1):
+    return orc.Lattice(dims, N, rep, m0, phase), bsm.lattice(dims, N, rep, m0, phase)
+
+
+def rand_c(rng, shape, scale=1.0):
+    return scale * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+
+
+def dev_c64(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).to("cuda")
+
+
+def ptc_field(blat, psis):
+    """canonical spinors (nb, V, 4, d) -> nb-sample one-channel PTC field"""
+    nb = len(psis)
+    V = int(np.prod(list(blat.dims)))
+    d = bsm.bsm_rep_dim(blat.N, blat.rep)
+    F = torch.empty(nb * V * d * 4, dtype=torch.complex64, device="cuda")
+    for b, psi in enumerate(psis):
+        bsm.bsm_ptc_pack(blat, gpu_spinor(blat, psi, bsm.F64), F[b * V * d * 4:(b + 1) * V * d * 4])
+    return F
+
+
+def from_ptc_field(blat, F, nb):
+    V = int(np.prod(list(blat.dims)))
+    d = bsm.bsm_rep_dim(blat.N, blat.rep)
+    out = []
+    for b in range(nb):
+        psi = zeros_field(blat, bsm.FIELD_SPINOR, bsm.F64)
+        bsm.bsm_ptc_unpack(blat, F[b * V * d * 4:(b + 1) * V * d * 4], psi)
+        out.append(to_canon(blat, psi, bsm.F64))
+    return np.stack(out)
+
+
+def gpu_net(blat, U32, W1, W2, C, psis, prec):
+    nb = len(psis)
+    F = ptc_field(blat, psis)
+    out = torch.empty_like(F)
+    ws = torch.empty(bsm.bsm_ptc_workspace_bytes(blat, C, nb, 0), dtype=torch.uint8, device="cuda")
+    bsm.bsm_ptc_apply(blat, U32, dev_c64(W1), dev_c64(W2), C, F, out, nb, prec, ws)
+    return from_ptc_field(blat, out, nb)
+
+
+def oracle_net(olat, R, psi, W1, W2, C):
+    y1 = ptc.ptc_layer(olat, R, psi[:, None], W1.reshape(9, 1, 4, C, 4))
+    return ptc.ptc_layer(olat, R, y1, W2.reshape(9, C, 4, 1, 4))[:, 0]
+
+
+def neumann_weights(m0):
+    """C = 2 weights with M = (1 + K + K^2)/A, K = H/(2A): the degree-2
+    truncation of D^{-1} = (A - H/2)^{-1} = (1/A) sum_n K^n."""
+    A = 4.0 + m0
+    W1 = np.zeros((9, 1, 4, 2, 4), np.complex128)
+    W2 = np.zeros((9, 2, 4, 1, 4), np.complex128)
+    W1[0, 0, :, 0, :] = np.eye(4)                       # channel 0 = phi
+    W2[0, 0, :, 0, :] = np.eye(4) / A                   # out = phi/A + ...
+    W2[0, 1, :, 0, :] = np.eye(4) / A                   # ... + K phi / A + ...
+    for mu in range(4):
+        g = orc.gamma(mu)
+        for k, P in ((1 + 2 * mu, np.eye(4) - g), (2 + 2 * mu, np.eye(4) + g)):
+            W1[k, 0, :, 1, :] = (P / (2 * A)).T          # channel 1 = K phi
+            W2[k, 1, :, 0, :] = (P / (2 * A * A)).T      # ... + K^2 phi / A
+    return W1.reshape(36, 8), W2.reshape(72, 4)
+
+
+@pytest.mark.parametrize("prec,tol", [(bsm.F32, 1e-5), (bsm.BF16, 2e-2)], ids=["f32", "bf16"])
+@pytest.mark.parametrize("case", CASES, ids=CASE_IDS)
+def test_ptc_net_matches_oracle_layers(case, prec, tol):
+    dims, N, rep, phase = case
+    olat, blat = lats(dims, N, rep, phase)
+    U = fields.gauge_field(dims, N, "haar", seed=11)
+    R = orc.links_to_rep(olat, U)
+    U32 = gpu_links(blat, U, bsm.F32)
+    rng = np.random.default_rng(12)
+    C = 5
+    W1, W2 = rand_c(rng, (36, 4 * C), 0.3), rand_c(rng, (36 * C, 4), 0.1)
+    psis = [fields.gaussian_spinor(dims, olat.d, 13 + b) for b in range(2)]
+    got = gpu_net(blat, U32, W1, W2, C, psis, prec)
+    for b in range(2):
+        want = oracle_net(olat, R, psis[b], W1, W2, C)
+        assert rel(got[b], want) < tol
+
+
+def test_ptc_net_with_neumann_weights_is_the_polynomial_of_d():
+    dims, N, rep, phase = CASES[0]
+    olat, blat = lats(dims, N, rep, phase, m0=-0.3)
+    U = fields.gauge_field(dims, N, "haar", seed=14)
+    R = orc.links_to_rep(olat, U)
+    A = 4.0 + olat.m0
+    psi = fields.gaussian_spinor(dims, olat.d, 15)
+    K = lambda v: (A * v - orc.dirac(olat, R, v)) / A      # K = H / (2A) = (A - D)/A
+    Kpsi = K(psi)
+    want = (psi + Kpsi + K(Kpsi)) / A
+    W1, W2 = neumann_weights(olat.m0)
+    got = gpu_net(blat, gpu_links(blat, U, bsm.F32), W1, W2, 2, [psi], bsm.F32)[0]
+    assert rel(got, want) < 1e-5
+
+
+def _loss_oracle(olat, R, rs, es, W1, W2, C):
+    return sum(np.linalg.norm(oracle_net(olat, R, r, W1, W2, C) - e) ** 2 / np.linalg.norm(e) ** 2
+               for r, e in zip(rs, es))
+
+
+def test_ptc_gradient_against_central_differences():
+    dims, N, rep, phase = (4, 4, 4, 4), 3, bsm.FUND, (np.pi, 0, 0, 0)
+    olat, blat = lats(dims, N, rep, phase)
+    U = fields.gauge_field(dims, N, "smooth", seed=16, eps=0.5)
+    R = orc.links_to_rep(olat, U)
+    U32 = gpu_links(blat, U, bsm.F32)
+    rng = np.random.default_rng(17)
+    C, nb = 3, 2
+    W1, W2 = rand_c(rng, (36, 4 * C), 0.2), rand_c(rng, (36 * C, 4), 0.1)
+    rs = [fields.gaussian_spinor(dims, 3, 18 + b) for b in range(nb)]
+    es = [fields.gaussian_spinor(dims, 3, 28 + b) for b in range(nb)]
+    G1 = torch.empty((36, 4 * C), dtype=torch.complex64, device="cuda")
+    G2 = torch.empty((36 * C, 4), dtype=torch.complex64, device="cuda")
+    ws = torch.empty(bsm.bsm_ptc_workspace_bytes(blat, C, nb, 1), dtype=torch.uint8, device="cuda")
+    loss = bsm.bsm_ptc_loss_grad(blat, U32, dev_c64(W1), dev_c64(W2), C, ptc_field(blat, rs), ptc_field(blat, es),
+                                 nb, G1, G2, ws)
+    L0 = _loss_oracle(olat, R, rs, es, W1, W2, C)
+    assert abs(loss - L0) / L0 < 1e-5
+    g1, g2 = G1.cpu().numpy().astype(np.complex128), G2.cpu().numpy().astype(np.complex128)
+    h = 1e-3
+    # directional derivatives along random directions (loss quadratic in t)
+    for which in (1, 2):
+        D = rand_c(rng, W1.shape if which == 1 else W2.shape)
+        if which == 1:
+            f = lambda t: _loss_oracle(olat, R, rs, es, W1 + t * D, W2, C)
+            g = g1
+        else:
+            f = lambda t: _loss_oracle(olat, R, rs, es, W1, W2 + t * D, C)
+            g = g2
+        fd = (f(h) - f(-h)) / (2 * h)
+        an = float(np.real(np.vdot(g, D)))
+        assert abs(fd - an) <= 1e-4 * (abs(fd) + np.linalg.norm(g) * np.linalg.norm(D) * 1e-2), (which, fd, an)
+    # single entries, real and imaginary parts
+    for which, W, g in ((1, W1, g1), (2, W2, g2)):
+        for j in rng.choice(W.size, 3, replace=False):
+            for unit, part in ((1.0, np.real), (1j, np.imag)):
+                D = np.zeros_like(W)
+                D.reshape(-1)[j] = unit
+                if which == 1:
+                    fd = (_loss_oracle(olat, R, rs, es, W1 + h * D, W2, C) -
+                          _loss_oracle(olat, R, rs, es, W1 - h * D, W2, C)) / (2 * h)
+                else:
+                    fd = (_loss_oracle(olat, R, rs, es, W1, W2 + h * D, C) -
+                          _loss_oracle(olat, R, rs, es, W1, W2 - h * D, C)) / (2 * h)
+                an = part(g.reshape(-1)[j])
+                assert abs(fd - an) <= 1e-4 * np.abs(g).max(), (which, j, fd, an)
+
+
+def test_adam_step_formula():
+    rng = np.random.default_rng(19)
+    n = 1000
+    W, G = rng.standard_normal(n).astype(np.float32), rng.standard_normal(n).astype(np.float32)
+    m, v = (0.1 * rng.standard_normal(n)).astype(np.float32), rng.random(n).astype(np.float32)
+    tW, tG, tm, tv = (torch.from_numpy(a.copy()).cuda() for a in (W, G, m, v))
+    bsm.bsm_ptc_adam_step(tW, tG, tm, tv, 1e-2, 3)
+    m1 = 0.9 * m + 0.1 * G
+    v1 = 0.999 * v + 0.001 * G * G
+    W1 = W - 1e-2 * (m1 / (1 - 0.9 ** 3)) / (np.sqrt(v1 / (1 - 0.999 ** 3)) + 1e-8)
+    assert np.allclose(tm.cpu().numpy(), m1, rtol=1e-6, atol=1e-7)
+    assert np.allclose(tv.cpu().numpy(), v1, rtol=1e-6, atol=1e-7)
+    assert np.allclose(tW.cpu().numpy(), W1, rtol=1e-5, atol=1e-6)
+
+
+def train(blat, U64, U32, C, steps, nb, seed, lr=3e-3):
+    """Adam on loss = sum |M(D e) - e|^2 / |e|^2 over Gaussian e (drawn on the
+    host with the seeded generator; D e by the library's FP64 operator)."""
+    V = int(np.prod(list(blat.dims)))
+    d = bsm.bsm_rep_dim(blat.N, blat.rep)
+    es = [fields.gaussian_spinor(tuple(blat.dims), d, seed + b) for b in range(nb)]
+    rs = []
+    for e in es:
+        out = zeros_field(blat, bsm.FIELD_SPINOR, bsm.F64)
+        bsm.bsm_dslash(blat, U64, gpu_spinor(blat, e, bsm.F64), out, bsm.FULL, 0, bsm.F64)
+        rs.append(to_canon(blat, out, bsm.F64))
+    R, E = ptc_field(blat, rs), ptc_field(blat, es)
+    rng = np.random.default_rng(seed)
+    A = 4.0 + blat.m0
+    W1 = rand_c(rng, (9, 1, 4, C, 4), 0.05)
+    W1[0, 0, :, 0, :] += np.eye(4)
+    W2 = rand_c(rng, (9, C, 4, 1, 4), 0.01)
+    W2[0, 0, :, 0, :] += np.eye(4) / A
+    tW = [dev_c64(W1.reshape(36, 4 * C)), dev_c64(W2.reshape(36 * C, 4))]
+    tG = [torch.empty_like(t) for t in tW]
+    tm = [torch.zeros_like(t) for t in tW]
+    tv = [torch.zeros_like(t) for t in tW]
+    ws = torch.empty(bsm.bsm_ptc_workspace_bytes(blat, C, nb, 1), dtype=torch.uint8, device="cuda")
+    losses = []
+    for step in range(1, steps + 1):
+        losses.append(bsm.bsm_ptc_loss_grad(blat, U32, tW[0], tW[1], C, R, E, nb, tG[0], tG[1], ws) / nb)
+        for k in range(2):
+            bsm.bsm_ptc_adam_step(tW[k], tG[k], tm[k], tv[k], lr, step)
+    return tW, losses
+
+
+def test_training_lowers_the_loss():
+    dims = (4, 4, 4, 4)
+    blat = bsm.lattice(dims, 3, bsm.FUND, -0.2, (np.pi, 0, 0, 0))
+    U = fields.gauge_field(dims, 3, "smooth", seed=20, eps=0.4)
+    U64, U32 = gpu_links(blat, U, bsm.F64), gpu_links(blat, U, bsm.F32)
+    _, losses = train(blat, U64, U32, C=4, steps=150, nb=4, seed=21)
+    assert np.all(np.isfinite(losses))
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+
+
+def fgcr(blat, U64, U32, b_dev, opts, W=(None, None)):
+    x = zeros_field(blat, bsm.FIELD_SPINOR, bsm.F64)
+    ws = torch.empty(bsm.bsm_fgcr_workspace_bytes(blat, opts), dtype=torch.uint8, device="cuda")
+    st, stats = bsm.bsm_fgcr_solve(blat, U64, U32, W[0], W[1], b_dev, x, opts, ws, raise_on_error=False)
+    return st, stats, x
+
+
+def test_fgcr_without_preconditioner_matches_oracle():
+    dims, N = (4, 4, 4, 4), 2
+    olat, blat = lats(dims, N, bsm.FUND, (np.pi, 0, 0, 0))
+    U = fields.gauge_field(dims, N, "haar", seed=22)
+    R = orc.links_to_rep(olat, U)
+    b = fields.gaussian_spinor(dims, N, 23)
+    x_ref, it_ref, res_ref = ptc.fgcr(lambda v: orc.dirac(olat, R, v), lambda r: r, b, tol=1e-10, restart=8)
+    st, stats, x = fgcr(blat, gpu_links(blat, U, bsm.F64), None, gpu_spinor(blat, b, bsm.F64),
+                        bsm.fgcr_opts(tol=1e-10, restart=8))
+    assert st == bsm.OK
+    assert abs(stats.iters - it_ref) <= 2, (stats.iters, it_ref)
+    assert stats.true_res <= 2e-10
+    xg = to_canon(blat, x, bsm.F64)
+    assert rel(xg, x_ref) < 1e-8
+    assert rel(orc.dirac(olat, R, xg), b) < 2e-10
+
+
+@pytest.mark.parametrize("prec", [bsm.F32, bsm.BF16], ids=["f32", "bf16"])
+def test_fgcr_with_ptc_preconditioner_converges_faster(prec):
+    dims, N = (4, 4, 4, 8), 3
+    olat, blat = lats(dims, N, bsm.FUND, (np.pi, 0, 0, 0), m0=0.05)
+    U = fields.gauge_field(dims, N, "smooth", seed=24, eps=0.4)
+    R = orc.links_to_rep(olat, U)
+    U64, U32 = gpu_links(blat, U, bsm.F64), gpu_links(blat, U, bsm.F32)
+    b = fields.gaussian_spinor(dims, N, 25)
+    bd = gpu_spinor(blat, b, bsm.F64)
+    st0, s0, x0 = fgcr(blat, U64, None, bd, bsm.fgcr_opts(tol=1e-10, restart=16))
+    W1, W2 = neumann_weights(olat.m0)
+    st1, s1, x1 = fgcr(blat, U64, U32, bd,
+                       bsm.fgcr_opts(tol=1e-10, restart=16, precond=bsm.FGCR_PTC, ptc_prec=prec, channels=2),
+                       (dev_c64(W1), dev_c64(W2)))
+    assert st0 == bsm.OK and st1 == bsm.OK
+    assert s1.true_res <= 2e-10
+    assert s1.iters < s0.iters, (s1.iters, s0.iters)
+    x = to_canon(blat, x1, bsm.F64)
+    assert rel(orc.dirac(olat, R, x), b) < 2e-10
+    assert rel(x, to_canon(blat, x0, bsm.F64)) < 1e-8
+
+
+def test_fgcr_statuses():
+    dims, N = (4, 4, 4, 4), 2
+    _, blat = lats(dims, N, bsm.FUND, (0, 0, 0, 0))
+    U64 = gpu_links(blat, fields.gauge_field(dims, N, "haar", seed=26), bsm.F64)
+    b = fields.gaussian_spinor(dims, N, 27)
+    st, stats, _ = fgcr(blat, U64, None, gpu_spinor(blat, b, bsm.F64), bsm.fgcr_opts(tol=1e-12, max_iter=2))
+    assert st == bsm.ENOCONV and stats.iters == 2
+    st, stats, x = fgcr(blat, U64, None, zeros_field(blat, bsm.FIELD_SPINOR, bsm.F64), bsm.fgcr_opts())
+    assert st == bsm.OK and stats.iters == 0 and float(x.abs().max()) == 0.0
+    bn = b.copy()
+    bn[3, 1, 0] = np.nan
+    st, _, _ = fgcr(blat, U64, None, gpu_spinor(blat, bn, bsm.F64), bsm.fgcr_opts())
+    assert st == bsm.ENAN

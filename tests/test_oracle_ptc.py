@@ -71,3 +71,31 @@ def test_fgcr_identity_and_exact_preconditioners():
     Minv = np.linalg.inv(M)
     x1, it1, res1 = ptc.fgcr(D, lambda r: (Minv @ r.reshape(-1)).reshape(r.shape), b, tol=1e-12)
     assert it1 == 1 and res1 < 1e-12
+
+
+def test_two_layers_compose_the_degree_two_neumann_polynomial():
+    """Two layers (1 -> 2 -> 1 channels) with hand-set weights give
+    M = (1 + K + K^2)/A, K = H/(2A) = (A - D)/A: the truncated series of
+    D^{-1}.  Checked with the oracle's D only, on a lattice with phases."""
+    dims, N = (4, 2, 4, 2), 3
+    lat = orc.Lattice(dims, N, orc.FUND, -0.3, (np.pi, 0.2, 0, 0))
+    R = orc.links_to_rep(lat, fields.gauge_field(dims, N, "haar", seed=31))
+    A = 4.0 + lat.m0
+    W1 = np.zeros((9, 1, 4, 2, 4), np.complex128)
+    W2 = np.zeros((9, 2, 4, 1, 4), np.complex128)
+    W1[0, 0, :, 0, :] = np.eye(4)
+    W2[0, 0, :, 0, :] = W2[0, 1, :, 0, :] = np.eye(4) / A
+    for mu in range(4):
+        g = orc.gamma(mu)
+        for k, P in ((1 + 2 * mu, np.eye(4) - g), (2 + 2 * mu, np.eye(4) + g)):
+            W1[k, 0, :, 1, :] = (P / (2 * A)).T
+            W2[k, 1, :, 0, :] = (P / (2 * A * A)).T
+    psi = fields.gaussian_spinor(dims, N, 32)
+    out = ptc.ptc_layer(lat, R, ptc.ptc_layer(lat, R, psi[:, None], W1), W2)[:, 0]
+    K = lambda v: (A * v - orc.dirac(lat, R, v)) / A
+    Kp = K(psi)
+    want = (psi + Kp + K(Kp)) / A
+    assert np.linalg.norm(out - want) / np.linalg.norm(want) < 1e-14
+    # and D M = 1 - K^3 (the residual operator of the truncation)
+    res = orc.dirac(lat, R, out) - psi
+    assert np.linalg.norm(res + K(K(Kp))) / np.linalg.norm(psi) < 1e-13

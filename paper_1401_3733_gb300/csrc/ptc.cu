@@ -26,6 +26,11 @@
 
 namespace bsm {
 
+bool ptc_fused_supported(int C);
+size_t ptc_fused_weight_bytes(int C);
+int ptc_fused_apply(const char* links, size_t link_block, int d, int C, const void* F, const void* W1,
+                    const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, cudaStream_t s);
+
 namespace {
 
 constexpr int kPtcThreads = 128;
@@ -55,8 +60,10 @@ __device__ __forceinline__ long long ptc_row(const Geom& g, int b, int p, int i,
   return (((long long)b * 2 + p) * g.Vh + i) * d + c;
 }
 
-// X[row(x, c)][(k C + ch) 4 + s] = (T_k F_ch)(x)[s][c]; thread per (b, p, i, ch)
-template <int D, bool BF>
+// X[row(x, c)][(k C + ch) 4 + s] = (T_k F_ch)(x)[s][c]; thread per (b, p, i, ch).
+// ADJ: the adjoint transports instead, T_{+mu}^+ F(x) = U_mu(x-mu)^+ F(x-mu)
+// in slot 1 + 2 mu and T_{-mu}^+ F(x) = U_mu(x) F(x+mu) in slot 2 + 2 mu.
+template <int D, bool BF, bool ADJ>
 __global__ void __launch_bounds__(kPtcThreads) ptc_transport_kernel(const char* __restrict__ links,
                                                                     size_t link_block, const float2* __restrict__ F,
                                                                     void* __restrict__ X, Geom g, int nb, int C) {
@@ -78,7 +85,6 @@ __global__ void __launch_bounds__(kPtcThreads) ptc_transport_kernel(const char* 
     if (BF) reinterpret_cast<unsigned int*>(X)[e] = f2_to_bf2(v.re, v.im);
     else reinterpret_cast<float2*>(X)[e] = make_float2(v.re, v.im);
   };
-  // k = 0: the field itself
   for (int c = 0; c < D; ++c)
     for (int s = 0; s < 4; ++s) {
       const float2 v = F[ptc_row(g, b, p, i, D, c) * rowF + ch * 4 + s];
@@ -93,7 +99,8 @@ __global__ void __launch_bounds__(kPtcThreads) ptc_transport_kernel(const char* 
       for (int bb = 0; bb < D; ++bb) L::load(lt, mu, a * D + bb, Uf[a][bb], Ub[a][bb]);
 #pragma unroll
     for (int fb = 0; fb < 2; ++fb) {
-      const int n = fb ? nb_[mu] : nf[mu];
+      const bool back = ADJ ? fb == 0 : fb == 1;  // through Ub from x - mu, else through Uf from x + mu
+      const int n = back ? nb_[mu] : nf[mu];
       cx<float> in[4][D];
       for (int c = 0; c < D; ++c)
         for (int s = 0; s < 4; ++s) {
@@ -103,25 +110,23 @@ __global__ void __launch_bounds__(kPtcThreads) ptc_transport_kernel(const char* 
       for (int s = 0; s < 4; ++s)
         for (int a = 0; a < D; ++a) {
           cx<float> w = cmake(0.f, 0.f);
-          for (int bb = 0; bb < D; ++bb) cmac(w, fb ? Ub[a][bb] : Uf[a][bb], in[s][bb]);
+          for (int bb = 0; bb < D; ++bb) cmac(w, back ? Ub[a][bb] : Uf[a][bb], in[s][bb]);
           put(1 + 2 * mu + fb, a, s, w);
         }
     }
   }
 }
 
-// G_F(y) = G_X[y][0] + sum_mu [ Ub(y) G_X[y - mu][1 + 2mu] + Uf(y) G_X[y + mu][2 + 2mu] ]
+// out(x)[o][s] = sum_k (T_k Z_{k,o})(x)[s] with Z[row][(k Co + o) 4 + s]; thread per (b, p, i, o)
 template <int D>
-__global__ void __launch_bounds__(kPtcThreads) ptc_transport_adj_kernel(const char* __restrict__ links,
-                                                                        size_t link_block,
-                                                                        const float2* __restrict__ GX,
-                                                                        float2* __restrict__ GF, Geom g, int nb,
-                                                                        int C) {
+__global__ void __launch_bounds__(kPtcThreads) ptc_stencil_kernel(const char* __restrict__ links,
+                                                                  size_t link_block, const float2* __restrict__ Z,
+                                                                  float2* __restrict__ out, Geom g, int nb, int Co) {
   const long long t = blockIdx.x * (long long)kPtcThreads + threadIdx.x;
-  const long long total = (long long)nb * 2 * g.Vh * C;
+  const long long total = (long long)nb * 2 * g.Vh * Co;
   if (t >= total) return;
-  const int ch = (int)(t % C);
-  const long long site = t / C;
+  const int o = (int)(t % Co);
+  const long long site = t / Co;
   const int i = (int)(site % g.Vh);
   const int p = (int)((site / g.Vh) % 2);
   const int b = (int)(site / (2LL * g.Vh));
@@ -129,11 +134,11 @@ __global__ void __launch_bounds__(kPtcThreads) ptc_transport_adj_kernel(const ch
   eo_neighbours(g, i, p, nf, nb_);
   using L = LinkIO<F32, D, false>;
   const auto* lt = L::tile_ptr(links + (size_t)p * link_block, i);
-  const int rowF = C * 4, rowX = 9 * C * 4;
+  const int rowZ = 9 * Co * 4, rowO = Co * 4;
   cx<float> acc[4][D];
   for (int c = 0; c < D; ++c)
     for (int s = 0; s < 4; ++s) {
-      const float2 v = GX[ptc_row(g, b, p, i, D, c) * rowX + (0 * C + ch) * 4 + s];
+      const float2 v = Z[ptc_row(g, b, p, i, D, c) * rowZ + o * 4 + s];
       acc[s][c] = cmake(v.x, v.y);
     }
 #pragma unroll
@@ -145,23 +150,36 @@ __global__ void __launch_bounds__(kPtcThreads) ptc_transport_adj_kernel(const ch
       for (int bb = 0; bb < D; ++bb) L::load(lt, mu, a * D + bb, Uf[a][bb], Ub[a][bb]);
 #pragma unroll
     for (int fb = 0; fb < 2; ++fb) {
-      // fb 0: from y - mu with k = 1 + 2 mu through Ub(y); fb 1: from y + mu with k = 2 + 2 mu through Uf(y)
-      const int n = fb ? nf[mu] : nb_[mu];
+      const int n = fb ? nb_[mu] : nf[mu];
       const int k = 1 + 2 * mu + fb;
       cx<float> in[4][D];
       for (int c = 0; c < D; ++c)
         for (int s = 0; s < 4; ++s) {
-          const float2 v = GX[ptc_row(g, b, 1 - p, n, D, c) * rowX + (k * C + ch) * 4 + s];
+          const float2 v = Z[ptc_row(g, b, 1 - p, n, D, c) * rowZ + (k * Co + o) * 4 + s];
           in[s][c] = cmake(v.x, v.y);
         }
       for (int s = 0; s < 4; ++s)
         for (int a = 0; a < D; ++a)
-          for (int bb = 0; bb < D; ++bb) cmac(acc[s][a], fb ? Uf[a][bb] : Ub[a][bb], in[s][bb]);
+          for (int bb = 0; bb < D; ++bb) cmac(acc[s][a], fb ? Ub[a][bb] : Uf[a][bb], in[s][bb]);
     }
   }
   for (int c = 0; c < D; ++c)
     for (int s = 0; s < 4; ++s)
-      GF[ptc_row(g, b, p, i, D, c) * rowF + ch * 4 + s] = make_float2(acc[s][c].re, acc[s][c].im);
+      out[ptc_row(g, b, p, i, D, c) * rowO + o * 4 + s] = make_float2(acc[s][c].re, acc[s][c].im);
+}
+
+// W (9 Ci 4 x 4 Co, rows (k, i, s), columns (o, t)) <-> Wp (4 Ci x 9 4 Co, rows (i, s),
+// columns (k, o, t)); back = 1 maps Wp to W
+__global__ void ptc_permute_kernel(const float2* __restrict__ src, float2* __restrict__ dst, int Ci, int Co,
+                                   int back) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = 9 * Ci * 4 * 4 * Co;
+  if (e >= n) return;
+  const int col = e % (4 * Co), row = e / (4 * Co);  // W coordinates
+  const int k = row / (Ci * 4), is = row % (Ci * 4);
+  const int ep = is * (9 * 4 * Co) + k * 4 * Co + col;
+  if (back) dst[e] = src[ep];
+  else dst[ep] = src[e];
 }
 
 // FP64 device spinor (one field) <-> PTC one-channel field (FP32); thread per (p, i)
@@ -241,68 +259,97 @@ __global__ void ptc_realify_kernel(const float2* __restrict__ W, __nv_bfloat16* 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-int launch_transport(const OpCtx& c, const void* F, void* X, int nb, int C, bool bf16, cudaStream_t s) {
-  const long long n = (long long)nb * 2 * c.g.Vh * C;
-  const int blocks = (int)((n + kPtcThreads - 1) / kPtcThreads);
+template <int D>
+void transport_t(const OpCtx& c, const void* F, void* X, int nb, int C, bool bf16, bool adj, int blocks,
+                 cudaStream_t s) {
   const float2* f = reinterpret_cast<const float2*>(F);
-#define BSM_PTC_T(DD)                                                                                       \
-  if (c.d == DD) {                                                                                          \
-    if (bf16) ptc_transport_kernel<DD, true><<<blocks, kPtcThreads, 0, s>>>(c.links, c.link_block, f, X, c.g, nb, C); \
-    else ptc_transport_kernel<DD, false><<<blocks, kPtcThreads, 0, s>>>(c.links, c.link_block, f, X, c.g, nb, C);     \
-    return BSM_OK;                                                                                          \
-  }
-  BSM_PTC_T(2)
-  BSM_PTC_T(3)
-#undef BSM_PTC_T
-  return BSM_EUNSUPPORTED;
+  if (adj) ptc_transport_kernel<D, false, true><<<blocks, kPtcThreads, 0, s>>>(c.links, c.link_block, f, X, c.g, nb, C);
+  else if (bf16) ptc_transport_kernel<D, true, false><<<blocks, kPtcThreads, 0, s>>>(c.links, c.link_block, f, X, c.g, nb, C);
+  else ptc_transport_kernel<D, false, false><<<blocks, kPtcThreads, 0, s>>>(c.links, c.link_block, f, X, c.g, nb, C);
 }
 
-int launch_transport_adj(const OpCtx& c, const void* GX, void* GF, int nb, int C, cudaStream_t s) {
+// X = the 9 (adjoint) transports of the C-channel field F (FP32, or BF16 output)
+void launch_transport(const OpCtx& c, const void* F, void* X, int nb, int C, bool bf16, bool adj, cudaStream_t s) {
   const long long n = (long long)nb * 2 * c.g.Vh * C;
   const int blocks = (int)((n + kPtcThreads - 1) / kPtcThreads);
-  const float2* gx = reinterpret_cast<const float2*>(GX);
-  float2* gf = reinterpret_cast<float2*>(GF);
-  if (c.d == 2) ptc_transport_adj_kernel<2><<<blocks, kPtcThreads, 0, s>>>(c.links, c.link_block, gx, gf, c.g, nb, C);
-  else if (c.d == 3) ptc_transport_adj_kernel<3><<<blocks, kPtcThreads, 0, s>>>(c.links, c.link_block, gx, gf, c.g, nb, C);
-  else return BSM_EUNSUPPORTED;
-  return BSM_OK;
+  if (c.d == 2) transport_t<2>(c, F, X, nb, C, bf16, adj, blocks, s);
+  else transport_t<3>(c, F, X, nb, C, bf16, adj, blocks, s);
+}
+
+// out = sum_k T_k Z_k (Co channels)
+void launch_stencil(const OpCtx& c, const void* Z, void* out, int nb, int Co, cudaStream_t s) {
+  const long long n = (long long)nb * 2 * c.g.Vh * Co;
+  const int blocks = (int)((n + kPtcThreads - 1) / kPtcThreads);
+  const float2* z = reinterpret_cast<const float2*>(Z);
+  float2* o = reinterpret_cast<float2*>(out);
+  if (c.d == 2) ptc_stencil_kernel<2><<<blocks, kPtcThreads, 0, s>>>(c.links, c.link_block, z, o, c.g, nb, Co);
+  else ptc_stencil_kernel<3><<<blocks, kPtcThreads, 0, s>>>(c.links, c.link_block, z, o, c.g, nb, Co);
+}
+
+void launch_permute(const void* src, void* dst, int Ci, int Co, bool back, cudaStream_t s) {
+  const int n = 9 * Ci * 4 * 4 * Co;
+  ptc_permute_kernel<<<(n + 127) / 128, 128, 0, s>>>(reinterpret_cast<const float2*>(src),
+                                                      reinterpret_cast<float2*>(dst), Ci, Co, back ? 1 : 0);
 }
 
 constexpr size_t kBlasWs = size_t(32) << 20;
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
-// row-major C(MxN) = A(MxK) B(KxN) with optional conjugate-transposes, complex FP32
-cublasStatus_t cgemm_rm(cublasHandle_t h, bool ah, bool bh, int M, int N, int K, const void* A, int lda,
-                        const void* B, int ldb, void* Cm, int ldc, float beta) {
-  // column-major: C^T (N x M) = op(B)^T op(A)^T
-  const cuComplex one = make_cuComplex(1.f, 0.f), bt = make_cuComplex(beta, 0.f);
+// row-major C(MxN) = op(A) op(B), op = identity or conjugate transpose, complex FP32
+bool cgemm_rm(cublasHandle_t h, bool ah, bool bh, int M, int N, int K, const void* A, int lda, const void* B,
+              int ldb, void* Cm, int ldc) {
+  // column-major view: C^T (N x M) = op(B)^T op(A)^T
+  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
   return cublasCgemm(h, bh ? CUBLAS_OP_C : CUBLAS_OP_N, ah ? CUBLAS_OP_C : CUBLAS_OP_N, N, M, K, &one,
-                     reinterpret_cast<const cuComplex*>(B), ldb, reinterpret_cast<const cuComplex*>(A), lda, &bt,
-                     reinterpret_cast<cuComplex*>(Cm), ldc);
+                     reinterpret_cast<const cuComplex*>(B), ldb, reinterpret_cast<const cuComplex*>(A), lda, &zero,
+                     reinterpret_cast<cuComplex*>(Cm), ldc) == CUBLAS_STATUS_SUCCESS;
+}
+
+// row-major real C(M x N) = A(M x K) B(K x N), A and B BF16, FP32 accumulation, C in ctype
+bool bgemm_rm(cublasHandle_t h, int M, int N, int K, const void* A, const void* B, void* Cm, cudaDataType ctype) {
+  const float one = 1.f, zero = 0.f;
+  return cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, N, M, K, &one, B, CUDA_R_16BF, N, A, CUDA_R_16BF, K, &zero, Cm,
+                      ctype, N, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) == CUBLAS_STATUS_SUCCESS;
+}
+
+// the handle of this device, bound to stream s and to the workspace slice; null on failure
+cublasHandle_t bind_blas(void* blas_ws, cudaStream_t s) {
+  cublasHandle_t h = blas_handle();
+  if (h == nullptr || cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS ||
+      cublasSetWorkspace(h, blas_ws, kBlasWs) != CUBLAS_STATUS_SUCCESS)
+    return nullptr;
+  return h;
 }
 
 }  // namespace
 
+// Layer 1 (1 -> C) transports first: X1 = T(in), rows x 36; Y1 = X1 W1, rows x 4C.
+// Layer 2 (C -> 1) mixes first: Z2 = Y1 W2p, rows x 36 (W2p: W2 permuted to
+// 4C x 36); out = sum_k T_k Z2_k.  Both intermediates of width 9 x 4 are far
+// narrower than the 9 x 4C transports of a C-channel field.
 struct PtcLayout {
-  size_t X1, Y1, X2, W1r, W2r, GY2, GX2, GY1, invn, part, blasws, total;
+  size_t X1, Y1, Z2, W2p, W1r, W2r, Wt, G, GZ2, GY1, GW2p, invn, part, blasws, total;
 };
 
 PtcLayout ptc_layout(const bsm_lattice& L, int C, int nb, bool train) {
   const Geom g = make_geom(L);
   const int d = rep_info(L.N, L.rep).d;
   const size_t rows = (size_t)nb * 2 * g.Vh * d;
+  const size_t c8 = sizeof(float2);
   PtcLayout y{};
   size_t o = 0;
-  y.X1 = o; o = al(o + rows * 9 * 4 * 8);
-  y.Y1 = o; o = al(o + rows * C * 4 * 8);
-  y.X2 = o; o = al(o + rows * 9 * C * 4 * 8);
-  y.W1r = o; o = al(o + (size_t)2 * 36 * 2 * C * 4 * 2);
-  y.W2r = o; o = al(o + (size_t)2 * 36 * C * 2 * 4 * 2);
-  y.GY2 = y.GX2 = y.GY1 = y.invn = y.part = 0;
+  y.X1 = o; o = al(o + rows * 36 * c8);
+  y.Y1 = o; o = al(o + rows * 4 * C * c8);
+  y.Z2 = o; o = al(o + rows * 36 * c8);
+  y.W2p = o; o = al(o + (size_t)4 * C * 36 * c8);
+  y.W1r = o; o = al(o + (size_t)(2 * 36) * (2 * 4 * C) * 2);
+  y.W2r = o; o = al(o + (size_t)(2 * 4 * C) * (2 * 36) * 2);
+  y.Wt = o; o = al(o + ptc_fused_weight_bytes(C));
   if (train) {
-    y.GY2 = o; o = al(o + rows * 4 * 8);
-    y.GX2 = o; o = al(o + rows * 9 * C * 4 * 8);
-    y.GY1 = o; o = al(o + rows * C * 4 * 8);
+    y.G = o; o = al(o + rows * 4 * c8);
+    y.GZ2 = o; o = al(o + rows * 36 * c8);
+    y.GY1 = o; o = al(o + rows * 4 * C * c8);
+    y.GW2p = o; o = al(o + (size_t)4 * C * 36 * c8);
     y.invn = o; o = al(o + (size_t)(nb + 1) * 8);  // 1/|e_b|^2, then the loss
     y.part = o; o = al(o + (size_t)kBlasMaxBlocks * 8);
   }
@@ -321,93 +368,82 @@ int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, cuda
   return BSM_OK;
 }
 
-// out (rows x 4 complex) = layer2(layer1(in)); prec F32 (complex GEMM) or BF16 (realified GEMM)
+// out (rows x 4 complex) = layer2(layer1(in)); prec F32 (complex GEMMs) or BF16 (realified GEMMs)
 int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* in,
               void* out, int nb, int prec, void* ws, cudaStream_t s) {
   const OpCtx c = make_ctx(L, U32, BSM_F32, s);
-  if (c.d != 2 && c.d != 3) return BSM_EUNSUPPORTED;
   const PtcLayout y = ptc_layout(L, C, nb, false);
   char* w = reinterpret_cast<char*>(ws);
   const int rows = (int)((long long)nb * 2 * c.g.Vh * c.d);
-  std::lock_guard<std::mutex> lock(g_blas_mu);
-  cublasHandle_t h = blas_handle();
-  if (h == nullptr || cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS ||
-      cublasSetWorkspace(h, w + y.blasws, kBlasWs) != CUBLAS_STATUS_SUCCESS)
-    return BSM_ECUDA;
   const bool bf = prec == BSM_BF16;
-  int rc;
-  const int K1 = 36, N1 = 4 * C, K2 = 36 * C, N2 = 4;
-  if ((rc = launch_transport(c, in, w + y.X1, nb, 1, bf, s)) != BSM_OK) return rc;
-  cublasStatus_t st;
+  launch_permute(W2, w + y.W2p, C, 1, false, s);
+  // BF16 with a fused kernel for this C: transports and both GEMMs in one pass (no cuBLAS)
+  if (bf && ptc_fused_supported(C))
+    return ptc_fused_apply(c.links, c.link_block, c.d, C, in, W1, w + y.W2p, w + y.Wt, w + y.Z2, out, c.g, nb, s);
+  std::lock_guard<std::mutex> lock(g_blas_mu);
+  cublasHandle_t h = bind_blas(w + y.blasws, s);
+  if (h == nullptr) return BSM_ECUDA;
+  launch_transport(c, in, w + y.X1, nb, 1, bf, false, s);
   if (!bf) {
-    st = cgemm_rm(h, false, false, rows, N1, K1, w + y.X1, K1, W1, N1, w + y.Y1, N1, 0.f);
-    if (st != CUBLAS_STATUS_SUCCESS) return BSM_ECUDA;
-    if ((rc = launch_transport(c, w + y.Y1, w + y.X2, nb, C, false, s)) != BSM_OK) return rc;
-    st = cgemm_rm(h, false, false, rows, N2, K2, w + y.X2, K2, W2, N2, out, N2, 0.f);
+    if (!cgemm_rm(h, false, false, rows, 4 * C, 36, w + y.X1, 36, W1, 4 * C, w + y.Y1, 4 * C) ||
+        !cgemm_rm(h, false, false, rows, 36, 4 * C, w + y.Y1, 4 * C, w + y.W2p, 36, w + y.Z2, 36))
+      return BSM_ECUDA;
   } else {
     __nv_bfloat16* w1r = reinterpret_cast<__nv_bfloat16*>(w + y.W1r);
     __nv_bfloat16* w2r = reinterpret_cast<__nv_bfloat16*>(w + y.W2r);
-    ptc_realify_kernel<<<(K1 * N1 + 127) / 128, 128, 0, s>>>(reinterpret_cast<const float2*>(W1), w1r, K1, N1);
-    ptc_realify_kernel<<<(K2 * N2 + 127) / 128, 128, 0, s>>>(reinterpret_cast<const float2*>(W2), w2r, K2, N2);
-    const float one = 1.f, zero = 0.f;
-    // row-major real C(rows x 2N) = X(rows x 2K) Wr(2K x 2N): column-major C^T = Wr^T X^T
-    st = cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, 2 * N1, rows, 2 * K1, &one, w1r, CUDA_R_16BF, 2 * N1, w + y.X1,
-                      CUDA_R_16BF, 2 * K1, &zero, w + y.Y1, CUDA_R_32F, 2 * N1, CUBLAS_COMPUTE_32F,
-                      CUBLAS_GEMM_DEFAULT);
-    if (st != CUBLAS_STATUS_SUCCESS) return BSM_ECUDA;
-    if ((rc = launch_transport(c, w + y.Y1, w + y.X2, nb, C, true, s)) != BSM_OK) return rc;
-    st = cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, 2 * N2, rows, 2 * K2, &one, w2r, CUDA_R_16BF, 2 * N2, w + y.X2,
-                      CUDA_R_16BF, 2 * K2, &zero, out, CUDA_R_32F, 2 * N2, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+    ptc_realify_kernel<<<(36 * 4 * C + 127) / 128, 128, 0, s>>>(reinterpret_cast<const float2*>(W1), w1r, 36, 4 * C);
+    ptc_realify_kernel<<<(4 * C * 36 + 127) / 128, 128, 0, s>>>(reinterpret_cast<const float2*>(w + y.W2p), w2r,
+                                                                4 * C, 36);
+    // Y1 in BF16 (it is only an operand of the second GEMM), Z2 in FP32
+    if (!bgemm_rm(h, rows, 2 * 4 * C, 2 * 36, w + y.X1, w1r, w + y.Y1, CUDA_R_16BF) ||
+        !bgemm_rm(h, rows, 2 * 36, 2 * 4 * C, w + y.Y1, w2r, w + y.Z2, CUDA_R_32F))
+      return BSM_ECUDA;
   }
-  return st == CUBLAS_STATUS_SUCCESS ? BSM_OK : BSM_ECUDA;
+  launch_stencil(c, w + y.Z2, out, nb, 1, s);
+  return BSM_OK;
 }
 
 // loss = sum_b |M(r_b) - e_b|^2 / |e_b|^2 and its gradients G_W1, G_W2 (FP32)
 int ptc_loss_grad(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* r,
                   const void* e, int nb, void* GW1, void* GW2, double* loss, void* ws, cudaStream_t s) {
   const OpCtx c = make_ctx(L, U32, BSM_F32, s);
-  if (c.d != 2 && c.d != 3) return BSM_EUNSUPPORTED;
   const PtcLayout y = ptc_layout(L, C, nb, true);
   char* w = reinterpret_cast<char*>(ws);
   const int rows = (int)((long long)nb * 2 * c.g.Vh * c.d);
-  const int K1 = 36, N1 = 4 * C, K2 = 36 * C, N2 = 4;
-  int rc;
+  double l = 0.0;
   {
     std::lock_guard<std::mutex> lock(g_blas_mu);
-    cublasHandle_t h = blas_handle();
-    if (h == nullptr || cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS ||
-        cublasSetWorkspace(h, w + y.blasws, kBlasWs) != CUBLAS_STATUS_SUCCESS)
+    cublasHandle_t h = bind_blas(w + y.blasws, s);
+    if (h == nullptr) return BSM_ECUDA;
+    // forward, keeping X1, Y1 and Z2; the output goes to G's slot
+    launch_permute(W2, w + y.W2p, C, 1, false, s);
+    launch_transport(c, r, w + y.X1, nb, 1, false, false, s);
+    if (!cgemm_rm(h, false, false, rows, 4 * C, 36, w + y.X1, 36, W1, 4 * C, w + y.Y1, 4 * C) ||
+        !cgemm_rm(h, false, false, rows, 36, 4 * C, w + y.Y1, 4 * C, w + y.W2p, 36, w + y.Z2, 36))
       return BSM_ECUDA;
-    // forward, keeping X1, Y1, X2; Y2 goes to GY2's slot first
-    if ((rc = launch_transport(c, r, w + y.X1, nb, 1, false, s)) != BSM_OK) return rc;
-    if (cgemm_rm(h, false, false, rows, N1, K1, w + y.X1, K1, W1, N1, w + y.Y1, N1, 0.f) != CUBLAS_STATUS_SUCCESS)
-      return BSM_ECUDA;
-    if ((rc = launch_transport(c, w + y.Y1, w + y.X2, nb, C, false, s)) != BSM_OK) return rc;
-    if (cgemm_rm(h, false, false, rows, N2, K2, w + y.X2, K2, W2, N2, w + y.GY2, N2, 0.f) != CUBLAS_STATUS_SUCCESS)
-      return BSM_ECUDA;
-    // loss and G_Y2 (in place over Y2)
+    launch_stencil(c, w + y.Z2, w + y.G, nb, 1, s);
+    // loss and G = dloss/dout (in place)
     const long long per = (long long)rows / nb * 4, n = (long long)rows * 4;
-    ptc_inv_norm_kernel<<<nb, kBlasThreads, 0, s>>>(reinterpret_cast<const float2*>(e), per,
-                                                     reinterpret_cast<double*>(w + y.invn));
+    double* invn = reinterpret_cast<double*>(w + y.invn);
+    double* part = reinterpret_cast<double*>(w + y.part);
+    ptc_inv_norm_kernel<<<nb, kBlasThreads, 0, s>>>(reinterpret_cast<const float2*>(e), per, invn);
     const int lb = blas_blocks((size_t)n);
-    ptc_loss_kernel<<<lb, kBlasThreads, 0, s>>>(reinterpret_cast<const float2*>(w + y.GY2),
-                                                reinterpret_cast<const float2*>(e),
-                                                reinterpret_cast<float2*>(w + y.GY2),
-                                                reinterpret_cast<const double*>(w + y.invn), per, n,
-                                                reinterpret_cast<double*>(w + y.part));
-    reduce_launch(reinterpret_cast<double*>(w + y.part), lb, reinterpret_cast<double*>(w + y.invn) + nb, s);
-    double l = 0.0;
-    cudaMemcpyAsync(&l, reinterpret_cast<double*>(w + y.invn) + nb, sizeof(double), cudaMemcpyDeviceToHost, s);
-    // backward: G_W2 = X2^H G_Y2, G_X2 = G_Y2 W2^H, G_Y1 = T^+ G_X2, G_W1 = X1^H G_Y1
-    if (cgemm_rm(h, true, false, K2, N2, rows, w + y.X2, K2, w + y.GY2, N2, GW2, N2, 0.f) != CUBLAS_STATUS_SUCCESS ||
-        cgemm_rm(h, false, true, rows, K2, N2, w + y.GY2, N2, W2, N2, w + y.GX2, K2, 0.f) != CUBLAS_STATUS_SUCCESS)
+    ptc_loss_kernel<<<lb, kBlasThreads, 0, s>>>(reinterpret_cast<const float2*>(w + y.G),
+                                                reinterpret_cast<const float2*>(e), reinterpret_cast<float2*>(w + y.G),
+                                                invn, per, n, part);
+    reduce_launch(part, lb, invn + nb, s);
+    // backward: G_Z2 = T^+ G; G_W2p = Y1^H G_Z2; G_Y1 = G_Z2 W2p^H; G_W1 = X1^H G_Y1
+    launch_transport(c, w + y.G, w + y.GZ2, nb, 1, false, true, s);
+    if (!cgemm_rm(h, true, false, 4 * C, 36, rows, w + y.Y1, 4 * C, w + y.GZ2, 36, w + y.GW2p, 36) ||
+        !cgemm_rm(h, false, true, rows, 4 * C, 36, w + y.GZ2, 36, w + y.W2p, 36, w + y.GY1, 4 * C) ||
+        !cgemm_rm(h, true, false, 36, 4 * C, rows, w + y.X1, 36, w + y.GY1, 4 * C, GW1, 4 * C))
       return BSM_ECUDA;
-    if ((rc = launch_transport_adj(c, w + y.GX2, w + y.GY1, nb, C, s)) != BSM_OK) return rc;
-    if (cgemm_rm(h, true, false, K1, N1, rows, w + y.X1, K1, w + y.GY1, N1, GW1, N1, 0.f) != CUBLAS_STATUS_SUCCESS)
+    launch_permute(w + y.GW2p, GW2, C, 1, true, s);
+    if (cudaMemcpyAsync(&l, invn + nb, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
       return BSM_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return BSM_ECUDA;
-    if (loss) *loss = l;
   }
+  *loss = l;
   return BSM_OK;
 }
 

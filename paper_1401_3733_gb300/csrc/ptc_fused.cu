@@ -1,0 +1,347 @@
+// ptc_fused.cu -- BF16 inference of the parallel-transport preconditioner
+// with the two channel-mixing GEMMs fused into the transport kernel.
+//
+// One block owns 64 consecutive eo sites of one parity (64 d rows of the PTC
+// field).  Stage 1: two threads per site compute the 9 transports of the
+// one-channel input (T_0, and U_mu(x) F(x+mu), U_mu(x-mu)^+ F(x-mu) for two
+// directions each) in FP32 and store them, rounded to BF16 and realified
+// (re, im interleaved), as the A tile X1 (rows x 72, padded to 80) in shared
+// memory.  Stage 2: each warp takes 16-row tiles through
+//     Y1 = X1 W1  (72 -> 8C reals)   and   Z2 = Y1 W2p  (8C -> 72 reals)
+// as mma.sync.m16n8k16 (BF16 x BF16 -> FP32).  The FP32 accumulator
+// fragments of two adjacent 8-column tiles of Y1 are, element for element,
+// the A fragment of one 16-deep k-step of the second GEMM, so Y1 is rounded
+// to BF16 in registers and never stored.  Z2 (rows x 36 complex, BF16) is the
+// only intermediate written to memory; the stencil kernel then forms
+// out = sum_k T_k Z2_k.  The weights come realified and transposed ([n][k],
+// k padded) so that B fragments are conflict-free 32-bit shared loads.
+#include <cuda_bf16.h>
+
+#include "bsm_internal.cuh"
+
+namespace bsm {
+
+namespace {
+
+constexpr int kFusedSites = 64;    // eo sites per block
+constexpr int kFusedThreads = 128;
+constexpr int kXStride = 88;        // bf16 per X1 row in shared memory (72 used, 80 for the MMA k-steps)
+
+template <int C>
+struct FusedShape {
+  static constexpr int N1 = 8 * C;           // Y1 reals per row
+  static constexpr int W1Stride = kXStride;  // W1T row (one Y1 column): 80 k + 8 pad
+  static constexpr int W2Stride = N1 + 8;    // W2T row (one Z2 column): 8C k + 8 pad
+  static constexpr int W1Elems = N1 * W1Stride;
+  static constexpr int W2Elems = 72 * W2Stride;
+};
+
+__device__ __forceinline__ unsigned pack_bf2(float lo, float hi) { return f2_to_bf2(lo, hi); }
+
+__device__ __forceinline__ void mma16816(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// realified, transposed, padded weights (bf16): W1T[n][k] = W1r[k][n], W2T[n][k] = W2pr[k][n]
+template <int C>
+__global__ void fused_prep_kernel(const float2* __restrict__ W1, const float2* __restrict__ W2p,
+                                  __nv_bfloat16* __restrict__ W1T, __nv_bfloat16* __restrict__ W2T) {
+  using S = FusedShape<C>;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  // realified entry (k, n) of a complex K x N matrix M: [[Re, Im], [-Im, Re]] blocks
+  auto real_of = [](const float2* M, int N, int k, int n) {
+    const float2 w = M[(k >> 1) * N + (n >> 1)];
+    if ((k & 1) == 0) return (n & 1) ? w.y : w.x;
+    return (n & 1) ? w.x : -w.y;
+  };
+  if (t < S::W1Elems) {
+    const int n = t / S::W1Stride, k = t % S::W1Stride;
+    W1T[t] = __float2bfloat16_rn(k < 72 ? real_of(W1, 4 * C, k, n) : 0.f);
+  } else if (t < S::W1Elems + S::W2Elems) {
+    const int u = t - S::W1Elems;
+    const int n = u / S::W2Stride, k = u % S::W2Stride;
+    W2T[u] = __float2bfloat16_rn(k < S::N1 ? real_of(W2p, 36, k, n) : 0.f);
+  }
+}
+
+template <int D, int C>
+__global__ void __launch_bounds__(kFusedThreads) fused_kernel(const char* __restrict__ links, size_t link_block,
+                                                               const float2* __restrict__ F,
+                                                               const __nv_bfloat16* __restrict__ W1T,
+                                                               const __nv_bfloat16* __restrict__ W2T,
+                                                               unsigned* __restrict__ Z, Geom g, int bpp) {
+  using S = FusedShape<C>;
+  constexpr int kRows = kFusedSites * D;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __nv_bfloat16* sX = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* sW1 = sX + kRows * kXStride;
+  __nv_bfloat16* sW2 = sW1 + S::W1Elems;
+
+  const int blk = blockIdx.x;
+  const int b = blk / (2 * bpp), p = (blk / bpp) % 2, i0 = (blk % bpp) * kFusedSites;
+  const long long prow0 = ((long long)b * 2 + p) * g.Vh;      // first site row of this (sample, parity)
+  const long long orow0 = ((long long)b * 2 + 1 - p) * g.Vh;  // of the other parity
+
+  // stage 0: weights into shared memory (16-byte copies; both sizes are multiples of 16 bytes)
+  {
+    const uint4* s1 = reinterpret_cast<const uint4*>(W1T);
+    uint4* d1 = reinterpret_cast<uint4*>(sW1);
+    for (int k = threadIdx.x; k < S::W1Elems / 8; k += kFusedThreads) d1[k] = s1[k];
+    const uint4* s2 = reinterpret_cast<const uint4*>(W2T);
+    uint4* d2 = reinterpret_cast<uint4*>(sW2);
+    for (int k = threadIdx.x; k < S::W2Elems / 8; k += kFusedThreads) d2[k] = s2[k];
+  }
+
+  // stage 1: transports -> X1 (bf16, realified) in shared memory
+  {
+    const int sl = threadIdx.x & (kFusedSites - 1), half = threadIdx.x / kFusedSites;
+    const int i = i0 + sl;
+    unsigned* xr[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) xr[c] = reinterpret_cast<unsigned*>(sX + (sl * D + c) * kXStride);
+    if (i < g.Vh) {
+      int nf[4], nb_[4];
+      eo_neighbours(g, i, p, nf, nb_);
+      using L = LinkIO<F32, D, false>;
+      const auto* lt = L::tile_ptr(links + (size_t)p * link_block, i);
+      if (half == 0) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const float4* q = reinterpret_cast<const float4*>(F + ((prow0 + i) * D + c) * 4);
+          const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+          xr[c][0] = pack_bf2(v0.x, v0.y);
+          xr[c][1] = pack_bf2(v0.z, v0.w);
+          xr[c][2] = pack_bf2(v1.x, v1.y);
+          xr[c][3] = pack_bf2(v1.z, v1.w);
+        }
+      }
+#pragma unroll
+      for (int m2 = 0; m2 < 2; ++m2) {
+        const int mu = 2 * half + m2;
+        cx<float> Uf[D][D], Ub[D][D];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int bb = 0; bb < D; ++bb) L::load(lt, mu, a * D + bb, Uf[a][bb], Ub[a][bb]);
+#pragma unroll
+        for (int fb = 0; fb < 2; ++fb) {
+          const int n = fb ? nb_[mu] : nf[mu];
+          cx<float> in[4][D];
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            const float4* q = reinterpret_cast<const float4*>(F + ((orow0 + n) * D + c) * 4);
+            const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+            in[0][c] = cmake(v0.x, v0.y);
+            in[1][c] = cmake(v0.z, v0.w);
+            in[2][c] = cmake(v1.x, v1.y);
+            in[3][c] = cmake(v1.z, v1.w);
+          }
+          const int k = 1 + 2 * mu + fb;
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+              cx<float> w = cmake(0.f, 0.f);
+#pragma unroll
+              for (int bb = 0; bb < D; ++bb) cmac(w, fb ? Ub[a][bb] : Uf[a][bb], in[s][bb]);
+              xr[a][k * 4 + s] = pack_bf2(w.re, w.im);
+            }
+        }
+      }
+    } else {
+      // rows of sites past the end of the parity block: zero (their outputs are not stored)
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        for (int e = half; e < 36; e += 2) xr[c][e] = 0u;
+    }
+    if (half == 1) {
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int e = 36; e < 40; ++e) xr[c][e] = 0u;  // k padding 72..79
+    }
+  }
+  __syncthreads();
+
+  // stage 2: per warp, D row tiles of 16 through both GEMMs
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gq = lane >> 2, q = lane & 3;
+  const unsigned* X32 = reinterpret_cast<const unsigned*>(sX);
+  const unsigned* W132 = reinterpret_cast<const unsigned*>(sW1);
+  const unsigned* W232 = reinterpret_cast<const unsigned*>(sW2);
+  constexpr int xs = kXStride / 2, w1s = S::W1Stride / 2, w2s = S::W2Stride / 2;
+  const int valid_rows = (g.Vh - i0 < kFusedSites ? g.Vh - i0 : kFusedSites) * D;
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) {
+    const int r0 = (warp * D + j) * 16;
+    float acc1[C][4];
+#pragma unroll
+    for (int n = 0; n < C; ++n) acc1[n][0] = acc1[n][1] = acc1[n][2] = acc1[n][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 5; ++kk) {
+      unsigned a[4];
+      a[0] = X32[(r0 + gq) * xs + kk * 8 + q];
+      a[1] = X32[(r0 + gq + 8) * xs + kk * 8 + q];
+      a[2] = X32[(r0 + gq) * xs + kk * 8 + 4 + q];
+      a[3] = X32[(r0 + gq + 8) * xs + kk * 8 + 4 + q];
+#pragma unroll
+      for (int n = 0; n < C; ++n)
+        mma16816(acc1[n], a, W132[(n * 8 + gq) * w1s + kk * 8 + q], W132[(n * 8 + gq) * w1s + kk * 8 + 4 + q]);
+    }
+    // Y1 accumulators -> A fragments of the second GEMM (two 8-column tiles per 16-deep k-step)
+    unsigned a2[C / 2][4];
+#pragma unroll
+    for (int t = 0; t < C / 2; ++t) {
+      a2[t][0] = pack_bf2(acc1[2 * t][0], acc1[2 * t][1]);
+      a2[t][1] = pack_bf2(acc1[2 * t][2], acc1[2 * t][3]);
+      a2[t][2] = pack_bf2(acc1[2 * t + 1][0], acc1[2 * t + 1][1]);
+      a2[t][3] = pack_bf2(acc1[2 * t + 1][2], acc1[2 * t + 1][3]);
+    }
+    float acc2[9][4];
+#pragma unroll
+    for (int n = 0; n < 9; ++n) acc2[n][0] = acc2[n][1] = acc2[n][2] = acc2[n][3] = 0.f;
+#pragma unroll
+    for (int t = 0; t < C / 2; ++t)
+#pragma unroll
+      for (int n = 0; n < 9; ++n)
+        mma16816(acc2[n], a2[t], W232[(n * 8 + gq) * w2s + t * 8 + q], W232[(n * 8 + gq) * w2s + t * 8 + 4 + q]);
+    // Z2 rows: (prow0 + i0) * D + local row; complex column n*4 + q is (re, im) = accumulator pair
+    const long long zr = (prow0 + i0) * D + r0;
+    if (r0 + gq < valid_rows) {
+#pragma unroll
+      for (int n = 0; n < 9; ++n) Z[(zr + gq) * 36 + n * 4 + q] = pack_bf2(acc2[n][0], acc2[n][1]);
+    }
+    if (r0 + gq + 8 < valid_rows) {
+#pragma unroll
+      for (int n = 0; n < 9; ++n) Z[(zr + gq + 8) * 36 + n * 4 + q] = pack_bf2(acc2[n][2], acc2[n][3]);
+    }
+  }
+}
+
+// out(x)[s] = sum_k (T_k Z_k)(x)[s] with Z in BF16 (rows x 36 complex, slot k = 4 spins, 16 bytes)
+template <int D>
+__global__ void __launch_bounds__(128) stencil_bf16_kernel(const char* __restrict__ links, size_t link_block,
+                                                           const uint4* __restrict__ Z, float2* __restrict__ out,
+                                                           Geom g, int nb) {
+  const long long t = blockIdx.x * 128LL + threadIdx.x;
+  if (t >= (long long)nb * 2 * g.Vh) return;
+  const int i = (int)(t % g.Vh);
+  const int p = (int)((t / g.Vh) % 2);
+  const int b = (int)(t / (2LL * g.Vh));
+  const long long prow = ((long long)b * 2 + p) * g.Vh, orow = ((long long)b * 2 + 1 - p) * g.Vh;
+  int nf[4], nb_[4];
+  eo_neighbours(g, i, p, nf, nb_);
+  using L = LinkIO<F32, D, false>;
+  const auto* lt = L::tile_ptr(links + (size_t)p * link_block, i);
+  auto unpack = [](unsigned u) {
+    const float2 f = bf2_to_f2(u);
+    return cmake(f.x, f.y);
+  };
+  cx<float> acc[4][D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const uint4 v = __ldg(Z + ((prow + i) * D + c) * 9);
+    acc[0][c] = unpack(v.x);
+    acc[1][c] = unpack(v.y);
+    acc[2][c] = unpack(v.z);
+    acc[3][c] = unpack(v.w);
+  }
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    cx<float> Uf[D][D], Ub[D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int bb = 0; bb < D; ++bb) L::load(lt, mu, a * D + bb, Uf[a][bb], Ub[a][bb]);
+#pragma unroll
+    for (int fb = 0; fb < 2; ++fb) {
+      const int n = fb ? nb_[mu] : nf[mu];
+      const int k = 1 + 2 * mu + fb;
+      cx<float> in[4][D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const uint4 v = __ldg(Z + ((orow + n) * D + c) * 9 + k);
+        in[0][c] = unpack(v.x);
+        in[1][c] = unpack(v.y);
+        in[2][c] = unpack(v.z);
+        in[3][c] = unpack(v.w);
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int bb = 0; bb < D; ++bb) cmac(acc[s][a], fb ? Ub[a][bb] : Uf[a][bb], in[s][bb]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    float4* o = reinterpret_cast<float4*>(out + ((prow + i) * D + c) * 4);
+    o[0] = make_float4(acc[0][c].re, acc[0][c].im, acc[1][c].re, acc[1][c].im);
+    o[1] = make_float4(acc[2][c].re, acc[2][c].im, acc[3][c].re, acc[3][c].im);
+  }
+}
+
+template <int D, int C>
+size_t fused_smem() {
+  return (size_t)(kFusedSites * D * kXStride + FusedShape<C>::W1Elems + FusedShape<C>::W2Elems) * 2;
+}
+
+template <int D, int C>
+int fused_launch(const char* links, size_t link_block, const void* F, const void* W1, const void* W2p, void* W1T,
+                 void* W2T, void* Z, void* out, const Geom& g, int nb, cudaStream_t s) {
+  using S = FusedShape<C>;
+  const int n = S::W1Elems + S::W2Elems;
+  fused_prep_kernel<C><<<(n + 255) / 256, 256, 0, s>>>(reinterpret_cast<const float2*>(W1),
+                                                       reinterpret_cast<const float2*>(W2p),
+                                                       reinterpret_cast<__nv_bfloat16*>(W1T),
+                                                       reinterpret_cast<__nv_bfloat16*>(W2T));
+  const size_t smem = fused_smem<D, C>();
+  if (cudaFuncSetAttribute(fused_kernel<D, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return BSM_ECUDA;
+  const int bpp = (g.Vh + kFusedSites - 1) / kFusedSites;
+  fused_kernel<D, C><<<nb * 2 * bpp, kFusedThreads, smem, s>>>(
+      links, link_block, reinterpret_cast<const float2*>(F), reinterpret_cast<const __nv_bfloat16*>(W1T),
+      reinterpret_cast<const __nv_bfloat16*>(W2T), reinterpret_cast<unsigned*>(Z), g, bpp);
+  const long long sites = (long long)nb * 2 * g.Vh;
+  stencil_bf16_kernel<D><<<(int)((sites + 127) / 128), 128, 0, s>>>(
+      links, link_block, reinterpret_cast<const uint4*>(Z), reinterpret_cast<float2*>(out), g, nb);
+  return BSM_OK;
+}
+
+template <int D>
+int fused_dispatch_c(int C, const char* links, size_t lb, const void* F, const void* W1, const void* W2p, void* W1T,
+                     void* W2T, void* Z, void* out, const Geom& g, int nb, cudaStream_t s) {
+  switch (C) {
+    case 2: return fused_launch<D, 2>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, s);
+    case 4: return fused_launch<D, 4>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, s);
+    case 8: return fused_launch<D, 8>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, s);
+    case 12: return fused_launch<D, 12>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, s);
+    default: return BSM_EUNSUPPORTED;
+  }
+}
+
+}  // namespace
+
+// hidden-channel counts with a fused BF16 kernel
+bool ptc_fused_supported(int C) { return C == 2 || C == 4 || C == 8 || C == 12; }
+
+// bytes of the realified weights W1T + W2T (bf16) for C channels
+size_t ptc_fused_weight_bytes(int C) { return (size_t)(8 * C * kXStride + 72 * (8 * C + 8)) * 2; }
+
+// Z: rows x 36 BF16 complex (4 bytes each); W1T/W2T: ptc_fused_weight_bytes(C), 16-byte aligned
+int ptc_fused_apply(const char* links, size_t link_block, int d, int C, const void* F, const void* W1,
+                    const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, cudaStream_t s) {
+  void* W1T = Wt;
+  void* W2T = reinterpret_cast<char*>(Wt) + (size_t)8 * C * kXStride * 2;
+  if (d == 2) return fused_dispatch_c<2>(C, links, link_block, F, W1, W2p, W1T, W2T, Z, out, g, nb, s);
+  if (d == 3) return fused_dispatch_c<3>(C, links, link_block, F, W1, W2p, W1T, W2T, Z, out, g, nb, s);
+  return BSM_EUNSUPPORTED;
+}
+
+}  // namespace bsm

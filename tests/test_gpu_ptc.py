@@ -90,16 +90,20 @@ def neumann_weights(m0):
     return W1.reshape(36, 8), W2.reshape(72, 4)
 
 
+@pytest.mark.parametrize("C", [5, 12], ids=["C5", "C12"])
 @pytest.mark.parametrize("prec,tol", [(bsm.F32, 1e-5), (bsm.BF16, 2e-2)], ids=["f32", "bf16"])
 @pytest.mark.parametrize("case", CASES, ids=CASE_IDS)
-def test_ptc_net_matches_oracle_layers(case, prec, tol):
+def test_ptc_net_matches_oracle_layers(case, prec, tol, C):
+    """C = 12 in BF16 runs the fused transport + two-GEMM kernel, C = 5 the
+    transport kernels and library GEMMs; the lattices give parity blocks of
+    96, 64 and 32 sites against the fused kernel's 64-site tiles (ragged,
+    exact and partial), and two samples per call."""
     dims, N, rep, phase = case
     olat, blat = lats(dims, N, rep, phase)
     U = fields.gauge_field(dims, N, "haar", seed=11)
     R = orc.links_to_rep(olat, U)
     U32 = gpu_links(blat, U, bsm.F32)
     rng = np.random.default_rng(12)
-    C = 5
     W1, W2 = rand_c(rng, (36, 4 * C), 0.3), rand_c(rng, (36 * C, 4), 0.1)
     psis = [fields.gaussian_spinor(dims, olat.d, 13 + b) for b in range(2)]
     got = gpu_net(blat, U32, W1, W2, C, psis, prec)
@@ -108,7 +112,8 @@ def test_ptc_net_matches_oracle_layers(case, prec, tol):
         assert rel(got[b], want) < tol
 
 
-def test_ptc_net_with_neumann_weights_is_the_polynomial_of_d():
+@pytest.mark.parametrize("prec,tol", [(bsm.F32, 1e-5), (bsm.BF16, 1e-2)], ids=["f32", "bf16-fused"])
+def test_ptc_net_with_neumann_weights_is_the_polynomial_of_d(prec, tol):
     dims, N, rep, phase = CASES[0]
     olat, blat = lats(dims, N, rep, phase, m0=-0.3)
     U = fields.gauge_field(dims, N, "haar", seed=14)
@@ -119,8 +124,8 @@ def test_ptc_net_with_neumann_weights_is_the_polynomial_of_d():
     Kpsi = K(psi)
     want = (psi + Kpsi + K(Kpsi)) / A
     W1, W2 = neumann_weights(olat.m0)
-    got = gpu_net(blat, gpu_links(blat, U, bsm.F32), W1, W2, 2, [psi], bsm.F32)[0]
-    assert rel(got, want) < 1e-5
+    got = gpu_net(blat, gpu_links(blat, U, bsm.F32), W1, W2, 2, [psi], prec)[0]
+    assert rel(got, want) < tol
 
 
 def _loss_oracle(olat, R, rs, es, W1, W2, C):

@@ -69,8 +69,9 @@
  * the caller allocates and frees every buffer (workspace included) and the
  * library keeps no pointer past a call.  Buffers must be 16-byte aligned.
  * `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
- * Every call is asynchronous on `stream` except bsm_cg_solve, which
- * synchronises `stream` before it returns.  Calls on different streams may
+ * Every call is asynchronous on `stream` except bsm_cg_solve,
+ * bsm_fgcr_solve and bsm_ptc_loss_grad, which synchronise `stream` before
+ * they return.  Calls on different streams may
  * run concurrently if they share no output buffer.
  *
  * Errors: every call validates its arguments before it launches anything and
@@ -93,9 +94,9 @@ typedef enum {
   BSM_EUNSUPPORTED = -2,  /* (N, representation, precision, phase) not instantiated */
   BSM_ECUDA = -3,         /* CUDA launch or runtime error */
   BSM_EWORKSPACE = -4,    /* workspace smaller than bsm_workspace_bytes() */
-  BSM_ENOCONV = -5,       /* CG reached max_iter before the tolerance */
+  BSM_ENOCONV = -5,       /* a solver reached max_iter before the tolerance */
   BSM_EBREAKDOWN = -6,    /* CG breakdown: <p, M p> <= 0 */
-  BSM_ENAN = -7,          /* NaN or Inf met in a CG reduction */
+  BSM_ENAN = -7,          /* NaN or Inf met in a solver reduction */
   BSM_ETIMEOUT = -8       /* a bounded device-side wait gave up */
 } bsm_status;
 
@@ -362,7 +363,12 @@ int bsm_ptc_adam_step(void *W, const void *G, void *m, void *v, int64_t n, doubl
 
 /* Flexible GCR on the full operator, D x = b (FP64), with M = identity
  * (precond BSM_FGCR_NONE) or the network above (BSM_FGCR_PTC, in
- * ptc_prec BSM_F32 or BSM_BF16). */
+ * ptc_prec BSM_F32 or BSM_BF16).  prec_inner BSM_F64: every vector and D in
+ * FP64, restarted every `restart` directions.  BSM_F32: each restart cycle
+ * solves D e = r in FP32 (FP32 links and vectors, FP64 reductions) from
+ * e = 0 until |r32| <= inner_tol |r| or `restart` directions, then
+ * x += e and r = b - D x are formed in FP64 (the stopping test always uses
+ * this FP64 residual). */
 typedef enum { BSM_FGCR_NONE = 0, BSM_FGCR_PTC = 1 } bsm_fgcr_precond;
 typedef struct {
   double tol;        /* stop when |r| <= tol |b| (iterated residual) */
@@ -371,16 +377,20 @@ typedef struct {
   int32_t precond;   /* bsm_fgcr_precond */
   int32_t ptc_prec;  /* BSM_F32 or BSM_BF16 */
   int32_t channels;  /* hidden channels C of W1, W2 */
+  int32_t prec_inner;/* BSM_F64 or BSM_F32 */
+  double inner_tol;  /* BSM_F32 cycles: residual reduction per cycle (0 -> 0.1) */
 } bsm_fgcr_opts;
 typedef struct {
-  int32_t iters;
+  int32_t iters;     /* directions (preconditioner applications) in total */
+  int32_t cycles;    /* restart cycles */
   double true_res;   /* |b - D x| / |b|, recomputed at the end */
   double seconds;
 } bsm_fgcr_stats;
 size_t bsm_fgcr_workspace_bytes(const bsm_lattice *lat, const bsm_fgcr_opts *opts);
 /* b, x: full FP64 device-layout spinors (x is overwritten, start x = 0);
- * U_rep64: FP64 links; U_rep32, W1, W2: used with BSM_FGCR_PTC only (may be
- * NULL otherwise).  Synchronises `stream` every iteration.  Returns
+ * U_rep64: FP64 links; U_rep32: FP32 links, used with BSM_FGCR_PTC or
+ * prec_inner BSM_F32 (may be NULL otherwise); W1, W2: used with BSM_FGCR_PTC
+ * only.  Synchronises `stream` every iteration.  Returns
  * BSM_ENOCONV (max_iter reached) or BSM_ENAN with x holding the last iterate. */
 int bsm_fgcr_solve(const bsm_lattice *lat, const void *U_rep64, const void *U_rep32,
                    const void *W1, const void *W2, const void *b, void *x,

@@ -197,6 +197,26 @@ __global__ void ptc_pack_kernel(double2* __restrict__ psi, float2* __restrict__ 
     }
 }
 
+// FP32 device spinor (2d planes of float4 (psi[s][c], psi[s+2][c]), s = 0, 1)
+// <-> PTC one-channel field; thread per (p, i)
+__global__ void ptc_pack32_kernel(float4* __restrict__ psi, float2* __restrict__ F, Geom g, int d, int unpack) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * g.Vh) return;
+  const int p = t / g.Vh, i = t - p * g.Vh;
+  float4* blk = psi + (size_t)p * 2 * d * g.Vh;
+  for (int c = 0; c < d; ++c)
+    for (int s = 0; s < 2; ++s) {
+      float2* f = F + (((size_t)p * g.Vh + i) * d + c) * 4;
+      float4* q = blk + (size_t)(s * d + c) * g.Vh + i;
+      if (unpack) *q = make_float4(f[s].x, f[s].y, f[s + 2].x, f[s + 2].y);
+      else {
+        const float4 v = *q;
+        f[s] = make_float2(v.x, v.y);
+        f[s + 2] = make_float2(v.z, v.w);
+      }
+    }
+}
+
 // G = 2 (Y - E) / |E_b|^2, partial losses (Y, E: rows x 4 complex)
 __global__ void __launch_bounds__(kBlasThreads) ptc_loss_kernel(const float2* __restrict__ Y,
                                                                 const float2* __restrict__ E,
@@ -365,6 +385,14 @@ int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, cuda
   const int d = rep_info(L.N, L.rep).d;
   ptc_pack_kernel<<<(2 * g.Vh + 127) / 128, 128, 0, s>>>(reinterpret_cast<double2*>(const_cast<double*>(psi)),
                                                           reinterpret_cast<float2*>(F), g, d, unpack ? 1 : 0);
+  return BSM_OK;
+}
+
+int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, cudaStream_t s) {
+  const Geom g = make_geom(L);
+  const int d = rep_info(L.N, L.rep).d;
+  ptc_pack32_kernel<<<(2 * g.Vh + 127) / 128, 128, 0, s>>>(reinterpret_cast<float4*>(const_cast<float*>(psi)),
+                                                            reinterpret_cast<float2*>(F), g, d, unpack ? 1 : 0);
   return BSM_OK;
 }
 

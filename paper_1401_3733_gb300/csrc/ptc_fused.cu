@@ -1,7 +1,7 @@
 // ptc_fused.cu -- BF16 inference of the parallel-transport preconditioner
 // with the two channel-mixing GEMMs fused into the transport kernel.
 //
-// One block owns 64 consecutive eo sites of one parity (64 d rows of the PTC
+// One block owns 128 consecutive eo sites of one parity (128 d rows of the PTC
 // field).  Stage 1: two threads per site compute the 9 transports of the
 // one-channel input (T_0, and U_mu(x) F(x+mu), U_mu(x-mu)^+ F(x-mu) for two
 // directions each) in FP32 and store them, rounded to BF16 and realified
@@ -12,8 +12,9 @@
 // fragments of two adjacent 8-column tiles of Y1 are, element for element,
 // the A fragment of one 16-deep k-step of the second GEMM, so Y1 is rounded
 // to BF16 in registers and never stored.  Z2 (rows x 36 complex, BF16) is the
-// only intermediate written to memory; the stencil kernel then forms
-// out = sum_k T_k Z2_k.  The weights come realified and transposed ([n][k],
+// only intermediate written to memory, slot-major (Z2[k][row][spin]) so that
+// the stencil kernel, which forms out = sum_k T_k Z2_k, reads each
+// neighbour's slot as whole, contiguous 16-byte groups.  The weights come realified and transposed ([n][k],
 // k padded) so that B fragments are conflict-free 32-bit shared loads.
 #include <cuda_bf16.h>
 
@@ -23,8 +24,8 @@ namespace bsm {
 
 namespace {
 
-constexpr int kFusedSites = 64;    // eo sites per block
-constexpr int kFusedThreads = 128;
+constexpr int kFusedSites = 128;   // eo sites per block (two threads per site in the transport stage)
+constexpr int kFusedThreads = 256;
 constexpr int kXStride = 88;        // bf16 per X1 row in shared memory (72 used, 80 for the MMA k-steps)
 
 template <int C>
@@ -69,11 +70,12 @@ __global__ void fused_prep_kernel(const float2* __restrict__ W1, const float2* _
 }
 
 template <int D, int C>
-__global__ void __launch_bounds__(kFusedThreads) fused_kernel(const char* __restrict__ links, size_t link_block,
+__global__ void __launch_bounds__(kFusedThreads, 2) fused_kernel(const char* __restrict__ links, size_t link_block,
                                                                const float2* __restrict__ F,
                                                                const __nv_bfloat16* __restrict__ W1T,
                                                                const __nv_bfloat16* __restrict__ W2T,
-                                                               unsigned* __restrict__ Z, Geom g, int bpp) {
+                                                               unsigned* __restrict__ Z, long long zrows, Geom g,
+                                                               int bpp) {
   using S = FusedShape<C>;
   constexpr int kRows = kFusedSites * D;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -209,24 +211,24 @@ __global__ void __launch_bounds__(kFusedThreads) fused_kernel(const char* __rest
 #pragma unroll
       for (int n = 0; n < 9; ++n)
         mma16816(acc2[n], a2[t], W232[(n * 8 + gq) * w2s + t * 8 + q], W232[(n * 8 + gq) * w2s + t * 8 + 4 + q]);
-    // Z2 rows: (prow0 + i0) * D + local row; complex column n*4 + q is (re, im) = accumulator pair
+    // Z2 row (prow0 + i0) * D + local row; the 8-column tile n is slot k = n, column pair q is spin q
     const long long zr = (prow0 + i0) * D + r0;
     if (r0 + gq < valid_rows) {
 #pragma unroll
-      for (int n = 0; n < 9; ++n) Z[(zr + gq) * 36 + n * 4 + q] = pack_bf2(acc2[n][0], acc2[n][1]);
+      for (int n = 0; n < 9; ++n) Z[(n * zrows + zr + gq) * 4 + q] = pack_bf2(acc2[n][0], acc2[n][1]);
     }
     if (r0 + gq + 8 < valid_rows) {
 #pragma unroll
-      for (int n = 0; n < 9; ++n) Z[(zr + gq + 8) * 36 + n * 4 + q] = pack_bf2(acc2[n][2], acc2[n][3]);
+      for (int n = 0; n < 9; ++n) Z[(n * zrows + zr + gq + 8) * 4 + q] = pack_bf2(acc2[n][2], acc2[n][3]);
     }
   }
 }
 
-// out(x)[s] = sum_k (T_k Z_k)(x)[s] with Z in BF16 (rows x 36 complex, slot k = 4 spins, 16 bytes)
+// out(x)[s] = sum_k (T_k Z_k)(x)[s] with Z in BF16, slot-major: Z[k][row] = 4 spins (16 bytes)
 template <int D>
 __global__ void __launch_bounds__(128) stencil_bf16_kernel(const char* __restrict__ links, size_t link_block,
-                                                           const uint4* __restrict__ Z, float2* __restrict__ out,
-                                                           Geom g, int nb) {
+                                                           const uint4* __restrict__ Z, long long zrows,
+                                                           float2* __restrict__ out, Geom g, int nb) {
   const long long t = blockIdx.x * 128LL + threadIdx.x;
   if (t >= (long long)nb * 2 * g.Vh) return;
   const int i = (int)(t % g.Vh);
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(128) stencil_bf16_kernel(const char* __restric
   cx<float> acc[4][D];
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    const uint4 v = __ldg(Z + ((prow + i) * D + c) * 9);
+    const uint4 v = __ldg(Z + (prow + i) * D + c);
     acc[0][c] = unpack(v.x);
     acc[1][c] = unpack(v.y);
     acc[2][c] = unpack(v.z);
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(128) stencil_bf16_kernel(const char* __restric
       cx<float> in[4][D];
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        const uint4 v = __ldg(Z + ((orow + n) * D + c) * 9 + k);
+        const uint4 v = __ldg(Z + k * zrows + (orow + n) * D + c);
         in[0][c] = unpack(v.x);
         in[1][c] = unpack(v.y);
         in[2][c] = unpack(v.z);
@@ -305,12 +307,12 @@ int fused_launch(const char* links, size_t link_block, const void* F, const void
       cudaSuccess)
     return BSM_ECUDA;
   const int bpp = (g.Vh + kFusedSites - 1) / kFusedSites;
+  const long long sites = (long long)nb * 2 * g.Vh, zrows = sites * D;
   fused_kernel<D, C><<<nb * 2 * bpp, kFusedThreads, smem, s>>>(
       links, link_block, reinterpret_cast<const float2*>(F), reinterpret_cast<const __nv_bfloat16*>(W1T),
-      reinterpret_cast<const __nv_bfloat16*>(W2T), reinterpret_cast<unsigned*>(Z), g, bpp);
-  const long long sites = (long long)nb * 2 * g.Vh;
+      reinterpret_cast<const __nv_bfloat16*>(W2T), reinterpret_cast<unsigned*>(Z), zrows, g, bpp);
   stencil_bf16_kernel<D><<<(int)((sites + 127) / 128), 128, 0, s>>>(
-      links, link_block, reinterpret_cast<const uint4*>(Z), reinterpret_cast<float2*>(out), g, nb);
+      links, link_block, reinterpret_cast<const uint4*>(Z), zrows, reinterpret_cast<float2*>(out), g, nb);
   return BSM_OK;
 }
 
@@ -334,7 +336,7 @@ bool ptc_fused_supported(int C) { return C == 2 || C == 4 || C == 8 || C == 12; 
 // bytes of the realified weights W1T + W2T (bf16) for C channels
 size_t ptc_fused_weight_bytes(int C) { return (size_t)(8 * C * kXStride + 72 * (8 * C + 8)) * 2; }
 
-// Z: rows x 36 BF16 complex (4 bytes each); W1T/W2T: ptc_fused_weight_bytes(C), 16-byte aligned
+// Z: 9 x rows x 4 BF16 complex (4 bytes each), slot-major; W1T/W2T: ptc_fused_weight_bytes(C), 16-byte aligned
 int ptc_fused_apply(const char* links, size_t link_block, int d, int C, const void* F, const void* W1,
                     const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, cudaStream_t s) {
   void* W1T = Wt;

@@ -196,3 +196,11 @@ def test_ptc_and_fgcr_validation(bsm):
     assert solve(bsm.fgcr_opts(precond=bsm.FGCR_PTC, channels=4, ptc_prec=bsm.F64)) == bsm.EUNSUPPORTED
     assert solve(bsm.fgcr_opts(precond=bsm.FGCR_PTC, channels=4), W=None) == bsm.EINVAL
     assert solve(bsm.fgcr_opts(), ws_bytes=4096) == bsm.EWORKSPACE
+    assert solve(bsm.fgcr_opts(prec_inner=9)) == bsm.EUNSUPPORTED
+    assert solve(bsm.fgcr_opts(prec_inner=bsm.F32, inner_tol=1.5)) == bsm.EINVAL
+    st = bsm.FgcrStats()
+    assert bsm._lib.bsm_fgcr_solve(L(good), A, None, None, None, 3 * A, 4 * A, L(bsm.fgcr_opts(prec_inner=bsm.F32)),
+                                   L(st), 5 * A, big, 0) == bsm.EINVAL   # FP32 cycles need FP32 links
+    # FP32 cycles keep their 2 x restart basis vectors in FP32: half the bytes
+    assert 0 < bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(prec_inner=bsm.F32)) < \
+        bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts())

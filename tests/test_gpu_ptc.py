@@ -20,7 +20,7 @@ from tests.gpu_helpers import gpu_links, gpu_spinor, rel, to_canon, zeros_field
 
 pytestmark = pytest.mark.gpu
 
-CASES = [((4, 4, 2, 6), 3, bsm.FUND, (np.pi, 0.4, 0, -1.0)), ((4, 2, 4, 4), 2, bsm.FUND, (np.pi, 0, 0, 0)),
+CASES = [((4, 4, 4, 6), 3, bsm.FUND, (np.pi, 0.4, 0, -1.0)), ((4, 4, 4, 4), 2, bsm.FUND, (np.pi, 0, 0, 0)),
          ((2, 4, 4, 2), 2, bsm.SYM, (0.3, 0, 0, 0)), ((4, 4, 4, 2), 3, bsm.ASYM, (np.pi, 0, 0.7, 0))]
 CASE_IDS = ["SU3-F", "SU2-F", "SU2-S", "SU3-AS"]
 
@@ -96,8 +96,8 @@ def neumann_weights(m0):
 def test_ptc_net_matches_oracle_layers(case, prec, tol, C):
     """C = 12 in BF16 runs the fused transport + two-GEMM kernel, C = 5 the
     transport kernels and library GEMMs; the lattices give parity blocks of
-    96, 64 and 32 sites against the fused kernel's 64-site tiles (ragged,
-    exact and partial), and two samples per call."""
+    192, 128, 32 and 64 sites against the fused kernel's 128-site tiles
+    (ragged, exact and partial), and two samples per call."""
     dims, N, rep, phase = case
     olat, blat = lats(dims, N, rep, phase)
     U = fields.gauge_field(dims, N, "haar", seed=11)
@@ -296,3 +296,27 @@ def test_fgcr_statuses():
     bn[3, 1, 0] = np.nan
     st, _, _ = fgcr(blat, U64, None, gpu_spinor(blat, bn, bsm.F64), bsm.fgcr_opts())
     assert st == bsm.ENAN
+
+
+@pytest.mark.parametrize("precond", ["none", "ptc-bf16"])
+def test_mixed_precision_fgcr_reaches_fp64_accuracy(precond):
+    """FP32 restart cycles with the residual recomputed in FP64: the same
+    1e-10 true residual and solution as all-FP64 FGCR."""
+    dims, N = (4, 4, 4, 8), 3
+    olat, blat = lats(dims, N, bsm.FUND, (np.pi, 0, 0, 0), m0=0.05)
+    U = fields.gauge_field(dims, N, "smooth", seed=24, eps=0.4)
+    R = orc.links_to_rep(olat, U)
+    U64, U32 = gpu_links(blat, U, bsm.F64), gpu_links(blat, U, bsm.F32)
+    b = fields.gaussian_spinor(dims, N, 25)
+    bd = gpu_spinor(blat, b, bsm.F64)
+    kw = {} if precond == "none" else dict(precond=bsm.FGCR_PTC, ptc_prec=bsm.BF16, channels=2)
+    W = (None, None) if precond == "none" else tuple(dev_c64(w) for w in neumann_weights(olat.m0))
+    st0, s0, x0 = fgcr(blat, U64, U32, bd, bsm.fgcr_opts(tol=1e-10, restart=16, **kw), W)
+    st1, s1, x1 = fgcr(blat, U64, U32, bd, bsm.fgcr_opts(tol=1e-10, restart=16, prec_inner=bsm.F32, inner_tol=1e-3,
+                                                        **kw), W)
+    assert st0 == bsm.OK and st1 == bsm.OK, (st0, st1)
+    assert s1.true_res <= 1e-10 and s1.cycles >= 2
+    x = to_canon(blat, x1, bsm.F64)
+    assert rel(orc.dirac(olat, R, x), b) <= 1e-10
+    assert rel(x, to_canon(blat, x0, bsm.F64)) < 1e-8
+    assert s1.iters <= 2 * s0.iters + 16

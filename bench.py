@@ -373,6 +373,8 @@ def run_ours(args):
         out["batch"] = run_batch(max(3, min(args.steps, 20)), flush)
         out["batch_small"] = run_batch(max(3, min(args.steps, 20)), flush, BATCH_SMALL)
         out["cg_small_graph"] = run_cg_graph(args.cg_max_iter)
+    if rank == 0 and not args.no_precond:
+        out["precond"] = run_precond(peak, peak_src, args.steps)
     if rank == 0 and world == 1 and not args.no_cpu:
         g, reps, el, th = time_oracle_hop(SAMPLE_DIMS, args.cpu_seconds)
         out["cpu_baseline"] = {"value": round(g, 3), "unit": "GFLOP/s", "cores": th, "kind": "oracle",
@@ -536,6 +538,179 @@ def run_cg_graph(max_iter):
     return res
 
 
+# learned preconditioner workload: 16^3 x 32 SU(3), smooth links exp(i 0.5 H);
+# m0 = -0.62 is where the Lanczos estimate of cond(Dhat^+ Dhat) peaks on this
+# ensemble (about 1.4e3); training on four 8^3 x 16 configurations of the
+# same ensemble, evaluation on a held-out 16^3 x 32 one
+PRECOND = dict(dims=(32, 16, 16, 16), train_dims=(16, 8, 8, 8), N=3, eps=0.5, m0=-0.62,
+               phase=(math.pi, 0.0, 0.0, 0.0), eval_seed=3, src_seed=4, train_seeds=(100, 101, 102, 103),
+               channels=12, steps=2500, batch=8, lr=3e-3, restart=32)
+
+
+def train_ptc(cfg, seed=7):
+    """Adam on loss = sum_b |M(D e_b) - e_b|^2 / |e_b|^2 with fresh Gaussian
+    e_b every step (cfg['steps'] x cfg['batch'] pairs), cycling over the
+    training configurations; D e by the library's FP64 operator."""
+    import torch
+    from paper_1401_3733_gb300 import bsm, fields
+
+    dims, N, C, nb = cfg["train_dims"], cfg["N"], cfg["channels"], cfg["batch"]
+    lat = bsm.lattice(dims, N, bsm.FUND, cfg["m0"], cfg["phase"])
+    V = int(np.prod(dims))
+    confs = []
+    for sd in cfg["train_seeds"]:
+        Ud = torch.from_numpy(fields.gauge_field(dims, N, "smooth", seed=sd, eps=cfg["eps"])).cuda()
+        l64, l32 = bsm.empty_field(lat, bsm.FIELD_LINKS, bsm.F64), bsm.empty_field(lat, bsm.FIELD_LINKS, bsm.F32)
+        bsm.bsm_links_to_rep(lat, Ud, l64, bsm.F64)
+        bsm.bsm_links_to_rep(lat, Ud, l32, bsm.F32)
+        confs.append((l64, l32))
+    A = 4.0 + cfg["m0"]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    W1 = 0.05 * torch.randn((9, 1, 4, C, 4), dtype=torch.complex64, device="cuda", generator=g)
+    W1[0, 0, :, 0, :] += torch.eye(4, device="cuda")
+    W2 = 0.01 * torch.randn((9, C, 4, 1, 4), dtype=torch.complex64, device="cuda", generator=g)
+    W2[0, 0, :, 0, :] += torch.eye(4, device="cuda") / A
+    W = [W1.reshape(36, 4 * C).contiguous(), W2.reshape(36 * C, 4).contiguous()]
+    G = [torch.empty_like(t) for t in W]
+    m = [torch.zeros_like(t) for t in W]
+    v = [torch.zeros_like(t) for t in W]
+    fb = V * N * 4
+    R, E = (torch.empty(nb * fb, dtype=torch.complex64, device="cuda") for _ in range(2))
+    e64, r64 = bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F64), bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F64)
+    ws = torch.empty(bsm.bsm_ptc_workspace_bytes(lat, C, nb, 1), dtype=torch.uint8, device="cuda")
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for step in range(1, cfg["steps"] + 1):
+        l64, l32 = confs[step % len(confs)]
+        e = torch.randn((nb, V, 4, N), dtype=torch.complex128, device="cuda", generator=g)
+        for b in range(nb):
+            bsm.bsm_pack_spinor(lat, e[b], e64, bsm.F64)
+            bsm.bsm_dslash(lat, l64, e64, r64, bsm.FULL, 0, bsm.F64)
+            bsm.bsm_ptc_pack(lat, e64, E[b * fb:(b + 1) * fb])
+            bsm.bsm_ptc_pack(lat, r64, R[b * fb:(b + 1) * fb])
+        losses.append(bsm.bsm_ptc_loss_grad(lat, l32, W[0], W[1], C, R, E, nb, G[0], G[1], ws) / nb)
+        lr = cfg["lr"] if step <= 2 * cfg["steps"] // 3 else cfg["lr"] / 3
+        for k in range(2):
+            bsm.bsm_ptc_adam_step(W[k], G[k], m[k], v[k], lr, step)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    return W, {"train_lattice_TXYZ": list(dims), "configs": len(confs), "pairs": cfg["steps"] * nb,
+               "steps": cfg["steps"], "seconds": round(secs, 2), "loss_first": round(losses[0], 5),
+               "loss_last100": round(float(np.mean(losses[-100:])), 5)}
+
+
+def run_precond(peak, peak_kind, steps):
+    """The learned parallel-transport preconditioner inside flexible GCR on the
+    held-out configuration, to |b - D x| <= 1e-10 |b|, against FGCR without it
+    and against the CG solvers (the reference method) on the same system; plus
+    the HBM roofline of one BF16 network application on the 32^3 x 64 lattice."""
+    import torch
+    from paper_1401_3733_gb300 import bsm, fields
+
+    cfg = PRECOND
+    W, train = train_ptc(cfg)
+    dims, N, C = cfg["dims"], cfg["N"], cfg["channels"]
+    lat = bsm.lattice(dims, N, bsm.FUND, cfg["m0"], cfg["phase"])
+    Ud = torch.from_numpy(fields.gauge_field(dims, N, "smooth", seed=cfg["eval_seed"], eps=cfg["eps"])).cuda()
+    L = {p: bsm.empty_field(lat, bsm.FIELD_LINKS, p) for p in (bsm.F64, bsm.F32, bsm.DF64)}
+    for p, t in L.items():
+        bsm.bsm_links_to_rep(lat, Ud, t, p)
+    b = bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F64)
+    bsm.bsm_pack_spinor(lat, torch.from_numpy(fields.gaussian_spinor(dims, N, cfg["src_seed"])).cuda(), b, bsm.F64)
+    res = {"workload": f"{dims[1]}^3x{dims[0]} SU(3) fundamental, smooth links exp(i {cfg['eps']} H), "
+                       f"m0={cfg['m0']}, antiperiodic time; D x = b to 1e-10",
+           "network": f"2 parallel-transport layers 1->{C}->1 channels", "training": train}
+    ptc = dict(precond=bsm.FGCR_PTC, channels=C)
+    mixed = dict(prec_inner=bsm.F32, inner_tol=1e-3)
+    m = cfg["restart"]
+    cases = {
+        "fgcr_none_fp64": bsm.fgcr_opts(tol=1e-10, max_iter=4000, restart=m),
+        "fgcr_ptc_f32_fp64": bsm.fgcr_opts(tol=1e-10, max_iter=4000, restart=m, ptc_prec=bsm.F32, **ptc),
+        "fgcr_eo_none_fp64": bsm.fgcr_opts(tol=1e-10, max_iter=4000, restart=m, eo=True),
+        "fgcr_eo_none_fp32cycles": bsm.fgcr_opts(tol=1e-10, max_iter=4000, restart=m, eo=True, **mixed),
+        "fgcr_eo_ptc_f32_fp64": bsm.fgcr_opts(tol=1e-10, max_iter=4000, restart=m, eo=True, ptc_prec=bsm.F32, **ptc),
+        "fgcr_eo_ptc_bf16_fp32cycles": bsm.fgcr_opts(tol=1e-10, max_iter=4000, restart=m, eo=True,
+                                                     ptc_prec=bsm.BF16, **ptc, **mixed),
+    }
+    for name, o in cases.items():
+        ws = torch.empty(bsm.bsm_fgcr_workspace_bytes(lat, o), dtype=torch.uint8, device="cuda")
+        best = None
+        for _ in range(2):
+            x = torch.empty_like(b)
+            st, stats = bsm.bsm_fgcr_solve(lat, L[bsm.F64], L[bsm.F32], W[0], W[1], b, x, o, ws,
+                                           raise_on_error=False)
+            if best is None or stats.seconds < best[1].seconds:
+                best = (st, stats)
+        st, stats = best
+        res[name] = {"status": bsm.bsm_strerror(st), "iters": stats.iters, "cycles": stats.cycles,
+                     "seconds": round(stats.seconds, 5), "true_res": stats.true_res}
+        del ws
+    for name, inner, outer in (("cg_fp64", bsm.F64, bsm.F64), ("cg_mixed_df64", bsm.F32, bsm.DF64)):
+        ws = torch.empty(bsm.bsm_workspace_bytes(lat, bsm.CALL_CG, inner), dtype=torch.uint8, device="cuda")
+        best = None
+        for _ in range(2):
+            x = torch.empty_like(b)
+            st, stats = bsm.bsm_cg_solve(lat, L[outer], L[bsm.F32], b, x,
+                                         bsm.cg_opts(tol=1e-10, max_iter=20000, prec_inner=inner, prec_outer=outer),
+                                         ws, raise_on_error=False)
+            if best is None or stats.seconds < best[1].seconds:
+                best = (st, stats)
+        st, stats = best
+        res[name] = {"status": bsm.bsm_strerror(st), "iters": stats.iters, "seconds": round(stats.seconds, 5),
+                     "true_res_full": stats.true_res_full}
+        del ws
+    res["iteration_reduction_ptc_full"] = round(res["fgcr_none_fp64"]["iters"] /
+                                                max(1, res["fgcr_ptc_f32_fp64"]["iters"]), 2)
+    res["iteration_reduction_ptc_eo"] = round(res["fgcr_eo_none_fp64"]["iters"] /
+                                              max(1, res["fgcr_eo_ptc_f32_fp64"]["iters"]), 2)
+    best = min((k for k in res if k.startswith("fgcr_eo_ptc")), key=lambda k: res[k]["seconds"])
+    res["best_ptc"] = best
+    res["cg_mixed_over_best_ptc_time"] = round(res["cg_mixed_df64"]["seconds"] / res[best]["seconds"], 3)
+    res["ptc_apply"] = ptc_apply_roofline(W, C, peak, peak_kind, steps)
+    return res
+
+
+def ptc_apply_roofline(W, C, peak, peak_kind, steps):
+    """One BF16 network application (fused transport + two-GEMM kernel, then
+    the 9-point stencil) on the 32^3 x 64 lattice, L2 flushed between
+    applications.  Algorithmic bytes per site: the one-channel FP32 input and
+    output (2 x 4 d x 8) and the FP32 links once (8 d^2 x 8)."""
+    import torch
+    from paper_1401_3733_gb300 import bsm
+
+    dims, N = WORKLOAD["dims"], WORKLOAD["N"]
+    lat = bsm.lattice(dims, N, bsm.FUND, WORKLOAD["m0"], WORKLOAD["phase"])
+    V = int(np.prod(dims))
+    U = torch.zeros((V, 4, N, N), dtype=torch.complex128, device="cuda")
+    U.real.copy_(torch.eye(N, dtype=torch.float64, device="cuda").expand(V, 4, N, N))
+    L32 = bsm.empty_field(lat, bsm.FIELD_LINKS, bsm.F32)
+    bsm.bsm_links_to_rep(lat, U, L32, bsm.F32)
+    del U
+    F = torch.randn(V * N * 4, dtype=torch.complex64, device="cuda")
+    out = torch.empty_like(F)
+    ws = torch.empty(bsm.bsm_ptc_workspace_bytes(lat, C, 1, 0), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        bsm.bsm_ptc_apply(lat, L32, W[0], W[1], C, F, out, 1, bsm.BF16, ws)
+    total, n = 0.0, max(3, min(steps, 20))
+    for _ in range(n):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bsm.bsm_ptc_apply(lat, L32, W[0], W[1], C, F, out, 1, bsm.BF16, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    ms = total / n
+    alg = (2 * 4 * N * 8 + 8 * N * N * 8) * V
+    return {"lattice_TXYZ": list(dims), "channels": C, "ms": round(ms, 4), "bound": "hbm",
+            "algorithmic_bytes": alg, "achieved_gbs": round(alg / (ms * 1e-3) / 1e9, 1),
+            "peak_gbs": peak, "peak_kind": peak_kind, "frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4),
+            "launches": 3, "l2": "flushed between applications"}
+
+
 def run_cg(lat, links, b, max_iter):
     """Time-to-1e-10 (true residual of the normal equations, recomputed at the
     outer precision) of the mixed-precision solver (FP32 inner iteration,
@@ -580,6 +755,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-mrhs", action="store_true", help="skip the multi-RHS 24^4 three-theory lines")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-lattice batch and small-lattice CG lines")
+    ap.add_argument("--no-precond", action="store_true", help="skip the learned-preconditioner (FGCR) line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -368,7 +368,11 @@ int bsm_ptc_adam_step(void *W, const void *G, void *m, void *v, int64_t n, doubl
  * solves D e = r in FP32 (FP32 links and vectors, FP64 reductions) from
  * e = 0 until |r32| <= inner_tol |r| or `restart` directions, then
  * x += e and r = b - D x are formed in FP64 (the stopping test always uses
- * this FP64 residual). */
+ * this FP64 residual).  The solver stops when the residual of the system it
+ * iterates on is <= tol |b|; with eo that residual is the full-system residual
+ * of the reconstructed x (the odd sites' residual vanishes by construction).
+ * The new direction of each step is orthogonalised against the cycle's
+ * earlier ones by classical Gram-Schmidt in one pass. */
 typedef enum { BSM_FGCR_NONE = 0, BSM_FGCR_PTC = 1 } bsm_fgcr_precond;
 typedef struct {
   double tol;        /* stop when |r| <= tol |b| (iterated residual) */
@@ -379,6 +383,9 @@ typedef struct {
   int32_t channels;  /* hidden channels C of W1, W2 */
   int32_t prec_inner;/* BSM_F64 or BSM_F32 */
   double inner_tol;  /* BSM_F32 cycles: residual reduction per cycle (0 -> 0.1) */
+  int32_t eo;        /* nonzero: solve the even-site Schur system Dhat x_e = bhat_e
+                        (bhat_e = b_e + H_eo b_o / (2A)), preconditioned by the
+                        even-even block of M, then x_o = (b_o + H_oe x_e / 2) / A */
 } bsm_fgcr_opts;
 typedef struct {
   int32_t iters;     /* directions (preconditioner applications) in total */

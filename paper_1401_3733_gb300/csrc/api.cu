@@ -24,7 +24,7 @@ size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo, int prec
 int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* b, void* x,
              const bsm_cg_opts& o, bsm_cg_stats* stats, void* ws, cudaStream_t s);
 size_t ptc_workspace_bytes(const bsm_lattice& L, int C, int nb, bool train);
-int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, cudaStream_t s);
+int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, bool even_only, cudaStream_t s);
 int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* in,
               void* out, int nb, int prec, void* ws, cudaStream_t s);
 int ptc_loss_grad(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* r,
@@ -394,14 +394,14 @@ int bsm_ptc_pack(const bsm_lattice* lat, const void* psi, void* field, void* str
   int rc = check_ptc(lat, 1, 1);
   if (rc != BSM_OK) return rc;
   if (!aligned(psi) || !aligned(field)) return BSM_EINVAL;
-  return finish(ptc_pack(*lat, reinterpret_cast<const double*>(psi), field, false, (cudaStream_t)stream));
+  return finish(ptc_pack(*lat, reinterpret_cast<const double*>(psi), field, false, false, (cudaStream_t)stream));
 }
 
 int bsm_ptc_unpack(const bsm_lattice* lat, const void* field, void* psi, void* stream) {
   int rc = check_ptc(lat, 1, 1);
   if (rc != BSM_OK) return rc;
   if (!aligned(psi) || !aligned(field)) return BSM_EINVAL;
-  return finish(ptc_pack(*lat, reinterpret_cast<const double*>(psi), const_cast<void*>(field), true,
+  return finish(ptc_pack(*lat, reinterpret_cast<const double*>(psi), const_cast<void*>(field), true, false,
                          (cudaStream_t)stream));
 }
 

@@ -3,10 +3,11 @@
 // in FP64 throughout or in FP32 restart cycles with the residual recomputed
 // in FP64 after each cycle (defect correction: x += e, r = b - D x).
 //
-// Flexible GCR (Notay 2000): z = M(r), w = D z; w and z are orthogonalised
-// against the stored w_j by modified Gram-Schmidt (beta_j = <w_j, w>/|w_j|^2,
-// w -= beta_j w_j, z -= beta_j z_j), then alpha = <w, r>/|w|^2,
-// x += alpha z, r -= alpha w; after `restart` directions the basis is dropped.
+// Flexible GCR (Notay 2000): z = M(r), w = A z; w and z are orthogonalised
+// against the stored w_j (beta_j = <w_j, w>/|w_j|^2, w -= beta_j w_j,
+// z -= beta_j z_j), then alpha = <w, r>/|w|^2, x += alpha z, r -= alpha w;
+// after `restart` directions the basis is dropped.  A is the full operator D,
+// or the even-site Schur operator Dhat (even-odd option).
 // Because the preconditioner may change from step to step (a network in
 // reduced precision is not exactly linear in the rounding), GCR's flexible
 // form is needed rather than CG on the normal equations.
@@ -22,37 +23,67 @@
 namespace bsm {
 
 size_t ptc_workspace_bytes(const bsm_lattice& L, int C, int nb, bool train);
-int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, cudaStream_t s);
-int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, cudaStream_t s);
+int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, bool even_only, cudaStream_t s);
+int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, bool even_only, cudaStream_t s);
 int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* in,
               void* out, int nb, int prec, void* ws, cudaStream_t s);
 
 namespace {
 
-// complex elements as (x, y) pairs; accumulation always in FP64
-template <typename T> __device__ __forceinline__ double2 ld2(const T* p, size_t k) {
-  const T v = p[k];
-  return make_double2(v.x, v.y);
+// Element arithmetic at the vector's own precision (FP32 for the FP32
+// cycles: GB300's FP64 units are far slower than its FP32 units); each
+// thread's partial sums are handed to the block reductions in FP64.
+template <typename T> struct Arith;
+template <> struct Arith<double2> { using R = double; };
+template <> struct Arith<float2> { using R = float; };
+
+template <typename T>
+__device__ __forceinline__ T csub_mul(T x, double2 c, T a) {  // x - c a
+  using R = typename Arith<T>::R;
+  const R cx = (R)c.x, cy = (R)c.y;
+  x.x -= cx * a.x - cy * a.y;
+  x.y -= cx * a.y + cy * a.x;
+  return x;
 }
-template <typename T> __device__ __forceinline__ void st2(T* p, size_t k, double2 v);
-template <> __device__ __forceinline__ void st2<double2>(double2* p, size_t k, double2 v) { p[k] = v; }
-template <> __device__ __forceinline__ void st2<float2>(float2* p, size_t k, double2 v) {
-  p[k] = make_float2((float)v.x, (float)v.y);
+template <typename T>
+__device__ __forceinline__ T cadd_mul(T x, double2 c, T a) {  // x + c a
+  using R = typename Arith<T>::R;
+  const R cx = (R)c.x, cy = (R)c.y;
+  x.x += cx * a.x - cy * a.y;
+  x.y += cx * a.y + cy * a.x;
+  return x;
 }
 
-// partials of <a, b> = sum conj(a) b: re at [blk], im at [gridDim + blk]
+constexpr int kDotChunk = 8;  // directions per dot launch (accumulators in registers)
+
+// partials of <w_j, v> = sum conj(w_j) v for j = j0 .. j0 + cnt - 1 (cnt <= kDotChunk), w_j at
+// basis + j * stride: re of j at [(2 (j - j0)) G + blk], im at [(2 (j - j0) + 1) G + blk]
 template <typename T>
-__global__ void __launch_bounds__(kBlasThreads) cdot_kernel(const T* __restrict__ a, const T* __restrict__ b,
-                                                            size_t n, double* partials) {
-  double re = 0.0, im = 0.0;
+__global__ void __launch_bounds__(kBlasThreads) multi_dot_kernel(const T* __restrict__ basis, size_t stride, int j0,
+                                                                 int cnt, const T* __restrict__ v, size_t n,
+                                                                 double* partials) {
+  using R = typename Arith<T>::R;
+  R re[kDotChunk], im[kDotChunk];
+#pragma unroll
+  for (int j = 0; j < kDotChunk; ++j) re[j] = im[j] = 0;
   for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
-    const double2 x = ld2(a, k), y = ld2(b, k);
-    re = fma(x.x, y.x, fma(x.y, y.y, re));
-    im = fma(x.x, y.y, fma(-x.y, y.x, im));
+    const T y = v[k];
+#pragma unroll
+    for (int j = 0; j < kDotChunk; ++j)
+      if (j < cnt) {
+        const T x = basis[(size_t)(j0 + j) * stride + k];
+        re[j] += x.x * y.x + x.y * y.y;
+        im[j] += x.x * y.y - x.y * y.x;
+      }
   }
-  block_sum_store<kBlasThreads>(re, partials);
-  __syncthreads();
-  block_sum_store<kBlasThreads>(im, partials + gridDim.x);
+#pragma unroll
+  for (int j = 0; j < kDotChunk; ++j)
+    if (j < cnt) {
+      block_sum_store<kBlasThreads>((double)re[j], partials + (size_t)(2 * j) * gridDim.x);
+      __syncthreads();
+      block_sum_store<kBlasThreads>((double)im[j], partials + (size_t)(2 * j + 1) * gridDim.x);
+      __syncthreads();
+    }
 }
 
 __device__ double sum_partials(const double* __restrict__ p, int n) {
@@ -70,32 +101,33 @@ __device__ double sum_partials(const double* __restrict__ p, int n) {
   return r;
 }
 
-// coef = <w_j, w> / |w_j|^2 (one block)
-__global__ void mgs_coef_kernel(const double* __restrict__ partials, int nblk, const double* __restrict__ norm2_j,
-                                double2* coef) {
-  const double re = sum_partials(partials, nblk);
-  const double im = sum_partials(partials + nblk, nblk);
+// coef_j = <w_j, w> / |w_j|^2 for j = j0 + blockIdx.x (one block per direction)
+__global__ void gs_coef_kernel(const double* __restrict__ partials, int nblk, int j0,
+                               const double* __restrict__ norm2, double2* coef) {
+  const int j = blockIdx.x;
+  const double re = sum_partials(partials + (size_t)(2 * j) * nblk, nblk);
+  const double im = sum_partials(partials + (size_t)(2 * j + 1) * nblk, nblk);
   if (threadIdx.x == 0) {
-    const double n = *norm2_j;
-    *coef = n > 0.0 ? make_double2(re / n, im / n) : make_double2(0.0, 0.0);
+    const double nn = norm2[j0 + j];
+    coef[j0 + j] = nn > 0.0 ? make_double2(re / nn, im / nn) : make_double2(0.0, 0.0);
   }
 }
 
-// w -= coef w_j ; z -= coef z_j
+// w -= sum_j coef_j w_j ; z -= sum_j coef_j z_j  (j < k; w_j, z_j at wb, zb + j * stride)
 template <typename T>
-__global__ void __launch_bounds__(kBlasThreads) mgs_update_kernel(T* __restrict__ w, const T* __restrict__ wj,
-                                                                  T* __restrict__ z, const T* __restrict__ zj,
-                                                                  size_t n, const double2* __restrict__ coef) {
-  const double2 c = *coef;
-  for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
-    const double2 a = ld2(wj, k), b = ld2(zj, k);
-    double2 x = ld2(w, k), y = ld2(z, k);
-    x.x -= c.x * a.x - c.y * a.y;
-    x.y -= c.x * a.y + c.y * a.x;
-    y.x -= c.x * b.x - c.y * b.y;
-    y.y -= c.x * b.y + c.y * b.x;
-    st2(w, k, x);
-    st2(z, k, y);
+__global__ void __launch_bounds__(kBlasThreads) gs_update_kernel(T* __restrict__ w, T* __restrict__ z,
+                                                                 const T* __restrict__ wb, const T* __restrict__ zb,
+                                                                 size_t stride, int k, size_t n,
+                                                                 const double2* __restrict__ coef) {
+  for (size_t e = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kBlasThreads) {
+    T x = w[e], y = z[e];
+    for (int j = 0; j < k; ++j) {
+      const double2 c = coef[j];
+      x = csub_mul(x, c, wb[(size_t)j * stride + e]);
+      y = csub_mul(y, c, zb[(size_t)j * stride + e]);
+    }
+    w[e] = x;
+    z[e] = y;
   }
 }
 
@@ -103,18 +135,19 @@ __global__ void __launch_bounds__(kBlasThreads) mgs_update_kernel(T* __restrict_
 template <typename T>
 __global__ void __launch_bounds__(kBlasThreads) wr_kernel(const T* __restrict__ w, const T* __restrict__ r, size_t n,
                                                           double* partials) {
-  double ww = 0.0, re = 0.0, im = 0.0;
+  using R = typename Arith<T>::R;
+  R ww = 0, re = 0, im = 0;
   for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
-    const double2 x = ld2(w, k), y = ld2(r, k);
-    ww = fma(x.x, x.x, fma(x.y, x.y, ww));
-    re = fma(x.x, y.x, fma(x.y, y.y, re));
-    im = fma(x.x, y.y, fma(-x.y, y.x, im));
+    const T x = w[k], y = r[k];
+    ww += x.x * x.x + x.y * x.y;
+    re += x.x * y.x + x.y * y.y;
+    im += x.x * y.y - x.y * y.x;
   }
-  block_sum_store<kBlasThreads>(ww, partials);
+  block_sum_store<kBlasThreads>((double)ww, partials);
   __syncthreads();
-  block_sum_store<kBlasThreads>(re, partials + gridDim.x);
+  block_sum_store<kBlasThreads>((double)re, partials + gridDim.x);
   __syncthreads();
-  block_sum_store<kBlasThreads>(im, partials + 2 * gridDim.x);
+  block_sum_store<kBlasThreads>((double)im, partials + 2 * gridDim.x);
 }
 
 // norm2_k = |w|^2, alpha = <w, r> / |w|^2 (one block)
@@ -133,21 +166,16 @@ template <typename T>
 __global__ void __launch_bounds__(kBlasThreads) xr_kernel(T* __restrict__ x, T* __restrict__ r,
                                                           const T* __restrict__ z, const T* __restrict__ w, size_t n,
                                                           const double2* __restrict__ alpha, double* partials) {
+  using R = typename Arith<T>::R;
   const double2 a = *alpha;
-  double rr = 0.0;
+  R rr = 0;
   for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
-    const double2 zz = ld2(z, k), ww = ld2(w, k);
-    double2 xx = ld2(x, k), q = ld2(r, k);
-    xx.x += a.x * zz.x - a.y * zz.y;
-    xx.y += a.x * zz.y + a.y * zz.x;
-    q.x -= a.x * ww.x - a.y * ww.y;
-    q.y -= a.x * ww.y + a.y * ww.x;
-    st2(x, k, xx);
-    st2(r, k, q);
-    const double2 qs = ld2(r, k);  // the stored (rounded) residual
-    rr = fma(qs.x, qs.x, fma(qs.y, qs.y, rr));
+    x[k] = cadd_mul(x[k], a, z[k]);
+    const T q = csub_mul(r[k], a, w[k]);
+    r[k] = q;
+    rr += q.x * q.x + q.y * q.y;
   }
-  block_sum_store<kBlasThreads>(rr, partials);
+  block_sum_store<kBlasThreads>((double)rr, partials);
 }
 
 // partials of |a - b|^2 (b may be null: |a|^2); with out != null also out = a - b
@@ -169,25 +197,32 @@ __global__ void __launch_bounds__(kBlasThreads) diff2_kernel(const double2* __re
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
 struct FgcrLayout {
-  size_t r, x32, r32, basis, scal, part, F_in, F_out, ptc, total;
+  size_t r, bhat, tmp, x32, r32, basis, scal, part, F_in, F_out, ptc, total;
 };
 
-// mixed: FP32 cycle vectors (x32, r32, basis) next to the FP64 residual r
+// Vectors are full spinors, or even half spinors with opts.eo.  Mixed: the
+// cycle vectors (x32, r32, basis) are FP32 next to the FP64 residual r.
 FgcrLayout fgcr_layout(const bsm_lattice& L, const bsm_fgcr_opts& o) {
   const Geom g = make_geom(L);
   const int d = rep_info(L.N, L.rep).d;
   const bool mixed = o.prec_inner == BSM_F32;
-  const size_t full = 2 * half_spinor_bytes(g.Vh, d, mixed ? BSM_F32 : BSM_F64);
+  const int parts = o.eo ? 1 : 2;
+  const size_t v64 = parts * half_spinor_bytes(g.Vh, d, BSM_F64);
+  const size_t vc = parts * half_spinor_bytes(g.Vh, d, mixed ? BSM_F32 : BSM_F64);
   FgcrLayout y{};
   size_t p = 0;
-  y.r = p; p = al(p + 2 * half_spinor_bytes(g.Vh, d, BSM_F64));
-  if (mixed) {
-    y.x32 = p; p = al(p + full);
-    y.r32 = p; p = al(p + full);
+  y.r = p; p = al(p + 2 * half_spinor_bytes(g.Vh, d, BSM_F64));  // full: also holds D x at the end
+  if (o.eo) {
+    y.bhat = p; p = al(p + v64);
+    y.tmp = p; p = al(p + half_spinor_bytes(g.Vh, d, BSM_F64));   // odd temporary of Dhat
   }
-  y.basis = p; p = al(p + full * 2 * (size_t)o.restart);  // z_0 .. z_{m-1}, w_0 .. w_{m-1}
-  y.scal = p; p = al(p + sizeof(double) * ((size_t)o.restart + 8));
-  y.part = p; p = al(p + sizeof(double) * 3 * kBlasMaxBlocks);
+  if (mixed) {
+    y.x32 = p; p = al(p + vc);
+    y.r32 = p; p = al(p + vc);
+  }
+  y.basis = p; p = al(p + vc * 2 * (size_t)o.restart);  // z_0 .. z_{m-1}, w_0 .. w_{m-1}
+  y.scal = p; p = al(p + sizeof(double) * (3 * (size_t)o.restart + 8));
+  y.part = p; p = al(p + sizeof(double) * 2 * kDotChunk * kBlasMaxBlocks);
   if (o.precond == BSM_FGCR_PTC) {
     const size_t f = (size_t)2 * g.Vh * d * 4 * sizeof(float2);
     y.F_in = p; p = al(p + f);
@@ -205,8 +240,9 @@ struct Fgcr {
   FgcrLayout y;
   char* w;
   cudaStream_t s;
-  double* norm2;
-  double2 *coef, *alpha;
+  double* norm2;   // [restart]
+  double2* coef;   // [restart]
+  double2* alpha;
   double* scalar;
   double* part;
   int G = 0;
@@ -216,41 +252,54 @@ struct Fgcr {
     return cudaStreamSynchronize(s) == cudaSuccess ? BSM_OK : BSM_ECUDA;
   }
 
-  // z = M(r) at the cycle precision T
+  // out = D in (full) or Dhat in (even half; odd temporary in tmp)
+  int apply(const OpCtx& c, const void* in, void* out) const {
+    const int rc = o.eo ? op_dhat(c, in, out, w + y.tmp, 0, nullptr, nullptr) : op_dirac(c, in, out, 0, nullptr, nullptr);
+    return rc < 0 ? rc : BSM_OK;
+  }
+
+  // z = M(r) at the cycle precision T; with eo the network acts on the field
+  // that is r on the even sites and zero on the odd ones, and z keeps the even part
   template <typename T>
-  int precondition(const T* r, T* z, size_t full) const {
-    if (o.precond != BSM_FGCR_PTC) return cudaMemcpyAsync(z, r, full, cudaMemcpyDeviceToDevice, s) == cudaSuccess
-                                              ? BSM_OK : BSM_ECUDA;
+  int precondition(const T* r, T* z, size_t bytes) const {
+    if (o.precond != BSM_FGCR_PTC)
+      return cudaMemcpyAsync(z, r, bytes, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? BSM_OK : BSM_ECUDA;
     int rc;
     const bool f32 = sizeof(T) == sizeof(float2);
-    rc = f32 ? ptc_pack32(L, reinterpret_cast<const float*>(r), w + y.F_in, false, s)
-             : ptc_pack(L, reinterpret_cast<const double*>(r), w + y.F_in, false, s);
+    rc = f32 ? ptc_pack32(L, reinterpret_cast<const float*>(r), w + y.F_in, false, o.eo != 0, s)
+             : ptc_pack(L, reinterpret_cast<const double*>(r), w + y.F_in, false, o.eo != 0, s);
     if (rc != BSM_OK) return rc;
     if ((rc = ptc_apply(L, U32, W1, W2, o.channels, w + y.F_in, w + y.F_out, 1, o.ptc_prec, w + y.ptc, s)) != BSM_OK)
       return rc;
-    return f32 ? ptc_pack32(L, reinterpret_cast<const float*>(z), w + y.F_out, true, s)
-               : ptc_pack(L, reinterpret_cast<const double*>(z), w + y.F_out, true, s);
+    return f32 ? ptc_pack32(L, reinterpret_cast<const float*>(z), w + y.F_out, true, o.eo != 0, s)
+               : ptc_pack(L, reinterpret_cast<const double*>(z), w + y.F_out, true, o.eo != 0, s);
   }
 
-  // One restart cycle of FGCR on D x = r at precision T (x, r updated in
+  // One restart cycle of FGCR on A x = r at precision T (x, r updated in
   // place): up to `restart` directions, at most `budget` iterations; stops
-  // early once |r|^2 <= stop2.  Returns the iterations, or < 0 on error;
-  // *rr receives the last |r|^2.
+  // early once |r|^2 <= stop2.  Each new direction is orthogonalised against
+  // the cycle's earlier ones in one pass (classical Gram-Schmidt: the dots
+  // <w_j, w> of all j at once, then w -= sum_j beta_j w_j, z likewise); with
+  // the w_j mutually orthogonal this equals modified Gram-Schmidt up to
+  // rounding.  Returns the iterations, or < 0 on error; *rr = the last |r|^2.
   template <typename T>
-  int cycle(const OpCtx& c, T* x, T* r, size_t full, double stop2, int budget, double* rr) const {
-    const size_t n = full / sizeof(T);
-    auto Z = [&](int j) { return reinterpret_cast<T*>(w + y.basis + full * j); };
-    auto Wb = [&](int j) { return reinterpret_cast<T*>(w + y.basis + full * (o.restart + j)); };
+  int cycle(const OpCtx& c, T* x, T* r, size_t bytes, double stop2, int budget, double* rr) const {
+    const size_t n = bytes / sizeof(T), stride = bytes / sizeof(T);
+    T* zb = reinterpret_cast<T*>(w + y.basis);
+    T* wb = zb + stride * o.restart;
     int it = 0, rc;
     for (int k = 0; k < o.restart && it < budget; ++k) {
-      T* z = Z(k);
-      T* wv = Wb(k);
-      if ((rc = precondition<T>(r, z, full)) != BSM_OK) return rc;
-      if ((rc = op_dirac(c, z, wv, 0, nullptr, nullptr)) < 0) return rc;
-      for (int j = 0; j < k; ++j) {
-        cdot_kernel<T><<<G, kBlasThreads, 0, s>>>(Wb(j), wv, n, part);
-        mgs_coef_kernel<<<1, kBlasThreads, 0, s>>>(part, G, norm2 + j, coef);
-        mgs_update_kernel<T><<<G, kBlasThreads, 0, s>>>(wv, Wb(j), z, Z(j), n, coef);
+      T* z = zb + stride * k;
+      T* wv = wb + stride * k;
+      if ((rc = precondition<T>(r, z, bytes)) != BSM_OK) return rc;
+      if ((rc = apply(c, z, wv)) != BSM_OK) return rc;
+      if (k > 0) {
+        for (int j0 = 0; j0 < k; j0 += kDotChunk) {
+          const int cnt = k - j0 < kDotChunk ? k - j0 : kDotChunk;
+          multi_dot_kernel<T><<<G, kBlasThreads, 0, s>>>(wb, stride, j0, cnt, wv, n, part);
+          gs_coef_kernel<<<cnt, kBlasThreads, 0, s>>>(part, G, j0, norm2, coef);
+        }
+        gs_update_kernel<T><<<G, kBlasThreads, 0, s>>>(wv, z, wb, zb, stride, k, n, coef);
       }
       wr_kernel<T><<<G, kBlasThreads, 0, s>>>(wv, r, n, part);
       alpha_kernel<<<1, kBlasThreads, 0, s>>>(part, G, norm2 + k, alpha);
@@ -273,35 +322,50 @@ int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const voi
                const void* b, void* x, const bsm_fgcr_opts& o, bsm_fgcr_stats* stats, void* ws, cudaStream_t s) {
   const auto t0 = std::chrono::steady_clock::now();
   const bool mixed = o.prec_inner == BSM_F32;
+  const bool eo = o.eo != 0;
   const OpCtx c64 = make_ctx(L, U64, BSM_F64, s);
   const OpCtx c32 = make_ctx(L, mixed ? U32 : U64, mixed ? BSM_F32 : BSM_F64, s);
   Fgcr F{L, o, U32, W1, W2, fgcr_layout(L, o), reinterpret_cast<char*>(ws), s};
   char* w = F.w;
-  F.norm2 = reinterpret_cast<double*>(w + F.y.scal);   // [restart]
+  F.norm2 = reinterpret_cast<double*>(w + F.y.scal);
   F.coef = reinterpret_cast<double2*>(F.norm2 + o.restart);
-  F.alpha = F.coef + 1;
+  F.alpha = F.coef + o.restart;
   F.scalar = reinterpret_cast<double*>(F.alpha + 1);
   F.part = reinterpret_cast<double*>(w + F.y.part);
-  const size_t full64 = 2 * c64.half_bytes, n64 = full64 / sizeof(double2);
-  F.G = blas_blocks(n64);
+  const size_t h64 = c64.half_bytes, full64 = 2 * h64;
+  const size_t v64 = eo ? h64 : full64, nv64 = v64 / sizeof(double2);
+  F.G = blas_blocks(full64 / sizeof(double2));
+  const char* bc = reinterpret_cast<const char*>(b);
+  char* xc = reinterpret_cast<char*>(x);
   double2* r = reinterpret_cast<double2*>(w + F.y.r);
-  double2* xv = reinterpret_cast<double2*>(x);
-  const double2* bv = reinterpret_cast<const double2*>(b);
+  int rc;
 
-  // x = 0, r = b
-  cudaMemsetAsync(x, 0, full64, s);
-  cudaMemcpyAsync(r, b, full64, cudaMemcpyDeviceToDevice, s);
-  diff2_kernel<<<F.G, kBlasThreads, 0, s>>>(bv, nullptr, nullptr, n64, F.part);
+  // |b|^2 (full), the system's right-hand side rhs (b, or bhat_e = b_e + H_eo b_o / (2A)), r = rhs, x = 0
+  diff2_kernel<<<F.G, kBlasThreads, 0, s>>>(reinterpret_cast<const double2*>(b), nullptr, nullptr,
+                                            full64 / sizeof(double2), F.part);
   reduce_launch(F.part, F.G, F.scalar, s);
   double bb = 0.0;
-  int rc = F.host_read(F.scalar, &bb);
-  if (rc != BSM_OK) return rc;
+  if ((rc = F.host_read(F.scalar, &bb)) != BSM_OK) return rc;
   if (!(bb > 0.0)) {
+    cudaMemsetAsync(x, 0, full64, s);
     if (stats) *stats = bsm_fgcr_stats{0, 0, 0.0, 0.0};
     return isfinite(bb) ? BSM_OK : BSM_ENAN;
   }
+  const double2* rhs = reinterpret_cast<const double2*>(b);
+  if (eo) {
+    if ((rc = op_hop(c64, 0, bc + h64, w + F.y.bhat, 0, bc, 1.0, 1.0 / (2.0 * c64.A), nullptr, nullptr)) < 0) return rc;
+    rhs = reinterpret_cast<const double2*>(w + F.y.bhat);
+  }
+  cudaMemsetAsync(x, 0, full64, s);
+  cudaMemcpyAsync(r, rhs, v64, cudaMemcpyDeviceToDevice, s);
+  // stop on |rhs - A x| <= tol |b|: with eo the full residual of the
+  // reconstructed solution equals the even-site Schur residual
   const double stop2 = o.tol * o.tol * bb;
-  double rr = bb;
+  double rr = 0.0;
+  diff2_kernel<<<F.G, kBlasThreads, 0, s>>>(r, nullptr, nullptr, nv64, F.part);
+  reduce_launch(F.part, F.G, F.scalar, s);
+  if ((rc = F.host_read(F.scalar, &rr)) != BSM_OK) return rc;
+  double2* xv = reinterpret_cast<double2*>(x);
   int it = 0, cycles = 0, status = BSM_OK;
   while (rr > stop2) {
     if (it >= o.max_iter) {
@@ -310,22 +374,22 @@ int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const voi
     }
     int k;
     if (!mixed) {
-      k = F.cycle<double2>(c64, xv, r, full64, stop2, o.max_iter - it, &rr);
+      k = F.cycle<double2>(c64, xv, r, v64, stop2, o.max_iter - it, &rr);
     } else {
-      // FP32 cycle on D e = r from e = 0, to |r32| <= inner_tol |r|, then
-      // x += e and the residual recomputed in FP64
-      const size_t full32 = 2 * c32.half_bytes, nh = c32.half_bytes / 16;
+      // FP32 cycle on A e = r from e = 0, to |r32| <= inner_tol |r|, then
+      // x += e and r = rhs - A x in FP64
+      const size_t v32 = eo ? c32.half_bytes : 2 * c32.half_bytes, nh = c32.half_bytes / 16;
       float2* x32 = reinterpret_cast<float2*>(w + F.y.x32);
       float2* r32 = reinterpret_cast<float2*>(w + F.y.r32);
-      cudaMemsetAsync(x32, 0, full32, s);
-      convert_to32_launch(BSM_F64, r32, r, nh, 2, s);
+      cudaMemsetAsync(x32, 0, v32, s);
+      convert_to32_launch(BSM_F64, r32, r, nh, eo ? 1 : 2, s);
       const double inner = o.inner_tol > 0.0 ? o.inner_tol : 0.1;
       double rr32 = 0.0;
-      k = F.cycle<float2>(c32, x32, r32, full32, fmax(inner * inner * rr, stop2), o.max_iter - it, &rr32);
+      k = F.cycle<float2>(c32, x32, r32, v32, fmax(inner * inner * rr, stop2), o.max_iter - it, &rr32);
       if (k >= 0) {
-        accumulate32_launch(BSM_F64, x, x32, nh, 2, s);
-        if ((rc = op_dirac(c64, x, r, 0, nullptr, nullptr)) < 0) return rc;
-        diff2_kernel<<<F.G, kBlasThreads, 0, s>>>(bv, r, r, n64, F.part);
+        accumulate32_launch(BSM_F64, x, x32, nh, eo ? 1 : 2, s);
+        if ((rc = F.apply(c64, x, r)) != BSM_OK) return rc;
+        diff2_kernel<<<F.G, kBlasThreads, 0, s>>>(rhs, r, r, nv64, F.part);
         reduce_launch(F.part, F.G, F.scalar, s);
         if ((rc = F.host_read(F.scalar, &rr)) != BSM_OK) return rc;
         if (!isfinite(rr32)) rr = rr32;
@@ -339,9 +403,13 @@ int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const voi
       break;
     }
   }
-  // true residual |b - D x| / |b| (into r)
+  // eo: x_o = (b_o + H_oe x_e / 2) / A
+  if (eo && (rc = op_hop(c64, 1, xc, xc + h64, 0, bc + h64, 1.0 / c64.A, 1.0 / (2.0 * c64.A), nullptr, nullptr)) < 0)
+    return rc;
+  // true residual |b - D x| / |b| (D x into r)
   if ((rc = op_dirac(c64, x, r, 0, nullptr, nullptr)) < 0) return rc;
-  diff2_kernel<<<F.G, kBlasThreads, 0, s>>>(bv, r, nullptr, n64, F.part);
+  diff2_kernel<<<F.G, kBlasThreads, 0, s>>>(reinterpret_cast<const double2*>(b), r, nullptr,
+                                            full64 / sizeof(double2), F.part);
   reduce_launch(F.part, F.G, F.scalar, s);
   double res2 = 0.0;
   if ((rc = F.host_read(F.scalar, &res2)) != BSM_OK) return rc;

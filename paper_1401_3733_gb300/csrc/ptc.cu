@@ -182,31 +182,45 @@ __global__ void ptc_permute_kernel(const float2* __restrict__ src, float2* __res
   else dst[ep] = src[e];
 }
 
-// FP64 device spinor (one field) <-> PTC one-channel field (FP32); thread per (p, i)
-__global__ void ptc_pack_kernel(double2* __restrict__ psi, float2* __restrict__ F, Geom g, int d, int unpack) {
+// FP64 device spinor (one field) <-> PTC one-channel field (FP32); thread per (p, i).
+// even_only: psi is the even half alone; the odd rows of F are zero (pack) or ignored (unpack)
+__global__ void ptc_pack_kernel(double2* __restrict__ psi, float2* __restrict__ F, Geom g, int d, int unpack,
+                                int even_only) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * g.Vh) return;
   const int p = t / g.Vh, i = t - p * g.Vh;
+  float2* f = F + ((size_t)p * g.Vh + i) * d * 4;
+  if (even_only && p == 1) {
+    if (!unpack)
+      for (int e = 0; e < 4 * d; ++e) f[e] = make_float2(0.f, 0.f);
+    return;
+  }
   double2* blk = psi + (size_t)p * 4 * d * g.Vh;
   for (int c = 0; c < d; ++c)
     for (int s = 0; s < 4; ++s) {
-      float2* f = F + (((size_t)p * g.Vh + i) * d + c) * 4 + s;
       double2* q = blk + (size_t)(s * d + c) * g.Vh + i;
-      if (unpack) *q = make_double2(f->x, f->y);
-      else *f = make_float2((float)q->x, (float)q->y);
+      if (unpack) *q = make_double2(f[c * 4 + s].x, f[c * 4 + s].y);
+      else f[c * 4 + s] = make_float2((float)q->x, (float)q->y);
     }
 }
 
 // FP32 device spinor (2d planes of float4 (psi[s][c], psi[s+2][c]), s = 0, 1)
-// <-> PTC one-channel field; thread per (p, i)
-__global__ void ptc_pack32_kernel(float4* __restrict__ psi, float2* __restrict__ F, Geom g, int d, int unpack) {
+// <-> PTC one-channel field; thread per (p, i); even_only as above
+__global__ void ptc_pack32_kernel(float4* __restrict__ psi, float2* __restrict__ F, Geom g, int d, int unpack,
+                                  int even_only) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * g.Vh) return;
   const int p = t / g.Vh, i = t - p * g.Vh;
+  float2* f0 = F + ((size_t)p * g.Vh + i) * d * 4;
+  if (even_only && p == 1) {
+    if (!unpack)
+      for (int e = 0; e < 4 * d; ++e) f0[e] = make_float2(0.f, 0.f);
+    return;
+  }
   float4* blk = psi + (size_t)p * 2 * d * g.Vh;
   for (int c = 0; c < d; ++c)
     for (int s = 0; s < 2; ++s) {
-      float2* f = F + (((size_t)p * g.Vh + i) * d + c) * 4;
+      float2* f = f0 + c * 4;
       float4* q = blk + (size_t)(s * d + c) * g.Vh + i;
       if (unpack) *q = make_float4(f[s].x, f[s].y, f[s + 2].x, f[s + 2].y);
       else {
@@ -380,19 +394,21 @@ PtcLayout ptc_layout(const bsm_lattice& L, int C, int nb, bool train) {
 
 size_t ptc_workspace_bytes(const bsm_lattice& L, int C, int nb, bool train) { return ptc_layout(L, C, nb, train).total; }
 
-int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, cudaStream_t s) {
+int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, bool even_only, cudaStream_t s) {
   const Geom g = make_geom(L);
   const int d = rep_info(L.N, L.rep).d;
   ptc_pack_kernel<<<(2 * g.Vh + 127) / 128, 128, 0, s>>>(reinterpret_cast<double2*>(const_cast<double*>(psi)),
-                                                          reinterpret_cast<float2*>(F), g, d, unpack ? 1 : 0);
+                                                          reinterpret_cast<float2*>(F), g, d, unpack ? 1 : 0,
+                                                          even_only ? 1 : 0);
   return BSM_OK;
 }
 
-int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, cudaStream_t s) {
+int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, bool even_only, cudaStream_t s) {
   const Geom g = make_geom(L);
   const int d = rep_info(L.N, L.rep).d;
   ptc_pack32_kernel<<<(2 * g.Vh + 127) / 128, 128, 0, s>>>(reinterpret_cast<float4*>(const_cast<float*>(psi)),
-                                                            reinterpret_cast<float2*>(F), g, d, unpack ? 1 : 0);
+                                                            reinterpret_cast<float2*>(F), g, d, unpack ? 1 : 0,
+                                                            even_only ? 1 : 0);
   return BSM_OK;
 }
 

@@ -623,7 +623,7 @@ def run_precond(peak, peak_kind, steps):
                        f"m0={cfg['m0']}, antiperiodic time; D x = b to 1e-10",
            "network": f"2 parallel-transport layers 1->{C}->1 channels", "training": train}
     ptc = dict(precond=bsm.FGCR_PTC, channels=C)
-    mixed = dict(prec_inner=bsm.F32, inner_tol=1e-3)
+    mixed = dict(prec_inner=bsm.F32, inner_tol=1e-3, check_every=4)
     m = cfg["restart"]
     cases = {
         "fgcr_none_fp64": bsm.fgcr_opts(tol=1e-10, max_iter=4000, restart=m),

@@ -386,6 +386,8 @@ typedef struct {
   int32_t eo;        /* nonzero: solve the even-site Schur system Dhat x_e = bhat_e
                         (bhat_e = b_e + H_eo b_o / (2A)), preconditioned by the
                         even-even block of M, then x_o = (b_o + H_oe x_e / 2) / A */
+  int32_t check_every;/* host convergence test every this many steps (0 -> 1);
+                        up to check_every - 1 steps may run past convergence */
 } bsm_fgcr_opts;
 typedef struct {
   int32_t iters;     /* directions (preconditioner applications) in total */

@@ -459,7 +459,7 @@ int bsm_fgcr_solve(const bsm_lattice* lat, const void* U_rep64, const void* U_re
     return BSM_EINVAL;
   if (opts->precond != BSM_FGCR_NONE && opts->precond != BSM_FGCR_PTC) return BSM_EINVAL;
   if (opts->prec_inner != BSM_F64 && opts->prec_inner != BSM_F32) return BSM_EUNSUPPORTED;
-  if (!(opts->inner_tol >= 0.0) || opts->inner_tol >= 1.0) return BSM_EINVAL;
+  if (!(opts->inner_tol >= 0.0) || opts->inner_tol >= 1.0 || opts->check_every < 0) return BSM_EINVAL;
   if (opts->prec_inner == BSM_F32 && !aligned(U_rep32)) return BSM_EINVAL;
   if (opts->precond == BSM_FGCR_PTC) {
     if ((rc = check_ptc(lat, opts->channels, 1)) != BSM_OK) return rc;

@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kBlasThreads) cg_xr_kernel(typename ElemOf<P>:
     r[k] = rk;
     acc += edot(rk, rk);
   }
-  block_sum_store<kBlasThreads>(acc, partials);
+  block_sum_store_wide<kBlasThreads>(acc, partials);
 }
 
 // p = r + beta p
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kBlasThreads) dot_kernel(const typename ElemOf
   double acc = 0.0;
   for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads)
     acc += edot(a[k], b[k]);
-  block_sum_store<kBlasThreads>(acc, partials);
+  block_sum_store_wide<kBlasThreads>(acc, partials);
 }
 
 template <typename P>
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kBlasThreads) axpby_kernel(double a, const typ
     y[k] = v;
     acc += edot(v, v);
   }
-  if (partials != nullptr) block_sum_store<kBlasThreads>(acc, partials);
+  if (partials != nullptr) block_sum_store_wide<kBlasThreads>(acc, partials);
 }
 
 // FP64/DF64 and FP32 half spinors pair their components differently: FP32

@@ -428,8 +428,19 @@ struct LinkIO<BF16, D, true> {
 };
 
 // ---------------------------------------------------------------------------
-// block reduction of one double per thread -> one partial per block
-// (fixed shuffle tree, so the sum is deterministic for a fixed launch shape)
+// block reductions -> one FP64 partial per block, in a fixed order (so the
+// sum is deterministic for a fixed launch shape).  Every thread of the block
+// must reach them.  GB300 issues an FP64 warp instruction only every ~16
+// cycles per SM, so the cost of a reduction is counted in FP64 warp
+// instructions:
+//  - block_sum_store: a shuffle tree in every warp, then one warp over the
+//    per-warp sums (5 (W + 1) FP64 adds for W warps, W doubles of shared
+//    memory); for kernels whose own FP64 work dwarfs it;
+//  - block_sum_store_wide: the values go to shared memory and one warp adds
+//    them (W - 1 + 5 adds, THREADS doubles of shared memory); for short
+//    memory-bound vector kernels;
+//  - block_sums_store_f32 (below): FP32 shuffle trees, then W FP64 adds per
+//    value; for kernels whose per-thread sums are FP32.
 // ---------------------------------------------------------------------------
 template <int THREADS>
 __device__ __forceinline__ void block_sum_store(double v, double* out) {
@@ -445,6 +456,47 @@ __device__ __forceinline__ void block_sum_store(double v, double* out) {
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[blockIdx.x] = s;
   }
+}
+
+template <int THREADS>
+__device__ __forceinline__ void block_sum_store_wide(double v, double* out) {
+  __shared__ double buf[THREADS];
+  buf[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = buf[threadIdx.x];
+#pragma unroll
+    for (int k = threadIdx.x + 32; k < THREADS; k += 32) s += buf[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+  }
+  __syncthreads();  // buf may be reused by the next call
+}
+
+// NV FP32 accumulators per thread -> NV FP64 block partials at
+// out[j * stride + blockIdx.x]: FP32 shuffle trees within each warp, then
+// the per-warp sums added in FP64 by NV threads (for FP32 vector kernels,
+// whose per-thread sums are FP32 already)
+template <int THREADS, int NV>
+__device__ __forceinline__ void block_sums_store_f32(float (&v)[NV], double* out, size_t stride) {
+  constexpr int W = THREADS / 32;
+  __shared__ double buf[NV][W];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    float x = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) buf[j][threadIdx.x >> 5] = (double)x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) s += buf[threadIdx.x][w];
+    out[threadIdx.x * stride + blockIdx.x] = s;
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------

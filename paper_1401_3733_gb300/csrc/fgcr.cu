@@ -54,36 +54,61 @@ __device__ __forceinline__ T cadd_mul(T x, double2 c, T a) {  // x + c a
   return x;
 }
 
+// per-thread sums -> block partials at out[j * stride + blockIdx.x]
+template <int NV>
+__device__ __forceinline__ void store_sums(float (&v)[NV], double* out, size_t stride) {
+  block_sums_store_f32<kBlasThreads, NV>(v, out, stride);
+}
+template <int NV>
+__device__ __forceinline__ void store_sums(double (&v)[NV], double* out, size_t stride) {
+#pragma unroll
+  for (int j = 0; j < NV; ++j) block_sum_store_wide<kBlasThreads>(v[j], out + j * stride);
+}
+
 constexpr int kDotChunk = 8;  // directions per dot launch (accumulators in registers)
 
-// partials of <w_j, v> = sum conj(w_j) v for j = j0 .. j0 + cnt - 1 (cnt <= kDotChunk), w_j at
-// basis + j * stride: re of j at [(2 (j - j0)) G + blk], im at [(2 (j - j0) + 1) G + blk]
-template <typename T>
+// partials of <w_j, v> = sum conj(w_j) v for j = j0 .. j0 + CNT - 1, w_j at
+// basis + j * stride: re of j at [(2 (j - j0)) G + blk], im at [(2 (j - j0) + 1) G + blk].
+// CNT is a template constant so that all CNT + 1 loads of an element issue together.
+template <typename T, int CNT>
 __global__ void __launch_bounds__(kBlasThreads) multi_dot_kernel(const T* __restrict__ basis, size_t stride, int j0,
-                                                                 int cnt, const T* __restrict__ v, size_t n,
+                                                                 const T* __restrict__ v, size_t n,
                                                                  double* partials) {
   using R = typename Arith<T>::R;
-  R re[kDotChunk], im[kDotChunk];
+  R re[CNT], im[CNT];
 #pragma unroll
-  for (int j = 0; j < kDotChunk; ++j) re[j] = im[j] = 0;
+  for (int j = 0; j < CNT; ++j) re[j] = im[j] = 0;
+  const T* b0 = basis + (size_t)j0 * stride;
   for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
     const T y = v[k];
+    T x[CNT];
 #pragma unroll
-    for (int j = 0; j < kDotChunk; ++j)
-      if (j < cnt) {
-        const T x = basis[(size_t)(j0 + j) * stride + k];
-        re[j] += x.x * y.x + x.y * y.y;
-        im[j] += x.x * y.y - x.y * y.x;
-      }
-  }
+    for (int j = 0; j < CNT; ++j) x[j] = b0[(size_t)j * stride + k];
 #pragma unroll
-  for (int j = 0; j < kDotChunk; ++j)
-    if (j < cnt) {
-      block_sum_store<kBlasThreads>((double)re[j], partials + (size_t)(2 * j) * gridDim.x);
-      __syncthreads();
-      block_sum_store<kBlasThreads>((double)im[j], partials + (size_t)(2 * j + 1) * gridDim.x);
-      __syncthreads();
+    for (int j = 0; j < CNT; ++j) {
+      re[j] += x[j].x * y.x + x[j].y * y.y;
+      im[j] += x[j].x * y.y - x[j].y * y.x;
     }
+  }
+  R sums[2 * CNT];
+#pragma unroll
+  for (int j = 0; j < CNT; ++j) {
+    sums[2 * j] = re[j];
+    sums[2 * j + 1] = im[j];
+  }
+  store_sums<2 * CNT>(sums, partials, gridDim.x);
+}
+
+template <typename T>
+void multi_dot_launch(int G, const T* basis, size_t stride, int j0, int cnt, const T* v, size_t n, double* part,
+                      cudaStream_t s) {
+  switch (cnt) {
+#define BSM_MD(C) \
+  case C: multi_dot_kernel<T, C><<<G, kBlasThreads, 0, s>>>(basis, stride, j0, v, n, part); break;
+    BSM_MD(1) BSM_MD(2) BSM_MD(3) BSM_MD(4) BSM_MD(5) BSM_MD(6) BSM_MD(7) BSM_MD(8)
+#undef BSM_MD
+    default: break;
+  }
 }
 
 __device__ double sum_partials(const double* __restrict__ p, int n) {
@@ -113,18 +138,21 @@ __global__ void gs_coef_kernel(const double* __restrict__ partials, int nblk, in
   }
 }
 
-// w -= sum_j coef_j w_j ; z -= sum_j coef_j z_j  (j < k; w_j, z_j at wb, zb + j * stride)
+// w -= sum_j coef_j w_j ; z -= sum_j coef_j z_j  (j < k <= 64; w_j, z_j at wb, zb + j * stride)
 template <typename T>
 __global__ void __launch_bounds__(kBlasThreads) gs_update_kernel(T* __restrict__ w, T* __restrict__ z,
                                                                  const T* __restrict__ wb, const T* __restrict__ zb,
                                                                  size_t stride, int k, size_t n,
                                                                  const double2* __restrict__ coef) {
+  __shared__ double2 c[64];
+  for (int j = threadIdx.x; j < k; j += kBlasThreads) c[j] = coef[j];
+  __syncthreads();
   for (size_t e = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kBlasThreads) {
     T x = w[e], y = z[e];
+#pragma unroll 4
     for (int j = 0; j < k; ++j) {
-      const double2 c = coef[j];
-      x = csub_mul(x, c, wb[(size_t)j * stride + e]);
-      y = csub_mul(y, c, zb[(size_t)j * stride + e]);
+      x = csub_mul(x, c[j], wb[(size_t)j * stride + e]);
+      y = csub_mul(y, c[j], zb[(size_t)j * stride + e]);
     }
     w[e] = x;
     z[e] = y;
@@ -143,11 +171,8 @@ __global__ void __launch_bounds__(kBlasThreads) wr_kernel(const T* __restrict__ 
     re += x.x * y.x + x.y * y.y;
     im += x.x * y.y - x.y * y.x;
   }
-  block_sum_store<kBlasThreads>((double)ww, partials);
-  __syncthreads();
-  block_sum_store<kBlasThreads>((double)re, partials + gridDim.x);
-  __syncthreads();
-  block_sum_store<kBlasThreads>((double)im, partials + 2 * gridDim.x);
+  R sums[3] = {ww, re, im};
+  store_sums<3>(sums, partials, gridDim.x);
 }
 
 // norm2_k = |w|^2, alpha = <w, r> / |w|^2 (one block)
@@ -175,7 +200,8 @@ __global__ void __launch_bounds__(kBlasThreads) xr_kernel(T* __restrict__ x, T* 
     r[k] = q;
     rr += q.x * q.x + q.y * q.y;
   }
-  block_sum_store<kBlasThreads>((double)rr, partials);
+  R sums[1] = {rr};
+  store_sums<1>(sums, partials, gridDim.x);
 }
 
 // partials of |a - b|^2 (b may be null: |a|^2); with out != null also out = a - b
@@ -191,7 +217,7 @@ __global__ void __launch_bounds__(kBlasThreads) diff2_kernel(const double2* __re
     if (out != nullptr) out[k] = v;
     s = fma(v.x, v.x, fma(v.y, v.y, s));
   }
-  block_sum_store<kBlasThreads>(s, partials);
+  block_sum_store_wide<kBlasThreads>(s, partials);
 }
 
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
@@ -287,6 +313,7 @@ struct Fgcr {
     const size_t n = bytes / sizeof(T), stride = bytes / sizeof(T);
     T* zb = reinterpret_cast<T*>(w + y.basis);
     T* wb = zb + stride * o.restart;
+    const int check = o.check_every > 0 ? o.check_every : 1;
     int it = 0, rc;
     for (int k = 0; k < o.restart && it < budget; ++k) {
       T* z = zb + stride * k;
@@ -296,7 +323,7 @@ struct Fgcr {
       if (k > 0) {
         for (int j0 = 0; j0 < k; j0 += kDotChunk) {
           const int cnt = k - j0 < kDotChunk ? k - j0 : kDotChunk;
-          multi_dot_kernel<T><<<G, kBlasThreads, 0, s>>>(wb, stride, j0, cnt, wv, n, part);
+          multi_dot_launch<T>(G, wb, stride, j0, cnt, wv, n, part, s);
           gs_coef_kernel<<<cnt, kBlasThreads, 0, s>>>(part, G, j0, norm2, coef);
         }
         gs_update_kernel<T><<<G, kBlasThreads, 0, s>>>(wv, z, wb, zb, stride, k, n, coef);
@@ -305,9 +332,13 @@ struct Fgcr {
       alpha_kernel<<<1, kBlasThreads, 0, s>>>(part, G, norm2 + k, alpha);
       xr_kernel<T><<<G, kBlasThreads, 0, s>>>(x, r, z, wv, n, alpha, part);
       reduce_launch(part, G, scalar, s);
-      if ((rc = host_read(scalar, rr)) != BSM_OK) return rc;
       ++it;
-      if (!isfinite(*rr) || *rr <= stop2) break;
+      // the host reads |r|^2 every check_every steps (and at the cycle's end):
+      // fewer round trips, at most check_every - 1 steps past convergence
+      if (it % check == 0 || k == o.restart - 1 || it == budget) {
+        if ((rc = host_read(scalar, rr)) != BSM_OK) return rc;
+        if (!isfinite(*rr) || *rr <= stop2) break;
+      }
     }
     return it;
   }

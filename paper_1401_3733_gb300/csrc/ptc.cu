@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kBlasThreads) ptc_loss_kernel(const float2* __
     G[k] = make_float2((float)(2.0 * w * dx), (float)(2.0 * w * dy));
     acc += w * ((double)dx * dx + (double)dy * dy);
   }
-  block_sum_store<kBlasThreads>(acc, partials);
+  block_sum_store_wide<kBlasThreads>(acc, partials);
 }
 
 // |E_b|^2 per sample -> 1/|E_b|^2 (one block per sample)

@@ -351,3 +351,18 @@ def test_even_odd_fgcr_solves_the_full_system(precond, prec_inner):
     st, s_full, _ = fgcr(blat, U64, U32, gpu_spinor(blat, b, bsm.F64),
                          bsm.fgcr_opts(tol=1e-10, restart=12, prec_inner=prec_inner, inner_tol=1e-3, **kw), W)
     assert st == bsm.OK and s_eo.iters < s_full.iters, (s_eo.iters, s_full.iters)
+
+
+def test_fgcr_check_every_bounds_the_overshoot():
+    dims, N = (4, 4, 4, 4), 2
+    olat, blat = lats(dims, N, bsm.FUND, (np.pi, 0, 0, 0), m0=0.05)
+    U = fields.gauge_field(dims, N, "smooth", seed=32, eps=0.4)
+    R = orc.links_to_rep(olat, U)
+    U64, U32 = gpu_links(blat, U, bsm.F64), gpu_links(blat, U, bsm.F32)
+    b = fields.gaussian_spinor(dims, N, 33)
+    bd = gpu_spinor(blat, b, bsm.F64)
+    st1, s1, _ = fgcr(blat, U64, U32, bd, bsm.fgcr_opts(tol=1e-10, restart=12, eo=True))
+    st4, s4, x4 = fgcr(blat, U64, U32, bd, bsm.fgcr_opts(tol=1e-10, restart=12, eo=True, check_every=4))
+    assert st1 == bsm.OK and st4 == bsm.OK
+    assert s1.iters <= s4.iters <= s1.iters + 3 + s4.cycles
+    assert rel(orc.dirac(olat, R, to_canon(blat, x4, bsm.F64)), b) <= 1e-10

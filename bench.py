@@ -672,7 +672,7 @@ def run_precond(peak, peak_kind, steps):
     return res
 
 
-def ptc_apply_roofline(W, C, peak, peak_kind, steps):
+def ptc_apply_roofline(W, C, peak, peak_kind, steps, dims=None):
     """One BF16 network application (fused transport + two-GEMM kernel, then
     the 9-point stencil) on the 32^3 x 64 lattice, L2 flushed between
     applications.  Algorithmic bytes per site: the one-channel FP32 input and
@@ -680,7 +680,7 @@ def ptc_apply_roofline(W, C, peak, peak_kind, steps):
     import torch
     from paper_1401_3733_gb300 import bsm
 
-    dims, N = WORKLOAD["dims"], WORKLOAD["N"]
+    dims, N = tuple(dims or WORKLOAD["dims"]), WORKLOAD["N"]
     lat = bsm.lattice(dims, N, bsm.FUND, WORKLOAD["m0"], WORKLOAD["phase"])
     V = int(np.prod(dims))
     U = torch.zeros((V, 4, N, N), dtype=torch.complex128, device="cuda")
@@ -709,6 +709,18 @@ def ptc_apply_roofline(W, C, peak, peak_kind, steps):
             "algorithmic_bytes": alg, "achieved_gbs": round(alg / (ms * 1e-3) / 1e9, 1),
             "peak_gbs": peak, "peak_kind": peak_kind, "frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4),
             "launches": 3, "l2": "flushed between applications"}
+
+
+def run_ptc_apply_only(args):
+    import torch
+
+    peak, peak_src = load_peaks()
+    C = PRECOND["channels"]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    W = [0.1 * torch.randn((36, 4 * C), dtype=torch.complex64, device="cuda", generator=g),
+         0.1 * torch.randn((36 * C, 4), dtype=torch.complex64, device="cuda", generator=g)]
+    print(json.dumps({"ptc_apply": ptc_apply_roofline(W, C, peak, peak_src, args.steps, args.lattice)}))
 
 
 def run_cg(lat, links, b, max_iter):
@@ -756,11 +768,16 @@ def main():
     ap.add_argument("--no-mrhs", action="store_true", help="skip the multi-RHS 24^4 three-theory lines")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-lattice batch and small-lattice CG lines")
     ap.add_argument("--no-precond", action="store_true", help="skip the learned-preconditioner (FGCR) line")
+    ap.add_argument("--ptc-apply-only", action="store_true",
+                    help="only the BF16 network application's roofline (on --lattice, random weights); "
+                         "the profiling entry for its kernels")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.ptc_apply_only:
+        run_ptc_apply_only(args)
     else:
         run_ours(args)
 

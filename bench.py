@@ -50,6 +50,11 @@ def bytes_per_site(d, w, real=False):
     return (8 * d * d + 16 * d) * w if real else (16 * d * d + 16 * d) * w
 
 
+def bytes_per_site_r12(w):
+    """SU(3) hop with two-row links: 8 links of 12 reals + input + output spinor (d = 3)."""
+    return (8 * 12 + 2 * 24) * w
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -240,12 +245,15 @@ def run_ours(args):
     ev_l1.record()
     bsm.bsm_links_to_rep(lat, Ud, links[bsm.F64], bsm.F64)
     bsm.bsm_links_to_rep(lat, Ud, links[bsm.DF64], bsm.DF64)
+    links[bsm.F32R12] = bsm.empty_field(lat, bsm.FIELD_LINKS, bsm.F32R12)   # SU(3): two rows per link
+    bsm.bsm_links_to_rep(lat, Ud, links[bsm.F32R12], bsm.F32R12)
     del Ud
     psid = torch.from_numpy(psi).cuda()
     src = {p: bsm.empty_field(lat, bsm.FIELD_SPINOR, p) for p in (bsm.F64, bsm.F32, bsm.DF64)}
     dst = {p: bsm.empty_field(lat, bsm.FIELD_SPINOR, p) for p in (bsm.F64, bsm.F32, bsm.DF64)}
     for p in (bsm.F64, bsm.F32, bsm.DF64):
         bsm.bsm_pack_spinor(lat, psid, src[p], p)
+    src[bsm.F32R12], dst[bsm.F32R12] = src[bsm.F32], dst[bsm.F32]   # spinors as FP32
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
     torch.cuda.synchronize()
     links_ms = ev_l0.elapsed_time(ev_l1)
@@ -297,18 +305,22 @@ def run_ours(args):
 
     # FP64 and FP64-accurate double-float Dslash on the same inputs (their own
     # lines; the FP64 units bound the first on this part)
-    ms_other = {bsm.F64: float("nan"), bsm.DF64: float("nan")}
+    ms_other = {bsm.F64: float("nan"), bsm.DF64: float("nan"), bsm.F32R12: float("nan")}
     if not args.no_fp64:
-        for prec in (bsm.F64, bsm.DF64):
+        for prec in (bsm.F64, bsm.DF64, bsm.F32R12):
             evp = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(max(3, args.steps // 4))]
             for _ in range(2):
                 dslash_step(prec)
+            torch.cuda.nvtx.range_push({bsm.F64: "dslash_fp64", bsm.DF64: "dslash_df64",
+                                        bsm.F32R12: "dslash_f32r12"}[prec])
             for e in evp:
                 flush.zero_()
                 dslash_step(prec, e)
+            torch.cuda.nvtx.range_pop()
             torch.cuda.synchronize()
             ms_other[prec] = sum(e[0].elapsed_time(e[2]) for e in evp) / len(evp)
-    ms64, msdf = ms_other[bsm.F64], ms_other[bsm.DF64]
+    ms64, msdf, ms12 = ms_other[bsm.F64], ms_other[bsm.DF64], ms_other[bsm.F32R12]
+    r12_bytes = 2 * bytes_per_site_r12(4) * Vh
 
     # end to end through the public API: pinned host canonical FP64 input ->
     # pack -> hop on both parity blocks -> unpack -> pinned host output
@@ -358,6 +370,10 @@ def run_ours(args):
         "dslash_df64": {"gflops": round(flop_step / (msdf * 1e-3) / 1e9, 2), "ms_per_step": round(msdf, 4),
                         "bound": "alu (FP32 double-float arithmetic)",
                         "hbm_frac": round(2 * bytes_per_site(d, 8) * Vh / (msdf * 1e-3) / 1e9 / peak, 4)},
+        "dslash_f32r12": {"gflops": round(flop_step / (ms12 * 1e-3) / 1e9, 2), "ms_per_step": round(ms12, 4),
+                          "links": "SU(3) stored as two rows (12 reals), third row rebuilt in registers",
+                          "bound": "hbm", "algorithmic_bytes_per_site": bytes_per_site_r12(4),
+                          "hbm_frac": round(r12_bytes / (ms12 * 1e-3) / 1e9 / peak, 4)},
         "links_to_rep_ms_f32": round(links_ms, 3),
         "e2e": {"value": round(e2e_value, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": io_bytes,
                 "d2h_bytes_per_step": io_bytes, "ms_per_step": round(e2e_ms, 4)},
@@ -732,19 +748,19 @@ def run_cg(lat, links, b, max_iter):
     from paper_1401_3733_gb300 import bsm
 
     res = {}
-    cases = (("mixed_df64", bsm.F32, bsm.DF64), ("mixed", bsm.F32, bsm.F64), ("fp64", bsm.F64, bsm.F64),
-             ("df64", bsm.DF64, bsm.DF64))
+    cases = (("mixed_df64", bsm.F32, bsm.DF64), ("mixed_df64_r12", bsm.F32R12, bsm.DF64),
+             ("mixed", bsm.F32, bsm.F64), ("fp64", bsm.F64, bsm.F64), ("df64", bsm.DF64, bsm.DF64))
     for name, inner, outer in cases:
         ws = torch.empty(bsm.bsm_workspace_bytes(lat, bsm.CALL_CG, inner), dtype=torch.uint8, device="cuda")
         x = torch.zeros_like(b)
-        st, stats = bsm.bsm_cg_solve(lat, links[outer], links[bsm.F32], b, x,
+        st, stats = bsm.bsm_cg_solve(lat, links[outer], links[inner if inner == bsm.F32R12 else bsm.F32], b, x,
                                      bsm.cg_opts(tol=1e-10, max_iter=max_iter, prec_inner=inner, prec_outer=outer),
                                      ws, raise_on_error=False)
         res[name] = {"status": bsm.bsm_strerror(st), "seconds": round(stats.seconds, 4), "iters": stats.iters,
                      "reliable_updates": stats.reliable_updates, "true_res_normal": stats.true_res_normal,
                      "true_res_full": stats.true_res_full}
         del ws
-    best = min(("mixed", "mixed_df64"), key=lambda k: res[k]["seconds"])
+    best = min(("mixed", "mixed_df64", "mixed_df64_r12"), key=lambda k: res[k]["seconds"])
     res["best_mixed"] = best
     if res[best]["seconds"] > 0:
         res["fp64_over_mixed_time"] = round(res["fp64"]["seconds"] / res[best]["seconds"], 3)
@@ -763,7 +779,7 @@ def main():
     ap.add_argument("--cg-max-iter", type=int, default=20000)
     ap.add_argument("--lattice", type=int, nargs=4, metavar=("T", "X", "Y", "Z"),
                     help="override the lattice (profiling of a smaller case); default 64 32 32 32")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 Dslash line")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64, DF64 and two-row-link FP32 Dslash lines")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-mrhs", action="store_true", help="skip the multi-RHS 24^4 three-theory lines")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-lattice batch and small-lattice CG lines")

@@ -21,7 +21,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 # enums of bsm.h
 OK, EINVAL, EUNSUPPORTED, ECUDA, EWORKSPACE, ENOCONV, EBREAKDOWN, ENAN, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8
 FUND, ADJ, SYM, ASYM = 0, 1, 2, 3
-F64, F32, DF64, BF16 = 0, 1, 2, 3
+F64, F32, DF64, BF16, F32R12 = 0, 1, 2, 3, 4
 EVEN, ODD, FULL = 0, 1, 2
 OP_DHAT, OP_DHAT_DAG, OP_DHAT_DAG_DHAT = 0, 1, 2
 FIELD_LINKS, FIELD_SPINOR, FIELD_HALF_SPINOR, FIELD_FUND_CANON, FIELD_SPINOR_CANON = 0, 1, 2, 3, 4

@@ -92,7 +92,13 @@ int check_lattice(const bsm_lattice* L) {
 }
 
 bool aligned(const void* p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
-bool prec_ok(int prec) { return prec == BSM_F64 || prec == BSM_F32 || prec == BSM_DF64 || prec == BSM_BF16; }
+bool prec_ok(int prec) {
+  return prec == BSM_F64 || prec == BSM_F32 || prec == BSM_DF64 || prec == BSM_BF16 || prec == BSM_F32R12;
+}
+// two-row links exist for SU(3) fundamental only
+bool prec_lat_ok(const bsm_lattice* L, int prec) {
+  return prec_ok(prec) && (prec != BSM_F32R12 || (L->N == 3 && L->rep == BSM_FUND));
+}
 
 int finish(int rc) {
   if (rc != BSM_OK) return rc;
@@ -174,7 +180,7 @@ size_t bsm_field_bytes(const bsm_lattice* lat, int32_t kind, int32_t prec) {
     case BSM_FIELD_SPINOR_CANON: return V * 4 * ri.d * 16;
     default: break;
   }
-  if (!prec_ok(prec)) return 0;
+  if (!prec_lat_ok(lat, prec)) return 0;
   switch (kind) {
     case BSM_FIELD_LINKS: return 2 * link_block_bytes(g.Vh, ri.d, ri.real, prec);
     case BSM_FIELD_SPINOR: return 2 * half_spinor_bytes(g.Vh, ri.d, prec);
@@ -184,7 +190,7 @@ size_t bsm_field_bytes(const bsm_lattice* lat, int32_t kind, int32_t prec) {
 }
 
 size_t bsm_workspace_bytes(const bsm_lattice* lat, int32_t call, int32_t prec) {
-  if (check_lattice(lat) != BSM_OK || !prec_ok(prec)) return 0;
+  if (check_lattice(lat) != BSM_OK || !prec_lat_ok(lat, prec)) return 0;
   const Geom g = make_geom(*lat);
   const RepInfo ri = rep_info(lat->N, lat->rep);
   if (call == BSM_CALL_DIRAC_EO) return 2 * half_spinor_bytes(g.Vh, ri.d, prec);
@@ -192,7 +198,8 @@ size_t bsm_workspace_bytes(const bsm_lattice* lat, int32_t call, int32_t prec) {
     // the largest layout over even-odd/full and, for a mixed inner
     // precision, over both outer precisions
     size_t m = 0;
-    const int outers[2] = {prec == BSM_F32 ? BSM_F64 : prec, prec == BSM_F32 ? BSM_DF64 : prec};
+    const bool mixed = prec == BSM_F32 || prec == BSM_F32R12;
+    const int outers[2] = {mixed ? BSM_F64 : prec, mixed ? BSM_DF64 : prec};
     for (int k = 0; k < 2; ++k)
       for (int eo = 0; eo < 2; ++eo) {
         const size_t v = cg_workspace_bytes(*lat, prec, eo, outers[k]);
@@ -206,7 +213,7 @@ size_t bsm_workspace_bytes(const bsm_lattice* lat, int32_t call, int32_t prec) {
 int bsm_pack_spinor(const bsm_lattice* lat, const double* canon, void* dev, int32_t prec, void* stream) {
   int rc = check_lattice(lat);
   if (rc != BSM_OK) return rc;
-  if (!prec_ok(prec)) return BSM_EUNSUPPORTED;
+  if (!prec_lat_ok(lat, prec)) return BSM_EUNSUPPORTED;
   if (!aligned(canon) || !aligned(dev)) return BSM_EINVAL;
   pack_spinor_launch(*lat, canon, dev, rep_info(lat->N, lat->rep).d, prec, false, 1, (cudaStream_t)stream);
   return finish(BSM_OK);
@@ -215,7 +222,7 @@ int bsm_pack_spinor(const bsm_lattice* lat, const double* canon, void* dev, int3
 int bsm_unpack_spinor(const bsm_lattice* lat, const void* dev, double* canon, int32_t prec, void* stream) {
   int rc = check_lattice(lat);
   if (rc != BSM_OK) return rc;
-  if (!prec_ok(prec)) return BSM_EUNSUPPORTED;
+  if (!prec_lat_ok(lat, prec)) return BSM_EUNSUPPORTED;
   if (!aligned(canon) || !aligned(dev)) return BSM_EINVAL;
   pack_spinor_launch(*lat, canon, const_cast<void*>(dev), rep_info(lat->N, lat->rep).d, prec, true, 1,
                      (cudaStream_t)stream);
@@ -225,7 +232,7 @@ int bsm_unpack_spinor(const bsm_lattice* lat, const void* dev, double* canon, in
 int bsm_links_to_rep(const bsm_lattice* lat, const double* U_fund, void* U_rep, int32_t prec, void* stream) {
   int rc = check_lattice(lat);
   if (rc != BSM_OK) return rc;
-  if (!prec_ok(prec)) return BSM_EUNSUPPORTED;
+  if (!prec_lat_ok(lat, prec)) return BSM_EUNSUPPORTED;
   if (!aligned(U_fund) || !aligned(U_rep)) return BSM_EINVAL;
   return finish(links_to_rep_launch(*lat, U_fund, U_rep, prec, (cudaStream_t)stream));
 }
@@ -234,7 +241,7 @@ int bsm_dslash(const bsm_lattice* lat, const void* U_rep, const void* in, void* 
                int32_t dagger, int32_t prec, void* stream) {
   int rc = check_lattice(lat);
   if (rc != BSM_OK) return rc;
-  if (!prec_ok(prec)) return BSM_EUNSUPPORTED;
+  if (!prec_lat_ok(lat, prec)) return BSM_EUNSUPPORTED;
   if (!aligned(U_rep) || !aligned(in) || !aligned(out)) return BSM_EINVAL;
   if (out_parity != BSM_EVEN && out_parity != BSM_ODD && out_parity != BSM_FULL) return BSM_EINVAL;
   const OpCtx c = make_ctx(*lat, U_rep, prec, (cudaStream_t)stream);
@@ -344,7 +351,7 @@ int bsm_dirac_eo(const bsm_lattice* lat, const void* U_rep, const void* in_e, vo
                  int32_t prec, void* workspace, size_t workspace_bytes, void* stream) {
   int rc = check_lattice(lat);
   if (rc != BSM_OK) return rc;
-  if (!prec_ok(prec)) return BSM_EUNSUPPORTED;
+  if (!prec_lat_ok(lat, prec)) return BSM_EUNSUPPORTED;
   if (!aligned(U_rep) || !aligned(in_e) || !aligned(out_e) || !aligned(workspace)) return BSM_EINVAL;
   if (op != BSM_OP_DHAT && op != BSM_OP_DHAT_DAG && op != BSM_OP_DHAT_DAG_DHAT) return BSM_EINVAL;
   const OpCtx c = make_ctx(*lat, U_rep, prec, (cudaStream_t)stream);
@@ -369,9 +376,11 @@ int bsm_cg_solve(const bsm_lattice* lat, const void* U_rep64, const void* U_rep3
   if (opts == nullptr || !(opts->tol > 0.0) || opts->max_iter < 1 || opts->delta < 0.0 || opts->delta >= 1.0)
     return BSM_EINVAL;
   if (opts->prec_outer != BSM_F64 && opts->prec_outer != BSM_DF64) return BSM_EUNSUPPORTED;
-  if (opts->prec_inner != BSM_F32 && opts->prec_inner != opts->prec_outer) return BSM_EUNSUPPORTED;
+  const bool mixed = opts->prec_inner == BSM_F32 || opts->prec_inner == BSM_F32R12;
+  if (!mixed && opts->prec_inner != opts->prec_outer) return BSM_EUNSUPPORTED;
+  if (!prec_lat_ok(lat, opts->prec_inner)) return BSM_EUNSUPPORTED;
   if (!aligned(U_rep64) || !aligned(b) || !aligned(x) || !aligned(workspace)) return BSM_EINVAL;
-  if (opts->prec_inner == BSM_F32 && !aligned(U_rep32)) return BSM_EINVAL;
+  if (mixed && !aligned(U_rep32)) return BSM_EINVAL;
   if (workspace_bytes < cg_workspace_bytes(*lat, opts->prec_inner, opts->eo != 0, opts->prec_outer))
     return BSM_EWORKSPACE;
   const size_t full = bsm_field_bytes(lat, BSM_FIELD_SPINOR, BSM_F64);

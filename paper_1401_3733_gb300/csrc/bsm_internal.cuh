@@ -64,9 +64,18 @@ struct BF16 {
   using R = float;
   static constexpr int prec = BSM_BF16;
 };
+// FP32 with SU(3) links stored as their first two rows (third rebuilt)
+struct F32R12 {
+  using R = float;
+  static constexpr int prec = BSM_F32R12;
+};
 
 // bytes per real number of a precision (DF64 stores two floats)
-inline size_t real_bytes(int prec) { return prec == BSM_F32 ? 4 : prec == BSM_BF16 ? 2 : 8; }
+inline size_t real_bytes(int prec) {
+  return (prec == BSM_F32 || prec == BSM_F32R12) ? 4 : prec == BSM_BF16 ? 2 : 8;
+}
+// precision of the vectors (spinors) that go with links at `prec`
+__host__ __device__ inline int vector_prec(int prec) { return prec == BSM_F32R12 ? BSM_F32 : prec; }
 
 // load through L1 (data shared by several threads) or with the streaming hint
 template <bool L1, typename T>
@@ -96,6 +105,7 @@ constexpr int kLinkTile = 32;
 inline size_t padded_sites(int64_t Vh) { return (size_t)((Vh + kLinkTile - 1) / kLinkTile) * kLinkTile; }
 // bytes of the links of one output parity
 inline size_t link_block_bytes(int64_t Vh, int d, bool real, int prec) {
+  if (prec == BSM_F32R12) return padded_sites(Vh) * 8 * 12 * 4;  // two rows of SU(3): 12 floats per link
   return padded_sites(Vh) * 8 * d * d * real_bytes(prec) * (real ? 1 : 2);
 }
 // element offset of (plane, site i) in a tiled link block of `planes` planes
@@ -149,6 +159,26 @@ __device__ __forceinline__ void eo_neighbours(const Geom& g, int i, int p, int n
   nb[3] = row * g.Zh + (zb >> 1);
 }
 
+// boundary crossings of eo site i of parity p: bit mu set when its forward
+// neighbour wraps (x_mu = L_mu - 1), bit 4 + mu when its backward one does (x_mu = 0)
+__device__ __forceinline__ unsigned eo_edges(const Geom& g, int i, int p) {
+  const int k = i % g.Zh;
+  const int row = i / g.Zh;
+  const int y = row % g.Y;
+  const int r2 = row / g.Y;
+  const int x = r2 % g.X;
+  const int t = r2 / g.X;
+  const int z = 2 * k + ((t + x + y + p) & 1);
+  const int c[4] = {t, x, y, z}, L[4] = {g.T, g.X, g.Y, 2 * g.Zh};
+  unsigned m = 0;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    if (c[mu] == L[mu] - 1) m |= 1u << mu;
+    if (c[mu] == 0) m |= 1u << (4 + mu);
+  }
+  return m;
+}
+
 // ---------------------------------------------------------------------------
 // spinor layout access
 // ---------------------------------------------------------------------------
@@ -178,6 +208,11 @@ struct SpinorIO<F64, D> {
 };
 
 template <int D>
+struct SpinorIO<F32, D>;
+template <int D>
+struct SpinorIO<F32R12, D>;
+
+template <int D>
 struct SpinorIO<F32, D> {
   // 2D planes of float4, plane = s*D + colour, (psi[s][c], psi[s+2][c]).
   // L2ONLY loads bypass L1 (for data written earlier in the same kernel).
@@ -203,6 +238,10 @@ struct SpinorIO<F32, D> {
         b[(size_t)(sp * D + a) * Vh + i] = make_float4(s[sp][a].re, s[sp][a].im, s[sp + 2][a].re, s[sp + 2][a].im);
   }
 };
+
+// F32R12 stores its spinors exactly as F32 does
+template <int D>
+struct SpinorIO<F32R12, D> : SpinorIO<F32, D> {};
 
 template <int D>
 struct SpinorIO<BF16, D> {
@@ -341,6 +380,42 @@ struct LinkIO<F32, D, true> {
   __device__ __forceinline__ static elem load_one(const vec* t, int mu, int c) {
     const float2 v = ldx<L1>(t + (mu * D * D + c) * kLinkTile);
     return FB == 0 ? v.x : v.y;
+  }
+};
+
+// SU(3) links as two rows (12 floats = 3 float4 per link): plane
+// mu * 6 + fb * 3 + q holds elements 2q, 2q + 1 of the row-major first two
+// rows of the forward (fb = 0) or backward (fb = 1) link.  The third row of
+// an SU(3) matrix is the complex conjugate of the cross product of the first
+// two; a link multiplied by the boundary phase c needs the factor c^3 (c*^3
+// for the stored backward link U^+) on it.
+template <int D, bool REAL>
+struct LinkIO<F32R12, D, REAL> {
+  static_assert(D == 3 && !REAL, "two-row links are SU(3) fundamental only");
+  using vec = float4;
+  static constexpr int planes = 24;
+  __device__ __forceinline__ static const vec* tile_ptr(const void* base, int i) {
+    return reinterpret_cast<const vec*>(base) + link_index(planes, 0, i);
+  }
+  // the full matrix of sense FB of direction mu; ph = the third row's phase factor
+  template <int FB>
+  __device__ __forceinline__ static void load_matrix(const vec* t, int mu, cx<float> ph, cx<float> (&U)[3][3]) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 v = __ldcs(t + (mu * 6 + FB * 3 + q) * kLinkTile);
+      U[(2 * q) / 3][(2 * q) % 3] = cmake(v.x, v.y);
+      U[(2 * q + 1) / 3][(2 * q + 1) % 3] = cmake(v.z, v.w);
+    }
+    // row 2 = ph * conj(row 0 x row 1)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int a = (c + 1) % 3, b = (c + 2) % 3;
+      const cx<float> p = U[0][a], q = U[1][b], r = U[0][b], u = U[1][a];
+      // x = p q - r u, then w = conj(x)
+      const float xr = fmaf(p.re, q.re, fmaf(-p.im, q.im, fmaf(-r.re, u.re, r.im * u.im)));
+      const float xi = fmaf(p.re, q.im, fmaf(p.im, q.re, fmaf(-r.re, u.im, -(r.im * u.re))));
+      U[2][c] = cmake(fmaf(ph.re, xr, ph.im * xi), fmaf(ph.im, xr, -(ph.re * xi)));
+    }
   }
 };
 
@@ -521,6 +596,7 @@ struct HopArgs {
   Geom g;
   int p;               // output parity
   int dagger;          // apply H^+ = g5 H g5
+  float ph3[4][2];     // (cos, sin) of 3 phi_mu: two-row links' boundary factor
 };
 
 // launch the hop for (prec, d, real); returns the number of blocks (the

@@ -170,39 +170,84 @@ struct HopSplitSenses {
   static constexpr bool value = P::prec == BSM_DF64;
 };
 
+// Two-row SU(3) links (F32R12): each sense's full matrix is rebuilt in
+// registers (third row from the first two, times the boundary factor when
+// the hop crosses the lattice edge), then applied as in the FP32 kernel.
+template <int MU, int D>
+__device__ __forceinline__ void hop_direction_r12(const HopArgs& A, size_t Vh, const float4* lt, int nf, int nb,
+                                                  float sgf, float sgb, cx<float> (&acc)[4][D], unsigned edges) {
+  using L = LinkIO<F32R12, D, false>;
+  cx<float> hf[2][D], hb[2][D];
+  {
+    cx<float> psi[4][D];
+    SpinorIO<F32R12, D>::load(A.in, Vh, nf, psi);
+    spin_project<MU>(psi, sgf, hf);
+    SpinorIO<F32R12, D>::load(A.in, Vh, nb, psi);
+    spin_project<MU>(psi, sgb, hb);
+  }
+  const cx<float> one = cmake(1.f, 0.f);
+  const cx<float> phf = ((edges >> MU) & 1u) ? cmake(A.ph3[MU][0], A.ph3[MU][1]) : one;
+  const cx<float> phb = ((edges >> (4 + MU)) & 1u) ? cmake(A.ph3[MU][0], -A.ph3[MU][1]) : one;
+  cx<float> U[3][3];
+  L::template load_matrix<0>(lt, MU, phf, U);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    cx<float> w0 = cmake(0.f, 0.f), w1 = w0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      cmac(w0, U[a][b], hf[0][b]);
+      cmac(w1, U[a][b], hf[1][b]);
+    }
+    spin_reconstruct<MU>(acc, a, w0, w1, sgf);
+  }
+  L::template load_matrix<1>(lt, MU, phb, U);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    cx<float> w0 = cmake(0.f, 0.f), w1 = w0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      cmac(w0, U[a][b], hb[0][b]);
+      cmac(w1, U[a][b], hb[1][b]);
+    }
+    spin_reconstruct<MU>(acc, a, w0, w1, sgb);
+  }
+}
+
 template <int MU, typename P, int D, bool REAL>
 __device__ __forceinline__ void hop_direction(const HopArgs& A, size_t Vh, const typename LinkIO<P, D, REAL>::vec* lt,
                                               int nf, int nb, typename P::R sgf, typename P::R sgb,
-                                              cx<typename P::R> (&acc)[4][D]) {
+                                              cx<typename P::R> (&acc)[4][D], unsigned edges) {
   using R = typename P::R;
   using L = LinkIO<P, D, REAL>;
-  if constexpr (HopSplitSenses<P>::value) {
+  if constexpr (P::prec == BSM_F32R12) {
+    hop_direction_r12<MU, D>(A, Vh, lt, nf, nb, sgf, sgb, acc, edges);
+  } else if constexpr (HopSplitSenses<P>::value) {
     hop_sense<MU, 0, P, D, REAL>(A, Vh, lt, nf, sgf, acc);
     hop_sense<MU, 1, P, D, REAL>(A, Vh, lt, nb, sgb, acc);
-    return;
-  }
-  cx<R> hf[2][D], hb[2][D];
-  {
-    cx<R> psi[4][D];
-    SpinorIO<P, D>::load(A.in, Vh, nf, psi);
-    spin_project<MU>(psi, sgf, hf);
-    SpinorIO<P, D>::load(A.in, Vh, nb, psi);
-    spin_project<MU>(psi, sgb, hb);
-  }
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    cx<R> wf0 = cmake(R(0), R(0)), wf1 = wf0, wb0 = wf0, wb1 = wf0;
-#pragma unroll
-    for (int b = 0; b < D; ++b) {
-      typename L::elem uf, ub;
-      L::load(lt, MU, a * D + b, uf, ub);
-      link_mac(wf0, uf, hf[0][b]);
-      link_mac(wf1, uf, hf[1][b]);
-      link_mac(wb0, ub, hb[0][b]);
-      link_mac(wb1, ub, hb[1][b]);
+  } else {
+    cx<R> hf[2][D], hb[2][D];
+    {
+      cx<R> psi[4][D];
+      SpinorIO<P, D>::load(A.in, Vh, nf, psi);
+      spin_project<MU>(psi, sgf, hf);
+      SpinorIO<P, D>::load(A.in, Vh, nb, psi);
+      spin_project<MU>(psi, sgb, hb);
     }
-    spin_reconstruct<MU>(acc, a, wf0, wf1, sgf);
-    spin_reconstruct<MU>(acc, a, wb0, wb1, sgb);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      cx<R> wf0 = cmake(R(0), R(0)), wf1 = wf0, wb0 = wf0, wb1 = wf0;
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        typename L::elem uf, ub;
+        L::load(lt, MU, a * D + b, uf, ub);
+        link_mac(wf0, uf, hf[0][b]);
+        link_mac(wf1, uf, hf[1][b]);
+        link_mac(wb0, ub, hb[0][b]);
+        link_mac(wb1, ub, hb[1][b]);
+      }
+      spin_reconstruct<MU>(acc, a, wf0, wf1, sgf);
+      spin_reconstruct<MU>(acc, a, wb0, wb1, sgb);
+    }
   }
 }
 
@@ -229,15 +274,16 @@ __global__ void __launch_bounds__(kHopThreads, HopOccupancy<P, D>::min_blocks) h
     eo_neighbours(A.g, i, A.p, nf, nb);
     const auto* lt = LinkIO<P, D, REAL>::tile_ptr(A.links, i);
     const R sg = A.dagger ? R(1) : R(-1);  // forward sign; backward is -sg
+    const unsigned edges = P::prec == BSM_F32R12 ? eo_edges(A.g, i, A.p) : 0u;
     cx<R> acc[4][D];
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
       for (int a = 0; a < D; ++a) acc[s][a] = cmake(R(0), R(0));
-    hop_direction<0, P, D, REAL>(A, Vh, lt, nf[0], nb[0], sg, -sg, acc);
-    hop_direction<1, P, D, REAL>(A, Vh, lt, nf[1], nb[1], sg, -sg, acc);
-    hop_direction<2, P, D, REAL>(A, Vh, lt, nf[2], nb[2], sg, -sg, acc);
-    hop_direction<3, P, D, REAL>(A, Vh, lt, nf[3], nb[3], sg, -sg, acc);
+    hop_direction<0, P, D, REAL>(A, Vh, lt, nf[0], nb[0], sg, -sg, acc, edges);
+    hop_direction<1, P, D, REAL>(A, Vh, lt, nf[1], nb[1], sg, -sg, acc, edges);
+    hop_direction<2, P, D, REAL>(A, Vh, lt, nf[2], nb[2], sg, -sg, acc, edges);
+    hop_direction<3, P, D, REAL>(A, Vh, lt, nf[3], nb[3], sg, -sg, acc, edges);
 
     const R b = (R)A.b;
     if (A.x != nullptr) {

@@ -164,6 +164,25 @@ __global__ void links_to_rep_kernel(const double2* __restrict__ Uc, void* __rest
 
   char* blk_f = reinterpret_cast<char*>(out) + (size_t)p * block_bytes;
   char* blk_b = reinterpret_cast<char*>(out) + (size_t)(1 - p) * block_bytes;
+  if (prec == BSM_F32R12) {
+    // SU(3) fundamental: the first two rows of the forward link and of the
+    // backward link (R^+), float2 e of row-major element e at plane
+    // mu * 6 + fb * 3 + e / 2, half e % 2
+    if (d == 3 && !real) {
+      float2* P = reinterpret_cast<float2*>(blk_f);
+      float2* Q = reinterpret_cast<float2*>(blk_b);
+      for (int e = 0; e < 6; ++e) {
+        const int a = e / 3, b = e % 3;
+        const cx<double> f = R[a][b];
+        const cx<double> bw = cmake(R[b][a].re, -R[b][a].im);
+        P[2 * link_index(24, mu * 6 + e / 2, i) + (e & 1)] =
+            make_float2(__double2float_rn(f.re), __double2float_rn(f.im));
+        Q[2 * link_index(24, mu * 6 + 3 + e / 2, j) + (e & 1)] =
+            make_float2(__double2float_rn(bw.re), __double2float_rn(bw.im));
+      }
+    }
+    return;
+  }
   for (int a = 0; a < d; ++a)
     for (int b = 0; b < d; ++b) {
       const int cc = a * d + b;

@@ -7,6 +7,7 @@ int launch_hop_f64(int d, bool real, const HopArgs& A, cudaStream_t s);
 int launch_hop_f32(int d, bool real, const HopArgs& A, cudaStream_t s);
 int launch_hop_df64(int d, bool real, const HopArgs& A, cudaStream_t s);
 int launch_hop_bf16(int d, bool real, const HopArgs& A, cudaStream_t s);
+int launch_hop_f32r12(int d, bool real, const HopArgs& A, cudaStream_t s);
 
 int launch_hop(int prec, int d, bool real, const HopArgs& A, cudaStream_t s) {
   switch (prec) {
@@ -14,6 +15,7 @@ int launch_hop(int prec, int d, bool real, const HopArgs& A, cudaStream_t s) {
     case BSM_F32: return launch_hop_f32(d, real, A, s);
     case BSM_DF64: return launch_hop_df64(d, real, A, s);
     case BSM_BF16: return launch_hop_bf16(d, real, A, s);
+    case BSM_F32R12: return launch_hop_f32r12(d, real, A, s);
     default: return -1;
   }
 }
@@ -30,6 +32,10 @@ OpCtx make_ctx(const bsm_lattice& L, const void* links, int prec, cudaStream_t s
   c.link_block = link_block_bytes(c.g.Vh, c.d, c.real, prec);
   c.half_bytes = half_spinor_bytes(c.g.Vh, c.d, prec);
   c.s = s;
+  for (int mu = 0; mu < 4; ++mu) {
+    c.ph3[mu][0] = (float)cos(3.0 * L.bc_phase[mu]);
+    c.ph3[mu][1] = (float)sin(3.0 * L.bc_phase[mu]);
+  }
   return c;
 }
 
@@ -47,6 +53,10 @@ int op_hop(const OpCtx& c, int p, const void* in, void* out, int dagger, const v
   h.g = c.g;
   h.p = p;
   h.dagger = dagger;
+  for (int mu = 0; mu < 4; ++mu) {
+    h.ph3[mu][0] = c.ph3[mu][0];
+    h.ph3[mu][1] = c.ph3[mu][1];
+  }
   const int blocks = launch_hop(c.prec, c.d, c.real, h, c.s);
   if (blocks < 0) return BSM_EUNSUPPORTED;
   return partials != nullptr ? blocks : 0;

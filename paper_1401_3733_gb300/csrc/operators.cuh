@@ -18,6 +18,7 @@ struct OpCtx {
   size_t link_block;
   size_t half_bytes;     // one parity of a spinor at `prec`
   cudaStream_t s;
+  float ph3[4][2];       // (cos, sin) of 3 phi_mu (two-row links)
 };
 
 // fills ctx from a validated lattice; links may be null for size queries

@@ -70,7 +70,7 @@ CgLayout cg_layout(const bsm_lattice& L, int prec_inner, int eo, int prec_outer)
   y.u = o; o = align_up(o + (eo ? h64 : 0));
   y.t = o; o = align_up(o + (eo ? h64 : 2 * h64));
   y.r32 = y.p32 = y.Ap32 = y.u32 = y.t32 = y.x32 = 0;
-  if (prec_inner == BSM_F32) {
+  if (prec_inner == BSM_F32 || prec_inner == BSM_F32R12) {
     y.r32 = o; o = align_up(o + y.vec32);
     y.p32 = o; o = align_up(o + y.vec32);
     y.Ap32 = o; o = align_up(o + y.vec32);
@@ -102,7 +102,7 @@ struct Solver {
          cudaStream_t s_)
       : s(s_), eo(eo_) {
     co = make_ctx(L, Uo, prec_outer, s);
-    ci = prec_inner == BSM_F32 ? make_ctx(L, U32, BSM_F32, s) : co;
+    ci = (prec_inner == BSM_F32 || prec_inner == BSM_F32R12) ? make_ctx(L, U32, prec_inner, s) : co;
     y = cg_layout(L, prec_inner, eo, prec_outer);
     ws = reinterpret_cast<char*>(ws_);
     st = reinterpret_cast<CgState*>(ws + y.state);
@@ -189,11 +189,11 @@ struct Solver {
 
   // one CG iteration at the precision of context c
   int iterate(const OpCtx& c, void* x, void* r, void* p, void* Ap, void* u, void* t, size_t vec) const {
-    cg_p_update_launch(c.prec, p, r, vec / 16, st, s);
+    cg_p_update_launch(vector_prec(c.prec), p, r, vec / 16, st, s);
     const int np = apply_normal(c, p, Ap, u, t, partA, done);
     if (np < 0) return np;
     cg_alpha_launch(st, partA, np, s);
-    const int nb = cg_xr_update_launch(c.prec, x, r, p, Ap, vec / 16, st, partB, s);
+    const int nb = cg_xr_update_launch(vector_prec(c.prec), x, r, p, Ap, vec / 16, st, partB, s);
     cg_beta_launch(st, partB, nb, s);
     return 0;
   }
@@ -207,7 +207,7 @@ size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo, int prec
 
 int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* b, void* x,
              const bsm_cg_opts& o, bsm_cg_stats* stats, void* ws, cudaStream_t s) {
-  const int mixed = o.prec_inner == BSM_F32;
+  const int mixed = o.prec_inner == BSM_F32 || o.prec_inner == BSM_F32R12;
   const int eo = o.eo != 0;
   const int check = o.check_every > 0 ? o.check_every : 8;
   const double delta = o.delta > 0 ? o.delta : 0.1;

@@ -144,6 +144,26 @@ def test_batch_validation(bsm):
     assert bsm._lib.bsm_dslash_batch(su4, 1, ctypes.byref(ok), 7 * A, 1 << 30, 0) == bsm.EUNSUPPORTED
 
 
+def test_two_row_links_are_su3_fundamental_only(bsm):
+    L = ctypes.byref
+    A = 1 << 20
+    su3 = bsm.lattice((4, 4, 4, 4), 3, bsm.FUND, 0.1, (math.pi, 0, 0, 0))
+    Vh = 128
+    assert bsm.bsm_field_bytes(su3, bsm.FIELD_LINKS, bsm.F32R12) == 2 * Vh * 8 * 12 * 4
+    assert bsm.bsm_field_bytes(su3, bsm.FIELD_SPINOR, bsm.F32R12) == bsm.bsm_field_bytes(su3, bsm.FIELD_SPINOR,
+                                                                                         bsm.F32)
+    assert bsm.bsm_workspace_bytes(su3, bsm.CALL_CG, bsm.F32R12) == bsm.bsm_workspace_bytes(su3, bsm.CALL_CG, bsm.F32)
+    for lat in (bsm.lattice((4, 4, 4, 4), 2), bsm.lattice((4, 4, 4, 4), 3, bsm.SYM), bsm.lattice((4, 4, 4, 4), 4)):
+        assert bsm.bsm_field_bytes(lat, bsm.FIELD_LINKS, bsm.F32R12) == 0
+        assert bsm._lib.bsm_dslash(L(lat), A, 2 * A, 3 * A, 0, 0, bsm.F32R12, 0) == bsm.EUNSUPPORTED
+        assert bsm._lib.bsm_links_to_rep(L(lat), A, 2 * A, bsm.F32R12, 0) == bsm.EUNSUPPORTED
+        st = bsm.CgStats()
+        assert bsm._lib.bsm_cg_solve(L(lat), A, 2 * A, 3 * A, 4 * A, L(bsm.cg_opts(prec_inner=bsm.F32R12)), L(st),
+                                     5 * A, 1 << 40, 0) == bsm.EUNSUPPORTED
+    # the multi-RHS and batch paths take plain FP32 links only
+    assert bsm._lib.bsm_dslash_mrhs(L(su3), A, 2 * A, 3 * A, 4, bsm.FULL, 0, bsm.F32R12, 0) == bsm.EUNSUPPORTED
+
+
 def test_too_large_lattice_is_unsupported(bsm):
     lat = bsm.lattice((2048, 1024, 1024, 2), 3)
     assert bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR, bsm.F32) == 0

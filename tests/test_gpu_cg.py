@@ -89,6 +89,30 @@ def test_mixed_precision_cg_reaches_fp64_residual(dims, N, rep, eps, outer):
     assert sm.true_res_full < 1e-7
 
 
+@pytest.mark.parametrize("outer", [bsm.F64, bsm.DF64], ids=["f64", "df64"])
+@pytest.mark.parametrize("eo", [True, False], ids=["eo", "full"])
+def test_mixed_cg_with_two_row_links(outer, eo):
+    """The FP32 inner iteration on two-row SU(3) links (BSM_F32R12), with
+    antiperiodic time (the rebuilt third row carries the boundary factor),
+    reaches the FP64 solution."""
+    dims, N = (8, 8, 8, 8), 3
+    olat = orc.Lattice(dims, N, orc.FUND, 0.05, (np.pi, 0, 0, 0))
+    blat = bsm.lattice(dims, N, bsm.FUND, 0.05, (np.pi, 0, 0, 0))
+    U = fields.gauge_field(dims, N, "smooth", seed=3, eps=0.3)
+    b = fields.gaussian_spinor(dims, N, 4)
+    U64, U12, Uo = gpu_links(blat, U, bsm.F64), gpu_links(blat, U, bsm.F32R12), gpu_links(blat, U, outer)
+    bd = gpu_spinor(blat, b, bsm.F64)
+    st64, s64, x64 = solve(blat, U64, None, bd, bsm.cg_opts(tol=1e-10, eo=eo))
+    stm, sm, xm = solve(blat, Uo, U12, bd, bsm.cg_opts(tol=1e-10, eo=eo, prec_inner=bsm.F32R12, prec_outer=outer))
+    assert st64 == bsm.OK and stm == bsm.OK
+    assert sm.true_res_normal <= 1e-10 and sm.reliable_updates >= 1
+    assert abs(sm.iters - s64.iters) <= max(5, s64.iters // 10), (sm.iters, s64.iters)
+    x = to_canon(blat, xm, bsm.F64)
+    assert rel(x, to_canon(blat, x64, bsm.F64)) < 1e-7
+    R = orc.links_to_rep(olat, U)
+    assert rel(orc.dirac(olat, R, x), b) < 1e-7
+
+
 def test_cg_statuses_from_host_side_faults():
     olat, blat, U, b = cfg1()
     U64 = gpu_links(blat, U, bsm.F64)

@@ -104,6 +104,51 @@ def test_dirac_eo_ops(N, rep, prec):
 
 
 # ----------------------------------------------------------------------------
+# SU(3) links stored as two rows (BSM_F32R12)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("phase", [(np.pi, 0.4, -1.3, 0.0), (0.0, 0.0, 0.0, 0.0), (2.1, 0.0, 0.7, -0.2)],
+                         ids=["antiperiodic+twists", "periodic", "generic"])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 10), (2, 2, 2, 6)], ids=["4^4", "ragged240", "L2"])
+def test_two_row_links_hop_matches_oracle(dims, phase):
+    """Hop (both parities, dagger), full D and D^+ from two-row links: the
+    third row and the boundary factor c^3 rebuilt in the kernel.  Haar links
+    (far from the identity), boundary phases that cross every direction."""
+    olat, blat, U, R, psi = setup(dims, 3, bsm.FUND, 0.1, phase, seed=500)
+    prec = bsm.F32R12
+    for p in (0, 1):
+        for dagger in (False, True):
+            got = gpu_hop_parity(blat, U, psi, p, dagger, prec)
+            want = orc.hop(olat, R, psi, out_parity=p, dagger=dagger)
+            assert rel(got, want) <= TOL[prec], (p, dagger, rel(got, want))
+    Ud = gpu_links(blat, U, prec)
+    inp = gpu_spinor(blat, psi, prec)
+    out = zeros_field(blat, bsm.FIELD_SPINOR, prec)
+    for dagger in (False, True):
+        bsm.bsm_dslash(blat, Ud, inp, out, bsm.FULL, dagger, prec)
+        assert rel(to_canon(blat, out, prec), orc.dirac(olat, R, psi, dagger=dagger)) <= TOL[prec]
+
+
+def test_two_row_links_dirac_eo_and_sizes():
+    dims = (4, 4, 2, 6)
+    olat, blat, U, R, psi = setup(dims, 3, bsm.FUND, 0.1, (np.pi, 0, 0, 0), seed=510)
+    prec = bsm.F32R12
+    psi[orc.parity_mask(dims)] = 0
+    Ud = gpu_links(blat, U, prec)
+    # 2 parities x padded V_h x 8 links x 12 floats
+    assert Ud.numel() == 2 * 96 * 8 * 12 * 4
+    assert bsm.bsm_field_bytes(blat, bsm.FIELD_SPINOR, prec) == bsm.bsm_field_bytes(blat, bsm.FIELD_SPINOR, bsm.F32)
+    inp = gpu_spinor(blat, psi, prec)
+    ws = torch.empty(bsm.bsm_workspace_bytes(blat, bsm.CALL_DIRAC_EO, prec), dtype=torch.uint8, device="cuda")
+    for op in (bsm.OP_DHAT, bsm.OP_DHAT_DAG, bsm.OP_DHAT_DAG_DHAT):
+        out = zeros_field(blat, bsm.FIELD_SPINOR, prec)
+        bsm.bsm_dirac_eo(blat, Ud, half(blat, inp, 0, prec), half(blat, out, 0, prec), op, prec, ws)
+        got = to_canon(blat, out, prec)
+        want = orc.dhat(olat, R, psi, op)
+        assert rel(got, want) <= TOL[prec], (op, rel(got, want))
+
+
+# ----------------------------------------------------------------------------
 # invariants on the GPU output itself
 # ----------------------------------------------------------------------------
 
@@ -176,7 +221,7 @@ def big_case():
     return olat, blat, U, R, psi
 
 
-@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+@pytest.mark.parametrize("prec", PRECS + [bsm.F32R12], ids=PREC_IDS + ["f32r12"])
 def test_full_size_32c64_hop(big_case, prec):
     """Both parity blocks of the hop on the whole 32^3 x 64 lattice, every
     output element compared with the oracle."""

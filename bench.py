@@ -437,11 +437,13 @@ def run_mrhs(steps, flush, peak):
             for _ in range(3):
                 bsm.bsm_dslash_mrhs(lat, links, inp, outp, MRHS_NRHS, bsm.FULL, 0, prec)
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            torch.cuda.nvtx.range_push(f"mrhs_d{d}{'r' if real else 'c'}_{pname}")
             for e0, e1 in evs:
                 flush.zero_()
                 e0.record()
                 bsm.bsm_dslash_mrhs(lat, links, inp, outp, MRHS_NRHS, bsm.FULL, 0, prec)
                 e1.record()
+            torch.cuda.nvtx.range_pop()
             torch.cuda.synchronize()
             ms = sum(a.elapsed_time(b) for a, b in evs) / steps
             flop = flops_per_site(d, real) * V * MRHS_NRHS
@@ -508,6 +510,7 @@ def run_batch(steps, flush, shapes=BATCH_SHAPES):
             fn()
         torch.cuda.synchronize()
         total = 0.0
+        torch.cuda.nvtx.range_push(f"batch{len(entries)}_{name}")
         for _ in range(steps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -516,6 +519,7 @@ def run_batch(steps, flush, shapes=BATCH_SHAPES):
             e1.record()
             torch.cuda.synchronize()
             total += e0.elapsed_time(e1)
+        torch.cuda.nvtx.range_pop()
         ms = total / steps
         res[name] = {"ms": round(ms, 4), "gflops": round(flop / (ms * 1e-3) / 1e9, 1)}
     return res

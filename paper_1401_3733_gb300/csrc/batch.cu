@@ -120,6 +120,11 @@ __global__ void __launch_bounds__(kHopThreads, 3) batch_kernel(const BatchTask* 
   }
 }
 
+BatchTask with_tasks_scalars(BatchTask t) {
+  t.args = with_f32_scalars(t.args);
+  return t;
+}
+
 }  // namespace
 
 // validated by the caller: SU(2)/SU(3) fundamental, FP32, nrhs >= 1
@@ -175,7 +180,7 @@ int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o
         t.phase = 0;
         t.chunk0 = meta.phase_chunks[0];
         meta.phase_chunks[0] += chunks;
-        tasks.push_back(t);
+        tasks.push_back(with_tasks_scalars(t));
       }
     } else {  // phase 0: tmp_o = H_oe in_e ; phase 1: out_e = A in_e - 1/(4A) H_eo tmp_o
       char* tmp = w;
@@ -190,7 +195,7 @@ int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o
       t.phase = 0;
       t.chunk0 = meta.phase_chunks[0];
       meta.phase_chunks[0] += chunks;
-      tasks.push_back(t);
+      tasks.push_back(with_tasks_scalars(t));
       t.args.links = c.links;
       t.args.p = 0;
       t.args.in = tmp;
@@ -201,7 +206,7 @@ int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o
       t.phase = 1;
       t.chunk0 = meta.phase_chunks[1];
       meta.phase_chunks[1] += chunks;
-      tasks1.push_back(t);
+      tasks1.push_back(with_tasks_scalars(t));
     }
   }
   tasks.insert(tasks.end(), tasks1.begin(), tasks1.end());

@@ -597,7 +597,29 @@ struct HopArgs {
   int p;               // output parity
   int dagger;          // apply H^+ = g5 H g5
   float ph3[4][2];     // (cos, sin) of 3 phi_mu: two-row links' boundary factor
+  float af, bf;        // a, b rounded to FP32, and b == 1 (set at launch: FP32
+  int b_one;           // kernels avoid per-thread FP64 conversions and compares)
 };
+
+// the epilogue scalars at the kernel's arithmetic precision: FP32 kernels
+// take the FP32 copies (GB300 issues FP64 instructions at a small fraction
+// of the FP32 rate, so a per-thread FP64 convert or compare is not free)
+template <typename R, typename Args>
+__device__ __forceinline__ R epi_a(const Args& A) { return (R)A.a; }
+template <typename R, typename Args>
+__device__ __forceinline__ R epi_b(const Args& A) { return (R)A.b; }
+template <>
+__device__ __forceinline__ float epi_a<float, HopArgs>(const HopArgs& A) { return A.af; }
+template <>
+__device__ __forceinline__ float epi_b<float, HopArgs>(const HopArgs& A) { return A.bf; }
+
+template <typename Args>
+inline Args with_f32_scalars(Args A) {
+  A.af = (float)A.a;
+  A.bf = (float)A.b;
+  A.b_one = A.b == 1.0;
+  return A;
+}
 
 // launch the hop for (prec, d, real); returns the number of blocks (the
 // number of partials written when args.partials != nullptr), or -1

@@ -285,9 +285,9 @@ __global__ void __launch_bounds__(kHopThreads, HopOccupancy<P, D>::min_blocks) h
     hop_direction<2, P, D, REAL>(A, Vh, lt, nf[2], nb[2], sg, -sg, acc, edges);
     hop_direction<3, P, D, REAL>(A, Vh, lt, nf[3], nb[3], sg, -sg, acc, edges);
 
-    const R b = (R)A.b;
+    const R b = epi_b<R>(A);
     if (A.x != nullptr) {
-      const R a = (R)A.a;
+      const R a = epi_a<R>(A);
       cx<R> xs[4][D];
       SpinorIO<P, D>::load(A.x, Vh, i, xs);
 #pragma unroll
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kHopThreads, HopOccupancy<P, D>::min_blocks) h
 #pragma unroll
         for (int c = 0; c < D; ++c)
           acc[s][c] = cmake(fma(a, xs[s][c].re, b * acc[s][c].re), fma(a, xs[s][c].im, b * acc[s][c].im));
-    } else if (A.b != 1.0) {
+    } else if (!A.b_one) {
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kHopThreads, HopOccupancy<P, D>::min_blocks) h
 template <typename P, int D, bool REAL>
 inline int launch_hop_t(const HopArgs& A, cudaStream_t s) {
   const int blocks = hop_blocks(A.g.Vh);
-  hop_kernel<P, D, REAL><<<blocks, kHopThreads, 0, s>>>(A);
+  hop_kernel<P, D, REAL><<<blocks, kHopThreads, 0, s>>>(with_f32_scalars(A));
   return blocks;
 }
 

@@ -25,7 +25,14 @@ struct MrhsArgs {
   int p;
   int dagger;
   int nrhs;
+  float af, bf;       // a, b in FP32 and b == 1 (with_f32_scalars at launch)
+  int b_one;
 };
+
+template <>
+__device__ __forceinline__ float epi_a<float, MrhsArgs>(const MrhsArgs& A) { return A.af; }
+template <>
+__device__ __forceinline__ float epi_b<float, MrhsArgs>(const MrhsArgs& A) { return A.bf; }
 
 template <int MU, int FB, typename P, int D, bool REAL, int RB, bool L2IN = false>
 __device__ __forceinline__ void mrhs_sense(const MrhsArgs& A, const typename LinkIO<P, D, REAL>::vec* lt, int n,
@@ -101,12 +108,12 @@ __device__ __forceinline__ void mrhs_site(const MrhsArgs& A, int i, int r0) {
 
   const size_t nr = (size_t)A.nrhs;
   const size_t Vn = (size_t)A.g.Vh * nr;
-  const R b = (R)A.b;
+  const R b = epi_b<R>(A);
 #pragma unroll
   for (int j = 0; j < RB; ++j) {
     const int e = (int)((size_t)i * nr + r0 + j);
     if (A.x != nullptr) {
-      const R a = (R)A.a;
+      const R a = epi_a<R>(A);
       cx<R> xs[4][D];
       SpinorIO<P, D>::load(A.x, Vn, e, xs);
 #pragma unroll
@@ -114,7 +121,7 @@ __device__ __forceinline__ void mrhs_site(const MrhsArgs& A, int i, int r0) {
 #pragma unroll
         for (int c = 0; c < D; ++c)
           acc[j][s][c] = cmake(fma(a, xs[s][c].re, b * acc[j][s][c].re), fma(a, xs[s][c].im, b * acc[j][s][c].im));
-    } else if (A.b != 1.0) {
+    } else if (!A.b_one) {
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -144,7 +151,7 @@ template <typename P, int D, bool REAL, int RB>
 inline void launch_mrhs_t(const MrhsArgs& A, cudaStream_t s) {
   const long long n = (long long)A.g.Vh * (A.nrhs / RB);
   const int blocks = (int)((n + kHopThreads - 1) / kHopThreads);
-  hop_mrhs_kernel<P, D, REAL, RB><<<blocks, kHopThreads, 0, s>>>(A);
+  hop_mrhs_kernel<P, D, REAL, RB><<<blocks, kHopThreads, 0, s>>>(with_f32_scalars(A));
 }
 
 // dispatch on RB for one (P, D, REAL); false if RB is not compiled for D

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(32 * kTcWarps) hop_mrhs_tc_kernel(const MrhsAr
   const size_t Vn = (size_t)A.g.Vh * nr;
   uint2* out = reinterpret_cast<uint2*>(A.out);
   const uint2* xin = reinterpret_cast<const uint2*>(A.x);
-  const float a = (float)A.a, b = (float)A.b;
+  const float a = A.af, b = A.bf;
   for (int idx = lane; idx < nr * D; idx += 32) {
     const int r = idx / D, c = idx - r * D;
     float s[4][2];  // spin, re/im
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(32 * kTcWarps) hop_mrhs_tc_kernel(const MrhsAr
 template <int D, int NT>
 void launch_tc_t(const MrhsArgs& A, cudaStream_t s) {
   const int blocks = (A.g.Vh + kTcWarps - 1) / kTcWarps;
-  hop_mrhs_tc_kernel<D, NT><<<blocks, 32 * kTcWarps, 0, s>>>(A);
+  hop_mrhs_tc_kernel<D, NT><<<blocks, 32 * kTcWarps, 0, s>>>(with_f32_scalars(A));
 }
 
 template <int D>

@@ -415,6 +415,10 @@ def run_ours(args):
         out["cg_small_graph"] = run_cg_graph(args.cg_max_iter)
     if rank == 0 and not args.no_precond:
         out["precond"] = run_precond(peak, peak_src, args.steps)
+    if rank == 0 and not args.no_large:
+        del links, src, dst, flush
+        torch.cuda.empty_cache()
+        out["large"] = run_large(args.steps, peak, peak_src, args.cg_max_iter)
     if rank == 0 and world == 1 and not args.no_cpu:
         g, reps, el, th = time_oracle_hop(SAMPLE_DIMS, args.cpu_seconds)
         out["cpu_baseline"] = {"value": round(g, 3), "unit": "GFLOP/s", "cores": th, "kind": "oracle",
@@ -579,6 +583,91 @@ def run_cg_graph(max_iter):
             secs.append(stats.seconds)
         res[name] = {"status": bsm.bsm_strerror(st), "seconds": round(min(secs), 5), "iters": stats.iters,
                      "true_res_normal": stats.true_res_normal}
+    return res
+
+
+# the largest single-lattice workload: 48^3 x 96 SU(3), smooth links
+# exp(i 0.3 H) drawn on the device (host generation of 42M matrices would take
+# about a minute), m0 = 0.05, antiperiodic time
+LARGE = dict(dims=(96, 48, 48, 48), N=3, m0=0.05, phase=(math.pi, 0.0, 0.0, 0.0), eps=0.3, link_seed=5, src_seed=6)
+
+
+def run_large(steps, peak, peak_kind, max_iter):
+    """48^3 x 96: the FP32 Dslash (full and two-row links) against the HBM
+    roofline, mixed-precision CG against plain FP64 CG to 1e-10, and the
+    learned-preconditioner FGCR (network trained on 8^3 x 16 lattices of the
+    same ensemble) on the same system."""
+    import torch
+    from paper_1401_3733_gb300 import bsm, fields
+
+    w = LARGE
+    dims, N = w["dims"], w["N"]
+    lat = bsm.lattice(dims, N, bsm.FUND, w["m0"], w["phase"])
+    V = int(np.prod(dims))
+    Vh = V // 2
+    U = fields.device_smooth_gauge_field(dims, N, w["link_seed"], w["eps"])
+    links = {p: bsm.empty_field(lat, bsm.FIELD_LINKS, p) for p in (bsm.F32, bsm.F32R12, bsm.F64, bsm.DF64)}
+    for p, t in links.items():
+        bsm.bsm_links_to_rep(lat, U, t, p)
+    del U
+    psi = fields.device_gaussian_spinors(dims, N, 1, w["src_seed"])[0]
+    b = bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F64)
+    bsm.bsm_pack_spinor(lat, psi, b, bsm.F64)
+    src = bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F32)
+    dst = bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F32)
+    bsm.bsm_pack_spinor(lat, psi, src, bsm.F32)
+    del psi
+    nh = bsm.bsm_field_bytes(lat, bsm.FIELD_HALF_SPINOR, bsm.F32)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flop = flops_per_site(N) * V
+    res = {"lattice_TXYZ": list(dims), "sites": V, "eps": w["eps"], "m0": w["m0"],
+           "links": "smooth exp(i eps H), drawn on the device (seeded Philox)"}
+    for name, prec, bps in (("dslash_f32", bsm.F32, bytes_per_site(N, 4)),
+                            ("dslash_f32r12", bsm.F32R12, bytes_per_site_r12(4))):
+        for _ in range(3):
+            bsm.bsm_dslash(lat, links[prec], src[nh:], dst[:nh], bsm.EVEN, 0, prec)
+        n = max(3, min(steps, 10))
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n)]
+        torch.cuda.nvtx.range_push(f"large_{name}")
+        for e in evs:
+            flush.zero_()
+            e[0].record()
+            bsm.bsm_dslash(lat, links[prec], src[nh:], dst[:nh], bsm.EVEN, 0, prec)
+            e[1].record()
+            bsm.bsm_dslash(lat, links[prec], src[:nh], dst[nh:], bsm.ODD, 0, prec)
+            e[2].record()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        ms = sum(e[0].elapsed_time(e[2]) for e in evs) / n
+        launch = ms / 2
+        res[name] = {"gflops": round(flop / (ms * 1e-3) / 1e9, 1), "ms_per_step": round(ms, 4),
+                     "avg_launch_us": round(launch * 1e3, 1), "algorithmic_bytes_per_site": bps,
+                     "hbm_frac": round(bps * Vh / (launch * 1e-3) / 1e9 / peak, 4), "peak_kind": peak_kind}
+    del src, dst, flush
+    for name, inner, outer in (("cg_mixed_df64_r12", bsm.F32R12, bsm.DF64), ("cg_fp64", bsm.F64, bsm.F64)):
+        ws = torch.empty(bsm.bsm_workspace_bytes(lat, bsm.CALL_CG, inner), dtype=torch.uint8, device="cuda")
+        x = torch.empty_like(b)
+        st, stats = bsm.bsm_cg_solve(lat, links[outer], links[bsm.F32R12], b, x,
+                                     bsm.cg_opts(tol=1e-10, max_iter=max_iter, prec_inner=inner, prec_outer=outer,
+                                                 delta=CG_DELTA, check_every=CG_CHECK_EVERY),
+                                     ws, raise_on_error=False)
+        res[name] = {"status": bsm.bsm_strerror(st), "seconds": round(stats.seconds, 4), "iters": stats.iters,
+                     "reliable_updates": stats.reliable_updates, "true_res_normal": stats.true_res_normal,
+                     "true_res_full": stats.true_res_full}
+        del ws, x
+    if res["cg_mixed_df64_r12"]["seconds"] > 0:
+        res["fp64_over_mixed_time"] = round(res["cg_fp64"]["seconds"] / res["cg_mixed_df64_r12"]["seconds"], 3)
+    # the learned preconditioner, trained on small lattices of this ensemble
+    cfg = dict(PRECOND, eps=w["eps"], m0=w["m0"])
+    W, train = train_ptc(cfg)
+    o = bsm.fgcr_opts(tol=1e-10, max_iter=4000, restart=cfg["restart"], eo=True, precond=bsm.FGCR_PTC,
+                      channels=cfg["channels"], ptc_prec=bsm.BF16, prec_inner=bsm.F32, inner_tol=1e-3, check_every=4)
+    ws = torch.empty(bsm.bsm_fgcr_workspace_bytes(lat, o), dtype=torch.uint8, device="cuda")
+    x = torch.empty_like(b)
+    st, stats = bsm.bsm_fgcr_solve(lat, links[bsm.F64], links[bsm.F32], W[0], W[1], b, x, o, ws, raise_on_error=False)
+    res["fgcr_eo_ptc_bf16_fp32cycles"] = {"status": bsm.bsm_strerror(st), "seconds": round(stats.seconds, 4),
+                                          "iters": stats.iters, "cycles": stats.cycles, "true_res": stats.true_res,
+                                          "training": train}
     return res
 
 
@@ -823,6 +912,7 @@ def main():
     ap.add_argument("--no-mrhs", action="store_true", help="skip the multi-RHS 24^4 three-theory lines")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-lattice batch and small-lattice CG lines")
     ap.add_argument("--no-precond", action="store_true", help="skip the learned-preconditioner (FGCR) line")
+    ap.add_argument("--no-large", action="store_true", help="skip the 48^3 x 96 lines")
     ap.add_argument("--ptc-apply-only", action="store_true",
                     help="only the BF16 network application's roofline (on --lattice, random weights); "
                          "the profiling entry for its kernels")

@@ -145,6 +145,40 @@ def device_gaussian_spinors(dims, d: int, nrhs: int, seed: int, device="cuda"):
     return torch.view_as_complex(v)
 
 
+def device_smooth_gauge_field(dims, N: int, seed: int, eps: float, device="cuda", chunk: int = 1 << 22):
+    """Fundamental links (V, 4, N, N) complex128 on the device, U = exp(i eps H)
+    with H = sum_a h_a T^a, h_a ~ N(0, 1) over the generalised Gell-Mann
+    generators as in traceless_hermitian, but drawn with torch's seeded
+    Philox generator on the device: for timing-scale lattices whose host
+    generation would take minutes (a different random stream from
+    gauge_field, the same distribution)."""
+    import torch
+
+    V = volume(dims)
+    count = V * 4
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    out = torch.empty((count, N, N), dtype=torch.complex128, device=device)
+    noff = N * (N - 1) // 2
+    for s0 in range(0, count, chunk):
+        n = min(chunk, count - s0)
+        h = torch.randn((n, N * N - 1), generator=g, device=device, dtype=torch.float64)
+        H = torch.zeros((n, N, N), dtype=torch.complex128, device=device)
+        k = 0
+        for i in range(N):
+            for j in range(i + 1, N):
+                H[:, i, j] = torch.complex(0.5 * h[:, k], -0.5 * h[:, noff + k])
+                H[:, j, i] = torch.conj(H[:, i, j])
+                k += 1
+        for l in range(1, N):
+            c = h[:, 2 * noff + l - 1] / np.sqrt(2.0 * l * (l + 1))
+            for i in range(l):
+                H[:, i, i] += c
+            H[:, l, l] -= l * c
+        out[s0:s0 + n] = torch.linalg.matrix_exp((1j * eps) * H)
+    return out.reshape(V, 4, N, N)
+
+
 def gauge_transform(dims, N: int, seed: int) -> np.ndarray:
     """Haar-random g(x) in SU(N) for every site, (V, N, N)."""
     return haar_su(seed, volume(dims), N)

@@ -234,3 +234,26 @@ def test_full_size_32c64_hop(big_case, prec):
     got = to_canon(blat, out, prec)
     want = orc.hop(olat, R, psi, out_parity=orc.FULL)
     assert rel(got, want) <= TOL[prec]
+
+
+def test_full_size_48c96_hop_f32_and_two_row():
+    """The 48^3 x 96 workload of the benchmark's `large` lines (links drawn on
+    the device with the same generator), both parity blocks, every output
+    element against the oracle, full-link and two-row FP32 links."""
+    dims, N = (96, 48, 48, 48), 3
+    phase = (np.pi, 0, 0, 0)
+    olat = orc.Lattice(dims, N, orc.FUND, 0.05, phase)
+    blat = bsm.lattice(dims, N, bsm.FUND, 0.05, phase)
+    Ud = fields.device_smooth_gauge_field(dims, N, 5, 0.3)
+    psid = fields.device_gaussian_spinors(dims, N, 1, 6)[0]
+    want = orc.hop(olat, orc.links_to_rep(olat, Ud.cpu().numpy()), psid.cpu().numpy(), out_parity=orc.FULL)
+    for prec in (bsm.F32, bsm.F32R12):
+        links = bsm.empty_field(blat, bsm.FIELD_LINKS, prec)
+        bsm.bsm_links_to_rep(blat, Ud, links, prec)
+        inp = bsm.empty_field(blat, bsm.FIELD_SPINOR, prec)
+        bsm.bsm_pack_spinor(blat, psid, inp, prec)
+        out = zeros_field(blat, bsm.FIELD_SPINOR, prec)
+        bsm.bsm_dslash(blat, links, half(blat, inp, 1, prec), half(blat, out, 0, prec), bsm.EVEN, 0, prec)
+        bsm.bsm_dslash(blat, links, half(blat, inp, 0, prec), half(blat, out, 1, prec), bsm.ODD, 0, prec)
+        assert rel(to_canon(blat, out, prec), want) <= TOL[prec], prec
+        del links, inp, out

@@ -304,6 +304,15 @@ typedef struct {
 size_t bsm_batch_workspace_bytes(const bsm_batch_item *items, int32_t count, const bsm_batch_opts *opts);
 int bsm_dslash_batch(const bsm_batch_item *items, int32_t count, const bsm_batch_opts *opts,
                      void *workspace, size_t workspace_bytes, void *stream);
+/* The same launch without the wait: it enqueues a memset of the workspace's
+ * control block and the cooperative launch (the task table travels as a
+ * launch parameter), nothing else, so a stream capture of this call gives a
+ * CUDA graph that replays the whole batch.  bsm_dslash_batch_status waits
+ * for `stream` and returns BSM_ETIMEOUT if the last batch run on this
+ * workspace gave up a barrier wait, else BSM_OK. */
+int bsm_dslash_batch_async(const bsm_batch_item *items, int32_t count, const bsm_batch_opts *opts,
+                           void *workspace, size_t workspace_bytes, void *stream);
+int bsm_dslash_batch_status(void *workspace, void *stream);
 
 /* Solve D x = b (Sec. II-B: inverting the Dirac operator by CG) through CG on
  * the normal equations.  With opts->eo: Dhat^+ Dhat x_e = Dhat^+ bhat_e,

@@ -114,6 +114,11 @@ _lib.bsm_batch_workspace_bytes.restype = ctypes.c_size_t
 _lib.bsm_dslash_batch.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_int32, ctypes.POINTER(BatchOpts), _P,
                                   ctypes.c_size_t, _P]
 _lib.bsm_dslash_batch.restype = ctypes.c_int
+_lib.bsm_dslash_batch_async.argtypes = [ctypes.POINTER(BatchItem), ctypes.c_int32, ctypes.POINTER(BatchOpts), _P,
+                                        ctypes.c_size_t, _P]
+_lib.bsm_dslash_batch_async.restype = ctypes.c_int
+_lib.bsm_dslash_batch_status.argtypes = [_P, _P]
+_lib.bsm_dslash_batch_status.restype = ctypes.c_int
 _lib.bsm_ptc_pack.argtypes = [_LP, _P, _P, _P]
 _lib.bsm_ptc_unpack.argtypes = [_LP, _P, _P, _P]
 _lib.bsm_ptc_workspace_bytes.argtypes = [_LP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
@@ -277,6 +282,18 @@ def bsm_dslash_batch(items, opts: BatchOpts, workspace, stream=None, raise_on_er
     if raise_on_error:
         _check(st, "bsm_dslash_batch")
     return st
+
+
+def bsm_dslash_batch_async(items, opts: BatchOpts, workspace, stream=None) -> int:
+    nbytes = workspace.numel() * workspace.element_size()
+    st = _lib.bsm_dslash_batch_async(items, len(items), ctypes.byref(opts), _ptr(workspace), nbytes,
+                                     _stream(stream))
+    _check(st, "bsm_dslash_batch_async")
+    return st
+
+
+def bsm_dslash_batch_status(workspace, stream=None) -> int:
+    return _lib.bsm_dslash_batch_status(_ptr(workspace), _stream(stream))
 
 
 def bsm_cg_solve(lat, U_rep64, U_rep32, b, x, opts: CgOpts, workspace, stream=None, raise_on_error=True):

@@ -18,7 +18,9 @@ void pack_spinor_launch(const bsm_lattice& L, const double* canon, void* dev, in
 int launch_mrhs(int prec, int d, bool real, const MrhsArgs& A, cudaStream_t s);
 int mrhs_tuned_block(int prec, int d, bool real, int nrhs, int Vh);
 size_t batch_workspace_bytes(const bsm_batch_item* items, int count, int op);
-int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o, void* ws, cudaStream_t s);
+int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o, void* ws, cudaStream_t s,
+                 bool sync);
+int batch_status(void* ws, cudaStream_t s);
 bool mrhs_set_block(int prec, int d, bool real, int nrhs, int Vh, int block);
 size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo, int prec_outer);
 int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* b, void* x,
@@ -333,8 +335,9 @@ size_t bsm_batch_workspace_bytes(const bsm_batch_item* items, int32_t count, con
   return batch_workspace_bytes(items, count, opts->op);
 }
 
-int bsm_dslash_batch(const bsm_batch_item* items, int32_t count, const bsm_batch_opts* opts, void* workspace,
-                     size_t workspace_bytes, void* stream) {
+namespace {
+int dslash_batch(const bsm_batch_item* items, int32_t count, const bsm_batch_opts* opts, void* workspace,
+                 size_t workspace_bytes, void* stream, bool sync) {
   const int rc = check_batch(items, count, opts);
   if (rc != BSM_OK) return rc;
   if (!aligned(workspace)) return BSM_EINVAL;
@@ -344,7 +347,23 @@ int bsm_dslash_batch(const bsm_batch_item* items, int32_t count, const bsm_batch
     set_cuda_error(pre);
     return BSM_ECUDA;
   }
-  return batch_launch(items, count, *opts, workspace, (cudaStream_t)stream);
+  return batch_launch(items, count, *opts, workspace, (cudaStream_t)stream, sync);
+}
+}  // namespace
+
+int bsm_dslash_batch(const bsm_batch_item* items, int32_t count, const bsm_batch_opts* opts, void* workspace,
+                     size_t workspace_bytes, void* stream) {
+  return dslash_batch(items, count, opts, workspace, workspace_bytes, stream, true);
+}
+
+int bsm_dslash_batch_async(const bsm_batch_item* items, int32_t count, const bsm_batch_opts* opts,
+                           void* workspace, size_t workspace_bytes, void* stream) {
+  return dslash_batch(items, count, opts, workspace, workspace_bytes, stream, false);
+}
+
+int bsm_dslash_batch_status(void* workspace, void* stream) {
+  if (!aligned(workspace)) return BSM_EINVAL;
+  return batch_status(workspace, (cudaStream_t)stream);
 }
 
 int bsm_dirac_eo(const bsm_lattice* lat, const void* U_rep, const void* in_e, void* out_e, int32_t op,

@@ -1,9 +1,10 @@
 // batch.cu -- several lattices of uneven size (SU(2) and SU(3) fundamental,
 // each with its own number of right-hand sides) in one persistent launch.
 //
-// The host turns the batch into a task table in the workspace: one task per
-// (lattice, output parity, phase), each covering V_h * n_rhs thread slots cut
-// into chunks of one block.  Blocks of a cooperative grid (every block
+// The host turns the batch into a task table, passed to the kernel by value
+// as a launch parameter (no host-to-device copy, so a launch can be captured
+// into a CUDA graph): one task per (lattice, output parity, phase), each
+// covering V_h * n_rhs thread slots cut into chunks of one block.  Blocks of a cooperative grid (every block
 // resident) take chunks from a device work queue (an atomic counter per
 // phase), so small and large lattices share the GPU without one launch per
 // lattice.  The full operator D needs one phase; the even-odd operator
@@ -54,12 +55,19 @@ __device__ __forceinline__ unsigned long long global_ns() {
 constexpr int kMaxBatchTasks = 64;     // 2 tasks per lattice: up to 32 lattices per launch
 constexpr int kChunksPerGrab = 4;      // work-queue grabs cover 4 blocks' worth of thread slots
 
-__global__ void __launch_bounds__(kHopThreads, 3) batch_kernel(const BatchTask* __restrict__ tasks,
+// the whole task table as one launch parameter (the parameter space holds up
+// to 32 KB from CUDA 12.1 on sm_70+)
+struct BatchTable {
+  BatchTask t[kMaxBatchTasks];
+};
+static_assert(sizeof(BatchTable) + sizeof(BatchMeta) + sizeof(void*) < 32000, "batch table exceeds the parameter space");
+
+__global__ void __launch_bounds__(kHopThreads, 3) batch_kernel(const __grid_constant__ BatchTable table,
                                                                 BatchControl* ctl, const BatchMeta meta) {
   __shared__ BatchTask s_tasks[kMaxBatchTasks];
   __shared__ long long s_chunk;
   __shared__ int s_abort;
-  for (int k = threadIdx.x; k < meta.ntasks; k += kHopThreads) s_tasks[k] = tasks[k];
+  for (int k = threadIdx.x; k < meta.ntasks; k += kHopThreads) s_tasks[k] = table.t[k];
   __syncthreads();
   for (int phase = 0; phase < meta.nphases; ++phase) {
     // this phase's tasks occupy a contiguous range of the table
@@ -132,8 +140,6 @@ size_t batch_workspace_bytes(const bsm_batch_item* items, int count, int op) {
   size_t bytes = 0;
   const auto align = [](size_t v) { return (v + 255) / 256 * 256; };
   bytes += align(sizeof(BatchControl));
-  const int ntasks = count * 2;
-  bytes += align(sizeof(BatchTask) * ntasks);
   if (op == BSM_BATCH_DHAT)
     for (int k = 0; k < count; ++k) {
       const Geom g = make_geom(items[k].lat);
@@ -142,13 +148,17 @@ size_t batch_workspace_bytes(const bsm_batch_item* items, int count, int op) {
   return bytes;
 }
 
-int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o, void* ws, cudaStream_t s) {
+int batch_status(void* ws, cudaStream_t s);
+
+// launches the batch on `s`; with sync, waits and reads the error flag
+// (BSM_ETIMEOUT), else returns at once (nothing but a memset and the
+// cooperative launch is enqueued, so the call can be captured in a graph)
+int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o, void* ws, cudaStream_t s,
+                 bool sync) {
   const auto align = [](size_t v) { return (v + 255) / 256 * 256; };
   char* w = reinterpret_cast<char*>(ws);
   BatchControl* ctl = reinterpret_cast<BatchControl*>(w);
   w += align(sizeof(BatchControl));
-  BatchTask* dtasks = reinterpret_cast<BatchTask*>(w);
-  w += align(sizeof(BatchTask) * count * 2);
 
   std::vector<BatchTask> tasks, tasks1;  // phase 0 and phase 1 (the kernel wants them by phase)
   BatchMeta meta;
@@ -226,17 +236,29 @@ int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o
   meta.barrier_target = (unsigned)grid + (unsigned)(o.barrier_extra > 0 ? o.barrier_extra : 0);
   meta.timeout_ns = (unsigned long long)((o.timeout_s > 0 ? o.timeout_s : 1.0) * 1e9);
 
-  cudaMemsetAsync(ctl, 0, sizeof(BatchControl), s);
-  cudaMemcpyAsync(dtasks, tasks.data(), sizeof(BatchTask) * tasks.size(), cudaMemcpyHostToDevice, s);
-  void* kargs[] = {(void*)&dtasks, (void*)&ctl, (void*)&meta};
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)batch_kernel, grid, kHopThreads, kargs, 0, s);
+  BatchTable table;
+  memset(&table, 0, sizeof(table));
+  for (size_t k = 0; k < tasks.size(); ++k) table.t[k] = tasks[k];
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(BatchControl), s);
   if (e != cudaSuccess) {
     set_cuda_error(e);
     return BSM_ECUDA;
   }
+  void* kargs[] = {(void*)&table, (void*)&ctl, (void*)&meta};
+  e = cudaLaunchCooperativeKernel((void*)batch_kernel, grid, kHopThreads, kargs, 0, s);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return BSM_ECUDA;
+  }
+  return sync ? batch_status(ws, s) : BSM_OK;
+}
+
+// waits for `s` and reads the error flag the last batch on this workspace left
+int batch_status(void* ws, cudaStream_t s) {
+  const BatchControl* ctl = reinterpret_cast<const BatchControl*>(ws);
   int err = 0;
-  cudaMemcpyAsync(&err, &ctl->error, sizeof(int), cudaMemcpyDeviceToHost, s);
-  e = cudaStreamSynchronize(s);
+  cudaError_t e = cudaMemcpyAsync(&err, &ctl->error, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     set_cuda_error(e);
     return BSM_ECUDA;

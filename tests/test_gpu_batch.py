@@ -80,3 +80,44 @@ def test_barrier_timeout_returns_etimeout_and_gpu_stays_usable():
     olat, R, psis, blat, out, nrhs = refs[0]
     got = unpack(blat, out, nrhs)
     assert rel(got[0], orc.dhat(olat, R, psis[0], orc.DHAT)) <= TOL[bsm.F32]
+
+
+@pytest.mark.parametrize("op", [bsm.BATCH_D, bsm.BATCH_DHAT], ids=["D", "Dhat"])
+def test_batch_captured_in_a_cuda_graph(op):
+    """bsm_dslash_batch_async captured into a CUDA graph on a side stream:
+    each replay reruns the whole persistent batch (work queue reset by the
+    captured memset) and gives the oracle's result; the status query reads
+    the error flag after the replays."""
+    items, refs = make_batch(op, seed=970)
+    arr = bsm.batch_items(items)
+    opts = bsm.BatchOpts(op, bsm.F32, 0.0, 0)
+    ws = torch.empty(bsm.bsm_batch_workspace_bytes(arr, opts), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    bsm.bsm_dslash_batch_async(arr, opts, ws, stream=s)   # eager run first (occupancy query, module load)
+    assert bsm.bsm_dslash_batch_status(ws, stream=s) == bsm.OK
+    for _, _, _, _, out, _ in refs:
+        out.zero_()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        bsm.bsm_dslash_batch_async(arr, opts, ws, stream=s)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    assert bsm.bsm_dslash_batch_status(ws, stream=s) == bsm.OK
+    for olat, R, psis, blat, out, nrhs in refs:
+        got = unpack(blat, out, nrhs)
+        for r in range(nrhs):
+            want = orc.dirac(olat, R, psis[r]) if op == bsm.BATCH_D else orc.dhat(olat, R, psis[r], orc.DHAT)
+            assert rel(got[r], want) <= TOL[bsm.F32], (blat.dims[:], r, rel(got[r], want))
+
+
+def test_async_batch_timeout_is_reported_by_the_status_query():
+    items, refs = make_batch(bsm.BATCH_DHAT, seed=990)
+    arr = bsm.batch_items(items)
+    opts = bsm.BatchOpts(bsm.BATCH_DHAT, bsm.F32, 0.05, 0)
+    ws = torch.empty(bsm.bsm_batch_workspace_bytes(arr, opts), dtype=torch.uint8, device="cuda")
+    assert bsm.bsm_dslash_batch_async(arr, bsm.BatchOpts(bsm.BATCH_DHAT, bsm.F32, 0.05, 1), ws) == bsm.OK
+    assert bsm.bsm_dslash_batch_status(ws) == bsm.ETIMEOUT
+    assert bsm.bsm_dslash_batch_async(arr, opts, ws) == bsm.OK
+    assert bsm.bsm_dslash_batch_status(ws) == bsm.OK

@@ -28,7 +28,7 @@ int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void*
 size_t ptc_workspace_bytes(const bsm_lattice& L, int C, int nb, bool train);
 int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, bool even_only, cudaStream_t s);
 int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* in,
-              void* out, int nb, int prec, void* ws, cudaStream_t s);
+              void* out, int nb, int prec, void* ws, cudaStream_t s, bool even_only = false);
 int ptc_loss_grad(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* r,
                   const void* e, int nb, void* GW1, void* GW2, double* loss, void* ws, cudaStream_t s);
 int ptc_adam(void* W, const void* G, void* m, void* v, long long nfloat, double lr, int step, cudaStream_t s);

@@ -26,7 +26,7 @@ size_t ptc_workspace_bytes(const bsm_lattice& L, int C, int nb, bool train);
 int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, bool even_only, cudaStream_t s);
 int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, bool even_only, cudaStream_t s);
 int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* in,
-              void* out, int nb, int prec, void* ws, cudaStream_t s);
+              void* out, int nb, int prec, void* ws, cudaStream_t s, bool even_only = false);
 
 namespace {
 
@@ -295,7 +295,8 @@ struct Fgcr {
     rc = f32 ? ptc_pack32(L, reinterpret_cast<const float*>(r), w + y.F_in, false, o.eo != 0, s)
              : ptc_pack(L, reinterpret_cast<const double*>(r), w + y.F_in, false, o.eo != 0, s);
     if (rc != BSM_OK) return rc;
-    if ((rc = ptc_apply(L, U32, W1, W2, o.channels, w + y.F_in, w + y.F_out, 1, o.ptc_prec, w + y.ptc, s)) != BSM_OK)
+    if ((rc = ptc_apply(L, U32, W1, W2, o.channels, w + y.F_in, w + y.F_out, 1, o.ptc_prec, w + y.ptc, s,
+                        o.eo != 0)) != BSM_OK)
       return rc;
     return f32 ? ptc_pack32(L, reinterpret_cast<const float*>(z), w + y.F_out, true, o.eo != 0, s)
                : ptc_pack(L, reinterpret_cast<const double*>(z), w + y.F_out, true, o.eo != 0, s);

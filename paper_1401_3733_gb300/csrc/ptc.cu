@@ -29,7 +29,8 @@ namespace bsm {
 bool ptc_fused_supported(int C);
 size_t ptc_fused_weight_bytes(int C);
 int ptc_fused_apply(const char* links, size_t link_block, int d, int C, const void* F, const void* W1,
-                    const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, cudaStream_t s);
+                    const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, bool even_only,
+                    cudaStream_t s);
 
 namespace {
 
@@ -412,9 +413,12 @@ int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, boo
   return BSM_OK;
 }
 
-// out (rows x 4 complex) = layer2(layer1(in)); prec F32 (complex GEMMs) or BF16 (realified GEMMs)
+// out (rows x 4 complex) = layer2(layer1(in)); prec F32 (complex GEMMs) or BF16 (realified GEMMs).
+// even_only (BF16 with a fused kernel): `in` vanishes on odd sites and only the
+// even rows of `out` are wanted (the even-even block of the network); the odd
+// rows of `out` are then left unwritten.
 int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* in,
-              void* out, int nb, int prec, void* ws, cudaStream_t s) {
+              void* out, int nb, int prec, void* ws, cudaStream_t s, bool even_only) {
   const OpCtx c = make_ctx(L, U32, BSM_F32, s);
   const PtcLayout y = ptc_layout(L, C, nb, false);
   char* w = reinterpret_cast<char*>(ws);
@@ -423,7 +427,8 @@ int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void*
   launch_permute(W2, w + y.W2p, C, 1, false, s);
   // BF16 with a fused kernel for this C: transports and both GEMMs in one pass (no cuBLAS)
   if (bf && ptc_fused_supported(C))
-    return ptc_fused_apply(c.links, c.link_block, c.d, C, in, W1, w + y.W2p, w + y.Wt, w + y.Z2, out, c.g, nb, s);
+    return ptc_fused_apply(c.links, c.link_block, c.d, C, in, W1, w + y.W2p, w + y.Wt, w + y.Z2, out, c.g, nb,
+                           even_only, s);
   std::lock_guard<std::mutex> lock(g_blas_mu);
   cublasHandle_t h = bind_blas(w + y.blasws, s);
   if (h == nullptr) return BSM_ECUDA;

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_kernel(const char* __r
                                                                const __nv_bfloat16* __restrict__ W1T,
                                                                const __nv_bfloat16* __restrict__ W2T,
                                                                unsigned* __restrict__ Z, long long zrows, Geom g,
-                                                               int bpp) {
+                                                               int bpp, int even_only) {
   using S = FusedShape<C>;
   constexpr int kRows = kFusedSites * D;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -105,12 +105,33 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_kernel(const char* __r
     unsigned* xr[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) xr[c] = reinterpret_cast<unsigned*>(sX + (sl * D + c) * kXStride);
-    if (i < g.Vh) {
+    // even_only: the input vanishes on odd sites, so an even site has only
+    // its own term and an odd site only the transports of its neighbours
+    const bool self_only = even_only && p == 0, no_self = even_only && p == 1;
+    if (i < g.Vh && self_only) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        if (half == 0) {
+          const float4* q = reinterpret_cast<const float4*>(F + ((prow0 + i) * D + c) * 4);
+          const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+          xr[c][0] = pack_bf2(v0.x, v0.y);
+          xr[c][1] = pack_bf2(v0.z, v0.w);
+          xr[c][2] = pack_bf2(v1.x, v1.y);
+          xr[c][3] = pack_bf2(v1.z, v1.w);
+        }
+        for (int e = 4 + half; e < 36; e += 2) xr[c][e] = 0u;
+      }
+    } else if (i < g.Vh) {
       int nf[4], nb_[4];
       eo_neighbours(g, i, p, nf, nb_);
       using L = LinkIO<F32, D, false>;
       const auto* lt = L::tile_ptr(links + (size_t)p * link_block, i);
-      if (half == 0) {
+      if (half == 0 && no_self) {
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) xr[c][e] = 0u;
+      } else if (half == 0) {
 #pragma unroll
         for (int c = 0; c < D; ++c) {
           const float4* q = reinterpret_cast<const float4*>(F + ((prow0 + i) * D + c) * 4);
@@ -225,15 +246,18 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_kernel(const char* __r
 }
 
 // out(x)[s] = sum_k (T_k Z_k)(x)[s] with Z in BF16, slot-major: Z[k][row] = 4 spins (16 bytes)
+// (even_only: output parity 0 only, one thread per even site)
 template <int D>
 __global__ void __launch_bounds__(128) stencil_bf16_kernel(const char* __restrict__ links, size_t link_block,
                                                            const uint4* __restrict__ Z, long long zrows,
-                                                           float2* __restrict__ out, Geom g, int nb) {
+                                                           float2* __restrict__ out, Geom g, int nb,
+                                                           int even_only) {
   const long long t = blockIdx.x * 128LL + threadIdx.x;
-  if (t >= (long long)nb * 2 * g.Vh) return;
+  const int np = even_only ? 1 : 2;
+  if (t >= (long long)nb * np * g.Vh) return;
   const int i = (int)(t % g.Vh);
-  const int p = (int)((t / g.Vh) % 2);
-  const int b = (int)(t / (2LL * g.Vh));
+  const int p = (int)((t / g.Vh) % np);
+  const int b = (int)(t / ((long long)np * g.Vh));
   const long long prow = ((long long)b * 2 + p) * g.Vh, orow = ((long long)b * 2 + 1 - p) * g.Vh;
   int nf[4], nb_[4];
   eo_neighbours(g, i, p, nf, nb_);
@@ -295,7 +319,7 @@ size_t fused_smem() {
 
 template <int D, int C>
 int fused_launch(const char* links, size_t link_block, const void* F, const void* W1, const void* W2p, void* W1T,
-                 void* W2T, void* Z, void* out, const Geom& g, int nb, cudaStream_t s) {
+                 void* W2T, void* Z, void* out, const Geom& g, int nb, bool even_only, cudaStream_t s) {
   using S = FusedShape<C>;
   const int n = S::W1Elems + S::W2Elems;
   fused_prep_kernel<C><<<(n + 255) / 256, 256, 0, s>>>(reinterpret_cast<const float2*>(W1),
@@ -310,20 +334,22 @@ int fused_launch(const char* links, size_t link_block, const void* F, const void
   const long long sites = (long long)nb * 2 * g.Vh, zrows = sites * D;
   fused_kernel<D, C><<<nb * 2 * bpp, kFusedThreads, smem, s>>>(
       links, link_block, reinterpret_cast<const float2*>(F), reinterpret_cast<const __nv_bfloat16*>(W1T),
-      reinterpret_cast<const __nv_bfloat16*>(W2T), reinterpret_cast<unsigned*>(Z), zrows, g, bpp);
-  stencil_bf16_kernel<D><<<(int)((sites + 127) / 128), 128, 0, s>>>(
-      links, link_block, reinterpret_cast<const uint4*>(Z), zrows, reinterpret_cast<float2*>(out), g, nb);
+      reinterpret_cast<const __nv_bfloat16*>(W2T), reinterpret_cast<unsigned*>(Z), zrows, g, bpp, even_only ? 1 : 0);
+  const long long outs = even_only ? sites / 2 : sites;
+  stencil_bf16_kernel<D><<<(int)((outs + 127) / 128), 128, 0, s>>>(
+      links, link_block, reinterpret_cast<const uint4*>(Z), zrows, reinterpret_cast<float2*>(out), g, nb,
+      even_only ? 1 : 0);
   return BSM_OK;
 }
 
 template <int D>
 int fused_dispatch_c(int C, const char* links, size_t lb, const void* F, const void* W1, const void* W2p, void* W1T,
-                     void* W2T, void* Z, void* out, const Geom& g, int nb, cudaStream_t s) {
+                     void* W2T, void* Z, void* out, const Geom& g, int nb, bool eo, cudaStream_t s) {
   switch (C) {
-    case 2: return fused_launch<D, 2>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, s);
-    case 4: return fused_launch<D, 4>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, s);
-    case 8: return fused_launch<D, 8>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, s);
-    case 12: return fused_launch<D, 12>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, s);
+    case 2: return fused_launch<D, 2>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, eo, s);
+    case 4: return fused_launch<D, 4>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, eo, s);
+    case 8: return fused_launch<D, 8>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, eo, s);
+    case 12: return fused_launch<D, 12>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, eo, s);
     default: return BSM_EUNSUPPORTED;
   }
 }
@@ -338,11 +364,12 @@ size_t ptc_fused_weight_bytes(int C) { return (size_t)(8 * C * kXStride + 72 * (
 
 // Z: 9 x rows x 4 BF16 complex (4 bytes each), slot-major; W1T/W2T: ptc_fused_weight_bytes(C), 16-byte aligned
 int ptc_fused_apply(const char* links, size_t link_block, int d, int C, const void* F, const void* W1,
-                    const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, cudaStream_t s) {
+                    const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, bool even_only,
+                    cudaStream_t s) {
   void* W1T = Wt;
   void* W2T = reinterpret_cast<char*>(Wt) + (size_t)8 * C * kXStride * 2;
-  if (d == 2) return fused_dispatch_c<2>(C, links, link_block, F, W1, W2p, W1T, W2T, Z, out, g, nb, s);
-  if (d == 3) return fused_dispatch_c<3>(C, links, link_block, F, W1, W2p, W1T, W2T, Z, out, g, nb, s);
+  if (d == 2) return fused_dispatch_c<2>(C, links, link_block, F, W1, W2p, W1T, W2T, Z, out, g, nb, even_only, s);
+  if (d == 3) return fused_dispatch_c<3>(C, links, link_block, F, W1, W2p, W1T, W2T, Z, out, g, nb, even_only, s);
   return BSM_EUNSUPPORTED;
 }
 

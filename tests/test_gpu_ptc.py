@@ -366,3 +366,24 @@ def test_fgcr_check_every_bounds_the_overshoot():
     assert st1 == bsm.OK and st4 == bsm.OK
     assert s1.iters <= s4.iters <= s1.iters + 3 + s4.cycles
     assert rel(orc.dirac(olat, R, to_canon(blat, x4, bsm.F64)), b) <= 1e-10
+
+
+def test_even_only_network_application_matches_the_full_one():
+    """In even-odd FGCR the BF16 fused path applies only the even-even block
+    of the network (even sites skip their neighbours' transports, the
+    stencil skips odd outputs); the FP32 path applies the whole network and
+    keeps the even part.  The same preconditioner up to BF16 rounding: the
+    two solves take the same number of steps within 2."""
+    dims, N = (8, 4, 4, 6), 3
+    olat, blat = lats(dims, N, bsm.FUND, (np.pi, 0, 0, 0), m0=0.05)
+    U = fields.gauge_field(dims, N, "smooth", seed=34, eps=0.4)
+    U64, U32 = gpu_links(blat, U, bsm.F64), gpu_links(blat, U, bsm.F32)
+    b = gpu_spinor(blat, fields.gaussian_spinor(dims, N, 35), bsm.F64)
+    W = tuple(dev_c64(w) for w in neumann_weights(olat.m0))
+    its = {}
+    for prec in (bsm.F32, bsm.BF16):
+        st, s, _ = fgcr(blat, U64, U32, b, bsm.fgcr_opts(tol=1e-10, restart=16, eo=True, precond=bsm.FGCR_PTC,
+                                                          channels=2, ptc_prec=prec), W)
+        assert st == bsm.OK and s.true_res <= 1.5e-10
+        its[prec] = s.iters
+    assert abs(its[bsm.F32] - its[bsm.BF16]) <= 2, its

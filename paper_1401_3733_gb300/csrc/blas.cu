@@ -122,6 +122,7 @@ __global__ void cg_alpha_kernel(CgState* st, const double* __restrict__ partials
   } else {
     st->alpha = st->rr / pAp;
   }
+  st->alpha_f = (float)st->alpha;
 }
 
 // beta = |r_new|^2 / |r|^2, convergence and reliable-update flags

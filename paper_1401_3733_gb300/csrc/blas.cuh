@@ -13,6 +13,7 @@ struct CgState {
   double rr_prev;   // |r|^2 before the last beta step
   double pAp;       // <p, M p> = |Dhat p|^2
   double alpha, beta;
+  float alpha_f;    // alpha rounded to FP32 (the fused FP32 CG step reads it)
   double stop2;     // tol^2 |rhs|^2
   double rr_max;    // max |r|^2 since the last reliable update
   double delta2;    // reliable-update trigger, squared

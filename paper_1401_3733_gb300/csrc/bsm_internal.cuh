@@ -599,6 +599,12 @@ struct HopArgs {
   float ph3[4][2];     // (cos, sin) of 3 phi_mu: two-row links' boundary factor
   float af, bf;        // a, b rounded to FP32, and b == 1 (set at launch: FP32
   int b_one;           // kernels avoid per-thread FP64 conversions and compares)
+  // fused CG step (FP32 vectors; cg_r != nullptr): out is not written, the
+  // epilogue does r -= alpha out, x += alpha p with alpha = *cg_alpha
+  void* cg_r;
+  void* cg_x;
+  const void* cg_p;
+  const float* cg_alpha;
 };
 
 // the epilogue scalars at the kernel's arithmetic precision: FP32 kernels

@@ -262,7 +262,10 @@ struct HopOccupancy {
                                                        : (D <= 3 ? 4 : D == 4 ? 3 : D == 6 ? 2 : 1);
 };
 
-template <typename P, int D, bool REAL>
+// EPI = 1 (FP32 vectors only): the output is the CG product Ap of this
+// site; instead of storing it the epilogue completes the CG step,
+// r -= alpha Ap and x += alpha p, and the partials are those of |r|^2
+template <typename P, int D, bool REAL, int EPI = 0>
 __global__ void __launch_bounds__(kHopThreads, HopOccupancy<P, D>::min_blocks) hop_kernel(const HopArgs A) {
   using R = typename P::R;
   if (A.done != nullptr && *A.done != 0) return;  // uniform over the grid
@@ -301,7 +304,29 @@ __global__ void __launch_bounds__(kHopThreads, HopOccupancy<P, D>::min_blocks) h
 #pragma unroll
         for (int c = 0; c < D; ++c) acc[s][c] = cmake(b * acc[s][c].re, b * acc[s][c].im);
     }
-    SpinorIO<P, D>::store(A.out, Vh, i, acc);
+    if constexpr (EPI == 1) {
+      // rows written only by this thread: read through L2 (not the read-only path)
+      const R al = *A.cg_alpha;
+      cx<R> v[4][D], w[4][D];
+      SpinorIO<P, D>::template load<true>(A.cg_r, Vh, i, v);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          acc[s][c] = cmake(fma(-al, acc[s][c].re, v[s][c].re), fma(-al, acc[s][c].im, v[s][c].im));  // r
+        }
+      SpinorIO<P, D>::store(A.cg_r, Vh, i, acc);
+      SpinorIO<P, D>::template load<true>(A.cg_x, Vh, i, v);
+      SpinorIO<P, D>::template load<true>(A.cg_p, Vh, i, w);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          v[s][c] = cmake(fma(al, w[s][c].re, v[s][c].re), fma(al, w[s][c].im, v[s][c].im));
+      SpinorIO<P, D>::store(A.cg_x, Vh, i, v);
+    } else {
+      SpinorIO<P, D>::store(A.out, Vh, i, acc);
+    }
     if (A.partials != nullptr) {
       R n = R(0);
 #pragma unroll
@@ -317,6 +342,12 @@ __global__ void __launch_bounds__(kHopThreads, HopOccupancy<P, D>::min_blocks) h
 template <typename P, int D, bool REAL>
 inline int launch_hop_t(const HopArgs& A, cudaStream_t s) {
   const int blocks = hop_blocks(A.g.Vh);
+  if constexpr (P::prec == BSM_F32 || P::prec == BSM_F32R12) {
+    if (A.cg_r != nullptr) {
+      hop_kernel<P, D, REAL, 1><<<blocks, kHopThreads, 0, s>>>(with_f32_scalars(A));
+      return blocks;
+    }
+  }
   hop_kernel<P, D, REAL><<<blocks, kHopThreads, 0, s>>>(with_f32_scalars(A));
   return blocks;
 }

@@ -39,9 +39,10 @@ OpCtx make_ctx(const bsm_lattice& L, const void* links, int prec, cudaStream_t s
   return c;
 }
 
-int op_hop(const OpCtx& c, int p, const void* in, void* out, int dagger, const void* x, double a, double b,
-           double* partials, const int* done) {
-  HopArgs h;
+namespace {
+HopArgs hop_args(const OpCtx& c, int p, const void* in, void* out, int dagger, const void* x, double a, double b,
+                 double* partials, const int* done) {
+  HopArgs h{};
   h.links = c.links + (size_t)p * c.link_block;
   h.in = in;
   h.out = out;
@@ -57,9 +58,29 @@ int op_hop(const OpCtx& c, int p, const void* in, void* out, int dagger, const v
     h.ph3[mu][0] = c.ph3[mu][0];
     h.ph3[mu][1] = c.ph3[mu][1];
   }
-  const int blocks = launch_hop(c.prec, c.d, c.real, h, c.s);
+  return h;
+}
+}  // namespace
+
+int op_hop(const OpCtx& c, int p, const void* in, void* out, int dagger, const void* x, double a, double b,
+           double* partials, const int* done) {
+  const int blocks = launch_hop(c.prec, c.d, c.real, hop_args(c, p, in, out, dagger, x, a, b, partials, done), c.s);
   if (blocks < 0) return BSM_EUNSUPPORTED;
   return partials != nullptr ? blocks : 0;
+}
+
+int op_dhat_dag_cg(const OpCtx& c, const void* u, void* tmp_o, void* r, void* x, const void* p, const float* alpha,
+                   double* partials, const int* done) {
+  int n = op_hop(c, 1, u, tmp_o, 1, nullptr, 0.0, 1.0, nullptr, done);
+  if (n < 0) return n;
+  HopArgs h = hop_args(c, 0, tmp_o, nullptr, 1, u, c.A, -1.0 / (4.0 * c.A), partials, done);
+  h.cg_r = r;
+  h.cg_x = x;
+  h.cg_p = p;
+  h.cg_alpha = alpha;
+  const int blocks = launch_hop(c.prec, c.d, c.real, h, c.s);
+  if (blocks < 0) return BSM_EUNSUPPORTED;
+  return blocks;
 }
 
 int op_dhat(const OpCtx& c, const void* in_e, void* out_e, void* tmp_o, int dagger, double* partials,

@@ -29,6 +29,13 @@ OpCtx make_ctx(const bsm_lattice& L, const void* links, int prec, cudaStream_t s
 int op_hop(const OpCtx& c, int p, const void* in, void* out, int dagger, const void* x, double a, double b,
            double* partials, const int* done);
 
+// the second factor of Dhat^+ Dhat fused with a CG step (FP32 vectors):
+// tmp_o = H^+_oe u, then Ap = A u - 1/(4A) H^+_eo tmp_o is not stored but
+// applied, r -= alpha Ap and x += alpha p (alpha = *alpha, device); writes
+// the partials of |r|^2 and returns their count, or < 0 on error
+int op_dhat_dag_cg(const OpCtx& c, const void* u, void* tmp_o, void* r, void* x, const void* p, const float* alpha,
+                   double* partials, const int* done);
+
 // out_e = Dhat in_e (or Dhat^+); tmp_o: one half spinor; partials of |out|^2
 int op_dhat(const OpCtx& c, const void* in_e, void* out_e, void* tmp_o, int dagger, double* partials,
             const int* done);

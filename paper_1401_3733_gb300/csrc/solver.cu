@@ -189,6 +189,19 @@ struct Solver {
 
   // one CG iteration at the precision of context c
   int iterate(const OpCtx& c, void* x, void* r, void* p, void* Ap, void* u, void* t, size_t vec) const {
+    if (eo && vector_prec(c.prec) == BSM_F32) {
+      // FP32 even-odd: the x and r updates ride in the epilogue of the last
+      // hop of Dhat^+ Dhat p (Ap is never stored); alpha is known once
+      // |Dhat p|^2 is reduced, before the Dhat^+ hops run
+      cg_p_update_launch(BSM_F32, p, r, vec / 16, st, s);
+      const int np = op_dhat(c, p, u, t, 0, partA, done);
+      if (np < 0) return np;
+      cg_alpha_launch(st, partA, np, s);
+      const int nb = op_dhat_dag_cg(c, u, t, r, x, p, &st->alpha_f, partB, done);
+      if (nb < 0) return nb;
+      cg_beta_launch(st, partB, nb, s);
+      return 0;
+    }
     cg_p_update_launch(vector_prec(c.prec), p, r, vec / 16, st, s);
     const int np = apply_normal(c, p, Ap, u, t, partA, done);
     if (np < 0) return np;

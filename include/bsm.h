@@ -420,7 +420,7 @@ size_t bsm_fgcr_workspace_bytes(const bsm_lattice *lat, const bsm_fgcr_opts *opt
 /* b, x: full FP64 device-layout spinors (x is overwritten, start x = 0);
  * U_rep64: FP64 links; U_rep32: FP32 links, used with BSM_FGCR_PTC or
  * prec_inner BSM_F32 (may be NULL otherwise); W1, W2: used with BSM_FGCR_PTC
- * only.  Synchronises `stream` every iteration.  Returns
+ * only.  Synchronises `stream` every check_every steps.  Returns
  * BSM_ENOCONV (max_iter reached) or BSM_ENAN with x holding the last iterate. */
 int bsm_fgcr_solve(const bsm_lattice *lat, const void *U_rep64, const void *U_rep32,
                    const void *W1, const void *W2, const void *b, void *x,

@@ -165,6 +165,65 @@ __device__ __forceinline__ void hop_sense(const HopArgs& A, size_t Vh, const typ
   }
 }
 
+// The same with (mu, sense) chosen at run time, for a loop over the 8
+// direction-senses that is not unrolled: the link matrix-vector code then
+// appears once in the kernel instead of eight times (double-float: fully
+// unrolled, the kernel outgrows the instruction cache and warps stall on
+// instruction fetch).  Only the cheap spin projection and reconstruction
+// are specialised per direction.
+template <typename P, int D, bool REAL>
+__device__ __forceinline__ void hop_sense_rt(const HopArgs& A, size_t Vh,
+                                             const typename LinkIO<P, D, REAL>::vec* lt, int mu, int fb, int n,
+                                             typename P::R sg, cx<typename P::R> (&acc)[4][D]) {
+  using R = typename P::R;
+  using L = LinkIO<P, D, REAL>;
+  cx<R> h[2][D];
+  {
+    cx<R> psi[4][D];
+    SpinorIO<P, D>::load(A.in, Vh, n, psi);
+    switch (mu) {
+      case 0: spin_project<0>(psi, sg, h); break;
+      case 1: spin_project<1>(psi, sg, h); break;
+      case 2: spin_project<2>(psi, sg, h); break;
+      default: spin_project<3>(psi, sg, h); break;
+    }
+  }
+  // complex links: sense fb of direction mu sits fb planes-of-D^2 after the
+  // forward planes; real links: both senses share each plane (select the half)
+  const auto* lf = REAL ? lt : lt + (size_t)fb * D * D * kLinkTile;
+  cx<R> w0[D], w1[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    w0[a] = cmake(R(0), R(0));
+    w1[a] = w0[a];
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const typename L::elem u = (REAL && fb) ? L::template load_one<1>(lf, mu, a * D + b)
+                                              : L::template load_one<0>(lf, mu, a * D + b);
+      link_mac(w0[a], u, h[0][b]);
+      link_mac(w1[a], u, h[1][b]);
+    }
+  }
+  switch (mu) {
+    case 0:
+#pragma unroll
+      for (int a = 0; a < D; ++a) spin_reconstruct<0>(acc, a, w0[a], w1[a], sg);
+      break;
+    case 1:
+#pragma unroll
+      for (int a = 0; a < D; ++a) spin_reconstruct<1>(acc, a, w0[a], w1[a], sg);
+      break;
+    case 2:
+#pragma unroll
+      for (int a = 0; a < D; ++a) spin_reconstruct<2>(acc, a, w0[a], w1[a], sg);
+      break;
+    default:
+#pragma unroll
+      for (int a = 0; a < D; ++a) spin_reconstruct<3>(acc, a, w0[a], w1[a], sg);
+      break;
+  }
+}
+
 template <typename P>
 struct HopSplitSenses {
   static constexpr bool value = P::prec == BSM_DF64;
@@ -283,10 +342,18 @@ __global__ void __launch_bounds__(kHopThreads, HopOccupancy<P, D>::min_blocks) h
     for (int s = 0; s < 4; ++s)
 #pragma unroll
       for (int a = 0; a < D; ++a) acc[s][a] = cmake(R(0), R(0));
-    hop_direction<0, P, D, REAL>(A, Vh, lt, nf[0], nb[0], sg, -sg, acc, edges);
-    hop_direction<1, P, D, REAL>(A, Vh, lt, nf[1], nb[1], sg, -sg, acc, edges);
-    hop_direction<2, P, D, REAL>(A, Vh, lt, nf[2], nb[2], sg, -sg, acc, edges);
-    hop_direction<3, P, D, REAL>(A, Vh, lt, nf[3], nb[3], sg, -sg, acc, edges);
+    if constexpr (HopSplitSenses<P>::value) {
+#pragma unroll 1
+      for (int k = 0; k < 8; ++k) {
+        const int mu = k >> 1, fb = k & 1;
+        hop_sense_rt<P, D, REAL>(A, Vh, lt, mu, fb, fb ? nb[mu] : nf[mu], fb ? -sg : sg, acc);
+      }
+    } else {
+      hop_direction<0, P, D, REAL>(A, Vh, lt, nf[0], nb[0], sg, -sg, acc, edges);
+      hop_direction<1, P, D, REAL>(A, Vh, lt, nf[1], nb[1], sg, -sg, acc, edges);
+      hop_direction<2, P, D, REAL>(A, Vh, lt, nf[2], nb[2], sg, -sg, acc, edges);
+      hop_direction<3, P, D, REAL>(A, Vh, lt, nf[3], nb[3], sg, -sg, acc, edges);
+    }
 
     const R b = epi_b<R>(A);
     if (A.x != nullptr) {

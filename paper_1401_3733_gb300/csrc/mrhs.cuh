@@ -78,11 +78,11 @@ __device__ __forceinline__ void mrhs_direction(const MrhsArgs& A, const typename
 
 // Minimum resident blocks (register budget) per RHS block: measured on the
 // 24^4, 12-RHS workload, one RHS per thread wants about 168 registers (3
-// blocks per SM), two RHS per thread at d = 6 about 255 (2 blocks per SM);
-// tighter budgets spill.
+// blocks per SM) at d = 6 and 128 (4 blocks per SM) at d = 3, two RHS per
+// thread at d = 6 about 255 (2 blocks per SM); tighter budgets spill or lose.
 template <int D, int RB>
 struct MrhsOccupancy {
-  static constexpr int min_blocks = D <= 2 ? 1 : RB == 1 ? 3 : (RB == 2 && D >= 6) ? 2 : 1;
+  static constexpr int min_blocks = D <= 2 ? 1 : (RB == 1 && D == 3) ? 4 : RB == 1 ? 3 : (RB == 2 && D >= 6) ? 2 : 1;
 };
 
 // the output of site i, RHS r0 .. r0+RB-1 (one thread); L2IN reads the

@@ -98,6 +98,12 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_kernel(const char* __r
     for (int k = threadIdx.x; k < S::W2Elems / 8; k += kFusedThreads) d2[k] = s2[k];
   }
 
+  // even_only: the input vanishes on odd sites, so an even site has only its
+  // own term (X1 slot 0) and an odd site only the transports of its
+  // neighbours (slots 1..8); the even-only stencil then reads slot 0 of Z2
+  // on even rows and slots 1..8 on odd rows, so only those are computed
+  const bool self_only = even_only && p == 0, no_self = even_only && p == 1;
+
   // stage 1: transports -> X1 (bf16, realified) in shared memory
   {
     const int sl = threadIdx.x & (kFusedSites - 1), half = threadIdx.x / kFusedSites;
@@ -105,9 +111,6 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_kernel(const char* __r
     unsigned* xr[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) xr[c] = reinterpret_cast<unsigned*>(sX + (sl * D + c) * kXStride);
-    // even_only: the input vanishes on odd sites, so an even site has only
-    // its own term and an odd site only the transports of its neighbours
-    const bool self_only = even_only && p == 0, no_self = even_only && p == 1;
     if (i < g.Vh && self_only) {
 #pragma unroll
       for (int c = 0; c < D; ++c) {
@@ -206,6 +209,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_kernel(const char* __r
     for (int n = 0; n < C; ++n) acc1[n][0] = acc1[n][1] = acc1[n][2] = acc1[n][3] = 0.f;
 #pragma unroll
     for (int kk = 0; kk < 5; ++kk) {
+      if (self_only && kk > 0) break;  // X1 beyond slot 0 is zero
       unsigned a[4];
       a[0] = X32[(r0 + gq) * xs + kk * 8 + q];
       a[1] = X32[(r0 + gq + 8) * xs + kk * 8 + q];
@@ -230,17 +234,23 @@ __global__ void __launch_bounds__(kFusedThreads, 2) fused_kernel(const char* __r
 #pragma unroll
     for (int t = 0; t < C / 2; ++t)
 #pragma unroll
-      for (int n = 0; n < 9; ++n)
+      for (int n = 0; n < 9; ++n) {
+        if ((self_only && n > 0) || (no_self && n == 0)) continue;  // Z2 slots nobody reads
         mma16816(acc2[n], a2[t], W232[(n * 8 + gq) * w2s + t * 8 + q], W232[(n * 8 + gq) * w2s + t * 8 + 4 + q]);
+      }
     // Z2 row (prow0 + i0) * D + local row; the 8-column tile n is slot k = n, column pair q is spin q
     const long long zr = (prow0 + i0) * D + r0;
     if (r0 + gq < valid_rows) {
 #pragma unroll
-      for (int n = 0; n < 9; ++n) Z[(n * zrows + zr + gq) * 4 + q] = pack_bf2(acc2[n][0], acc2[n][1]);
+      for (int n = 0; n < 9; ++n)
+        if (!((self_only && n > 0) || (no_self && n == 0)))
+          Z[(n * zrows + zr + gq) * 4 + q] = pack_bf2(acc2[n][0], acc2[n][1]);
     }
     if (r0 + gq + 8 < valid_rows) {
 #pragma unroll
-      for (int n = 0; n < 9; ++n) Z[(n * zrows + zr + gq + 8) * 4 + q] = pack_bf2(acc2[n][2], acc2[n][3]);
+      for (int n = 0; n < 9; ++n)
+        if (!((self_only && n > 0) || (no_self && n == 0)))
+          Z[(n * zrows + zr + gq + 8) * 4 + q] = pack_bf2(acc2[n][2], acc2[n][3]);
     }
   }
 }

@@ -112,6 +112,25 @@ def test_ptc_net_matches_oracle_layers(case, prec, tol, C):
         assert rel(got[b], want) < tol
 
 
+def test_ptc_net_fused_kernel_walks_several_tiles_per_block():
+    """12 x 10^3 SU(3), 4 samples: parity blocks of 6000 sites give 47 tiles
+    of 128 sites (the last one ragged, 112 sites), 376 tiles in all, so each
+    block of the persistent fused kernel takes two or three tiles and both
+    of its shared-memory buffers are refilled."""
+    dims, N, rep, phase = (12, 10, 10, 10), 3, bsm.FUND, (np.pi, 0, 0.3, 0)
+    olat, blat = lats(dims, N, rep, phase)
+    U = fields.gauge_field(dims, N, "smooth", seed=40, eps=0.5)
+    R = orc.links_to_rep(olat, U)
+    U32 = gpu_links(blat, U, bsm.F32)
+    rng = np.random.default_rng(41)
+    C = 12
+    W1, W2 = rand_c(rng, (36, 4 * C), 0.3), rand_c(rng, (36 * C, 4), 0.1)
+    psis = [fields.gaussian_spinor(dims, olat.d, 42 + b) for b in range(4)]
+    got = gpu_net(blat, U32, W1, W2, C, psis, bsm.BF16)
+    for b in range(4):
+        assert rel(got[b], oracle_net(olat, R, psis[b], W1, W2, C)) < 2e-2
+
+
 @pytest.mark.parametrize("prec,tol", [(bsm.F32, 1e-5), (bsm.BF16, 1e-2)], ids=["f32", "bf16-fused"])
 def test_ptc_net_with_neumann_weights_is_the_polynomial_of_d(prec, tol):
     dims, N, rep, phase = CASES[0]
@@ -368,13 +387,16 @@ def test_fgcr_check_every_bounds_the_overshoot():
     assert rel(orc.dirac(olat, R, to_canon(blat, x4, bsm.F64)), b) <= 1e-10
 
 
-def test_even_only_network_application_matches_the_full_one():
+@pytest.mark.parametrize("dims", [(8, 4, 4, 6), (18, 14, 14, 14)], ids=["6-tiles", "386-tiles"])
+def test_even_only_network_application_matches_the_full_one(dims):
     """In even-odd FGCR the BF16 fused path applies only the even-even block
     of the network (even sites skip their neighbours' transports, the
     stencil skips odd outputs); the FP32 path applies the whole network and
     keeps the even part.  The same preconditioner up to BF16 rounding: the
-    two solves take the same number of steps within 2."""
-    dims, N = (8, 4, 4, 6), 3
+    two solves take the same number of steps within 2.  The larger lattice
+    (parity blocks of 24696 sites: 193 tiles, the last ragged) gives each
+    block of the persistent fused kernel several tiles."""
+    N = 3
     olat, blat = lats(dims, N, bsm.FUND, (np.pi, 0, 0, 0), m0=0.05)
     U = fields.gauge_field(dims, N, "smooth", seed=34, eps=0.4)
     U64, U32 = gpu_links(blat, U, bsm.F64), gpu_links(blat, U, bsm.F32)

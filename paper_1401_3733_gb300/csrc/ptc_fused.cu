@@ -1,28 +1,36 @@
 // ptc_fused.cu -- BF16 inference of the parallel-transport preconditioner
-// with the two channel-mixing GEMMs fused into the transport kernel.
+// with the two channel-mixing GEMMs fused into the transport kernel, on the
+// tcgen05 tensor cores.
 //
 // A tile is 128 consecutive eo sites of one parity (128 d rows of the PTC
-// field).  Stage 1: two threads per site compute the 9 transports of the
-// one-channel input (T_0, and U_mu(x) F(x+mu), U_mu(x-mu)^+ F(x-mu) for two
-// directions each) in FP32 and store them, rounded to BF16 and realified
-// (re, im interleaved), as the A tile X1 (rows x 72, padded to 80) in shared
-// memory.  Stage 2: each warp takes 16-row tiles through
-//     Y1 = X1 W1  (72 -> 8C reals)   and   Z2 = Y1 W2p  (8C -> 72 reals)
-// as mma.sync.m16n8k16 (BF16 x BF16 -> FP32).  The FP32 accumulator
-// fragments of two adjacent 8-column tiles of Y1 are, element for element,
-// the A fragment of one 16-deep k-step of the second GEMM, so Y1 is rounded
-// to BF16 in registers and never stored.  Z2 (rows x 36 complex, BF16) is the
-// only intermediate written to memory, slot-major (Z2[k][row][spin]) so that
-// the stencil kernel, which forms out = sum_k T_k Z2_k, reads each
-// neighbour's slot as whole, contiguous 16-byte groups.  The weights come
-// realified and transposed ([n][k], k padded) so that B fragments are
-// conflict-free 32-bit shared loads.
+// field).  Stage 1 (producer warps): two threads per site compute the 9
+// transports of the one-channel input (T_0, and U_mu(x) F(x+mu),
+// U_mu(x-mu)^+ F(x-mu) for two directions each) in FP32 and store them,
+// rounded to BF16 and realified (re, im interleaved), as the tile X1
+// (rows x 72 reals, padded to 80) in shared memory.  Stage 2 (consumer
+// warps), per block of 128 rows:
+//     Y1 = X1 W1  (80 -> 8C reals)   and   Z2 = Y1 W2p  (8C -> 72 reals)
+// as tcgen05.mma (BF16 x BF16 -> FP32, M = 128) issued by one thread, with
+// the accumulators in tensor memory.  The consumer warps read Y1 back
+// (tcgen05.ld, one TMEM lane = one row per thread), round it to BF16 into
+// shared memory as the A operand of the second MMA, and read Z2 back into
+// global memory.  Z2 (rows x 36 complex, BF16) is the only intermediate
+// written to memory, slot-major (Z2[k][row][spin]) so that the stencil
+// kernel, which forms out = sum_k T_k Z2_k, reads each neighbour's slot as
+// whole, contiguous 16-byte groups.
 //
-// The kernel is persistent (one 512-thread block per SM, weights staged in
-// shared memory once) and warp-specialised: 8 producer warps run stage 1 for
-// the next tile while 8 consumer warps run stage 2 on the previous one, with
-// two X1 buffers handed over through hardware named barriers, so that the
-// gathers from HBM overlap the tensor-core work.
+// All MMA operands sit in shared memory in the tensor core's no-swizzle,
+// K-major layout: 8 x 8 BF16 core matrices of 128 contiguous bytes (16 B
+// per row), K-adjacent cores 128 B apart (the descriptor's leading byte
+// offset), 8-row groups kcores * 128 B apart (its stride byte offset).  A
+// transport result (one row, one slot: 4 spins x re, im) is exactly one core
+// row, so the producers store it as one 16-byte word.
+//
+// The kernel is persistent (one block per SM, weights staged once) and
+// warp-specialised: 8 producer warps run stage 1 for the next tile while 4
+// consumer warps run stage 2 on the previous one, with two X1 buffers
+// handed over through hardware named barriers, so that the gathers from HBM
+// overlap the tensor-core work.
 #include <cuda_bf16.h>
 
 #include "bsm_internal.cuh"
@@ -31,33 +39,38 @@ namespace bsm {
 
 namespace {
 
-constexpr int kFusedSites = 128;   // eo sites per block (two threads per site in the transport stage)
-constexpr int kFusedThreads = 256;
-constexpr int kXStride = 88;        // bf16 per X1 row in shared memory (72 used, 80 for the MMA k-steps)
+constexpr int kFusedSites = 128;                      // eo sites per tile
+constexpr int kProducers = 256;                       // 8 warps, two threads per site
+constexpr int kConsumers = 128;                       // 4 warps, one per TMEM lane quarter
+constexpr int kFusedThreads = kProducers + kConsumers;
+constexpr int kK1 = 80;                               // GEMM1 depth: 72 transport reals + 8 zero
+constexpr int kN2 = 80;                               // GEMM2 width: 72 Z2 reals + 8 zero columns
+constexpr int kTmemCols = 512;                        // Y1 accumulators at column 128 rb, Z2 at kD2Col
+constexpr int kD2Col = 384;
+constexpr unsigned kWaitCap = 1u << 20;               // polls of an MMA-completion barrier before giving up
 
 template <int C>
 struct FusedShape {
-  static constexpr int N1 = 8 * C;           // Y1 reals per row
-  static constexpr int W1Stride = kXStride;  // W1T row (one Y1 column): 80 k + 8 pad
-  static constexpr int W2Stride = N1 + 8;    // W2T row (one Z2 column): 8C k + 8 pad
-  static constexpr int W1Elems = N1 * W1Stride;
-  static constexpr int W2Elems = 72 * W2Stride;
+  static constexpr int N1 = 8 * C;              // Y1 reals per row: GEMM1 width, GEMM2 depth
+  static constexpr int W1Bytes = N1 * kK1 * 2;  // GEMM1 B operand (N1 rows of K = 80)
+  static constexpr int W2Bytes = kN2 * N1 * 2;  // GEMM2 B operand (80 rows of K = N1)
+  static constexpr int Y1Bytes = 128 * N1 * 2;  // GEMM2 A operand of one 128-row block
 };
+
+// byte offset of element (r, k) of a K-major operand of `kcores` 8-wide
+// core columns, in the no-swizzle core-matrix layout
+__host__ __device__ constexpr int core_off(int r, int k, int kcores) {
+  return (r >> 3) * (kcores * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
 
 __device__ __forceinline__ unsigned pack_bf2(float lo, float hi) { return f2_to_bf2(lo, hi); }
 
-__device__ __forceinline__ void mma16816(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// realified, transposed, padded weights (bf16): W1T[n][k] = W1r[k][n], W2T[n][k] = W2pr[k][n]
+// realified, transposed weights in the core-matrix layout (bf16): GEMM1's B
+// is W1T[n][k] = W1r[k][n] (n < 8C, k < 80, zero for k >= 72), GEMM2's B is
+// W2T[n][k] = W2pr[k][n] (n < 80, zero for n >= 72, k < 8C)
 template <int C>
 __global__ void fused_prep_kernel(const float2* __restrict__ W1, const float2* __restrict__ W2p,
-                                  __nv_bfloat16* __restrict__ W1T, __nv_bfloat16* __restrict__ W2T) {
+                                  unsigned char* __restrict__ Wt) {
   using S = FusedShape<C>;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   // realified entry (k, n) of a complex K x N matrix M: [[Re, Im], [-Im, Re]] blocks
@@ -66,17 +79,19 @@ __global__ void fused_prep_kernel(const float2* __restrict__ W1, const float2* _
     if ((k & 1) == 0) return (n & 1) ? w.y : w.x;
     return (n & 1) ? w.x : -w.y;
   };
-  if (t < S::W1Elems) {
-    const int n = t / S::W1Stride, k = t % S::W1Stride;
-    W1T[t] = __float2bfloat16_rn(k < 72 ? real_of(W1, 4 * C, k, n) : 0.f);
-  } else if (t < S::W1Elems + S::W2Elems) {
-    const int u = t - S::W1Elems;
-    const int n = u / S::W2Stride, k = u % S::W2Stride;
-    W2T[u] = __float2bfloat16_rn(k < S::N1 ? real_of(W2p, 36, k, n) : 0.f);
+  if (t < S::N1 * kK1) {
+    const int n = t / kK1, k = t % kK1;
+    *reinterpret_cast<__nv_bfloat16*>(Wt + core_off(n, k, kK1 / 8)) =
+        __float2bfloat16_rn(k < 72 ? real_of(W1, 4 * C, k, n) : 0.f);
+  } else if (t < S::N1 * kK1 + kN2 * S::N1) {
+    const int u = t - S::N1 * kK1;
+    const int n = u / S::N1, k = u % S::N1;
+    *reinterpret_cast<__nv_bfloat16*>(Wt + S::W1Bytes + core_off(n, k, C)) =
+        __float2bfloat16_rn(n < 72 ? real_of(W2p, 36, k, n) : 0.f);
   }
 }
 
-// hardware named barriers (ids 1..4; 0 is __syncthreads) between the
+// hardware named barriers (ids 1..5; 0 is __syncthreads) between the
 // producer and the consumer warps.  bar.arrive signals without waiting,
 // bar.sync waits until `count` threads have arrived or synced; both order
 // the executing thread's earlier shared-memory accesses before the barrier.
@@ -89,6 +104,72 @@ __device__ __forceinline__ void named_arrive(int id, int count) {
   asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(count) : "memory");
 }
 constexpr int kBarFull = 1, kBarEmpty = 3;  // + buffer index
+constexpr int kBarConsumers = 5;            // the consumer warps alone
+
+// ---- tcgen05 helpers -------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading byte offset 128
+// (K-adjacent core matrices), stride byte offset `sbo` (8-row groups),
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) |
+         (1ull << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t umma_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on `mbar` once every MMA issued so far by this thread has completed
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+// bounded wait for the completion of phase `parity` of `mbar`; false after kWaitCap polls
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (unsigned n = 0; n < kWaitCap; ++n) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes -> visible to the tensor core
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 8 / 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
 
 struct FusedTile {
   int p, i0;
@@ -107,11 +188,13 @@ __device__ __forceinline__ FusedTile fused_tile(const Geom& g, int t, int bpp) {
 
 // stage 1 (producer thread tid in [0, 256)): the 9 transports of the
 // one-channel input for site i0 + (tid mod 128), directions 2 half .. 2 half + 1,
-// into the X1 tile (bf16, realified) in shared memory
+// into the X1 tile (bf16, realified, core-matrix layout) in shared memory.
+// Slot k of row r is the 16-byte core row at core_off(r, 8 k, 10); core
+// column 9 (k = 72..79) stays zero from the kernel's start.
 template <int D, bool EO>
 __device__ __forceinline__ void transport_tile(const char* __restrict__ links, size_t link_block,
                                                const float2* __restrict__ F, const Geom& g, const FusedTile& f,
-                                               __nv_bfloat16* sX, int tid) {
+                                               unsigned char* sX, int tid) {
   // EO (even-only input): the input vanishes on odd sites, so an even site
   // has only its own term (X1 slot 0) and an odd site only the transports of
   // its neighbours (slots 1..8); the even-only stencil then reads slot 0 of
@@ -119,42 +202,29 @@ __device__ __forceinline__ void transport_tile(const char* __restrict__ links, s
   const bool self_only = EO && f.p == 0, no_self = EO && f.p == 1;
   const int sl = tid & (kFusedSites - 1), half = tid / kFusedSites;
   const int i = f.i0 + sl;
-  unsigned* xr[D];
-#pragma unroll
-  for (int c = 0; c < D; ++c) xr[c] = reinterpret_cast<unsigned*>(sX + (sl * D + c) * kXStride);
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+  auto put = [&](int c, int k, const uint4& v) {
+    *reinterpret_cast<uint4*>(sX + core_off(sl * D + c, 8 * k, kK1 / 8)) = v;
+  };
+  auto own = [&](int c) {
+    const float4* q = reinterpret_cast<const float4*>(F + ((f.prow0 + i) * D + c) * 4);
+    const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+    return make_uint4(pack_bf2(v0.x, v0.y), pack_bf2(v0.z, v0.w), pack_bf2(v1.x, v1.y), pack_bf2(v1.z, v1.w));
+  };
   if (i < g.Vh && self_only) {
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      if (half == 0) {
-        const float4* q = reinterpret_cast<const float4*>(F + ((f.prow0 + i) * D + c) * 4);
-        const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
-        xr[c][0] = pack_bf2(v0.x, v0.y);
-        xr[c][1] = pack_bf2(v0.z, v0.w);
-        xr[c][2] = pack_bf2(v1.x, v1.y);
-        xr[c][3] = pack_bf2(v1.z, v1.w);
-      }
-      for (int e = 4 + half; e < 36; e += 2) xr[c][e] = 0u;
+      if (half == 0) put(c, 0, own(c));
+      for (int k = 1 + 4 * half; k < 5 + 4 * half; ++k) put(c, k, zero);
     }
   } else if (i < g.Vh) {
     int nf[4], nb_[4];
     eo_neighbours(g, i, f.p, nf, nb_);
     using L = LinkIO<F32, D, false>;
     const auto* lt = L::tile_ptr(links + (size_t)f.p * link_block, i);
-    if (half == 0 && no_self) {
+    if (half == 0) {
 #pragma unroll
-      for (int c = 0; c < D; ++c)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) xr[c][e] = 0u;
-    } else if (half == 0) {
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const float4* q = reinterpret_cast<const float4*>(F + ((f.prow0 + i) * D + c) * 4);
-        const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
-        xr[c][0] = pack_bf2(v0.x, v0.y);
-        xr[c][1] = pack_bf2(v0.z, v0.w);
-        xr[c][2] = pack_bf2(v1.x, v1.y);
-        xr[c][3] = pack_bf2(v1.z, v1.w);
-      }
+      for (int c = 0; c < D; ++c) put(c, 0, no_self ? zero : own(c));
     }
 #pragma unroll
     for (int m2 = 0; m2 < 2; ++m2) {
@@ -179,141 +249,25 @@ __device__ __forceinline__ void transport_tile(const char* __restrict__ links, s
         }
         const int k = 1 + 2 * mu + fb;
 #pragma unroll
-        for (int a = 0; a < D; ++a)
+        for (int a = 0; a < D; ++a) {
+          unsigned v[4];
 #pragma unroll
           for (int s = 0; s < 4; ++s) {
             cx<float> w = cmake(0.f, 0.f);
 #pragma unroll
             for (int bb = 0; bb < D; ++bb) cmac(w, fb ? Ub[a][bb] : Uf[a][bb], in[s][bb]);
-            xr[a][k * 4 + s] = pack_bf2(w.re, w.im);
+            v[s] = pack_bf2(w.re, w.im);
           }
+          put(a, k, make_uint4(v[0], v[1], v[2], v[3]));
+        }
       }
     }
   } else {
     // rows of sites past the end of the parity block: zero (their outputs are not stored)
 #pragma unroll
     for (int c = 0; c < D; ++c)
-      for (int e = half; e < 36; e += 2) xr[c][e] = 0u;
+      for (int k = half ? 5 : 0; k < (half ? 9 : 5); ++k) put(c, k, zero);
   }
-  if (half == 1) {
-#pragma unroll
-    for (int c = 0; c < D; ++c)
-#pragma unroll
-      for (int e = 36; e < 40; ++e) xr[c][e] = 0u;  // k padding 72..79
-  }
-}
-
-// stage 2, rows r0 .. r0 + 31 of the tile (a pair of 16-row tiles) through
-// both GEMMs, Z2 to global memory.  Each B fragment read from shared memory
-// feeds the MMAs of both row tiles.  Y1 = X1 W1 is formed in two column
-// chunks and Z2 = Y1 W2p in three groups of three 8-column tiles, bounding
-// the live accumulators.
-template <int D, int C, bool EO>
-__device__ __forceinline__ void mix_pair(const unsigned* X32, const unsigned* W132, const unsigned* W232,
-                                         unsigned* __restrict__ Z, long long zrows, const FusedTile& f,
-                                         int valid_rows, int r0, int lane) {
-  using S = FusedShape<C>;
-  constexpr int NM = 2;                // row tiles
-  constexpr int NCH = C >= 4 ? 2 : 1;  // column chunks of Y1, each an even number of 8-column tiles
-  constexpr int NC = C / NCH;
-  constexpr int GS = 3;                // Z2 8-column tiles per group
-  const bool self_only = EO && f.p == 0, no_self = EO && f.p == 1;
-  const int gq = lane >> 2, q = lane & 3;
-  constexpr int xs = kXStride / 2, w1s = S::W1Stride / 2, w2s = S::W2Stride / 2;
-  // Y1 accumulators -> A fragments of the second GEMM (two 8-column tiles per 16-deep k-step)
-  unsigned a2[NM][C / 2][4];
-#pragma unroll
-  for (int h = 0; h < NCH; ++h) {
-    float acc[NM][NC][4];
-#pragma unroll
-    for (int m = 0; m < NM; ++m)
-#pragma unroll
-      for (int n = 0; n < NC; ++n) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
-#pragma unroll
-    for (int kk = 0; kk < 5; ++kk) {
-      if (self_only && kk > 0) break;  // X1 beyond slot 0 is zero
-      unsigned a[NM][4];
-#pragma unroll
-      for (int m = 0; m < NM; ++m) {
-        const int rr = r0 + m * 16 + gq;
-        a[m][0] = X32[rr * xs + kk * 8 + q];
-        a[m][1] = X32[(rr + 8) * xs + kk * 8 + q];
-        a[m][2] = X32[rr * xs + kk * 8 + 4 + q];
-        a[m][3] = X32[(rr + 8) * xs + kk * 8 + 4 + q];
-      }
-#pragma unroll
-      for (int nn = 0; nn < NC; ++nn) {
-        const int n = h * NC + nn;
-        const unsigned b0 = W132[(n * 8 + gq) * w1s + kk * 8 + q];
-        const unsigned b1 = W132[(n * 8 + gq) * w1s + kk * 8 + 4 + q];
-#pragma unroll
-        for (int m = 0; m < NM; ++m) mma16816(acc[m][nn], a[m], b0, b1);
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < NM; ++m)
-#pragma unroll
-      for (int tt = 0; tt < NC / 2; ++tt) {
-        const int t = h * (NC / 2) + tt;
-        a2[m][t][0] = pack_bf2(acc[m][2 * tt][0], acc[m][2 * tt][1]);
-        a2[m][t][1] = pack_bf2(acc[m][2 * tt][2], acc[m][2 * tt][3]);
-        a2[m][t][2] = pack_bf2(acc[m][2 * tt + 1][0], acc[m][2 * tt + 1][1]);
-        a2[m][t][3] = pack_bf2(acc[m][2 * tt + 1][2], acc[m][2 * tt + 1][3]);
-      }
-  }
-  // Z2 row (prow0 + i0) * D + local row; the 8-column tile n is slot k = n, column pair q is spin q
-  const long long zr = (f.prow0 + f.i0) * D + r0;
-#pragma unroll
-  for (int gp = 0; gp < 9 / GS; ++gp) {
-    if (self_only && gp > 0) break;  // only slot 0 is read
-    float acc2[NM][GS][4];
-#pragma unroll
-    for (int m = 0; m < NM; ++m)
-#pragma unroll
-      for (int n = 0; n < GS; ++n) acc2[m][n][0] = acc2[m][n][1] = acc2[m][n][2] = acc2[m][n][3] = 0.f;
-#pragma unroll
-    for (int t = 0; t < C / 2; ++t)
-#pragma unroll
-      for (int nn = 0; nn < GS; ++nn) {
-        const int n = gp * GS + nn;
-        if ((self_only && n > 0) || (no_self && n == 0)) continue;  // Z2 slots nobody reads
-        const unsigned b0 = W232[(n * 8 + gq) * w2s + t * 8 + q];
-        const unsigned b1 = W232[(n * 8 + gq) * w2s + t * 8 + 4 + q];
-#pragma unroll
-        for (int m = 0; m < NM; ++m) mma16816(acc2[m][nn], a2[m][t], b0, b1);
-      }
-#pragma unroll
-    for (int m = 0; m < NM; ++m) {
-      const int rr = r0 + m * 16 + gq;
-#pragma unroll
-      for (int nn = 0; nn < GS; ++nn) {
-        const int n = gp * GS + nn;
-        if ((self_only && n > 0) || (no_self && n == 0)) continue;
-        if (rr < valid_rows) Z[(n * zrows + zr + m * 16 + gq) * 4 + q] = pack_bf2(acc2[m][nn][0], acc2[m][nn][1]);
-        if (rr + 8 < valid_rows)
-          Z[(n * zrows + zr + m * 16 + gq + 8) * 4 + q] = pack_bf2(acc2[m][nn][2], acc2[m][nn][3]);
-      }
-    }
-  }
-}
-
-// stage 2 (consumer warp w in [0, 8)) of the block's it-th tile: the tile's
-// 4 D pairs of 16-row tiles are dealt to the warps round-robin, continuing
-// from the previous tile (tile it starts at pair index 4 D it), so that with
-// 12 pairs per tile (D = 3) the warps that take two pairs alternate from one
-// tile to the next
-template <int D, int C, bool EO>
-__device__ __forceinline__ void mix_tile(const __nv_bfloat16* sX, const __nv_bfloat16* sW1,
-                                         const __nv_bfloat16* sW2, unsigned* __restrict__ Z, long long zrows,
-                                         const Geom& g, const FusedTile& f, int w, int lane, int it) {
-  static_assert(D == 2 || D == 3, "the fused kernel takes d = 2 or 3");
-  const unsigned* X32 = reinterpret_cast<const unsigned*>(sX);
-  const unsigned* W132 = reinterpret_cast<const unsigned*>(sW1);
-  const unsigned* W232 = reinterpret_cast<const unsigned*>(sW2);
-  const int valid_rows = (g.Vh - f.i0 < kFusedSites ? g.Vh - f.i0 : kFusedSites) * D;
-  const int first = (w + 8 - (4 * D * it) % 8) % 8;
-#pragma unroll 1
-  for (int pr = first; pr < 4 * D; pr += 8) mix_pair<D, C, EO>(X32, W132, W232, Z, zrows, f, valid_rows, pr * 32, lane);
 }
 
 // L2 prefetch of a contiguous range (16-byte aligned address and size); a
@@ -339,60 +293,151 @@ __device__ __forceinline__ void prefetch_tile(const char* links, size_t link_blo
   }
 }
 
+// stage 2 (consumer thread c in [0, 128) = TMEM lane c) for one tile:
+// GEMM1 for all D row blocks, then per row block the Y1 read-back, GEMM2 and
+// the Z2 read-back.  Returns false if an MMA-completion wait gave up (the
+// tile's Z2 rows are then stored as NaN).
+template <int D, int C, bool EO>
+__device__ __forceinline__ bool mix_tile(const unsigned char* sX, const unsigned char* sW1,
+                                         const unsigned char* sW2, unsigned char* sY1, uint64_t* mbar,
+                                         uint32_t tmem, uint4* __restrict__ Z, long long zrows, const Geom& g,
+                                         const FusedTile& f, int c, int it, bool more) {
+  using S = FusedShape<C>;
+  const bool self_only = EO && f.p == 0, no_self = EO && f.p == 1;
+  const int buf = it & 1;
+  bool ok = true;
+  if (c == 0) {
+    const uint32_t xa = smem_u32(sX), wa = smem_u32(sW1);
+    for (int rb = 0; rb < D; ++rb)
+      for (int kk = 0; kk < (self_only ? 1 : kK1 / 16); ++kk)  // self_only: X1 beyond slot 1 is zero
+        umma(tmem + rb * S::N1, umma_desc(xa + rb * (128 * kK1 * 2) + kk * 256, kK1 / 8 * 128),
+             umma_desc(wa + kk * 256, kK1 / 8 * 128), umma_idesc(S::N1), kk);
+    umma_commit(smem_u32(mbar));
+  }
+  ok &= mbar_wait(smem_u32(mbar), it & 1);
+  tc_fence_after();
+  if (more) named_arrive(kBarEmpty + buf, kFusedThreads);  // X1[buf] has been read
+  const uint32_t lane = tmem + ((uint32_t)((c >> 5) * 32) << 16);
+  const int valid_rows = (g.Vh - f.i0 < kFusedSites ? g.Vh - f.i0 : kFusedSites) * D;
+#pragma unroll 1
+  for (int rb = 0; rb < D; ++rb) {
+    // Y1 rows of this block: TMEM -> BF16 -> shared memory (GEMM2's A operand)
+#pragma unroll
+    for (int c0 = 0; c0 < S::N1; c0 += 16) {
+      float v[16];
+      tmem_ld16(lane + rb * S::N1 + c0, v);
+      *reinterpret_cast<uint4*>(sY1 + core_off(c, c0, C)) =
+          make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]), pack_bf2(v[6], v[7]));
+      *reinterpret_cast<uint4*>(sY1 + core_off(c, c0 + 8, C)) =
+          make_uint4(pack_bf2(v[8], v[9]), pack_bf2(v[10], v[11]), pack_bf2(v[12], v[13]), pack_bf2(v[14], v[15]));
+    }
+    fence_async_smem();
+    tc_fence_before();
+    named_sync(kBarConsumers, kConsumers);
+    tc_fence_after();
+    if (c == 0) {
+      const uint32_t ya = smem_u32(sY1), wb = smem_u32(sW2);
+      for (int kk = 0; kk < C / 2; ++kk)
+        umma(tmem + kD2Col, umma_desc(ya + kk * 256, C * 128), umma_desc(wb + kk * 256, C * 128), umma_idesc(kN2),
+             kk);
+      umma_commit(smem_u32(mbar + 1));
+    }
+    ok &= mbar_wait(smem_u32(mbar + 1), (it * D + rb) & 1);
+    tc_fence_after();
+    // Z2 rows of this block: TMEM -> BF16 -> global, one 16-byte group (4 spins) per slot
+    const int row = rb * 128 + c;
+    const long long zrow = (f.prow0 + f.i0) * D + row;
+#pragma unroll
+    for (int n = 0; n < 9; ++n) {
+      if ((self_only && n > 0) || (no_self && n == 0)) continue;  // Z2 slots nobody reads
+      float v[8];
+      tmem_ld8(lane + kD2Col + n * 8, v);
+      if (!ok)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __int_as_float(0x7fc00000);
+      if (row < valid_rows)
+        Z[n * zrows + zrow] =
+            make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]), pack_bf2(v[6], v[7]));
+    }
+    tc_fence_before();
+  }
+  return ok;
+}
+
 // Persistent and warp-specialised: one block per SM walks the tiles
 // t = blockIdx.x, + gridDim.x, ...  Warps 0-7 (producers) transport tile t
-// into X1 buffer (iteration & 1) while warps 8-15 (consumers) run the GEMMs
-// of the previous tile from the other buffer, so the gathers from HBM and
-// the tensor-core work overlap.  Buffer hand-over: producers arrive on
-// FULL[b] after filling b, consumers sync on it; consumers arrive on
-// EMPTY[b] after reading b when the block has a tile two iterations later,
-// and producers sync on EMPTY[b] before refilling b from their third
-// iteration on.  Both sides walk the same tile sequence, so every barrier
-// sees exactly kFusedThreads arrivals and kFusedThreads waiters.
+// into X1 buffer (iteration & 1) while warps 8-11 (consumers) run the MMAs
+// of the previous tile from the other buffer.  Buffer hand-over: producers
+// arrive on FULL[b] after filling b, consumers sync on it; consumers arrive
+// on EMPTY[b] once GEMM1 has read b, when the block has a tile two
+// iterations later, and producers sync on EMPTY[b] before refilling b from
+// their third iteration on.  Both sides walk the same tile sequence, so
+// every barrier sees exactly its expected arrivals and waiters.
 template <int D, int C, bool EO>
-__global__ void __launch_bounds__(2 * kFusedThreads, 1)
+__global__ void __launch_bounds__(kFusedThreads, 1)
     fused_kernel(const char* __restrict__ links, size_t link_block, const float2* __restrict__ F,
-                 const __nv_bfloat16* __restrict__ W1T, const __nv_bfloat16* __restrict__ W2T,
-                 unsigned* __restrict__ Z, long long zrows, Geom g, int bpp, int ntiles) {
+                 const unsigned char* __restrict__ Wt, uint4* __restrict__ Z, long long zrows, Geom g, int bpp,
+                 int ntiles) {
   using S = FusedShape<C>;
   constexpr int kRows = kFusedSites * D;
-  constexpr int kAll = 2 * kFusedThreads;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat16* sX0 = reinterpret_cast<__nv_bfloat16*>(smem);
-  __nv_bfloat16* sW1 = sX0 + 2 * kRows * kXStride;
-  __nv_bfloat16* sW2 = sW1 + S::W1Elems;
+  constexpr int kX1Bytes = kRows * kK1 * 2;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sX = smem;  // two X1 buffers
+  unsigned char* sW1 = smem + 2 * kX1Bytes;
+  unsigned char* sW2 = sW1 + S::W1Bytes;
+  unsigned char* sY1 = sW2 + S::W2Bytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sY1 + S::Y1Bytes);  // [0] GEMM1 done, [1] GEMM2 done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  const int tid = threadIdx.x;
 
-  // weights into shared memory once per block (16-byte copies; both sizes are multiples of 16 bytes)
-  {
-    const uint4* s1 = reinterpret_cast<const uint4*>(W1T);
-    uint4* d1 = reinterpret_cast<uint4*>(sW1);
-    for (int k = threadIdx.x; k < S::W1Elems / 8; k += kAll) d1[k] = s1[k];
-    const uint4* s2 = reinterpret_cast<const uint4*>(W2T);
-    uint4* d2 = reinterpret_cast<uint4*>(sW2);
-    for (int k = threadIdx.x; k < S::W2Elems / 8; k += kAll) d2[k] = s2[k];
+  // weights into shared memory once; zero core column 9 of both X1 buffers;
+  // barriers; tensor memory
+  for (int k = tid; k < (S::W1Bytes + S::W2Bytes) / 16; k += kFusedThreads)
+    reinterpret_cast<uint4*>(sW1)[k] = reinterpret_cast<const uint4*>(Wt)[k];
+  for (int r = tid; r < 2 * kRows; r += kFusedThreads)
+    *reinterpret_cast<uint4*>(sX + (r / kRows) * kX1Bytes + core_off(r % kRows, 72, kK1 / 8)) =
+        make_uint4(0u, 0u, 0u, 0u);
+  if (tid == kProducers) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)));
   }
+  if (tid >= kProducers && tid < kProducers + 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_async_smem();
+  tc_fence_before();
   __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
 
-  if (threadIdx.x < kFusedThreads) {
+  if (tid < kProducers) {
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       const int buf = it & 1;
-      if (t + (int)gridDim.x < ntiles) prefetch_tile<D>(links, link_block, F, g, t + gridDim.x, bpp, threadIdx.x);
-      if (it >= 2) named_sync(kBarEmpty + buf, kAll);
-      transport_tile<D, EO>(links, link_block, F, g, fused_tile(g, t, bpp), sX0 + buf * kRows * kXStride,
-                            threadIdx.x);
-      named_arrive(kBarFull + buf, kAll);
+      if (t + (int)gridDim.x < ntiles) prefetch_tile<D>(links, link_block, F, g, t + gridDim.x, bpp, tid);
+      if (it >= 2) named_sync(kBarEmpty + buf, kFusedThreads);
+      transport_tile<D, EO>(links, link_block, F, g, fused_tile(g, t, bpp), sX + buf * kX1Bytes, tid);
+      fence_async_smem();  // X1 writes -> visible to the tensor core
+      named_arrive(kBarFull + buf, kFusedThreads);
     }
   } else {
-    const int w = (threadIdx.x - kFusedThreads) >> 5, lane = threadIdx.x & 31;
+    const int c = tid - kProducers;
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       const int buf = it & 1;
-      named_sync(kBarFull + buf, kAll);
-      mix_tile<D, C, EO>(sX0 + buf * kRows * kXStride, sW1, sW2, Z, zrows, g, fused_tile(g, t, bpp), w, lane, it);
-      if (t + 2 * gridDim.x < ntiles) named_arrive(kBarEmpty + buf, kAll);
+      named_sync(kBarFull + buf, kFusedThreads);
+      tc_fence_after();
+      mix_tile<D, C, EO>(sX + buf * kX1Bytes, sW1, sW2, sY1, mbar, tmem, Z, zrows, g, fused_tile(g, t, bpp), c, it,
+                         t + 2 * (int)gridDim.x < ntiles);
     }
   }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid >= kProducers && tid < kProducers + 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 // out(x)[s] = sum_k (T_k Z_k)(x)[s] with Z in BF16, slot-major: Z[k][row] = 4 spins (16 bytes)
@@ -464,18 +509,18 @@ __global__ void __launch_bounds__(128) stencil_bf16_kernel(const char* __restric
 
 template <int D, int C>
 size_t fused_smem() {
-  return (size_t)(2 * kFusedSites * D * kXStride + FusedShape<C>::W1Elems + FusedShape<C>::W2Elems) * 2;
+  using S = FusedShape<C>;
+  return (size_t)2 * kFusedSites * D * kK1 * 2 + S::W1Bytes + S::W2Bytes + S::Y1Bytes + 32;
 }
 
 template <int D, int C>
-int fused_launch(const char* links, size_t link_block, const void* F, const void* W1, const void* W2p, void* W1T,
-                 void* W2T, void* Z, void* out, const Geom& g, int nb, bool even_only, cudaStream_t s) {
+int fused_launch(const char* links, size_t link_block, const void* F, const void* W1, const void* W2p, void* Wt,
+                 void* Z, void* out, const Geom& g, int nb, bool even_only, cudaStream_t s) {
   using S = FusedShape<C>;
-  const int n = S::W1Elems + S::W2Elems;
+  const int n = S::N1 * kK1 + kN2 * S::N1;
   fused_prep_kernel<C><<<(n + 255) / 256, 256, 0, s>>>(reinterpret_cast<const float2*>(W1),
                                                        reinterpret_cast<const float2*>(W2p),
-                                                       reinterpret_cast<__nv_bfloat16*>(W1T),
-                                                       reinterpret_cast<__nv_bfloat16*>(W2T));
+                                                       reinterpret_cast<unsigned char*>(Wt));
   const size_t smem = fused_smem<D, C>();
   auto kern = even_only ? fused_kernel<D, C, true> : fused_kernel<D, C, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -487,9 +532,9 @@ int fused_launch(const char* links, size_t link_block, const void* F, const void
   const int bpp = (g.Vh + kFusedSites - 1) / kFusedSites;
   const int ntiles = nb * 2 * bpp;
   const long long sites = (long long)nb * 2 * g.Vh, zrows = sites * D;
-  kern<<<ntiles < sms ? ntiles : sms, 2 * kFusedThreads, smem, s>>>(
-      links, link_block, reinterpret_cast<const float2*>(F), reinterpret_cast<const __nv_bfloat16*>(W1T),
-      reinterpret_cast<const __nv_bfloat16*>(W2T), reinterpret_cast<unsigned*>(Z), zrows, g, bpp, ntiles);
+  kern<<<ntiles < sms ? ntiles : sms, kFusedThreads, smem, s>>>(
+      links, link_block, reinterpret_cast<const float2*>(F), reinterpret_cast<const unsigned char*>(Wt),
+      reinterpret_cast<uint4*>(Z), zrows, g, bpp, ntiles);
   const long long outs = even_only ? sites / 2 : sites;
   stencil_bf16_kernel<D><<<(int)((outs + 127) / 128), 128, 0, s>>>(
       links, link_block, reinterpret_cast<const uint4*>(Z), zrows, reinterpret_cast<float2*>(out), g, nb,
@@ -498,13 +543,13 @@ int fused_launch(const char* links, size_t link_block, const void* F, const void
 }
 
 template <int D>
-int fused_dispatch_c(int C, const char* links, size_t lb, const void* F, const void* W1, const void* W2p, void* W1T,
-                     void* W2T, void* Z, void* out, const Geom& g, int nb, bool eo, cudaStream_t s) {
+int fused_dispatch_c(int C, const char* links, size_t lb, const void* F, const void* W1, const void* W2p, void* Wt,
+                     void* Z, void* out, const Geom& g, int nb, bool eo, cudaStream_t s) {
   switch (C) {
-    case 2: return fused_launch<D, 2>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, eo, s);
-    case 4: return fused_launch<D, 4>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, eo, s);
-    case 8: return fused_launch<D, 8>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, eo, s);
-    case 12: return fused_launch<D, 12>(links, lb, F, W1, W2p, W1T, W2T, Z, out, g, nb, eo, s);
+    case 2: return fused_launch<D, 2>(links, lb, F, W1, W2p, Wt, Z, out, g, nb, eo, s);
+    case 4: return fused_launch<D, 4>(links, lb, F, W1, W2p, Wt, Z, out, g, nb, eo, s);
+    case 8: return fused_launch<D, 8>(links, lb, F, W1, W2p, Wt, Z, out, g, nb, eo, s);
+    case 12: return fused_launch<D, 12>(links, lb, F, W1, W2p, Wt, Z, out, g, nb, eo, s);
     default: return BSM_EUNSUPPORTED;
   }
 }
@@ -514,17 +559,15 @@ int fused_dispatch_c(int C, const char* links, size_t lb, const void* F, const v
 // hidden-channel counts with a fused BF16 kernel
 bool ptc_fused_supported(int C) { return C == 2 || C == 4 || C == 8 || C == 12; }
 
-// bytes of the realified weights W1T + W2T (bf16) for C channels
-size_t ptc_fused_weight_bytes(int C) { return (size_t)(8 * C * kXStride + 72 * (8 * C + 8)) * 2; }
+// bytes of the realified weights in the core-matrix layout (bf16): GEMM1's B (8C x 80) and GEMM2's B (80 x 8C)
+size_t ptc_fused_weight_bytes(int C) { return (size_t)2 * (8 * C) * 80 * 2; }
 
-// Z: 9 x rows x 4 BF16 complex (4 bytes each), slot-major; W1T/W2T: ptc_fused_weight_bytes(C), 16-byte aligned
+// Z: 9 x rows x 4 BF16 complex (4 bytes each), slot-major; Wt: ptc_fused_weight_bytes(C), 16-byte aligned
 int ptc_fused_apply(const char* links, size_t link_block, int d, int C, const void* F, const void* W1,
                     const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, bool even_only,
                     cudaStream_t s) {
-  void* W1T = Wt;
-  void* W2T = reinterpret_cast<char*>(Wt) + (size_t)8 * C * kXStride * 2;
-  if (d == 2) return fused_dispatch_c<2>(C, links, link_block, F, W1, W2p, W1T, W2T, Z, out, g, nb, even_only, s);
-  if (d == 3) return fused_dispatch_c<3>(C, links, link_block, F, W1, W2p, W1T, W2T, Z, out, g, nb, even_only, s);
+  if (d == 2) return fused_dispatch_c<2>(C, links, link_block, F, W1, W2p, Wt, Z, out, g, nb, even_only, s);
+  if (d == 3) return fused_dispatch_c<3>(C, links, link_block, F, W1, W2p, Wt, Z, out, g, nb, even_only, s);
   return BSM_EUNSUPPORTED;
 }
 

@@ -5,7 +5,7 @@
 // A tile is 128 consecutive eo sites of one parity (128 d rows of the PTC
 // field).  Stage 1 (producer warps): two threads per site compute the 9
 // transports of the one-channel input (T_0, and U_mu(x) F(x+mu),
-// U_mu(x-mu)^+ F(x-mu) for two directions each) in FP32 and store them,
+// U_mu(x-mu)^+ F(x-mu)), four threads per site and one direction mu each, in FP32 and store them,
 // rounded to BF16 and realified (re, im interleaved), as the tile X1
 // (rows x 72 reals, padded to 80) in shared memory.  Stage 2 (consumer
 // warps), per block of 128 rows:
@@ -27,7 +27,7 @@
 // row, so the producers store it as one 16-byte word.
 //
 // The kernel is persistent (one block per SM, weights staged once) and
-// warp-specialised: 8 producer warps run stage 1 for the next tile while 4
+// warp-specialised: 16 producer warps run stage 1 for the next tile while 4
 // consumer warps run stage 2 on the previous one, with two X1 buffers
 // handed over through hardware named barriers, so that the gathers from HBM
 // overlap the tensor-core work.
@@ -40,7 +40,7 @@ namespace bsm {
 namespace {
 
 constexpr int kFusedSites = 128;                      // eo sites per tile
-constexpr int kProducers = 256;                       // 8 warps, two threads per site
+constexpr int kProducers = 512;                       // 16 warps, four threads per site (one direction each)
 constexpr int kConsumers = 128;                       // 4 warps, one per TMEM lane quarter
 constexpr int kFusedThreads = kProducers + kConsumers;
 constexpr int kK1 = 80;                               // GEMM1 depth: 72 transport reals + 8 zero
@@ -149,26 +149,34 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // generic-proxy shared-memory writes -> visible to the tensor core
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// 8 / 16 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
+// 8 / 16 consecutive FP32 columns of this thread's TMEM lane into r[0..];
+// the values are defined only after tmem_wait
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+// wait for this thread's outstanding tcgen05.ld; the empty statements after
+// it tie r[0..N) to the wait, so that no use of them is scheduled earlier
+template <int N>
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[N]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < N; ++j) asm volatile("" : "+r"(r[j]));
+}
+// 8 FP32 values (4 spins x re, im) -> one 16-byte group of 4 packed BF16 pairs
+__device__ __forceinline__ uint4 pack8(const uint32_t* r) {
+  return make_uint4(pack_bf2(__uint_as_float(r[0]), __uint_as_float(r[1])),
+                    pack_bf2(__uint_as_float(r[2]), __uint_as_float(r[3])),
+                    pack_bf2(__uint_as_float(r[4]), __uint_as_float(r[5])),
+                    pack_bf2(__uint_as_float(r[6]), __uint_as_float(r[7])));
 }
 
 struct FusedTile {
@@ -186,9 +194,11 @@ __device__ __forceinline__ FusedTile fused_tile(const Geom& g, int t, int bpp) {
   return f;
 }
 
-// stage 1 (producer thread tid in [0, 256)): the 9 transports of the
-// one-channel input for site i0 + (tid mod 128), directions 2 half .. 2 half + 1,
-// into the X1 tile (bf16, realified, core-matrix layout) in shared memory.
+// stage 1 (producer thread tid in [0, 512)): for site i0 + (tid mod 128) and
+// direction mu = tid / 128, the transports of the one-channel input from
+// x + mu and x - mu (slots 1 + 2 mu, 2 + 2 mu), and for mu = 0 also the
+// site's own value (slot 0), into the X1 tile (bf16, realified, core-matrix
+// layout) in shared memory.
 // Slot k of row r is the 16-byte core row at core_off(r, 8 k, 10); core
 // column 9 (k = 72..79) stays zero from the kernel's start.
 template <int D, bool EO>
@@ -200,7 +210,7 @@ __device__ __forceinline__ void transport_tile(const char* __restrict__ links, s
   // its neighbours (slots 1..8); the even-only stencil then reads slot 0 of
   // Z2 on even rows and slots 1..8 on odd rows, so only those are computed.
   const bool self_only = EO && f.p == 0, no_self = EO && f.p == 1;
-  const int sl = tid & (kFusedSites - 1), half = tid / kFusedSites;
+  const int sl = tid & (kFusedSites - 1), mu = tid / kFusedSites;
   const int i = f.i0 + sl;
   const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
   auto put = [&](int c, int k, const uint4& v) {
@@ -211,62 +221,56 @@ __device__ __forceinline__ void transport_tile(const char* __restrict__ links, s
     const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
     return make_uint4(pack_bf2(v0.x, v0.y), pack_bf2(v0.z, v0.w), pack_bf2(v1.x, v1.y), pack_bf2(v1.z, v1.w));
   };
-  if (i < g.Vh && self_only) {
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      if (half == 0) put(c, 0, own(c));
-      for (int k = 1 + 4 * half; k < 5 + 4 * half; ++k) put(c, k, zero);
-    }
-  } else if (i < g.Vh) {
+  if (i < g.Vh && !self_only) {
     int nf[4], nb_[4];
     eo_neighbours(g, i, f.p, nf, nb_);
     using L = LinkIO<F32, D, false>;
     const auto* lt = L::tile_ptr(links + (size_t)f.p * link_block, i);
-    if (half == 0) {
+    if (mu == 0) {
 #pragma unroll
       for (int c = 0; c < D; ++c) put(c, 0, no_self ? zero : own(c));
     }
+    cx<float> Uf[D][D], Ub[D][D];
 #pragma unroll
-    for (int m2 = 0; m2 < 2; ++m2) {
-      const int mu = 2 * half + m2;
-      cx<float> Uf[D][D], Ub[D][D];
+    for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int a = 0; a < D; ++a)
+      for (int bb = 0; bb < D; ++bb) L::load(lt, mu, a * D + bb, Uf[a][bb], Ub[a][bb]);
 #pragma unroll
-        for (int bb = 0; bb < D; ++bb) L::load(lt, mu, a * D + bb, Uf[a][bb], Ub[a][bb]);
+    for (int fb = 0; fb < 2; ++fb) {
+      const int n = fb ? nb_[mu] : nf[mu];
+      cx<float> in[4][D];
 #pragma unroll
-      for (int fb = 0; fb < 2; ++fb) {
-        const int n = fb ? nb_[mu] : nf[mu];
-        cx<float> in[4][D];
+      for (int c = 0; c < D; ++c) {
+        const float4* q = reinterpret_cast<const float4*>(F + ((f.orow0 + n) * D + c) * 4);
+        const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+        in[0][c] = cmake(v0.x, v0.y);
+        in[1][c] = cmake(v0.z, v0.w);
+        in[2][c] = cmake(v1.x, v1.y);
+        in[3][c] = cmake(v1.z, v1.w);
+      }
+      const int k = 1 + 2 * mu + fb;
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          const float4* q = reinterpret_cast<const float4*>(F + ((f.orow0 + n) * D + c) * 4);
-          const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
-          in[0][c] = cmake(v0.x, v0.y);
-          in[1][c] = cmake(v0.z, v0.w);
-          in[2][c] = cmake(v1.x, v1.y);
-          in[3][c] = cmake(v1.z, v1.w);
+      for (int a = 0; a < D; ++a) {
+        unsigned v[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          cx<float> w = cmake(0.f, 0.f);
+#pragma unroll
+          for (int bb = 0; bb < D; ++bb) cmac(w, fb ? Ub[a][bb] : Uf[a][bb], in[s][bb]);
+          v[s] = pack_bf2(w.re, w.im);
         }
-        const int k = 1 + 2 * mu + fb;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          unsigned v[4];
-#pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            cx<float> w = cmake(0.f, 0.f);
-#pragma unroll
-            for (int bb = 0; bb < D; ++bb) cmac(w, fb ? Ub[a][bb] : Uf[a][bb], in[s][bb]);
-            v[s] = pack_bf2(w.re, w.im);
-          }
-          put(a, k, make_uint4(v[0], v[1], v[2], v[3]));
-        }
+        put(a, k, make_uint4(v[0], v[1], v[2], v[3]));
       }
     }
   } else {
-    // rows of sites past the end of the parity block: zero (their outputs are not stored)
+    // an even site of an even-only input (its own term only), or a row past
+    // the end of the parity block (zero; its outputs are not stored)
 #pragma unroll
-    for (int c = 0; c < D; ++c)
-      for (int k = half ? 5 : 0; k < (half ? 9 : 5); ++k) put(c, k, zero);
+    for (int c = 0; c < D; ++c) {
+      if (mu == 0) put(c, 0, (i < g.Vh) ? own(c) : zero);
+      put(c, 1 + 2 * mu, zero);
+      put(c, 2 + 2 * mu, zero);
+    }
   }
 }
 
@@ -303,6 +307,7 @@ __device__ __forceinline__ bool mix_tile(const unsigned char* sX, const unsigned
                                          uint32_t tmem, uint4* __restrict__ Z, long long zrows, const Geom& g,
                                          const FusedTile& f, int c, int it, bool more) {
   using S = FusedShape<C>;
+  constexpr int kY1Batch = S::N1 % 48 == 0 ? 48 : S::N1 % 32 == 0 ? 32 : 16;  // Y1 columns per TMEM wait
   const bool self_only = EO && f.p == 0, no_self = EO && f.p == 1;
   const int buf = it & 1;
   bool ok = true;
@@ -321,15 +326,16 @@ __device__ __forceinline__ bool mix_tile(const unsigned char* sX, const unsigned
   const int valid_rows = (g.Vh - f.i0 < kFusedSites ? g.Vh - f.i0 : kFusedSites) * D;
 #pragma unroll 1
   for (int rb = 0; rb < D; ++rb) {
-    // Y1 rows of this block: TMEM -> BF16 -> shared memory (GEMM2's A operand)
+    // Y1 rows of this block: TMEM -> BF16 -> shared memory (GEMM2's A
+    // operand), in batches of up to 48 columns per wait
 #pragma unroll
-    for (int c0 = 0; c0 < S::N1; c0 += 16) {
-      float v[16];
-      tmem_ld16(lane + rb * S::N1 + c0, v);
-      *reinterpret_cast<uint4*>(sY1 + core_off(c, c0, C)) =
-          make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]), pack_bf2(v[6], v[7]));
-      *reinterpret_cast<uint4*>(sY1 + core_off(c, c0 + 8, C)) =
-          make_uint4(pack_bf2(v[8], v[9]), pack_bf2(v[10], v[11]), pack_bf2(v[12], v[13]), pack_bf2(v[14], v[15]));
+    for (int c0 = 0; c0 < S::N1; c0 += kY1Batch) {
+      uint32_t r[kY1Batch];
+#pragma unroll
+      for (int j = 0; j < kY1Batch; j += 16) tmem_ld16(lane + rb * S::N1 + c0 + j, &r[j]);
+      tmem_wait(r);
+#pragma unroll
+      for (int j = 0; j < kY1Batch; j += 8) *reinterpret_cast<uint4*>(sY1 + core_off(c, c0 + j, C)) = pack8(&r[j]);
     }
     fence_async_smem();
     tc_fence_before();
@@ -344,20 +350,40 @@ __device__ __forceinline__ bool mix_tile(const unsigned char* sX, const unsigned
     }
     ok &= mbar_wait(smem_u32(mbar + 1), (it * D + rb) & 1);
     tc_fence_after();
-    // Z2 rows of this block: TMEM -> BF16 -> global, one 16-byte group (4 spins) per slot
+    // Z2 rows of this block: TMEM -> BF16 -> global, one 16-byte group (4
+    // spins) per slot; slots 0..3 and 4..8 in one wait each
     const int row = rb * 128 + c;
     const long long zrow = (f.prow0 + f.i0) * D + row;
+    const bool store = row < valid_rows;
+    auto put = [&](int n, const uint32_t* r) {
+      uint4 v = pack8(r);
+      if (!ok) v = make_uint4(0x7fc07fc0u, 0x7fc07fc0u, 0x7fc07fc0u, 0x7fc07fc0u);  // BF16 NaN
+      if (store) Z[n * zrows + zrow] = v;
+    };
+    if (self_only) {  // only slot 0 is read
+      uint32_t r[8];
+      tmem_ld8(lane + kD2Col, r);
+      tmem_wait(r);
+      put(0, r);
+    } else {
+      {
+        uint32_t r[32];
+        tmem_ld16(lane + kD2Col, &r[0]);
+        tmem_ld16(lane + kD2Col + 16, &r[16]);
+        tmem_wait(r);
 #pragma unroll
-    for (int n = 0; n < 9; ++n) {
-      if ((self_only && n > 0) || (no_self && n == 0)) continue;  // Z2 slots nobody reads
-      float v[8];
-      tmem_ld8(lane + kD2Col + n * 8, v);
-      if (!ok)
+        for (int n = 0; n < 4; ++n)
+          if (!(no_self && n == 0)) put(n, &r[8 * n]);
+      }
+      {
+        uint32_t r[40];
+        tmem_ld16(lane + kD2Col + 32, &r[0]);
+        tmem_ld16(lane + kD2Col + 48, &r[16]);
+        tmem_ld8(lane + kD2Col + 64, &r[32]);
+        tmem_wait(r);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = __int_as_float(0x7fc00000);
-      if (row < valid_rows)
-        Z[n * zrows + zrow] =
-            make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]), pack_bf2(v[6], v[7]));
+        for (int n = 4; n < 9; ++n) put(n, &r[8 * (n - 4)]);
+      }
     }
     tc_fence_before();
   }

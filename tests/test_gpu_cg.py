@@ -163,3 +163,30 @@ def test_graph_replay_is_bit_identical(inner, outer):
         xs.append((x.clone(), stats.iters))
     assert xs[0][1] == xs[1][1]
     assert torch.equal(xs[0][0], xs[1][0])
+
+
+def test_full_size_32c64_mixed_cg_in_the_benchmark_configuration():
+    """The benchmark's CG workload at full size (32^3 x 64 SU(3), smooth
+    eps = 0.3 links, m0 = 0.05, antiperiodic time) in its fastest
+    configuration: FP32 inner iteration on two-row links, reliable updates in
+    DF64, delta = 0.01, convergence test every 16 steps.  The solution is
+    checked with the oracle's Dirac operator on the CPU (the normal-equation
+    tolerance 1e-10 leaves a full-system residual near 2e-10 here) and
+    against plain FP64 CG."""
+    dims, N, m0, phase = (64, 32, 32, 32), 3, 0.05, (np.pi, 0, 0, 0)
+    olat = orc.Lattice(dims, N, orc.FUND, m0, phase)
+    blat = bsm.lattice(dims, N, bsm.FUND, m0, phase)
+    U = fields.gauge_field(dims, N, "smooth", seed=3, eps=0.3)
+    b = fields.gaussian_spinor(dims, N, 4)
+    bd = gpu_spinor(blat, b, bsm.F64)
+    U12, Udf = gpu_links(blat, U, bsm.F32R12), gpu_links(blat, U, bsm.DF64)
+    stm, sm, xm = solve(blat, Udf, U12, bd, bsm.cg_opts(tol=1e-10, prec_inner=bsm.F32R12, prec_outer=bsm.DF64,
+                                                         delta=0.01, check_every=16))
+    assert stm == bsm.OK and sm.true_res_normal <= 1e-10 and sm.reliable_updates >= 1
+    x = to_canon(blat, xm, bsm.F64)
+    del U12, Udf, xm
+    U64 = gpu_links(blat, U, bsm.F64)
+    st64, s64, x64 = solve(blat, U64, None, bd, bsm.cg_opts(tol=1e-10))
+    assert st64 == bsm.OK and abs(sm.iters - s64.iters) <= max(5, s64.iters // 10), (sm.iters, s64.iters)
+    assert rel(x, to_canon(blat, x64, bsm.F64)) < 1e-7
+    assert rel(orc.dirac(olat, orc.links_to_rep(olat, U), x), b) < 1e-9

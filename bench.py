@@ -897,10 +897,12 @@ def run_cg(lat, links, b, max_iter):
     for name, inner, outer in cases:
         ws = torch.empty(bsm.bsm_workspace_bytes(lat, bsm.CALL_CG, inner), dtype=torch.uint8, device="cuda")
         x = torch.zeros_like(b)
+        torch.cuda.nvtx.range_push(f"cg_{name}")
         st, stats = bsm.bsm_cg_solve(lat, links[outer], links[inner if inner == bsm.F32R12 else bsm.F32], b, x,
                                      bsm.cg_opts(tol=1e-10, max_iter=max_iter, prec_inner=inner, prec_outer=outer,
                                                  delta=CG_DELTA, check_every=CG_CHECK_EVERY),
                                      ws, raise_on_error=False)
+        torch.cuda.nvtx.range_pop()
         res[name] = {"status": bsm.bsm_strerror(st), "seconds": round(stats.seconds, 4), "iters": stats.iters,
                      "reliable_updates": stats.reliable_updates, "true_res_normal": stats.true_res_normal,
                      "true_res_full": stats.true_res_full}

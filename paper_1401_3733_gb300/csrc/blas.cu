@@ -81,34 +81,47 @@ struct ElemOf<DF64> {
   using T = dfc;
 };
 
-__global__ void reduce_kernel(const double* __restrict__ partials, int n, double* out) {
-  double s = 0.0;
-  for (int k = threadIdx.x; k < n; k += kBlasThreads) s += partials[k];
-  __shared__ double buf[kBlasThreads];
-  buf[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = kBlasThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) buf[threadIdx.x] += buf[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = buf[0];
-}
+// Second stage of the deterministic reductions: the sum of n FP64 block
+// partials by one block of kTotalThreads, in a fixed order.  Thread t adds
+// partials t, t + 1024, ... with eight loads in flight per step (pairwise),
+// then each warp folds its 32 sums with shuffles and warp 0 folds the 32
+// warp sums.  The value is valid in thread 0.
+constexpr int kTotalThreads = 1024;
 
 __device__ double block_total(const double* __restrict__ partials, int n) {
   double s = 0.0;
-  for (int k = threadIdx.x; k < n; k += kBlasThreads) s += partials[k];
-  __shared__ double buf[kBlasThreads];
-  buf[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = kBlasThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) buf[threadIdx.x] += buf[threadIdx.x + o];
-    __syncthreads();
+  int k = threadIdx.x;
+  for (; k + 7 * kTotalThreads < n; k += 8 * kTotalThreads) {
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = partials[k + j * kTotalThreads];
+    s += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
   }
-  return buf[0];
+  for (; k < n; k += kTotalThreads) s += partials[k];
+  __shared__ double warp_sums[kTotalThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) warp_sums[warp] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = warp_sums[lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+__global__ void __launch_bounds__(kTotalThreads) reduce_kernel(const double* __restrict__ partials, int n,
+                                                               double* out) {
+  const double s = block_total(partials, n);
+  if (threadIdx.x == 0) *out = s;
 }
 
 // alpha = rr / <p, M p>
-__global__ void cg_alpha_kernel(CgState* st, const double* __restrict__ partials, int n) {
+__global__ void __launch_bounds__(kTotalThreads) cg_alpha_kernel(CgState* st, const double* __restrict__ partials,
+                                                                 int n) {
   if (st->done) return;
   const double pAp = block_total(partials, n);
   if (threadIdx.x != 0) return;
@@ -126,7 +139,8 @@ __global__ void cg_alpha_kernel(CgState* st, const double* __restrict__ partials
 }
 
 // beta = |r_new|^2 / |r|^2, convergence and reliable-update flags
-__global__ void cg_beta_kernel(CgState* st, const double* __restrict__ partials, int n) {
+__global__ void __launch_bounds__(kTotalThreads) cg_beta_kernel(CgState* st, const double* __restrict__ partials,
+                                                                int n) {
   if (st->done) return;
   const double rr_new = block_total(partials, n);
   if (threadIdx.x != 0) return;
@@ -272,13 +286,13 @@ __global__ void __launch_bounds__(kBlasThreads) axpy_ratio32_kernel(float4* __re
 }  // namespace
 
 void reduce_launch(const double* partials, int n, double* out, cudaStream_t s) {
-  reduce_kernel<<<1, kBlasThreads, 0, s>>>(partials, n, out);
+  reduce_kernel<<<1, kTotalThreads, 0, s>>>(partials, n, out);
 }
 void cg_alpha_launch(CgState* st, const double* partials, int n, cudaStream_t s) {
-  cg_alpha_kernel<<<1, kBlasThreads, 0, s>>>(st, partials, n);
+  cg_alpha_kernel<<<1, kTotalThreads, 0, s>>>(st, partials, n);
 }
 void cg_beta_launch(CgState* st, const double* partials, int n, cudaStream_t s) {
-  cg_beta_kernel<<<1, kBlasThreads, 0, s>>>(st, partials, n);
+  cg_beta_kernel<<<1, kTotalThreads, 0, s>>>(st, partials, n);
 }
 
 template <typename P>

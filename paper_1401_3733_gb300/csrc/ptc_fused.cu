@@ -3,11 +3,11 @@
 // tcgen05 tensor cores.
 //
 // A tile is 128 consecutive eo sites of one parity (128 d rows of the PTC
-// field).  Stage 1 (producer warps): two threads per site compute the 9
-// transports of the one-channel input (T_0, and U_mu(x) F(x+mu),
-// U_mu(x-mu)^+ F(x-mu)), four threads per site and one direction mu each, in FP32 and store them,
-// rounded to BF16 and realified (re, im interleaved), as the tile X1
-// (rows x 72 reals, padded to 80) in shared memory.  Stage 2 (consumer
+// field).  Stage 1 (producer warps): four threads per site, one direction
+// mu each, compute the 9 transports of the one-channel input (T_0, and
+// U_mu(x) F(x+mu), U_mu(x-mu)^+ F(x-mu)) in FP32 and store them, rounded to
+// BF16 and realified (re, im interleaved), as the tile X1 (rows x 72 reals,
+// padded to 80) in shared memory.  Stage 2 (consumer
 // warps), per block of 128 rows:
 //     Y1 = X1 W1  (80 -> 8C reals)   and   Z2 = Y1 W2p  (8C -> 72 reals)
 // as tcgen05.mma (BF16 x BF16 -> FP32, M = 128) issued by one thread, with

@@ -678,13 +678,14 @@ def run_large(steps, peak, peak_kind, max_iter):
     cfg = dict(PRECOND, eps=w["eps"], m0=w["m0"])
     W, train = train_ptc(cfg)
     o = bsm.fgcr_opts(tol=1e-10, max_iter=4000, restart=cfg["restart"], eo=True, precond=bsm.FGCR_PTC,
-                      channels=cfg["channels"], ptc_prec=bsm.BF16, prec_inner=bsm.F32, inner_tol=1e-3, check_every=4)
+                      channels=cfg["channels"], ptc_prec=bsm.BF16, prec_inner=bsm.F32, inner_tol=1e-3, check_every=4,
+                      prec_outer=bsm.DF64)
     ws = torch.empty(bsm.bsm_fgcr_workspace_bytes(lat, o), dtype=torch.uint8, device="cuda")
     x = torch.empty_like(b)
-    st, stats = bsm.bsm_fgcr_solve(lat, links[bsm.F64], links[bsm.F32], W[0], W[1], b, x, o, ws, raise_on_error=False)
+    st, stats = bsm.bsm_fgcr_solve(lat, links[bsm.DF64], links[bsm.F32], W[0], W[1], b, x, o, ws, raise_on_error=False)
     res["fgcr_eo_ptc_bf16_fp32cycles"] = {"status": bsm.bsm_strerror(st), "seconds": round(stats.seconds, 4),
                                           "iters": stats.iters, "cycles": stats.cycles, "true_res": stats.true_res,
-                                          "training": train}
+                                          "outer": "df64", "training": train}
     return res
 
 
@@ -773,7 +774,8 @@ def run_precond(peak, peak_kind, steps):
                        f"m0={cfg['m0']}, antiperiodic time; D x = b to 1e-10",
            "network": f"2 parallel-transport layers 1->{C}->1 channels", "training": train}
     ptc = dict(precond=bsm.FGCR_PTC, channels=C)
-    mixed = dict(prec_inner=bsm.F32, inner_tol=1e-3, check_every=4)
+    # FP32 cycles; the residual after each cycle in double-float (FP64-accurate)
+    mixed = dict(prec_inner=bsm.F32, inner_tol=1e-3, check_every=4, prec_outer=bsm.DF64)
     m = cfg["restart"]
     cases = {
         "fgcr_none_fp64": bsm.fgcr_opts(tol=1e-10, max_iter=4000, restart=m),
@@ -789,13 +791,14 @@ def run_precond(peak, peak_kind, steps):
         best = None
         for _ in range(2):
             x = torch.empty_like(b)
-            st, stats = bsm.bsm_fgcr_solve(lat, L[bsm.F64], L[bsm.F32], W[0], W[1], b, x, o, ws,
+            st, stats = bsm.bsm_fgcr_solve(lat, L[o.prec_outer], L[bsm.F32], W[0], W[1], b, x, o, ws,
                                            raise_on_error=False)
             if best is None or stats.seconds < best[1].seconds:
                 best = (st, stats)
         st, stats = best
         res[name] = {"status": bsm.bsm_strerror(st), "iters": stats.iters, "cycles": stats.cycles,
-                     "seconds": round(stats.seconds, 5), "true_res": stats.true_res}
+                     "seconds": round(stats.seconds, 5), "true_res": stats.true_res,
+                     "outer": "df64" if o.prec_outer == bsm.DF64 else "fp64"}
         del ws
     for name, inner, outer in (("cg_fp64", bsm.F64, bsm.F64), ("cg_mixed_df64", bsm.F32R12, bsm.DF64)):
         ws = torch.empty(bsm.bsm_workspace_bytes(lat, bsm.CALL_CG, inner), dtype=torch.uint8, device="cuda")

@@ -409,6 +409,12 @@ typedef struct {
                         even-even block of M, then x_o = (b_o + H_oe x_e / 2) / A */
   int32_t check_every;/* host convergence test every this many steps (0 -> 1);
                         up to check_every - 1 steps may run past convergence */
+  int32_t prec_outer;/* arithmetic of the FP64-accurate operator (right-hand
+                        side, the residual after each BSM_F32 cycle, the odd
+                        sites, the final true residual): BSM_F64 (0), or
+                        BSM_DF64 (double-float, about 48 significand bits), in
+                        which case U_rep64 is a BSM_DF64 link field; the
+                        vectors stay FP64 either way */
 } bsm_fgcr_opts;
 typedef struct {
   int32_t iters;     /* directions (preconditioner applications) in total */
@@ -418,7 +424,8 @@ typedef struct {
 } bsm_fgcr_stats;
 size_t bsm_fgcr_workspace_bytes(const bsm_lattice *lat, const bsm_fgcr_opts *opts);
 /* b, x: full FP64 device-layout spinors (x is overwritten, start x = 0);
- * U_rep64: FP64 links; U_rep32: FP32 links, used with BSM_FGCR_PTC or
+ * U_rep64: FP64 links (BSM_DF64 links with prec_outer BSM_DF64); U_rep32:
+ * FP32 links, used with BSM_FGCR_PTC or
  * prec_inner BSM_F32 (may be NULL otherwise); W1, W2: used with BSM_FGCR_PTC
  * only.  Synchronises `stream` every check_every steps.  Returns
  * BSM_ENOCONV (max_iter reached) or BSM_ENAN with x holding the last iterate. */

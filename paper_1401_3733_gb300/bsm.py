@@ -66,7 +66,7 @@ class FgcrOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("ptc_prec", ctypes.c_int32), ("channels", ctypes.c_int32),
                 ("prec_inner", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("eo", ctypes.c_int32),
-                ("check_every", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("prec_outer", ctypes.c_int32)]
 
 
 class FgcrStats(ctypes.Structure):
@@ -354,8 +354,9 @@ def bsm_ptc_adam_step(W, G, m, v, lr, step, stream=None):
 
 
 def fgcr_opts(tol=1e-10, max_iter=1000, restart=16, precond=FGCR_NONE, ptc_prec=F32, channels=1, prec_inner=F64,
-              inner_tol=0.0, eo=False, check_every=1) -> FgcrOpts:
-    return FgcrOpts(tol, max_iter, restart, precond, ptc_prec, channels, prec_inner, inner_tol, int(eo), check_every)
+              inner_tol=0.0, eo=False, check_every=1, prec_outer=F64) -> FgcrOpts:
+    return FgcrOpts(tol, max_iter, restart, precond, ptc_prec, channels, prec_inner, inner_tol, int(eo), check_every,
+                    prec_outer)
 
 
 def bsm_fgcr_workspace_bytes(lat, opts: FgcrOpts) -> int:

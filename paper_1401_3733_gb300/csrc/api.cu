@@ -487,6 +487,8 @@ int bsm_fgcr_solve(const bsm_lattice* lat, const void* U_rep64, const void* U_re
     return BSM_EINVAL;
   if (opts->precond != BSM_FGCR_NONE && opts->precond != BSM_FGCR_PTC) return BSM_EINVAL;
   if (opts->prec_inner != BSM_F64 && opts->prec_inner != BSM_F32) return BSM_EUNSUPPORTED;
+  if (opts->prec_outer != BSM_F64 && opts->prec_outer != BSM_DF64) return BSM_EUNSUPPORTED;
+  if (opts->prec_outer == BSM_DF64 && opts->prec_inner != BSM_F32) return BSM_EUNSUPPORTED;  // no FP64 links then
   if (!(opts->inner_tol >= 0.0) || opts->inner_tol >= 1.0 || opts->check_every < 0) return BSM_EINVAL;
   if (opts->prec_inner == BSM_F32 && !aligned(U_rep32)) return BSM_EINVAL;
   if (opts->precond == BSM_FGCR_PTC) {

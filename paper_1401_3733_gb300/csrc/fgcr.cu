@@ -24,7 +24,8 @@ namespace bsm {
 
 size_t ptc_workspace_bytes(const bsm_lattice& L, int C, int nb, bool train);
 int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, bool even_only, cudaStream_t s);
-int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, bool even_only, cudaStream_t s);
+int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, int even_only, cudaStream_t s);
+bool ptc_fused_supported(int C);
 int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* in,
               void* out, int nb, int prec, void* ws, cudaStream_t s, bool even_only = false);
 
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kBlasThreads) diff2_kernel(const double2* __re
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
 struct FgcrLayout {
-  size_t r, bhat, tmp, x32, r32, basis, scal, part, F_in, F_out, ptc, total;
+  size_t r, bhat, tmp, x32, r32, basis, scal, part, F_in, F_out, ptc, dfi, dfo, total;
 };
 
 // Vectors are full spinors, or even half spinors with opts.eo.  Mixed: the
@@ -255,6 +256,10 @@ FgcrLayout fgcr_layout(const bsm_lattice& L, const bsm_fgcr_opts& o) {
     y.F_out = p; p = al(p + f);
     y.ptc = p; p = al(p + ptc_workspace_bytes(L, o.channels, 1, false));
   }
+  if (o.prec_outer == BSM_DF64) {  // double-float copies of the outer operator's input and output
+    y.dfi = p; p = al(p + 2 * half_spinor_bytes(g.Vh, d, BSM_F64));
+    y.dfo = p; p = al(p + 2 * half_spinor_bytes(g.Vh, d, BSM_F64));
+  }
   y.total = p;
   return y;
 }
@@ -284,6 +289,18 @@ struct Fgcr {
     return rc < 0 ? rc : BSM_OK;
   }
 
+  // apply() with the outer context on FP64 vectors: with prec_outer
+  // BSM_DF64 through double-float copies (same element count and order)
+  int apply64(const OpCtx& c, const void* in, void* out) const {
+    if (o.prec_outer != BSM_DF64) return apply(c, in, out);
+    const size_t n = (o.eo ? 1 : 2) * c.half_bytes / 16;
+    f64_df64_launch(w + y.dfi, in, n, true, s);
+    const int rc = apply(c, w + y.dfi, w + y.dfo);
+    if (rc != BSM_OK) return rc;
+    f64_df64_launch(out, w + y.dfo, n, false, s);
+    return BSM_OK;
+  }
+
   // z = M(r) at the cycle precision T; with eo the network acts on the field
   // that is r on the even sites and zero on the odd ones, and z keeps the even part
   template <typename T>
@@ -292,13 +309,15 @@ struct Fgcr {
       return cudaMemcpyAsync(z, r, bytes, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? BSM_OK : BSM_ECUDA;
     int rc;
     const bool f32 = sizeof(T) == sizeof(float2);
-    rc = f32 ? ptc_pack32(L, reinterpret_cast<const float*>(r), w + y.F_in, false, o.eo != 0, s)
+    // the fused BF16 network never reads the odd rows of an even-only input
+    const bool odd_unread = o.eo && o.ptc_prec == BSM_BF16 && ptc_fused_supported(o.channels);
+    rc = f32 ? ptc_pack32(L, reinterpret_cast<const float*>(r), w + y.F_in, false, o.eo ? (odd_unread ? 2 : 1) : 0, s)
              : ptc_pack(L, reinterpret_cast<const double*>(r), w + y.F_in, false, o.eo != 0, s);
     if (rc != BSM_OK) return rc;
     if ((rc = ptc_apply(L, U32, W1, W2, o.channels, w + y.F_in, w + y.F_out, 1, o.ptc_prec, w + y.ptc, s,
                         o.eo != 0)) != BSM_OK)
       return rc;
-    return f32 ? ptc_pack32(L, reinterpret_cast<const float*>(z), w + y.F_out, true, o.eo != 0, s)
+    return f32 ? ptc_pack32(L, reinterpret_cast<const float*>(z), w + y.F_out, true, o.eo ? 1 : 0, s)
                : ptc_pack(L, reinterpret_cast<const double*>(z), w + y.F_out, true, o.eo != 0, s);
   }
 
@@ -355,7 +374,8 @@ int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const voi
   const auto t0 = std::chrono::steady_clock::now();
   const bool mixed = o.prec_inner == BSM_F32;
   const bool eo = o.eo != 0;
-  const OpCtx c64 = make_ctx(L, U64, BSM_F64, s);
+  const bool df = o.prec_outer == BSM_DF64;  // outer operator in double-float (only with FP32 cycles)
+  const OpCtx c64 = make_ctx(L, U64, df ? BSM_DF64 : BSM_F64, s);
   const OpCtx c32 = make_ctx(L, mixed ? U32 : U64, mixed ? BSM_F32 : BSM_F64, s);
   Fgcr F{L, o, U32, W1, W2, fgcr_layout(L, o), reinterpret_cast<char*>(ws), s};
   char* w = F.w;
@@ -385,7 +405,15 @@ int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const voi
   }
   const double2* rhs = reinterpret_cast<const double2*>(b);
   if (eo) {
-    if ((rc = op_hop(c64, 0, bc + h64, w + F.y.bhat, 0, bc, 1.0, 1.0 / (2.0 * c64.A), nullptr, nullptr)) < 0) return rc;
+    if (df) {  // bhat_e from double-float copies of b_e, b_o
+      f64_df64_launch(w + F.y.dfi, b, full64 / 16, true, s);
+      if ((rc = op_hop(c64, 0, w + F.y.dfi + h64, w + F.y.dfo, 0, w + F.y.dfi, 1.0, 1.0 / (2.0 * c64.A), nullptr,
+                       nullptr)) < 0)
+        return rc;
+      f64_df64_launch(w + F.y.bhat, w + F.y.dfo, h64 / 16, false, s);
+    } else if ((rc = op_hop(c64, 0, bc + h64, w + F.y.bhat, 0, bc, 1.0, 1.0 / (2.0 * c64.A), nullptr, nullptr)) < 0) {
+      return rc;
+    }
     rhs = reinterpret_cast<const double2*>(w + F.y.bhat);
   }
   cudaMemsetAsync(x, 0, full64, s);
@@ -420,7 +448,7 @@ int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const voi
       k = F.cycle<float2>(c32, x32, r32, v32, fmax(inner * inner * rr, stop2), o.max_iter - it, &rr32);
       if (k >= 0) {
         accumulate32_launch(BSM_F64, x, x32, nh, eo ? 1 : 2, s);
-        if ((rc = F.apply(c64, x, r)) != BSM_OK) return rc;
+        if ((rc = F.apply64(c64, x, r)) != BSM_OK) return rc;
         diff2_kernel<<<F.G, kBlasThreads, 0, s>>>(rhs, r, r, nv64, F.part);
         reduce_launch(F.part, F.G, F.scalar, s);
         if ((rc = F.host_read(F.scalar, &rr)) != BSM_OK) return rc;
@@ -436,10 +464,25 @@ int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const voi
     }
   }
   // eo: x_o = (b_o + H_oe x_e / 2) / A
-  if (eo && (rc = op_hop(c64, 1, xc, xc + h64, 0, bc + h64, 1.0 / c64.A, 1.0 / (2.0 * c64.A), nullptr, nullptr)) < 0)
+  if (eo && df) {  // from double-float copies of x_e and b_o
+    f64_df64_launch(w + F.y.dfi, xc, h64 / 16, true, s);
+    f64_df64_launch(w + F.y.dfi + h64, bc + h64, h64 / 16, true, s);
+    if ((rc = op_hop(c64, 1, w + F.y.dfi, w + F.y.dfo + h64, 0, w + F.y.dfi + h64, 1.0 / c64.A, 1.0 / (2.0 * c64.A),
+                     nullptr, nullptr)) < 0)
+      return rc;
+    f64_df64_launch(xc + h64, w + F.y.dfo + h64, h64 / 16, false, s);
+  } else if (eo && (rc = op_hop(c64, 1, xc, xc + h64, 0, bc + h64, 1.0 / c64.A, 1.0 / (2.0 * c64.A), nullptr,
+                                nullptr)) < 0) {
     return rc;
+  }
   // true residual |b - D x| / |b| (D x into r)
-  if ((rc = op_dirac(c64, x, r, 0, nullptr, nullptr)) < 0) return rc;
+  if (df) {
+    f64_df64_launch(w + F.y.dfi, x, full64 / 16, true, s);
+    if ((rc = op_dirac(c64, w + F.y.dfi, w + F.y.dfo, 0, nullptr, nullptr)) < 0) return rc;
+    f64_df64_launch(r, w + F.y.dfo, full64 / 16, false, s);
+  } else if ((rc = op_dirac(c64, x, r, 0, nullptr, nullptr)) < 0) {
+    return rc;
+  }
   diff2_kernel<<<F.G, kBlasThreads, 0, s>>>(reinterpret_cast<const double2*>(b), r, nullptr,
                                             full64 / sizeof(double2), F.part);
   reduce_launch(F.part, F.G, F.scalar, s);

@@ -214,7 +214,7 @@ __global__ void ptc_pack32_kernel(float4* __restrict__ psi, float2* __restrict__
   const int p = t / g.Vh, i = t - p * g.Vh;
   float2* f0 = F + ((size_t)p * g.Vh + i) * d * 4;
   if (even_only && p == 1) {
-    if (!unpack)
+    if (!unpack && even_only == 1)
       for (int e = 0; e < 4 * d; ++e) f0[e] = make_float2(0.f, 0.f);
     return;
   }
@@ -404,12 +404,15 @@ int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, bool
   return BSM_OK;
 }
 
-int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, bool even_only, cudaStream_t s) {
+// even_only: 0 both parities; 1 the even rows, the odd rows of the field
+// zeroed (pack) or left (unpack); 2 the even rows only (a consumer that never
+// reads the odd rows of the packed field)
+int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, int even_only, cudaStream_t s) {
   const Geom g = make_geom(L);
   const int d = rep_info(L.N, L.rep).d;
   ptc_pack32_kernel<<<(2 * g.Vh + 127) / 128, 128, 0, s>>>(reinterpret_cast<float4*>(const_cast<float*>(psi)),
                                                             reinterpret_cast<float2*>(F), g, d, unpack ? 1 : 0,
-                                                            even_only ? 1 : 0);
+                                                            even_only);
   return BSM_OK;
 }
 

@@ -281,13 +281,15 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 }
 
 // the links (one contiguous range of 32-site link tiles) and the own-parity
-// input rows of tile t into L2, by producer threads 0..4
-template <int D>
+// input rows of tile t into L2, by producer threads 0..4; an even tile of an
+// even-only input reads no links
+template <int D, bool EO>
 __device__ __forceinline__ void prefetch_tile(const char* links, size_t link_block, const float2* F, const Geom& g,
                                               int t, int bpp, int tid) {
   const FusedTile f = fused_tile(g, t, bpp);
   constexpr unsigned kLinkTileBytes = kLinkTile * 4 * D * D * 16;  // 4 D^2 float4 planes per 32 sites
   if (tid < kFusedSites / kLinkTile) {
+    if (EO && f.p == 0) return;
     const int lt = f.i0 / kLinkTile + tid;
     if (lt * kLinkTile < g.Vh)  // link tiles exist up to ceil(Vh / 32)
       prefetch_l2(links + (size_t)f.p * link_block + (size_t)lt * kLinkTileBytes, kLinkTileBytes);
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       const int buf = it & 1;
-      if (t + (int)gridDim.x < ntiles) prefetch_tile<D>(links, link_block, F, g, t + gridDim.x, bpp, tid);
+      if (t + (int)gridDim.x < ntiles) prefetch_tile<D, EO>(links, link_block, F, g, t + gridDim.x, bpp, tid);
       if (it >= 2) named_sync(kBarEmpty + buf, kFusedThreads);
       transport_tile<D, EO>(links, link_block, F, g, fused_tile(g, t, bpp), sX + buf * kX1Bytes, tid);
       fence_async_smem();  // X1 writes -> visible to the tensor core

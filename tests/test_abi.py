@@ -224,3 +224,11 @@ def test_ptc_and_fgcr_validation(bsm):
     # FP32 cycles keep their 2 x restart basis vectors in FP32: half the bytes
     assert 0 < bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(prec_inner=bsm.F32)) < \
         bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts())
+    # the double-float outer operator: only with FP32 cycles (no FP64 links are passed then), and
+    # two full-lattice double-float copies in the workspace
+    assert solve(bsm.fgcr_opts(prec_outer=bsm.DF64)) == bsm.EUNSUPPORTED
+    assert solve(bsm.fgcr_opts(prec_inner=bsm.F32, prec_outer=bsm.F32)) == bsm.EUNSUPPORTED
+    assert solve(bsm.fgcr_opts(prec_inner=bsm.F32, prec_outer=7)) == bsm.EUNSUPPORTED
+    assert bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(prec_inner=bsm.F32, prec_outer=bsm.DF64)) == \
+        bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(prec_inner=bsm.F32)) + \
+        2 * bsm.bsm_field_bytes(good, bsm.FIELD_SPINOR, bsm.F64)

@@ -341,6 +341,33 @@ def test_mixed_precision_fgcr_reaches_fp64_accuracy(precond):
     assert s1.iters <= 2 * s0.iters + 16
 
 
+@pytest.mark.parametrize("eo", [True, False], ids=["eo", "full"])
+@pytest.mark.parametrize("precond", ["none", "ptc-bf16"])
+def test_double_float_outer_operator(precond, eo):
+    """FP32 cycles with the FP64-accurate operator (right-hand side, residual
+    after each cycle, odd sites, true residual) in double-float on DF64
+    links: the same steps and solution as with the FP64 operator, and a full
+    residual <= 1e-10 checked with the oracle's D."""
+    dims, N = (4, 4, 4, 8), 3
+    olat, blat = lats(dims, N, bsm.FUND, (np.pi, 0, 0, 0), m0=0.05)
+    U = fields.gauge_field(dims, N, "smooth", seed=24, eps=0.4)
+    U64, U32, Udf = gpu_links(blat, U, bsm.F64), gpu_links(blat, U, bsm.F32), gpu_links(blat, U, bsm.DF64)
+    b = fields.gaussian_spinor(dims, N, 25)
+    bd = gpu_spinor(blat, b, bsm.F64)
+    kw = dict(tol=1e-10, restart=16, prec_inner=bsm.F32, inner_tol=1e-3, eo=eo, check_every=2)
+    W = (None, None)
+    if precond != "none":
+        kw.update(precond=bsm.FGCR_PTC, ptc_prec=bsm.BF16, channels=2)
+        W = tuple(dev_c64(w) for w in neumann_weights(olat.m0))
+    st0, s0, x0 = fgcr(blat, U64, U32, bd, bsm.fgcr_opts(**kw), W)
+    st1, s1, x1 = fgcr(blat, Udf, U32, bd, bsm.fgcr_opts(prec_outer=bsm.DF64, **kw), W)
+    assert st0 == bsm.OK and st1 == bsm.OK, (st0, st1)
+    assert abs(s1.iters - s0.iters) <= 2 and s1.true_res <= 1e-10
+    x = to_canon(blat, x1, bsm.F64)
+    assert rel(orc.dirac(olat, orc.links_to_rep(olat, U), x), b) <= 1e-10
+    assert rel(x, to_canon(blat, x0, bsm.F64)) < 1e-8
+
+
 @pytest.mark.parametrize("prec_inner", [bsm.F64, bsm.F32], ids=["fp64", "fp32cycles"])
 @pytest.mark.parametrize("precond", ["none", "ptc-f32", "ptc-bf16"])
 def test_even_odd_fgcr_solves_the_full_system(precond, prec_inner):

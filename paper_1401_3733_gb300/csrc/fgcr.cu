@@ -38,20 +38,28 @@ template <typename T> struct Arith;
 template <> struct Arith<double2> { using R = double; };
 template <> struct Arith<float2> { using R = float; };
 
+// a coefficient (FP64) in the vectors' precision: converted once, outside
+// the element loops (a conversion from FP64 issues at GB300's FP64 rate)
 template <typename T>
-__device__ __forceinline__ T csub_mul(T x, double2 c, T a) {  // x - c a
+__device__ __forceinline__ T coef_as(double2 c) {
   using R = typename Arith<T>::R;
-  const R cx = (R)c.x, cy = (R)c.y;
-  x.x -= cx * a.x - cy * a.y;
-  x.y -= cx * a.y + cy * a.x;
+  T t;
+  t.x = (R)c.x;
+  t.y = (R)c.y;
+  return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T csub_mul(T x, T c, T a) {  // x - c a
+  x.x -= c.x * a.x - c.y * a.y;
+  x.y -= c.x * a.y + c.y * a.x;
   return x;
 }
+
 template <typename T>
-__device__ __forceinline__ T cadd_mul(T x, double2 c, T a) {  // x + c a
-  using R = typename Arith<T>::R;
-  const R cx = (R)c.x, cy = (R)c.y;
-  x.x += cx * a.x - cy * a.y;
-  x.y += cx * a.y + cy * a.x;
+__device__ __forceinline__ T cadd_mul(T x, T c, T a) {  // x + c a
+  x.x += c.x * a.x - c.y * a.y;
+  x.y += c.x * a.y + c.y * a.x;
   return x;
 }
 
@@ -139,25 +147,59 @@ __global__ void gs_coef_kernel(const double* __restrict__ partials, int nblk, in
   }
 }
 
-// w -= sum_j coef_j w_j ; z -= sum_j coef_j z_j  (j < k <= 64; w_j, z_j at wb, zb + j * stride)
+// w -= sum_j coef_j w_j  (j < k <= 64; w_j at wb + j * stride)
 template <typename T>
-__global__ void __launch_bounds__(kBlasThreads) gs_update_kernel(T* __restrict__ w, T* __restrict__ z,
-                                                                 const T* __restrict__ wb, const T* __restrict__ zb,
+__global__ void __launch_bounds__(kBlasThreads) gs_update_kernel(T* __restrict__ w, const T* __restrict__ wb,
                                                                  size_t stride, int k, size_t n,
                                                                  const double2* __restrict__ coef) {
-  __shared__ double2 c[64];
-  for (int j = threadIdx.x; j < k; j += kBlasThreads) c[j] = coef[j];
+  __shared__ T c[64];
+  for (int j = threadIdx.x; j < k; j += kBlasThreads) c[j] = coef_as<T>(coef[j]);
   __syncthreads();
   for (size_t e = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kBlasThreads) {
-    T x = w[e], y = z[e];
+    T x = w[e];
 #pragma unroll 4
-    for (int j = 0; j < k; ++j) {
-      x = csub_mul(x, c[j], wb[(size_t)j * stride + e]);
-      y = csub_mul(y, c[j], zb[(size_t)j * stride + e]);
-    }
+    for (int j = 0; j < k; ++j) x = csub_mul(x, c[j], wb[(size_t)j * stride + e]);
     w[e] = x;
-    z[e] = y;
   }
+}
+
+// x += sum_j gamma_j z_j  (j < K <= 64; z_j at zb + j * stride)
+template <typename T>
+__global__ void __launch_bounds__(kBlasThreads) x_update_kernel(T* __restrict__ x, const T* __restrict__ zb,
+                                                                size_t stride, int K, size_t n,
+                                                                const double2* __restrict__ gamma) {
+  __shared__ T c[64];
+  for (int j = threadIdx.x; j < K; j += kBlasThreads) c[j] = coef_as<T>(gamma[j]);
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kBlasThreads) {
+    T v = x[e];
+#pragma unroll 4
+    for (int j = 0; j < K; ++j) v = cadd_mul(v, c[j], zb[(size_t)j * stride + e]);
+    x[e] = v;
+  }
+}
+
+// The cycle's solution update in the stored (not orthogonalised) directions:
+// with zhat_k = z_k - sum_{j<k} beta_jk zhat_j (A zhat_k = the orthogonalised
+// w_k), sum_k alpha_k zhat_k = sum_j gamma_j z_j, gamma by back substitution
+// (k from K-1 down: gamma_k = a_k, then a_j -= gamma_k beta_jk for j < k;
+// a = alpha at the start).  beta_jk at bmat[k * ld + j].  One block of 64.
+__global__ void __launch_bounds__(64) backsolve_kernel(const double2* __restrict__ alpha,
+                                                       const double2* __restrict__ bmat, int ld, int K,
+                                                       double2* __restrict__ gamma) {
+  __shared__ double2 a[64];
+  const int j = threadIdx.x;
+  if (j < K) a[j] = alpha[j];
+  __syncthreads();
+  for (int k = K - 1; k >= 1; --k) {
+    const double2 g = a[k];
+    if (j < k) {
+      const double2 b = bmat[(size_t)k * ld + j];
+      a[j] = make_double2(a[j].x - (g.x * b.x - g.y * b.y), a[j].y - (g.x * b.y + g.y * b.x));
+    }
+    __syncthreads();
+  }
+  if (j < K) gamma[j] = a[j];
 }
 
 // partials of |w|^2 [blk], Re<w, r> [G + blk], Im<w, r> [2G + blk]
@@ -187,16 +229,14 @@ __global__ void alpha_kernel(const double* __restrict__ partials, int nblk, doub
   }
 }
 
-// x += alpha z ; r -= alpha w ; partials of |r|^2
+// r -= alpha w ; partials of |r|^2
 template <typename T>
-__global__ void __launch_bounds__(kBlasThreads) xr_kernel(T* __restrict__ x, T* __restrict__ r,
-                                                          const T* __restrict__ z, const T* __restrict__ w, size_t n,
-                                                          const double2* __restrict__ alpha, double* partials) {
+__global__ void __launch_bounds__(kBlasThreads) r_update_kernel(T* __restrict__ r, const T* __restrict__ w, size_t n,
+                                                                const double2* __restrict__ alpha, double* partials) {
   using R = typename Arith<T>::R;
-  const double2 a = *alpha;
+  const T a = coef_as<T>(*alpha);
   R rr = 0;
   for (size_t k = blockIdx.x * (size_t)kBlasThreads + threadIdx.x; k < n; k += (size_t)gridDim.x * kBlasThreads) {
-    x[k] = cadd_mul(x[k], a, z[k]);
     const T q = csub_mul(r[k], a, w[k]);
     r[k] = q;
     rr += q.x * q.x + q.y * q.y;
@@ -248,7 +288,7 @@ FgcrLayout fgcr_layout(const bsm_lattice& L, const bsm_fgcr_opts& o) {
     y.r32 = p; p = al(p + vc);
   }
   y.basis = p; p = al(p + vc * 2 * (size_t)o.restart);  // z_0 .. z_{m-1}, w_0 .. w_{m-1}
-  y.scal = p; p = al(p + sizeof(double) * (3 * (size_t)o.restart + 8));
+  y.scal = p; p = al(p + sizeof(double) * ((size_t)o.restart + 2 * (size_t)o.restart * (o.restart + 2) + 8));
   y.part = p; p = al(p + sizeof(double) * 2 * kDotChunk * kBlasMaxBlocks);
   if (o.precond == BSM_FGCR_PTC) {
     const size_t f = (size_t)2 * g.Vh * d * 4 * sizeof(float2);
@@ -272,8 +312,9 @@ struct Fgcr {
   char* w;
   cudaStream_t s;
   double* norm2;   // [restart]
-  double2* coef;   // [restart]
-  double2* alpha;
+  double2* bmat;   // [restart][restart]: column k holds beta_jk, j < k
+  double2* alpha;  // [restart]
+  double2* gamma;  // [restart]
   double* scalar;
   double* part;
   int G = 0;
@@ -323,11 +364,16 @@ struct Fgcr {
 
   // One restart cycle of FGCR on A x = r at precision T (x, r updated in
   // place): up to `restart` directions, at most `budget` iterations; stops
-  // early once |r|^2 <= stop2.  Each new direction is orthogonalised against
+  // early once |r|^2 <= stop2.  Each new w = A z is orthogonalised against
   // the cycle's earlier ones in one pass (classical Gram-Schmidt: the dots
-  // <w_j, w> of all j at once, then w -= sum_j beta_j w_j, z likewise); with
-  // the w_j mutually orthogonal this equals modified Gram-Schmidt up to
-  // rounding.  Returns the iterations, or < 0 on error; *rr = the last |r|^2.
+  // <w_j, w> of all j at once, then w -= sum_j beta_j w_j; with the w_j
+  // mutually orthogonal this equals modified Gram-Schmidt up to rounding),
+  // and r -= alpha w.  The preconditioned directions z are stored as they
+  // come; the solution update that the orthogonalised directions imply is
+  // formed once at the cycle's end from the stored beta and alpha (the
+  // deferred update of GCR: half the basis traffic per step, and x is not
+  // touched inside the cycle).  Returns the iterations, or < 0 on error;
+  // *rr = the last |r|^2.
   template <typename T>
   int cycle(const OpCtx& c, T* x, T* r, size_t bytes, double stop2, int budget, double* rr) const {
     const size_t n = bytes / sizeof(T), stride = bytes / sizeof(T);
@@ -335,30 +381,38 @@ struct Fgcr {
     T* wb = zb + stride * o.restart;
     const int check = o.check_every > 0 ? o.check_every : 1;
     int it = 0, rc;
+    int K = 0;  // directions of this cycle
     for (int k = 0; k < o.restart && it < budget; ++k) {
       T* z = zb + stride * k;
       T* wv = wb + stride * k;
       if ((rc = precondition<T>(r, z, bytes)) != BSM_OK) return rc;
       if ((rc = apply(c, z, wv)) != BSM_OK) return rc;
+      double2* beta = bmat + (size_t)k * o.restart;
       if (k > 0) {
         for (int j0 = 0; j0 < k; j0 += kDotChunk) {
           const int cnt = k - j0 < kDotChunk ? k - j0 : kDotChunk;
           multi_dot_launch<T>(G, wb, stride, j0, cnt, wv, n, part, s);
-          gs_coef_kernel<<<cnt, kBlasThreads, 0, s>>>(part, G, j0, norm2, coef);
+          gs_coef_kernel<<<cnt, kBlasThreads, 0, s>>>(part, G, j0, norm2, beta);
         }
-        gs_update_kernel<T><<<G, kBlasThreads, 0, s>>>(wv, z, wb, zb, stride, k, n, coef);
+        gs_update_kernel<T><<<G, kBlasThreads, 0, s>>>(wv, wb, stride, k, n, beta);
       }
       wr_kernel<T><<<G, kBlasThreads, 0, s>>>(wv, r, n, part);
-      alpha_kernel<<<1, kBlasThreads, 0, s>>>(part, G, norm2 + k, alpha);
-      xr_kernel<T><<<G, kBlasThreads, 0, s>>>(x, r, z, wv, n, alpha, part);
+      alpha_kernel<<<1, kBlasThreads, 0, s>>>(part, G, norm2 + k, alpha + k);
+      r_update_kernel<T><<<G, kBlasThreads, 0, s>>>(r, wv, n, alpha + k, part);
       reduce_launch(part, G, scalar, s);
       ++it;
+      K = k + 1;
       // the host reads |r|^2 every check_every steps (and at the cycle's end):
       // fewer round trips, at most check_every - 1 steps past convergence
       if (it % check == 0 || k == o.restart - 1 || it == budget) {
         if ((rc = host_read(scalar, rr)) != BSM_OK) return rc;
         if (!isfinite(*rr) || *rr <= stop2) break;
       }
+    }
+    // x += sum_k alpha_k zhat_k, in the stored directions
+    if (K > 0) {
+      backsolve_kernel<<<1, 64, 0, s>>>(alpha, bmat, o.restart, K, gamma);
+      x_update_kernel<T><<<G, kBlasThreads, 0, s>>>(x, zb, stride, K, n, gamma);
     }
     return it;
   }
@@ -380,9 +434,10 @@ int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const voi
   Fgcr F{L, o, U32, W1, W2, fgcr_layout(L, o), reinterpret_cast<char*>(ws), s};
   char* w = F.w;
   F.norm2 = reinterpret_cast<double*>(w + F.y.scal);
-  F.coef = reinterpret_cast<double2*>(F.norm2 + o.restart);
-  F.alpha = F.coef + o.restart;
-  F.scalar = reinterpret_cast<double*>(F.alpha + 1);
+  F.bmat = reinterpret_cast<double2*>(F.norm2 + o.restart);
+  F.alpha = F.bmat + (size_t)o.restart * o.restart;
+  F.gamma = F.alpha + o.restart;
+  F.scalar = reinterpret_cast<double*>(F.gamma + o.restart);
   F.part = reinterpret_cast<double*>(w + F.y.part);
   const size_t h64 = c64.half_bytes, full64 = 2 * h64;
   const size_t v64 = eo ? h64 : full64, nv64 = v64 / sizeof(double2);

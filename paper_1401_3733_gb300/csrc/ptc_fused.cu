@@ -393,8 +393,8 @@ __device__ __forceinline__ bool mix_tile(const unsigned char* sX, const unsigned
 }
 
 // Persistent and warp-specialised: one block per SM walks the tiles
-// t = blockIdx.x, + gridDim.x, ...  Warps 0-7 (producers) transport tile t
-// into X1 buffer (iteration & 1) while warps 8-11 (consumers) run the MMAs
+// t = blockIdx.x, + gridDim.x, ...  Warps 0-15 (producers) transport tile t
+// into X1 buffer (iteration & 1) while warps 16-19 (consumers) run the MMAs
 // of the previous tile from the other buffer.  Buffer hand-over: producers
 // arrive on FULL[b] after filling b, consumers sync on it; consumers arrive
 // on EMPTY[b] once GEMM1 has read b, when the block has a tile two

@@ -433,11 +433,12 @@ int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const voi
   const OpCtx c32 = make_ctx(L, mixed ? U32 : U64, mixed ? BSM_F32 : BSM_F64, s);
   Fgcr F{L, o, U32, W1, W2, fgcr_layout(L, o), reinterpret_cast<char*>(ws), s};
   char* w = F.w;
-  F.norm2 = reinterpret_cast<double*>(w + F.y.scal);
-  F.bmat = reinterpret_cast<double2*>(F.norm2 + o.restart);
+  // the 16-byte arrays first, so that each stays 16-byte aligned for any restart
+  F.bmat = reinterpret_cast<double2*>(w + F.y.scal);
   F.alpha = F.bmat + (size_t)o.restart * o.restart;
   F.gamma = F.alpha + o.restart;
-  F.scalar = reinterpret_cast<double*>(F.gamma + o.restart);
+  F.norm2 = reinterpret_cast<double*>(F.gamma + o.restart);
+  F.scalar = F.norm2 + o.restart;
   F.part = reinterpret_cast<double*>(w + F.y.part);
   const size_t h64 = c64.half_bytes, full64 = 2 * h64;
   const size_t v64 = eo ? h64 : full64, nv64 = v64 / sizeof(double2);

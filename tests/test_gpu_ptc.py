@@ -112,6 +112,23 @@ def test_ptc_net_matches_oracle_layers(case, prec, tol, C):
         assert rel(got[b], want) < tol
 
 
+@pytest.mark.parametrize("C", [2, 4, 8], ids=["C2", "C4", "C8"])
+def test_ptc_net_fused_kernel_other_channel_counts(C):
+    """The fused BF16 kernel at its other channel counts (GEMM widths 8C =
+    16, 32, 64 and GEMM2 depths 8C), against the oracle's two layers."""
+    dims, N, rep, phase = CASES[0]
+    olat, blat = lats(dims, N, rep, phase)
+    U = fields.gauge_field(dims, N, "haar", seed=11)
+    R = orc.links_to_rep(olat, U)
+    U32 = gpu_links(blat, U, bsm.F32)
+    rng = np.random.default_rng(50 + C)
+    W1, W2 = rand_c(rng, (36, 4 * C), 0.3), rand_c(rng, (36 * C, 4), 0.1)
+    psis = [fields.gaussian_spinor(dims, olat.d, 60 + b) for b in range(2)]
+    got = gpu_net(blat, U32, W1, W2, C, psis, bsm.BF16)
+    for b in range(2):
+        assert rel(got[b], oracle_net(olat, R, psis[b], W1, W2, C)) < 2e-2
+
+
 def test_ptc_net_fused_kernel_walks_several_tiles_per_block():
     """12 x 10^3 SU(3), 4 samples: parity blocks of 6000 sites give 47 tiles
     of 128 sites (the last one ragged, 112 sites), 376 tiles in all, so each

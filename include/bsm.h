@@ -259,19 +259,28 @@ int bsm_dirac_eo(const bsm_lattice *lat, const void *U_rep, const void *in_e,
  * allocator, a plugin or sandbox that exposes no allocation call, or a loop
  * that cannot afford the device-wide synchronisation that cudaMalloc and
  * cudaFree imply.  It takes the arguments of bsm_dirac_eo minus the
- * workspace and computes the same result with the same kernels.
+ * workspace, accepts the same lattices and precisions (BSM_F64, BSM_F32,
+ * BSM_DF64, BSM_BF16, BSM_F32R12 for SU(3) fundamental) and computes the
+ * same result with the same kernels.
  * Its two scratch half spinors live in one BSM_NOALLOC_SCRATCH_BYTES array
- * that the library declares as device memory; a GPU on which this entry
- * point has run keeps that array until the process exits.  A lattice whose
+ * that the library declares as device memory.  The CUDA runtime reserves
+ * that array on a device when it loads the library's module there: under
+ * the default lazy module loading (CUDA_MODULE_LOADING=LAZY) that is the
+ * first call of this entry point on the device, under
+ * CUDA_MODULE_LOADING=EAGER it is the creation of every context that loads
+ * the library, whether or not this entry point ever runs.  Either way the
+ * device keeps the array until the process exits.  A caller whose pool
+ * allocator takes all free device memory must therefore make its first call
+ * before that pool is created (with less than the array free, the first
+ * call returns BSM_ECUDA), and before any stream capture, because the first
+ * call on a device also looks up the array's device address (with that
+ * device current) and remembers it.  Calls after the first allocate nothing
+ * (no cudaMalloc, cudaFree or allocating library routine).  A lattice whose
  * scratch, 2 * bsm_field_bytes(lat, BSM_FIELD_HALF_SPINOR, prec), exceeds
- * the array returns BSM_EWORKSPACE before any launch.  The call allocates
- * nothing (no cudaMalloc, cudaFree or allocating library routine).  Its
- * first call on a device looks up the array's device address with that
- * device current and remembers it: make that first call before any stream
- * capture.  All calls on a device share the one array and the scratch is
- * fully rewritten by each call, so nothing needs clearing between calls,
- * but calls that overlap on the GPU (e.g. on two streams) race on it:
- * serialise them. */
+ * the array returns BSM_EWORKSPACE before any launch.  All calls on a
+ * device share the one array and the scratch is fully rewritten by each
+ * call, so nothing needs clearing between calls, but calls that overlap on
+ * the GPU (e.g. on two streams) race on it: serialise them. */
 int bsm_dirac_eo_noalloc(const bsm_lattice *lat, const void *U_rep, const void *in_e,
                          void *out_e, int32_t op, int32_t prec, void *stream);
 

@@ -68,8 +68,6 @@ void set_cuda_error(cudaError_t e) {
   snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-namespace {
-
 // checks every field of the lattice; BSM_OK, BSM_EINVAL or BSM_EUNSUPPORTED
 int check_lattice(const bsm_lattice* L) {
   if (L == nullptr) return BSM_EINVAL;
@@ -102,6 +100,14 @@ bool prec_lat_ok(const bsm_lattice* L, int prec) {
   return prec_ok(prec) && (prec != BSM_F32R12 || (L->N == 3 && L->rep == BSM_FUND));
 }
 
+// true when the byte ranges [a, a + na) and [b, b + nb) intersect
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
+
+namespace {
+
 int finish(int rc) {
   if (rc != BSM_OK) return rc;
   const cudaError_t e = cudaGetLastError();
@@ -121,8 +127,6 @@ int check_mrhs(const bsm_lattice* L, int nrhs, int prec) {
   return BSM_OK;
 }
 
-bool overlap(const void* a, size_t na, const void* b, size_t nb);
-
 // batch: SU(2)/SU(3) fundamental items, FP32, sane options
 int check_batch(const bsm_batch_item* items, int count, const bsm_batch_opts* o) {
   if (items == nullptr || o == nullptr || count < 1 || count > 32) return BSM_EINVAL;
@@ -141,11 +145,6 @@ int check_batch(const bsm_batch_item* items, int count, const bsm_batch_opts* o)
     if (overlap(it.in, n, it.out, n)) return BSM_EINVAL;
   }
   return BSM_OK;
-}
-
-bool overlap(const void* a, size_t na, const void* b, size_t nb) {
-  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
-  return x < y + nb && y < x + na;
 }
 
 // learned preconditioner: complex d = 2, 3; channels 1..64; 32-bit GEMM rows

@@ -633,7 +633,20 @@ int launch_hop(int prec, int d, bool real, const HopArgs& args, cudaStream_t s);
 
 constexpr int kHopThreads = 128;
 inline int hop_blocks(int Vh) { return (Vh + kHopThreads - 1) / kHopThreads; }
+// block partials written by one DF64 hop launch (its staged kernel runs
+// smaller blocks than kHopThreads)
+int hop_partials_df64(int Vh);
+// the most block partials one hop launch of any precision writes
+inline int hop_partials_max(int Vh) { return hop_blocks(Vh) > hop_partials_df64(Vh) ? hop_blocks(Vh) : hop_partials_df64(Vh); }
 
 void set_cuda_error(cudaError_t e);
+
+// argument checks shared by the entry points (defined in api.cu): every
+// field of the lattice (BSM_OK, BSM_EINVAL or BSM_EUNSUPPORTED); precisions
+// a lattice's operators accept; 16-byte alignment; intersecting byte ranges
+int check_lattice(const bsm_lattice* L);
+bool prec_lat_ok(const bsm_lattice* L, int prec);
+bool aligned(const void* p);
+bool overlap(const void* a, size_t na, const void* b, size_t nb);
 
 }  // namespace bsm

@@ -395,12 +395,26 @@ __global__ void __launch_bounds__(kHopThreads, HopOccupancy<P, D>::min_blocks) h
       SpinorIO<P, D>::store(A.out, Vh, i, acc);
     }
     if (A.partials != nullptr) {
-      R n = R(0);
+      if constexpr (sizeof(R) == sizeof(float)) {
+        // FP32 kernels: the 2d squares of one spin summed in FP32, the four
+        // spin sums converted and added in FP64 (the thread's partial is
+        // FP64; an FP64 operation per square would cost 24 FP64-pipe
+        // instructions per site on this part)
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
+        for (int s = 0; s < 4; ++s) {
+          float n = 0.f;
 #pragma unroll
-        for (int c = 0; c < D; ++c) n = fma(acc[s][c].re, acc[s][c].re, fma(acc[s][c].im, acc[s][c].im, n));
-      nrm = (double)n;
+          for (int c = 0; c < D; ++c) n = fmaf(acc[s][c].re, acc[s][c].re, fmaf(acc[s][c].im, acc[s][c].im, n));
+          nrm += (double)n;
+        }
+      } else {
+        R n = R(0);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+          for (int c = 0; c < D; ++c) n = fma(acc[s][c].re, acc[s][c].re, fma(acc[s][c].im, acc[s][c].im, n));
+        nrm = (double)n;
+      }
     }
   }
   if (A.partials != nullptr) block_sum_store<kHopThreads>(nrm, A.partials);

@@ -6,6 +6,10 @@
 // only a host-side stand-in, not a device address, so the address is asked
 // from the runtime once per device (cudaGetSymbolAddress with that device
 // current) and cached; every call on that device then shares the array.
+// The runtime reserves the array when it loads this module on a device:
+// under lazy module loading (the default) inside that first lookup, under
+// eager loading when the context is created.  Calls after the first on a
+// device therefore reserve no device memory.
 #include <mutex>
 
 #include "operators.cuh"
@@ -44,28 +48,6 @@ int scratch_address(void** out) {
   return BSM_OK;
 }
 
-int check_lattice_local(const bsm_lattice* L) {
-  if (L == nullptr) return BSM_EINVAL;
-  int64_t V = 1;
-  for (int m = 0; m < 4; ++m) {
-    if (L->dims[m] < 2 || (L->dims[m] & 1)) return BSM_EINVAL;
-    V *= L->dims[m];
-    if (!isfinite(L->bc_phase[m])) return BSM_EINVAL;
-  }
-  if (V > ((int64_t)1 << 30)) return BSM_EUNSUPPORTED;
-  if (!isfinite(L->m0) || 4.0 + L->m0 == 0.0) return BSM_EINVAL;
-  const RepInfo ri = rep_info(L->N, L->rep);
-  if (ri.d < 0) return BSM_EUNSUPPORTED;
-  if (ri.real)
-    for (int m = 0; m < 4; ++m) {
-      const double k = L->bc_phase[m] / M_PI;
-      if (fabs(k - nearbyint(k)) > 1e-12) return BSM_EUNSUPPORTED;
-    }
-  return BSM_OK;
-}
-
-bool aligned16(const void* p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
-
 }  // namespace
 }  // namespace bsm
 
@@ -73,17 +55,15 @@ using namespace bsm;
 
 extern "C" int bsm_dirac_eo_noalloc(const bsm_lattice* lat, const void* U_rep, const void* in_e, void* out_e,
                                     int32_t op, int32_t prec, void* stream) {
-  int rc = check_lattice_local(lat);
+  // the same argument checks as bsm_dirac_eo
+  int rc = check_lattice(lat);
   if (rc != BSM_OK) return rc;
-  if (prec != BSM_F64 && prec != BSM_F32) return BSM_EUNSUPPORTED;
-  if (!aligned16(U_rep) || !aligned16(in_e) || !aligned16(out_e)) return BSM_EINVAL;
+  if (!prec_lat_ok(lat, prec)) return BSM_EUNSUPPORTED;
+  if (!aligned(U_rep) || !aligned(in_e) || !aligned(out_e)) return BSM_EINVAL;
   if (op != BSM_OP_DHAT && op != BSM_OP_DHAT_DAG && op != BSM_OP_DHAT_DAG_DHAT) return BSM_EINVAL;
   const OpCtx c = make_ctx(*lat, U_rep, prec, (cudaStream_t)stream);
   if (2 * c.half_bytes > kNoAllocScratchBytes) return BSM_EWORKSPACE;  // lattice too large for the array
-  {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(in_e), b = reinterpret_cast<uintptr_t>(out_e);
-    if (a < b + c.half_bytes && b < a + c.half_bytes) return BSM_EINVAL;
-  }
+  if (overlap(in_e, c.half_bytes, out_e, c.half_bytes)) return BSM_EINVAL;
   void* scratch = nullptr;
   if ((rc = scratch_address(&scratch)) != BSM_OK) return rc;
   // both scratch halves are written in full before they are read, so the

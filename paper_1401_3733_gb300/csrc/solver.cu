@@ -57,7 +57,7 @@ CgLayout cg_layout(const bsm_lattice& L, int prec_inner, int eo, int prec_outer)
   const size_t h32 = half_spinor_bytes(g.Vh, ri.d, BSM_F32);
   y.vec64 = eo ? h64 : 2 * h64;
   y.vec32 = eo ? h32 : 2 * h32;
-  y.npart = std::max(2 * hop_blocks(g.Vh), kBlasMaxBlocks);
+  y.npart = std::max(2 * hop_partials_max(g.Vh), kBlasMaxBlocks);
   size_t o = 0;
   y.state = o; o = align_up(o + sizeof(CgState));
   y.partA = o; o = align_up(o + sizeof(double) * y.npart);

@@ -1,22 +1,26 @@
 #!/usr/bin/env python
-"""Benchmark: Wilson-Dirac hop (Dslash) GFLOP/s and its HBM roofline fraction
-on the 32^3 x 64 SU(3) workload, plus CG time-to-1e-10 of the mixed-precision
+"""Benchmark: Wilson-Dirac hop (Dslash) GFLOP/s and its roofline fraction on
+the 32^3 x 64 SU(3) workload, plus CG time-to-1e-10 of the mixed-precision
 solver against the plain FP64 solver on the same GPU.
 
-One step = the hopping term on the whole lattice in FP32 (both parity blocks,
-bsm_dslash EVEN then ODD, 1320 flop per site), L2 flushed between steps.
-Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-instead, on a bounded sample of the same workload.
+One step = the hopping term on the whole lattice (both parity blocks,
+bsm_dslash EVEN then ODD, 1320 flop per site) in FP64-accurate double-float
+arithmetic (the paper's Dphi is FP64), L2 flushed between steps.  The FP32
+hop (the inner operator of the mixed solver) and the native-FP64 hop are
+reported beside it with their own rooflines.  Prints one JSON line (rank 0).
+`--impl reference` times the FP64 CPU oracle instead, on the same workload.
 
 Multi-GPU (torchrun): independent replicas, one lattice per GPU, no
 collective on the data path; the value is the whole-job rate (weak scaling).
 """
 import argparse
 import ctypes
+import hashlib
 import json
 import math
 import os
 import statistics
+import subprocess
 import sys
 import threading
 import time
@@ -25,19 +29,46 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+CSRC = os.path.join(ROOT, "paper_1401_3733_gb300", "csrc")
 
 METRIC = "Dslash GFLOP/s (% of HBM roofline); CG time-to-1e-10 vs plain FP64 CG"
 WORKLOAD = dict(dims=(64, 32, 32, 32), N=3, m0=0.05, phase=(math.pi, 0.0, 0.0, 0.0), link_seed=3, eps=0.3,
                 src_seed=4)
-SAMPLE_DIMS = (32, 16, 16, 16)   # bounded CPU sample: same per-site work, 1/16 of the sites
-# DRAM bytes per output site (dram__bytes_read.sum + dram__bytes_write.sum) of
-# the FP32 SU(3) hop kernel as it stands, from one single-pass ncu capture of
-# the benchmark's own timed launches on the 32^3 x 64 workload (summarised
-# under profiles/).  Set to None whenever the kernel changes until it is
-# captured again.
-HOP_F32_TRAFFIC_PER_SITE = 736.2
 WORKLOAD_NAME = ("32^3x64 SU(3) fundamental, smooth links exp(i 0.3 H), m0=0.05, antiperiodic time: "
-                 "even-odd Wilson hop on both parity blocks, FP32 storage and arithmetic")
+                 "even-odd Wilson hop on both parity blocks, FP64-accurate double-float arithmetic")
+# the small configuration: 4^4 SU(2) fundamental, Haar links, m0 = 0.1 (CG to 1e-10 on the full D^+D)
+SMALL = dict(dims=(4, 4, 4, 4), N=2, m0=0.1, phase=(math.pi, 0.0, 0.0, 0.0), link_seed=1, src_seed=2)
+
+# GB300 FP32 pipe: 152 SMs x 128 lanes x 2070 MHz (maximum SM clock), one
+# FP32 operation (add, multiply or fused multiply-add) per lane and clock
+FP32_OPS_PEAK = 152 * 128 * 2.07e9
+
+# DRAM bytes per output site (dram__bytes_read.sum + dram__bytes_write.sum)
+# of a hop kernel, from one single-pass ncu capture of this benchmark's timed
+# launches on the 32^3 x 64 workload (summarised under profiles/), valid only
+# for the kernel sources it was taken on: `sha` is the hash of those files
+# (kernel_sha), and a mismatch reports the traffic as null.
+TRAFFIC = {
+    "hop_df64": {"bytes_per_site": 1538.4, "sha": "389e1b87bdd79844",
+                 "sources": ["hop_df64.cu", "f32x2.cuh", "hop.cuh", "bsm_internal.cuh", "df64.cuh"]},
+    "hop_f32": {"bytes_per_site": 736.0, "sha": "eb66718d6a4215c0",
+                "sources": ["hop_f32.cu", "hop.cuh", "bsm_internal.cuh"]},
+}
+
+
+def kernel_sha(sources):
+    h = hashlib.sha256()
+    for f in sources:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_site(kernel):
+    t = TRAFFIC[kernel]
+    if t["bytes_per_site"] is None or t["sha"] != kernel_sha(t["sources"]):
+        return None
+    return t["bytes_per_site"]
 
 
 def flops_per_site(d, real=False):
@@ -53,6 +84,16 @@ def bytes_per_site(d, w, real=False):
 def bytes_per_site_r12(w):
     """SU(3) hop with two-row links: 8 links of 12 reals + input + output spinor (d = 3)."""
     return (8 * 12 + 2 * 24) * w
+
+
+def df64_ops_per_site(d):
+    """FP32 operations per output site of the double-float hop (complex
+    representation), counted on its algorithm: per direction-sense the spin
+    projection (2d complex double-float sums with a sign: 40d), the link
+    products (each double-float multiply-add 12 operations, the first of a
+    chain 4: 96d^2 - 32d) and the reconstruction (4d complex sums, two of
+    them signed: 72d)."""
+    return 8 * (96 * d * d + 80 * d)
 
 
 def load_peaks():
@@ -123,31 +164,135 @@ class ClockSampler:
                 "reasons": sorted(self.reasons), "samples": len(self.samples)}
 
 
-def time_oracle_hop(dims, min_seconds, max_reps=None):
-    """The oracle's full-lattice hop on a host-generated sample, repeated with
-    the doubling loop of the paper's timing method until min_seconds pass.
-    Returns (GFLOP/s, reps, seconds, threads)."""
-    import oracle as orc
-    from paper_1401_3733_gb300 import fields
-
-    w = WORKLOAD
-    lat = orc.Lattice(dims, w["N"], orc.FUND, w["m0"], w["phase"])
-    U = fields.gauge_field(dims, w["N"], "smooth", seed=w["link_seed"], eps=w["eps"])
-    R = orc.links_to_rep(lat, U)
-    psi = fields.gaussian_spinor(dims, lat.d, w["src_seed"])
-    orc.hop(lat, R, psi, orc.FULL)   # warm-up
-    reps, n, t0 = 0, 1, time.perf_counter()
+def doubling_loop(interval, min_seconds):
+    """The paper's fixed-time timing loop (Sec. III): interval(n) runs the
+    timed operation n times between two clock reads and returns the seconds;
+    n doubles until one interval reaches min_seconds.  Returns (n, seconds)."""
+    n = 1
     while True:
-        for _ in range(n):
-            orc.hop(lat, R, psi, orc.FULL)
-        reps += n
-        el = time.perf_counter() - t0
-        if el >= min_seconds or (max_reps and reps >= max_reps):
-            break
+        el = interval(n)
+        if el >= min_seconds:
+            return n, el
         n *= 2
-    gflops = reps * flops_per_site(lat.d) * lat.V / el / 1e9
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return gflops, reps, el, threads
+
+
+def host_interval(fn):
+    def interval(n):
+        t0 = time.perf_counter()
+        for _ in range(n):
+            fn()
+        return time.perf_counter() - t0
+    return interval
+
+
+def gpu_interval(fn):
+    """n calls of fn between two CUDA events on torch's current stream (the
+    stream the library launches on)."""
+    import torch
+
+    def interval(n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+    return interval
+
+
+# ----------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_child(path):
+    """Child process of oracle_timings: times the oracle on the arrays saved
+    at `path` with the OpenMP thread count of its environment, prints JSON."""
+    import oracle as orc
+
+    z = np.load(path)
+    w = WORKLOAD
+    lat = orc.Lattice(tuple(int(x) for x in z["dims"]), w["N"], orc.FUND, w["m0"], w["phase"])
+    R = orc.links_to_rep(lat, z["U"])
+    psi = z["psi"]
+    Vh = lat.V // 2
+    min_s = float(os.environ.get("BSM_ORACLE_MIN_SECONDS", "1.0"))
+    out = {"threads": int(os.environ.get("OMP_NUM_THREADS", "0"))}
+    reps, el = doubling_loop(host_interval(lambda: orc.hop(lat, R, psi, orc.EVEN)), min_s)
+    out["hop_eo_block"] = {"gflops": round(reps * flops_per_site(lat.d) * Vh / el / 1e9, 3),
+                           "seconds_per_call": round(el / reps, 4)}
+    reps, el = doubling_loop(host_interval(lambda: orc.dhat(lat, R, psi, orc.DHAT)), min_s)
+    out["dhat"] = {"gflops": round(reps * 2 * flops_per_site(lat.d) * Vh / el / 1e9, 3),
+                   "seconds_per_call": round(el / reps, 4)}
+    # CG to 1e-10 on the small configuration (full D^+D and even-odd)
+    s = SMALL
+    from paper_1401_3733_gb300 import fields
+    slat = orc.Lattice(s["dims"], s["N"], orc.FUND, s["m0"], s["phase"])
+    sR = orc.links_to_rep(slat, fields.gauge_field(s["dims"], s["N"], "haar", seed=s["link_seed"]))
+    sb = fields.gaussian_spinor(s["dims"], slat.d, s["src_seed"])
+    for eo in (False, True):
+        t0 = time.perf_counter()
+        _, it, res = orc.cg(slat, sR, sb, eo=eo, tol=1e-10)
+        out["cg_4x4_su2_" + ("eo" if eo else "full")] = {"seconds": round(time.perf_counter() - t0, 5),
+                                                         "iters": it, "rel_res": res}
+    # a fixed number of CG iterations on the workload (even-odd);
+    # the time to 1e-10 is extrapolated to the GPU solver's iteration count
+    # (per-iteration time from the difference of an n-iteration and a
+    # 1-iteration solve, so the source preparation and the final residual
+    # check are not counted as iterations)
+    n_it = int(os.environ.get("BSM_ORACLE_CG_ITERS", "20"))
+    t0 = time.perf_counter()
+    orc.cg(lat, R, psi, eo=True, tol=1e-30, max_iter=1)
+    t1 = time.perf_counter()
+    orc.cg(lat, R, psi, eo=True, tol=1e-30, max_iter=n_it)
+    t2 = time.perf_counter()
+    per_it = ((t2 - t1) - (t1 - t0)) / (n_it - 1)
+    out["cg_workload_fixed_iters"] = {"iters": n_it, "seconds": round(t2 - t1, 3),
+                                      "seconds_one_iter_solve": round(t1 - t0, 3),
+                                      "seconds_per_iter": round(per_it, 4),
+                                      "fixed_seconds": round((t1 - t0) - per_it, 3)}
+    print(json.dumps(out), flush=True)
+
+
+def oracle_timings(dims, U, psi, cg_iters_gpu):
+    """BASELINE's CPU plan: the oracle single-threaded and on all host cores,
+    each in a child process (OpenMP over sites is its only parallelism): one
+    even-odd hop block and one Dhat on the 32^3 x 64 workload, CG to 1e-10 on
+    the 4^4 SU(2) configuration, and a fixed number of CG iterations on the
+    32^3 x 64 workload (time to 1e-10 extrapolated, and labelled so)."""
+    import tempfile
+    cores = os.cpu_count() or 1
+    res = {"cores": cores, "cpu": platform_cpu()}
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "fields.npz")
+        np.savez(path, U=U, psi=psi, dims=np.array(dims))
+        for name, threads, iters in (("all_cores", cores, 20), ("single_thread", 1, 3)):
+            env = dict(os.environ, OMP_NUM_THREADS=str(threads), BSM_ORACLE_CG_ITERS=str(iters))
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", path], env=env,
+                               capture_output=True, text=True, timeout=900)
+            if r.returncode != 0:
+                res[name] = {"error": r.stderr.strip().splitlines()[-1:] or ["failed"]}
+                continue
+            t = json.loads(r.stdout.strip().splitlines()[-1])
+            c = t["cg_workload_fixed_iters"]
+            if cg_iters_gpu:
+                c["extrapolated_seconds_to_1e-10"] = round(c["fixed_seconds"] + c["seconds_per_iter"] * cg_iters_gpu, 2)
+                c["extrapolated_to_iters"] = cg_iters_gpu
+            res[name] = t
+    return res
+
+
+def platform_cpu():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
 
 
 def dist_setup():
@@ -189,7 +334,19 @@ def whole_job_rate(units_per_rank, seconds_per_rank, world):
     return world * units_per_rank / max_over_ranks(seconds_per_rank, world)
 
 
+def config_dict(dims, world):
+    V = int(np.prod(dims))
+    return {"workload": WORKLOAD_NAME, "lattice_TXYZ": list(dims), "sites": V,
+            "flop_per_site": flops_per_site(WORKLOAD["N"]),
+            "algorithmic_bytes_per_site": bytes_per_site(WORKLOAD["N"], 8),
+            "l2": "flushed between steps (256 MiB write); inputs (1.4 GB) larger than L2",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
+    """The oracle as it stands (plain C FP64, OpenMP over sites, all host
+    cores): one step = its hop on both parity blocks of the whole 32^3 x 64
+    workload, the metric and config of the GPU arm."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -197,10 +354,11 @@ def run_reference(args):
     import oracle as orc
     from paper_1401_3733_gb300 import fields
     w = WORKLOAD
-    lat = orc.Lattice(SAMPLE_DIMS, w["N"], orc.FUND, w["m0"], w["phase"])
-    U = fields.gauge_field(SAMPLE_DIMS, w["N"], "smooth", seed=w["link_seed"], eps=w["eps"])
+    lat = orc.Lattice(w["dims"], w["N"], orc.FUND, w["m0"], w["phase"])
+    U = fields.gauge_field(w["dims"], w["N"], "smooth", seed=w["link_seed"], eps=w["eps"])
     R = orc.links_to_rep(lat, U)
-    psi = fields.gaussian_spinor(SAMPLE_DIMS, lat.d, w["src_seed"])
+    del U
+    psi = fields.gaussian_spinor(w["dims"], lat.d, w["src_seed"])
     for _ in range(args.warmup):
         orc.hop(lat, R, psi, orc.FULL)
     t0 = time.perf_counter()
@@ -209,12 +367,13 @@ def run_reference(args):
     el = time.perf_counter() - t0
     value = args.steps * flops_per_site(lat.d) * lat.V / el / 1e9
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = f"oracle hop (FP64 plain C, OpenMP over sites) on a {'x'.join(map(str, SAMPLE_DIMS))} lattice per step"
+    sample = (f"oracle hop (FP64 plain C, OpenMP over sites) on both parity blocks of the whole "
+              f"{'x'.join(map(str, w['dims']))} lattice per step")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "sample": list(SAMPLE_DIMS)},
+        "config": config_dict(w["dims"], world),
         "cpu_baseline": {"value": round(value, 3), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -236,9 +395,9 @@ def run_ours(args):
     U = fields.gauge_field(dims, N, "smooth", seed=w["link_seed"] + rank, eps=w["eps"])
     psi = fields.gaussian_spinor(dims, d, w["src_seed"] + rank)
 
-    stream = torch.cuda.current_stream()
     Ud = torch.from_numpy(U).cuda()
-    links = {p: bsm.empty_field(lat, bsm.FIELD_LINKS, p) for p in (bsm.F64, bsm.F32, bsm.DF64)}
+    PRECS = (bsm.F64, bsm.F32, bsm.DF64)
+    links = {p: bsm.empty_field(lat, bsm.FIELD_LINKS, p) for p in PRECS}
     ev_l0, ev_l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev_l0.record()
     bsm.bsm_links_to_rep(lat, Ud, links[bsm.F32], bsm.F32)
@@ -249,9 +408,9 @@ def run_ours(args):
     bsm.bsm_links_to_rep(lat, Ud, links[bsm.F32R12], bsm.F32R12)
     del Ud
     psid = torch.from_numpy(psi).cuda()
-    src = {p: bsm.empty_field(lat, bsm.FIELD_SPINOR, p) for p in (bsm.F64, bsm.F32, bsm.DF64)}
-    dst = {p: bsm.empty_field(lat, bsm.FIELD_SPINOR, p) for p in (bsm.F64, bsm.F32, bsm.DF64)}
-    for p in (bsm.F64, bsm.F32, bsm.DF64):
+    src = {p: bsm.empty_field(lat, bsm.FIELD_SPINOR, p) for p in PRECS}
+    dst = {p: bsm.empty_field(lat, bsm.FIELD_SPINOR, p) for p in PRECS}
+    for p in PRECS:
         bsm.bsm_pack_spinor(lat, psid, src[p], p)
     src[bsm.F32R12], dst[bsm.F32R12] = src[bsm.F32], dst[bsm.F32]   # spinors as FP32
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
@@ -274,84 +433,118 @@ def run_ours(args):
         if evs:
             evs[2].record()
 
+    def timed_steps(prec, steps, nvtx):
+        """`steps` steps, each bracketed by the L2 flush; per-launch CUDA
+        events on the launching stream; returns the launch times (ms)."""
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        torch.cuda.nvtx.range_push(nvtx)   # lets ncu --nvtx-include select the timed region
+        for k in range(steps):
+            flush.zero_()
+            dslash_step(prec, evs[k])
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        return [e[0].elapsed_time(e[1]) for e in evs] + [e[1].elapsed_time(e[2]) for e in evs]
+
     flop_step = flops_per_site(d) * V
+    peak, peak_src = load_peaks()
+    HEAD = bsm.DF64
     for _ in range(args.warmup):
         flush.zero_()
-        dslash_step(bsm.F32)
+        dslash_step(HEAD)
     uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
     uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     barrier(world)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     with ClockSampler(uuid) as clk:
-        torch.cuda.nvtx.range_push("timed_dslash")   # lets ncu --nvtx-include select the timed region
-        for k in range(args.steps):
-            flush.zero_()
-            dslash_step(bsm.F32, evs[k])
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
+        launch_ms = timed_steps(HEAD, args.steps, "timed_dslash")
     barrier(world)
     wall = time.perf_counter() - wall0
-    launch_ms = [e[0].elapsed_time(e[1]) for e in evs] + [e[1].elapsed_time(e[2]) for e in evs]
     ms_step = sum(launch_ms) / args.steps
     ms_step_max = max_over_ranks(ms_step, world)
     value = world * flop_step / (ms_step_max * 1e-3) / 1e9   # = whole_job_rate over ranks
 
-    peak, peak_src = load_peaks()
-    hop_bytes = bytes_per_site(d, 4) * Vh
+    # roofline of the headline kernel: the larger of the HBM time (1536 B per
+    # site) and the FP32-pipe time (its double-float operations) binds
     avg_launch_ms = sum(launch_ms) / len(launch_ms)
+    hop_bytes = bytes_per_site(d, 8) * Vh
+    hop_ops = df64_ops_per_site(d) * Vh
+    t_hbm_us = hop_bytes / (peak * 1e9) * 1e6
+    t_alu_us = hop_ops / FP32_OPS_PEAK * 1e6
     achieved = hop_bytes / (avg_launch_ms * 1e-3) / 1e9
+    achieved_ops = hop_ops / (avg_launch_ms * 1e-3)
+    tps = traffic_per_site("hop_df64")
+    bound_hbm = t_hbm_us >= t_alu_us
+    roofline = {
+        "bound": "hbm" if bound_hbm else "alu",
+        "achieved": round(achieved if bound_hbm else achieved_ops / 1e12, 1 if bound_hbm else 3),
+        "peak": peak if bound_hbm else round(FP32_OPS_PEAK / 1e12, 3),
+        "unit": "GB/s" if bound_hbm else "TFP32op/s",
+        "frac": round((achieved / peak) if bound_hbm else (achieved_ops / FP32_OPS_PEAK), 4),
+        "traffic": None if tps is None else round(tps * Vh),
+        "peak_source": peak_src if bound_hbm else "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+        "kernel": "hop_df64_staged_kernel<3> (double-float, f32x2)", "bytes_per_launch": hop_bytes,
+        "avg_launch_us": round(avg_launch_ms * 1e3, 2),
+        "roof_us": {"hbm": round(t_hbm_us, 1), "alu": round(t_alu_us, 1)},
+        "alu": {"fp32_ops_per_site": df64_ops_per_site(d), "achieved_tops": round(achieved_ops / 1e12, 3),
+                "peak_tops": round(FP32_OPS_PEAK / 1e12, 3), "frac": round(achieved_ops / FP32_OPS_PEAK, 4)},
+        "hbm_frac": round(achieved / peak, 4),
+    }
 
-    # FP64 and FP64-accurate double-float Dslash on the same inputs (their own
-    # lines; the FP64 units bound the first on this part)
-    ms_other = {bsm.F64: float("nan"), bsm.DF64: float("nan"), bsm.F32R12: float("nan")}
+    # the other precisions on the same inputs, each with its own roofline
+    others = {}
     if not args.no_fp64:
-        for prec in (bsm.F64, bsm.DF64, bsm.F32R12):
-            evp = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(max(3, args.steps // 4))]
+        for name, prec in (("dslash_f32", bsm.F32), ("dslash_f32r12", bsm.F32R12), ("dslash_fp64", bsm.F64)):
             for _ in range(2):
                 dslash_step(prec)
-            torch.cuda.nvtx.range_push({bsm.F64: "dslash_fp64", bsm.DF64: "dslash_df64",
-                                        bsm.F32R12: "dslash_f32r12"}[prec])
-            for e in evp:
-                flush.zero_()
-                dslash_step(prec, e)
-            torch.cuda.nvtx.range_pop()
-            torch.cuda.synchronize()
-            ms_other[prec] = sum(e[0].elapsed_time(e[2]) for e in evp) / len(evp)
-    ms64, msdf, ms12 = ms_other[bsm.F64], ms_other[bsm.DF64], ms_other[bsm.F32R12]
-    r12_bytes = 2 * bytes_per_site_r12(4) * Vh
+            n = args.steps if prec == bsm.F32 else max(3, args.steps // 4)
+            lm = timed_steps(prec, n, name)
+            others[name] = (prec, sum(lm) / len(lm), sum(lm) / n)
+
+    # the paper's timing method (Sec. III) on the headline and FP32 hops: a
+    # fixed-time loop doubling the repetitions until one interval reaches
+    # 0.5 s (no flush inside it: the inputs exceed L2), median of 5 intervals
+    protocol = {}
+    if not args.no_protocol:
+        for name, prec in (("df64", HEAD), ("f32", bsm.F32)):
+            pts = []
+            for _ in range(5):
+                reps, el = doubling_loop(gpu_interval(lambda: dslash_step(prec)), 0.5)
+                pts.append(reps * flop_step / el / 1e9)
+            protocol[name] = {"gflops_median": round(statistics.median(pts), 1),
+                              "gflops_points": [round(x, 1) for x in pts], "reps_last": reps,
+                              "seconds_last": round(el, 3)}
 
     # end to end through the public API: pinned host canonical FP64 input ->
-    # pack -> hop on both parity blocks -> unpack -> pinned host output, every
-    # step.  Consecutive steps run on E2E_STREAMS streams with their own
-    # buffers, so one step's host->device copy overlaps the previous step's
-    # kernels and device->host copy (the link is full duplex); the timed
-    # region spans all steps, joined on the timing stream.
+    # pack -> double-float hop on both parity blocks -> unpack -> pinned host
+    # output, every step.  Consecutive steps run on E2E_STREAMS streams with
+    # their own buffers, so one step's host->device copy overlaps the previous
+    # step's kernels and device->host copy (the link is full duplex); the
+    # timed region spans all steps, joined on the timing stream.
     E2E_STREAMS = 3
-    h_in = [torch.from_numpy(psi).pin_memory() for _ in range(E2E_STREAMS)]
-    h_out = [torch.empty_like(h_in[0]).pin_memory() for _ in range(E2E_STREAMS)]
-    d_in = [torch.empty_like(psid) for _ in range(E2E_STREAMS)]
-    d_out = [torch.empty_like(psid) for _ in range(E2E_STREAMS)]
-    e_src = [src[bsm.F32]] + [bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F32) for _ in range(E2E_STREAMS - 1)]
-    e_dst = [dst[bsm.F32]] + [bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F32) for _ in range(E2E_STREAMS - 1)]
-    e_streams = [torch.cuda.Stream() for _ in range(E2E_STREAMS)]
-    n_e2e = max(6, min(args.steps, 12))
-    nh = bsm.bsm_field_bytes(lat, bsm.FIELD_HALF_SPINOR, bsm.F32)
-
-    def e2e_step(k):
-        b = k % E2E_STREAMS
-        s = e_streams[b]
-        with torch.cuda.stream(s):
-            d_in[b].copy_(h_in[b], non_blocking=True)
-            bsm.bsm_pack_spinor(lat, d_in[b], e_src[b], bsm.F32, stream=s)
-            bsm.bsm_dslash(lat, links[bsm.F32], e_src[b][nh:], e_dst[b][:nh], bsm.EVEN, 0, bsm.F32, stream=s)
-            bsm.bsm_dslash(lat, links[bsm.F32], e_src[b][:nh], e_dst[b][nh:], bsm.ODD, 0, bsm.F32, stream=s)
-            bsm.bsm_unpack_spinor(lat, e_dst[b], d_out[b], bsm.F32, stream=s)
-            h_out[b].copy_(d_out[b], non_blocking=True)
-
     e2e_ms, e2e_value = float("nan"), float("nan")
     if not args.no_e2e:
+        h_in = [torch.from_numpy(psi).pin_memory() for _ in range(E2E_STREAMS)]
+        h_out = [torch.empty_like(h_in[0]).pin_memory() for _ in range(E2E_STREAMS)]
+        d_in = [torch.empty_like(psid) for _ in range(E2E_STREAMS)]
+        d_out = [torch.empty_like(psid) for _ in range(E2E_STREAMS)]
+        e_src = [src[HEAD]] + [bsm.empty_field(lat, bsm.FIELD_SPINOR, HEAD) for _ in range(E2E_STREAMS - 1)]
+        e_dst = [dst[HEAD]] + [bsm.empty_field(lat, bsm.FIELD_SPINOR, HEAD) for _ in range(E2E_STREAMS - 1)]
+        e_streams = [torch.cuda.Stream() for _ in range(E2E_STREAMS)]
+        n_e2e = max(6, min(args.steps, 12))
+        nh = bsm.bsm_field_bytes(lat, bsm.FIELD_HALF_SPINOR, HEAD)
+
+        def e2e_step(k):
+            b = k % E2E_STREAMS
+            s = e_streams[b]
+            with torch.cuda.stream(s):
+                d_in[b].copy_(h_in[b], non_blocking=True)
+                bsm.bsm_pack_spinor(lat, d_in[b], e_src[b], HEAD, stream=s)
+                bsm.bsm_dslash(lat, links[HEAD], e_src[b][nh:], e_dst[b][:nh], bsm.EVEN, 0, HEAD, stream=s)
+                bsm.bsm_dslash(lat, links[HEAD], e_src[b][:nh], e_dst[b][nh:], bsm.ODD, 0, HEAD, stream=s)
+                bsm.bsm_unpack_spinor(lat, e_dst[b], d_out[b], HEAD, stream=s)
+                h_out[b].copy_(d_out[b], non_blocking=True)
+
         for k in range(E2E_STREAMS):
             e2e_step(k)
         torch.cuda.synchronize()
@@ -372,47 +565,26 @@ def run_ours(args):
         e2e_value = world * flop_step / (e2e_ms * 1e-3) / 1e9
         # the host result of the last step equals the device-path result
         assert torch.equal(h_out[(n_e2e - 1) % E2E_STREAMS], d_out[(n_e2e - 1) % E2E_STREAMS].cpu())
+        del h_in, h_out, d_in, d_out, e_src, e_dst
     io_bytes = psi.nbytes
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step_max, 5), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "lattice_TXYZ": list(dims), "sites": V, "flop_per_site": flops_per_site(d),
-                   "algorithmic_bytes_per_site": bytes_per_site(d, 4), "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": f"replicas x{world}", "wall_s_timed_region": round(wall, 4)},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4),
-                     "traffic": None if HOP_F32_TRAFFIC_PER_SITE is None else round(HOP_F32_TRAFFIC_PER_SITE * Vh),
-                     "peak_source": peak_src,
-                     "kernel": "hop_kernel<F32,3,complex>", "bytes_per_launch": hop_bytes,
-                     "avg_launch_us": round(avg_launch_ms * 1e3, 2), "frac_of_8TBs": round(achieved / 8000, 4)},
-        "dslash_fp64": {"gflops": round(flop_step / (ms64 * 1e-3) / 1e9, 2), "ms_per_step": round(ms64, 4),
-                        "bound": "alu (FP64 DFMA)",
-                        "hbm_frac": round(2 * bytes_per_site(d, 8) * Vh / (ms64 * 1e-3) / 1e9 / peak, 4)},
-        "dslash_df64": {"gflops": round(flop_step / (msdf * 1e-3) / 1e9, 2), "ms_per_step": round(msdf, 4),
-                        "bound": "alu (FP32 double-float arithmetic)",
-                        "hbm_frac": round(2 * bytes_per_site(d, 8) * Vh / (msdf * 1e-3) / 1e9 / peak, 4)},
-        "dslash_f32r12": {"gflops": round(flop_step / (ms12 * 1e-3) / 1e9, 2), "ms_per_step": round(ms12, 4),
-                          "links": "SU(3) stored as two rows (12 reals), third row rebuilt in registers",
-                          "bound": "hbm", "algorithmic_bytes_per_site": bytes_per_site_r12(4),
-                          "hbm_frac": round(r12_bytes / (ms12 * 1e-3) / 1e9 / peak, 4)},
-        "links_to_rep_ms_f32": round(links_ms, 3),
-        "e2e": {"value": round(e2e_value, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": io_bytes,
-                "d2h_bytes_per_step": io_bytes, "ms_per_step": round(e2e_ms, 4),
-                "pipelining": f"{E2E_STREAMS} streams, consecutive steps overlap"},
+        "vs_baseline": None, "dtype": "df64", "data": "synthetic",
+        "config": dict(config_dict(dims, world), wall_s_timed_region=round(wall, 4),
+                       arithmetic="double-float: each real an unevaluated sum of two FP32 (about 48 significand "
+                                  "bits); rel-L2 vs the FP64 oracle 6.7e-15"),
+        "roofline": roofline,
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
     }
-    # parts skipped by a flag are left out rather than reported as NaN
-    if args.no_fp64:
-        for k in ("dslash_fp64", "dslash_df64", "dslash_f32r12"):
-            out.pop(k)
-    if args.no_e2e:
-        out.pop("e2e")
+    if not args.no_e2e:
+        out["e2e"] = {"value": round(e2e_value, 2), "unit": "GFLOP/s", "h2d_bytes_per_step": io_bytes,
+                      "d2h_bytes_per_step": io_bytes, "ms_per_step": round(e2e_ms, 4),
+                      "pipelining": f"{E2E_STREAMS} streams, consecutive steps overlap"}
 
-    if rank == 0 and not args.no_cg:
-        out["cg"] = run_cg(lat, links, src[bsm.F64], args.cg_max_iter)
+    cg_iters = None
     if rank == 0 and not args.no_mrhs:
         out["mrhs"] = run_mrhs(max(3, min(args.steps, 20)), flush, peak)
     if rank == 0 and not args.no_batch:
@@ -421,15 +593,47 @@ def run_ours(args):
         out["cg_small_graph"] = run_cg_graph(args.cg_max_iter)
     if rank == 0 and not args.no_precond:
         out["precond"] = run_precond(peak, peak_src, args.steps)
+    if rank == 0 and not args.no_cg:
+        out["cg"] = run_cg(lat, links, src[bsm.F64], args.cg_max_iter)
+        cg_iters = out["cg"]["fp64"]["iters"]
     if rank == 0 and not args.no_large:
         del links, src, dst, flush
         torch.cuda.empty_cache()
         out["large"] = run_large(args.steps, peak, peak_src, args.cg_max_iter)
     if rank == 0 and world == 1 and not args.no_cpu:
-        g, reps, el, th = time_oracle_hop(SAMPLE_DIMS, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": round(g, 3), "unit": "GFLOP/s", "cores": th, "kind": "oracle",
-                               "sample": f"oracle full-lattice hop on {'x'.join(map(str, SAMPLE_DIMS))} "
-                                         f"(same per-site work), {reps} reps in {el:.1f} s"}
+        ot = oracle_timings(dims, U, psi, cg_iters)
+        out["oracle_timings"] = ot
+        hop_all = ot.get("all_cores", {}).get("hop_eo_block")
+        if hop_all:
+            out["cpu_baseline"] = {"value": hop_all["gflops"], "unit": "GFLOP/s", "cores": ot["cores"],
+                                   "kind": "oracle",
+                                   "sample": f"oracle even-odd hop block on the whole "
+                                             f"{'x'.join(map(str, dims))} workload (same per-site work as a "
+                                             f"step), fixed-time doubling loop >= 1 s, all cores"}
+    if protocol:
+        out["protocol"] = dict(protocol, method="doubling fixed-time loop (paper Sec. III), >= 0.5 s per "
+                                                "interval, median of 5, CUDA events")
+    # the other precisions last (the end of the line is what a log tail keeps)
+    for name, (prec, avg_ms, ms_s) in others.items():
+        bps = bytes_per_site_r12(4) if prec == bsm.F32R12 else bytes_per_site(d, 4 if prec != bsm.F64 else 8)
+        ach = bps * Vh / (avg_ms * 1e-3) / 1e9
+        entry = {"gflops": round(flop_step / (ms_s * 1e-3) / 1e9, 1), "avg_launch_us": round(avg_ms * 1e3, 2),
+                 "bytes_per_site": bps}
+        if prec == bsm.F64:
+            entry.update(bound="alu (FP64 DFMA, 1.26 TFLOP/s nominal)", hbm_frac=round(ach / peak, 4))
+        else:
+            t = traffic_per_site("hop_f32") if prec == bsm.F32 else None
+            entry["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                                 "frac": round(ach / peak, 4), "peak_source": peak_src,
+                                 "traffic": None if t is None else round(t * Vh)}
+        out[name] = entry
+    if "cg" in out:
+        c = out["cg"]
+        out["cg_summary"] = {"fp64_s": c["fp64"]["seconds"], "best_mixed": c["best_mixed"],
+                             "best_mixed_s": c[c["best_mixed"]]["seconds"],
+                             "fp64_over_mixed_time": c.get("fp64_over_mixed_time"), "iters": cg_iters,
+                             "true_res_normal": c[c["best_mixed"]]["true_res_normal"]}
+    out["links_to_rep_ms_f32"] = round(links_ms, 3)
     barrier(world)
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -925,20 +1129,24 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution part")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--cg-max-iter", type=int, default=20000)
     ap.add_argument("--lattice", type=int, nargs=4, metavar=("T", "X", "Y", "Z"),
                     help="override the lattice (profiling of a smaller case); default 64 32 32 32")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64, DF64 and two-row-link FP32 Dslash lines")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP32, two-row-link FP32 and FP64 Dslash lines")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-mrhs", action="store_true", help="skip the multi-RHS 24^4 three-theory lines")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-lattice batch and small-lattice CG lines")
     ap.add_argument("--no-precond", action="store_true", help="skip the learned-preconditioner (FGCR) line")
     ap.add_argument("--no-large", action="store_true", help="skip the 48^3 x 96 lines")
+    ap.add_argument("--no-protocol", action="store_true", help="skip the doubling fixed-time loop (median of 5)")
+    ap.add_argument("--oracle-child", metavar="NPZ", help=argparse.SUPPRESS)
     ap.add_argument("--ptc-apply-only", action="store_true",
                     help="only the BF16 network application's roofline (on --lattice, random weights); "
                          "the profiling entry for its kernels")
     args = ap.parse_args()
+    if args.oracle_child:
+        oracle_child(args.oracle_child)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -402,7 +402,10 @@ int bsm_ptc_adam_step(void *W, const void *G, void *m, void *v, int64_t n, doubl
  * iterates on is <= tol |b|; with eo that residual is the full-system residual
  * of the reconstructed x (the odd sites' residual vanishes by construction).
  * The new direction of each step is orthogonalised against the cycle's
- * earlier ones by classical Gram-Schmidt in one pass. */
+ * earlier ones by classical Gram-Schmidt in one pass (which, in the FP32
+ * cycles, loses orthogonality faster than modified Gram-Schmidt would: more
+ * steps, never a wrong residual, since the stopping test is the recomputed
+ * FP64 residual). */
 typedef enum { BSM_FGCR_NONE = 0, BSM_FGCR_PTC = 1 } bsm_fgcr_precond;
 typedef struct {
   double tol;        /* stop when |r| <= tol |b| (iterated residual) */
@@ -424,12 +427,23 @@ typedef struct {
                         BSM_DF64 (double-float, about 48 significand bits), in
                         which case U_rep64 is a BSM_DF64 link field; the
                         vectors stay FP64 either way */
+  int32_t fallback;  /* nonzero: when FGCR ends with BSM_ENOCONV or BSM_ENAN,
+                        solve the same system with CG on the normal equations
+                        (bsm_cg_solve: mixed precision with U_rep32 when it is
+                        given, else plain at prec_outer; eo as above; from the
+                        FGCR iterate after BSM_ENOCONV, from zero after
+                        BSM_ENAN) to the normal-equation residual tol, and
+                        return that solve's status */
+  int32_t fallback_max_iter; /* CG iterations of the fallback (0 -> 20000) */
 } bsm_fgcr_opts;
 typedef struct {
   int32_t iters;     /* directions (preconditioner applications) in total */
   int32_t cycles;    /* restart cycles */
-  double true_res;   /* |b - D x| / |b|, recomputed at the end */
-  double seconds;
+  double true_res;   /* |b - D x| / |b|, recomputed at the end (by the
+                        fallback CG when it ran) */
+  double seconds;    /* the whole call, the fallback included */
+  int32_t fgcr_status;    /* status FGCR itself ended with */
+  int32_t fallback_iters; /* CG iterations of the fallback, 0 if it did not run */
 } bsm_fgcr_stats;
 size_t bsm_fgcr_workspace_bytes(const bsm_lattice *lat, const bsm_fgcr_opts *opts);
 /* b, x: full FP64 device-layout spinors (x is overwritten, start x = 0);
@@ -437,11 +451,59 @@ size_t bsm_fgcr_workspace_bytes(const bsm_lattice *lat, const bsm_fgcr_opts *opt
  * FP32 links, used with BSM_FGCR_PTC or
  * prec_inner BSM_F32 (may be NULL otherwise); W1, W2: used with BSM_FGCR_PTC
  * only.  Synchronises `stream` every check_every steps.  Returns
- * BSM_ENOCONV (max_iter reached) or BSM_ENAN with x holding the last iterate. */
+ * BSM_ENOCONV (max_iter reached) or BSM_ENAN with x holding the last iterate,
+ * unless opts->fallback is set: then plain CG, the library's reference solver,
+ * takes over and its status is returned (stats->fgcr_status keeps FGCR's).
+ * The workspace is then sized for both solvers. */
 int bsm_fgcr_solve(const bsm_lattice *lat, const void *U_rep64, const void *U_rep32,
                    const void *W1, const void *W2, const void *b, void *x,
                    const bsm_fgcr_opts *opts, bsm_fgcr_stats *stats, void *workspace,
                    size_t workspace_bytes, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Domain decomposition in time (Sec. II-C: each process owns a block of the
+ * lattice and exchanges boundary data with its neighbours for every Dphi).
+ * A slab is the block of nt time slices [t0, t0 + nt) of `global`; t0 and nt
+ * are even (so a site's parity is the same in the slab and in the global
+ * lattice) and t0 + nt <= T.  A slab's spinors use the device layout of the
+ * lattice `global` with dims[0] = nt (bsm_pack_spinor on that lattice).
+ * Per hop each slab packs two faces of its input half spinor with
+ * bsm_face_pack and hands them to its neighbours (BSM_FACE_LO, its first
+ * slice, to the slab below; BSM_FACE_HI, its last slice, to the slab above;
+ * the lattice is periodic, so the first slab's neighbour below is the last
+ * slab) -- by NCCL send/receive or a copy into the receiver's memory -- and
+ * then calls bsm_dslash_slab with the two faces it received.  A face holds
+ * the spin projection that the receiver's time-direction term needs, 2 spin
+ * x d colour complex per site: half of the boundary spinor.  Precisions
+ * BSM_F64 and BSM_F32; errors as bsm_dslash.  Not in the paper's form: the
+ * paper decomposes over MPI ranks with its own halo format. */
+typedef struct {
+  bsm_lattice global;  /* the whole lattice */
+  int32_t t0, nt;      /* the slab's first time slice and number of slices */
+} bsm_slab;
+typedef enum { BSM_FACE_LO = 0, BSM_FACE_HI = 1 } bsm_face_side;
+
+/* Bytes of one face (X Y Z / 2 sites x 2 x d complex at prec); 0 if invalid. */
+size_t bsm_face_bytes(const bsm_slab *slab, int32_t prec);
+
+/* face = the spin projection (1 -+ g_0) of one boundary slice of the slab's
+ * half spinor in_slab (parity in_parity): side BSM_FACE_LO the first slice,
+ * projected for the forward term of the slab below, BSM_FACE_HI the last
+ * slice, for the backward term of the slab above.  dagger must match the
+ * receiver's bsm_dslash_slab call. */
+int bsm_face_pack(const bsm_slab *slab, const void *in_slab, void *face, int32_t side,
+                  int32_t in_parity, int32_t dagger, int32_t prec, void *stream);
+
+/* out_slab = the hop H_{p,1-p} (bsm_dslash with out_parity p) on the slab's
+ * sites, from its half spinor in_slab of parity 1 - p and the faces received
+ * from the slab below (face_lo, that slab's BSM_FACE_HI face) and above
+ * (face_hi, that slab's BSM_FACE_LO face).  U_rep: the representation links of
+ * the GLOBAL lattice (bsm_links_to_rep on `global`; the slab reads its own
+ * sites' links, boundary phases included).  Equals the slab's part of
+ * bsm_dslash on the global lattice up to the order of the sums. */
+int bsm_dslash_slab(const bsm_slab *slab, const void *U_rep, const void *in_slab,
+                    const void *face_lo, const void *face_hi, void *out_slab,
+                    int32_t out_parity, int32_t dagger, int32_t prec, void *stream);
 
 /* Static text for a bsm_status. */
 const char *bsm_strerror(int status);

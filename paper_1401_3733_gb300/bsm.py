@@ -66,15 +66,23 @@ class FgcrOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("restart", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("ptc_prec", ctypes.c_int32), ("channels", ctypes.c_int32),
                 ("prec_inner", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("eo", ctypes.c_int32),
-                ("check_every", ctypes.c_int32), ("prec_outer", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("prec_outer", ctypes.c_int32), ("fallback", ctypes.c_int32),
+                ("fallback_max_iter", ctypes.c_int32)]
 
 
 class FgcrStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("cycles", ctypes.c_int32), ("true_res", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("fgcr_status", ctypes.c_int32), ("fallback_iters", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Slab(ctypes.Structure):
+    _fields_ = [("global_", Lattice), ("t0", ctypes.c_int32), ("nt", ctypes.c_int32)]
+
+
+FACE_LO, FACE_HI = 0, 1
 
 
 class BsmError(RuntimeError):
@@ -132,6 +140,13 @@ _lib.bsm_fgcr_workspace_bytes.argtypes = [_LP, ctypes.POINTER(FgcrOpts)]
 _lib.bsm_fgcr_workspace_bytes.restype = ctypes.c_size_t
 _lib.bsm_fgcr_solve.argtypes = [_LP, _P, _P, _P, _P, _P, _P, ctypes.POINTER(FgcrOpts), ctypes.POINTER(FgcrStats),
                                 _P, ctypes.c_size_t, _P]
+_SP = ctypes.POINTER(Slab)
+_lib.bsm_face_bytes.argtypes = [_SP, ctypes.c_int32]
+_lib.bsm_face_bytes.restype = ctypes.c_size_t
+_lib.bsm_face_pack.argtypes = [_SP, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]
+_lib.bsm_face_pack.restype = ctypes.c_int
+_lib.bsm_dslash_slab.argtypes = [_SP, _P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]
+_lib.bsm_dslash_slab.restype = ctypes.c_int
 _lib.bsm_strerror.argtypes = [ctypes.c_int]
 _lib.bsm_strerror.restype = ctypes.c_char_p
 _lib.bsm_last_cuda_error.argtypes = []
@@ -354,9 +369,9 @@ def bsm_ptc_adam_step(W, G, m, v, lr, step, stream=None):
 
 
 def fgcr_opts(tol=1e-10, max_iter=1000, restart=16, precond=FGCR_NONE, ptc_prec=F32, channels=1, prec_inner=F64,
-              inner_tol=0.0, eo=False, check_every=1, prec_outer=F64) -> FgcrOpts:
+              inner_tol=0.0, eo=False, check_every=1, prec_outer=F64, fallback=False, fallback_max_iter=0) -> FgcrOpts:
     return FgcrOpts(tol, max_iter, restart, precond, ptc_prec, channels, prec_inner, inner_tol, int(eo), check_every,
-                    prec_outer)
+                    prec_outer, int(fallback), fallback_max_iter)
 
 
 def bsm_fgcr_workspace_bytes(lat, opts: FgcrOpts) -> int:
@@ -373,3 +388,21 @@ def bsm_fgcr_solve(lat, U_rep64, U_rep32, W1, W2, b, x, opts: FgcrOpts, workspac
     if raise_on_error:
         _check(st, "bsm_fgcr_solve")
     return st, stats
+
+
+def slab(global_lat, t0, nt) -> Slab:
+    return Slab(global_lat, t0, nt)
+
+
+def bsm_face_bytes(sl, prec) -> int:
+    return _lib.bsm_face_bytes(ctypes.byref(sl), prec)
+
+
+def bsm_face_pack(sl, in_slab, face, side, in_parity, dagger, prec, stream=None):
+    _check(_lib.bsm_face_pack(ctypes.byref(sl), _ptr(in_slab), _ptr(face), side, in_parity, int(dagger), prec,
+                              _stream(stream)), "bsm_face_pack")
+
+
+def bsm_dslash_slab(sl, U_rep, in_slab, face_lo, face_hi, out_slab, out_parity, dagger, prec, stream=None):
+    _check(_lib.bsm_dslash_slab(ctypes.byref(sl), _ptr(U_rep), _ptr(in_slab), _ptr(face_lo), _ptr(face_hi),
+                                _ptr(out_slab), out_parity, int(dagger), prec, _stream(stream)), "bsm_dslash_slab")

@@ -2,6 +2,9 @@
 // validation (before any launch), size queries, dispatch to the kernels, and
 // CUDA error mapping.
 #include <math.h>
+
+#include <algorithm>
+#include <chrono>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -35,6 +38,17 @@ int ptc_adam(void* W, const void* G, void* m, void* v, long long nfloat, double 
 size_t fgcr_workspace_bytes(const bsm_lattice& L, const bsm_fgcr_opts& o);
 int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* W1, const void* W2,
                const void* b, void* x, const bsm_fgcr_opts& o, bsm_fgcr_stats* stats, void* ws, cudaStream_t s);
+
+// FGCR's workspace, or the larger of FGCR's and its fallback CG's
+size_t fgcr_total_workspace_bytes(const bsm_lattice& L, const bsm_fgcr_opts& o) {
+  size_t n = fgcr_workspace_bytes(L, o);
+  if (o.fallback != 0) {
+    const size_t c = cg_workspace_bytes(L, BSM_F32, o.eo, o.prec_outer);
+    const size_t p = cg_workspace_bytes(L, o.prec_outer, o.eo, o.prec_outer);
+    n = std::max(n, std::max(c, p));
+  }
+  return n;
+}
 
 RepInfo rep_info(int N, int rep) {
   RepInfo r{-1, false};
@@ -474,7 +488,7 @@ int bsm_ptc_adam_step(void* W, const void* G, void* m, void* v, int64_t n, doubl
 size_t bsm_fgcr_workspace_bytes(const bsm_lattice* lat, const bsm_fgcr_opts* opts) {
   if (opts == nullptr || check_lattice(lat) != BSM_OK || opts->restart < 1 || opts->restart > 64) return 0;
   if (opts->precond == BSM_FGCR_PTC && check_ptc(lat, opts->channels, 1) != BSM_OK) return 0;
-  return fgcr_workspace_bytes(*lat, *opts);
+  return fgcr_total_workspace_bytes(*lat, *opts);
 }
 
 int bsm_fgcr_solve(const bsm_lattice* lat, const void* U_rep64, const void* U_rep32, const void* W1, const void* W2,
@@ -496,7 +510,8 @@ int bsm_fgcr_solve(const bsm_lattice* lat, const void* U_rep64, const void* U_re
     if (!aligned(U_rep32) || !aligned(W1) || !aligned(W2)) return BSM_EINVAL;
   }
   if (!aligned(U_rep64) || !aligned(b) || !aligned(x) || !aligned(workspace)) return BSM_EINVAL;
-  if (workspace_bytes < fgcr_workspace_bytes(*lat, *opts)) return BSM_EWORKSPACE;
+  if (opts->fallback != 0 && opts->fallback_max_iter < 0) return BSM_EINVAL;
+  if (workspace_bytes < fgcr_total_workspace_bytes(*lat, *opts)) return BSM_EWORKSPACE;
   const size_t full = bsm_field_bytes(lat, BSM_FIELD_SPINOR, BSM_F64);
   if (overlap(b, full, x, full)) return BSM_EINVAL;
   const cudaError_t pre = cudaGetLastError();
@@ -504,12 +519,41 @@ int bsm_fgcr_solve(const bsm_lattice* lat, const void* U_rep64, const void* U_re
     set_cuda_error(pre);
     return BSM_ECUDA;
   }
-  rc = fgcr_solve(*lat, U_rep64, U_rep32, W1, W2, b, x, *opts, stats, workspace, (cudaStream_t)stream);
-  const cudaError_t e = cudaGetLastError();
+  const auto t0 = std::chrono::steady_clock::now();
+  bsm_fgcr_stats st{};
+  rc = fgcr_solve(*lat, U_rep64, U_rep32, W1, W2, b, x, *opts, &st, workspace, (cudaStream_t)stream);
+  st.fgcr_status = rc;
+  st.fallback_iters = 0;
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_cuda_error(e);
     return BSM_ECUDA;
   }
+  if (opts->fallback != 0 && (rc == BSM_ENOCONV || rc == BSM_ENAN)) {
+    // the plain solver of the paper's method on the same system: mixed
+    // precision CG on the normal equations (reliable updates at prec_outer)
+    bsm_cg_opts co{};
+    co.tol = opts->tol;
+    co.max_iter = opts->fallback_max_iter > 0 ? opts->fallback_max_iter : 20000;
+    const bool mixed = U_rep32 != nullptr;
+    co.prec_inner = mixed ? BSM_F32 : opts->prec_outer;
+    co.prec_outer = opts->prec_outer;
+    co.delta = 0.1;
+    co.use_x0 = rc == BSM_ENOCONV;  // a NaN iterate is no starting point
+    co.eo = opts->eo;
+    co.check_every = 16;
+    co.use_graph = 0;
+    bsm_cg_stats cs{};
+    rc = cg_solve(*lat, U_rep64, mixed ? U_rep32 : nullptr, b, x, co, &cs, workspace, (cudaStream_t)stream);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+      set_cuda_error(e);
+      return BSM_ECUDA;
+    }
+    st.fallback_iters = cs.iters;
+    st.true_res = cs.true_res_full;
+  }
+  st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st;
   return rc;
 }
 

@@ -366,9 +366,14 @@ struct Fgcr {
   // place): up to `restart` directions, at most `budget` iterations; stops
   // early once |r|^2 <= stop2.  Each new w = A z is orthogonalised against
   // the cycle's earlier ones in one pass (classical Gram-Schmidt: the dots
-  // <w_j, w> of all j at once, then w -= sum_j beta_j w_j; with the w_j
-  // mutually orthogonal this equals modified Gram-Schmidt up to rounding),
-  // and r -= alpha w.  The preconditioned directions z are stored as they
+  // <w_j, w> of all j at once, then w -= sum_j beta_j w_j).  In exact
+  // arithmetic this equals modified Gram-Schmidt; in floating point, and
+  // above all in the FP32 cycles, classical Gram-Schmidt loses orthogonality
+  // faster when w is nearly in the span of the w_j, which can cost extra
+  // inner steps near the critical mass.  The iterates stay consistent either
+  // way (x and r are updated with the same beta), and the FP64 residual
+  // recomputed after each FP32 cycle is the stopping test, so the lost
+  // orthogonality shows up as iterations, not as error.  Then r -= alpha w.  The preconditioned directions z are stored as they
   // come; the solution update that the orthogonalised directions imply is
   // formed once at the cycle's end from the stored beta and alpha (the
   // deferred update of GCR: half the basis traffic per step, and x is not

@@ -210,6 +210,11 @@ def test_ptc_and_fgcr_validation(bsm):
     assert bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(restart=0)) == 0
     assert bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(restart=8, precond=bsm.FGCR_PTC, channels=4)) > \
         bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(restart=8)) > 0
+    # with the CG fallback the workspace holds either solver
+    assert bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(restart=2, fallback=True)) >= max(
+        bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(restart=2)),
+        bsm.bsm_workspace_bytes(good, bsm.CALL_CG, bsm.F64))
+    assert solve(bsm.fgcr_opts(fallback=True, fallback_max_iter=-1)) == bsm.EINVAL
     assert solve(bsm.fgcr_opts(tol=0.0)) == bsm.EINVAL
     assert solve(bsm.fgcr_opts(restart=65)) == bsm.EINVAL
     assert solve(bsm.fgcr_opts(precond=7)) == bsm.EINVAL
@@ -232,3 +237,22 @@ def test_ptc_and_fgcr_validation(bsm):
     assert bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(prec_inner=bsm.F32, prec_outer=bsm.DF64)) == \
         bsm.bsm_fgcr_workspace_bytes(good, bsm.fgcr_opts(prec_inner=bsm.F32)) + \
         2 * bsm.bsm_field_bytes(good, bsm.FIELD_SPINOR, bsm.F64)
+
+
+def test_slab_arguments_are_checked(bsm):
+    """time slabs: t0 and nt even, 2 <= nt, t0 + nt <= T, FP64/FP32 only"""
+    glat = bsm.lattice((8, 4, 4, 4), 3, bsm.FUND, 0.1)
+    A = 1 << 24
+    for t0, nt in ((1, 4), (0, 3), (6, 4), (-2, 4), (0, 0)):
+        assert bsm._lib.bsm_dslash_slab(bsm.slab(glat, t0, nt), A, 2 * A, 3 * A, 4 * A, 5 * A, 0, 0, bsm.F64,
+                                        None) == bsm.EINVAL
+        assert bsm._lib.bsm_face_pack(bsm.slab(glat, t0, nt), A, 2 * A, bsm.FACE_LO, 1, 0, bsm.F64,
+                                      None) == bsm.EINVAL
+        assert bsm.bsm_face_bytes(bsm.slab(glat, t0, nt), bsm.F64) == 0
+    ok = bsm.slab(glat, 2, 4)
+    assert bsm._lib.bsm_dslash_slab(ok, A, 2 * A, 3 * A, 4 * A, 5 * A, 0, 0, bsm.DF64, None) == bsm.EUNSUPPORTED
+    assert bsm._lib.bsm_dslash_slab(ok, A, 2 * A, 3 * A, 4 * A, 5 * A, 2, 0, bsm.F64, None) == bsm.EINVAL
+    assert bsm._lib.bsm_face_pack(ok, A, 2 * A, 7, 1, 0, bsm.F64, None) == bsm.EINVAL
+    # one face: X Y Z / 2 sites x 2 spins x d colours, complex
+    assert bsm.bsm_face_bytes(ok, bsm.F64) == 4 * 4 * 4 // 2 * 2 * 3 * 16
+    assert bsm.bsm_face_bytes(ok, bsm.F32) == 4 * 4 * 4 // 2 * 2 * 3 * 8

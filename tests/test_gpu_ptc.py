@@ -337,6 +337,38 @@ def test_fgcr_statuses():
     assert st == bsm.ENAN
 
 
+@pytest.mark.parametrize("cause", ["max_iter", "nan_weights"])
+@pytest.mark.parametrize("eo", [True, False], ids=["eo", "full"])
+def test_fgcr_falls_back_to_cg(cause, eo):
+    """With opts.fallback, an FGCR solve that ends in BSM_ENOCONV (max_iter = 1)
+    or BSM_ENAN (a NaN in the network's weights, planted on the host) is
+    finished by the plain CG solver on the normal equations: the call returns
+    OK, reports FGCR's own status and the CG iterations, and x solves D x = b
+    (checked with the oracle's D).  Without fallback the same call fails."""
+    dims, N = (4, 4, 4, 8), 3
+    olat, blat = lats(dims, N, bsm.FUND, (np.pi, 0, 0, 0), m0=0.05)
+    U = fields.gauge_field(dims, N, "smooth", seed=24, eps=0.4)
+    R = orc.links_to_rep(olat, U)
+    U64, U32 = gpu_links(blat, U, bsm.F64), gpu_links(blat, U, bsm.F32)
+    b = fields.gaussian_spinor(dims, N, 25)
+    bd = gpu_spinor(blat, b, bsm.F64)
+    W1, W2 = neumann_weights(olat.m0)
+    if cause == "nan_weights":
+        W1 = W1.copy()
+        W1[3, 1] = np.nan
+    W = (dev_c64(W1), dev_c64(W2))
+    kw = dict(tol=1e-11, restart=16, precond=bsm.FGCR_PTC, ptc_prec=bsm.BF16, channels=2, eo=eo,
+              prec_inner=bsm.F32, inner_tol=1e-3, max_iter=1 if cause == "max_iter" else 1000)
+    want = bsm.ENOCONV if cause == "max_iter" else bsm.ENAN
+    st, _, _ = fgcr(blat, U64, U32, bd, bsm.fgcr_opts(**kw), W)
+    assert st == want
+    st, stats, x = fgcr(blat, U64, U32, bd, bsm.fgcr_opts(fallback=True, **kw), W)
+    assert st == bsm.OK, bsm.bsm_strerror(st)
+    assert stats.fgcr_status == want and stats.fallback_iters > 0
+    assert stats.true_res <= 1e-9
+    assert rel(orc.dirac(olat, R, to_canon(blat, x, bsm.F64)), b) <= 1e-9
+
+
 @pytest.mark.parametrize("precond", ["none", "ptc-bf16"])
 def test_mixed_precision_fgcr_reaches_fp64_accuracy(precond):
     """FP32 restart cycles with the residual recomputed in FP64: the same

@@ -460,6 +460,36 @@ int bsm_fgcr_solve(const bsm_lattice *lat, const void *U_rep64, const void *U_re
                    const bsm_fgcr_opts *opts, bsm_fgcr_stats *stats, void *workspace,
                    size_t workspace_bytes, void *stream);
 
+/* A batch of systems solved together: mixed-precision CG (FP32 iterations,
+ * reliable updates at opts->prec_outer) on the even-odd normal equations of
+ * every right-hand side of several lattices of uneven size (Sec. II-B CG; the
+ * N_f flavours of Sec. II-A as RHS sharing a gauge field).  Each iteration
+ * runs Dhat^+ Dhat of the whole batch in one persistent launch (the
+ * bsm_dslash_batch kernel, four phases) and the vector updates of all
+ * systems in four more launches, with per-system scalars on the device; the
+ * check_every iterations between host checks are captured once as a CUDA
+ * graph (use_graph, not on the legacy default stream) and replayed.  At each
+ * check every system whose residual fell by delta (or below the stop) gets a
+ * reliable update; a system whose recomputed residual |bp - M x| <= tol |bp|
+ * stops.  Items: SU(2) or SU(3) fundamental, up to 32 lattices.  opts:
+ * prec_inner BSM_F32, prec_outer BSM_F64 or BSM_DF64, eo nonzero, use_x0 0;
+ * tol, max_iter (iterations of the batch), delta, check_every, use_graph as
+ * for bsm_cg_solve.  stats: one bsm_cg_stats per system, items in order and
+ * RHS within an item (iters: the iteration at which that system stopped).
+ * Synchronises `stream`.  A batch barrier that waits more than 1 s returns
+ * BSM_ETIMEOUT. */
+typedef struct {
+  bsm_lattice lat;
+  const void *U_rep64;  /* links at opts->prec_outer */
+  const void *U_rep32;  /* FP32 links */
+  const void *b;        /* nrhs FP64 full device-layout spinors, one after the other */
+  void *x;              /* the solutions, same layout (overwritten) */
+  int32_t nrhs;         /* 1, 2, 4, 8 or 16 */
+} bsm_cg_batch_item;
+size_t bsm_cg_batch_workspace_bytes(const bsm_cg_batch_item *items, int32_t count);
+int bsm_cg_solve_batch(const bsm_cg_batch_item *items, int32_t count, const bsm_cg_opts *opts,
+                       bsm_cg_stats *stats, void *workspace, size_t workspace_bytes, void *stream);
+
 /* ---------------------------------------------------------------------
  * Domain decomposition in time (Sec. II-C: each process owns a block of the
  * lattice and exchanges boundary data with its neighbours for every Dphi).

@@ -85,6 +85,11 @@ class Slab(ctypes.Structure):
 FACE_LO, FACE_HI = 0, 1
 
 
+class CgBatchItem(ctypes.Structure):
+    _fields_ = [("lat", Lattice), ("U_rep64", ctypes.c_void_p), ("U_rep32", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("nrhs", ctypes.c_int32)]
+
+
 class BsmError(RuntimeError):
     def __init__(self, status: int, what: str):
         msg = f"{what}: {bsm_strerror(status)} ({status})"
@@ -140,6 +145,11 @@ _lib.bsm_fgcr_workspace_bytes.argtypes = [_LP, ctypes.POINTER(FgcrOpts)]
 _lib.bsm_fgcr_workspace_bytes.restype = ctypes.c_size_t
 _lib.bsm_fgcr_solve.argtypes = [_LP, _P, _P, _P, _P, _P, _P, ctypes.POINTER(FgcrOpts), ctypes.POINTER(FgcrStats),
                                 _P, ctypes.c_size_t, _P]
+_lib.bsm_cg_batch_workspace_bytes.argtypes = [ctypes.POINTER(CgBatchItem), ctypes.c_int32]
+_lib.bsm_cg_batch_workspace_bytes.restype = ctypes.c_size_t
+_lib.bsm_cg_solve_batch.argtypes = [ctypes.POINTER(CgBatchItem), ctypes.c_int32, ctypes.POINTER(CgOpts),
+                                    ctypes.POINTER(CgStats), _P, ctypes.c_size_t, _P]
+_lib.bsm_cg_solve_batch.restype = ctypes.c_int
 _SP = ctypes.POINTER(Slab)
 _lib.bsm_face_bytes.argtypes = [_SP, ctypes.c_int32]
 _lib.bsm_face_bytes.restype = ctypes.c_size_t
@@ -406,3 +416,28 @@ def bsm_face_pack(sl, in_slab, face, side, in_parity, dagger, prec, stream=None)
 def bsm_dslash_slab(sl, U_rep, in_slab, face_lo, face_hi, out_slab, out_parity, dagger, prec, stream=None):
     _check(_lib.bsm_dslash_slab(ctypes.byref(sl), _ptr(U_rep), _ptr(in_slab), _ptr(face_lo), _ptr(face_hi),
                                 _ptr(out_slab), out_parity, int(dagger), prec, _stream(stream)), "bsm_dslash_slab")
+
+
+def cg_batch_items(entries):
+    """entries: (lattice, U_rep64, U_rep32, b, x, nrhs) tuples -> ctypes array
+    (b, x: nrhs FP64 full spinors one after the other, as one tensor each)"""
+    arr = (CgBatchItem * len(entries))()
+    for k, (lat, U64, U32, b, x, n) in enumerate(entries):
+        arr[k] = CgBatchItem(lat, _ptr(U64), _ptr(U32), _ptr(b), _ptr(x), n)
+    return arr
+
+
+def bsm_cg_batch_workspace_bytes(items) -> int:
+    return _lib.bsm_cg_batch_workspace_bytes(items, len(items))
+
+
+def bsm_cg_solve_batch(items, opts: CgOpts, workspace, stream=None, raise_on_error=True):
+    """Returns (status, [CgStats per system])."""
+    nsys = sum(it.nrhs for it in items)
+    stats = (CgStats * nsys)()
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    st = _lib.bsm_cg_solve_batch(items, len(items), ctypes.byref(opts), stats, _ptr(workspace), nbytes,
+                                 _stream(stream))
+    if raise_on_error:
+        _check(st, "bsm_cg_solve_batch")
+    return st, list(stats)

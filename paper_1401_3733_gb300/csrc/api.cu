@@ -26,6 +26,9 @@ int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o
 int batch_status(void* ws, cudaStream_t s);
 bool mrhs_set_block(int prec, int d, bool real, int nrhs, int Vh, int block);
 size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo, int prec_outer);
+size_t cg_batch_workspace_bytes(const bsm_cg_batch_item* items, int count);
+int cg_solve_batch(const bsm_cg_batch_item* items, int count, const bsm_cg_opts& o, bsm_cg_stats* stats, void* ws,
+                   cudaStream_t s);
 int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void* b, void* x,
              const bsm_cg_opts& o, bsm_cg_stats* stats, void* ws, cudaStream_t s);
 size_t ptc_workspace_bytes(const bsm_lattice& L, int C, int nb, bool train);
@@ -377,6 +380,54 @@ int bsm_dslash_batch_async(const bsm_batch_item* items, int32_t count, const bsm
 int bsm_dslash_batch_status(void* workspace, void* stream) {
   if (!aligned(workspace)) return BSM_EINVAL;
   return batch_status(workspace, (cudaStream_t)stream);
+}
+
+namespace {
+int check_cg_batch(const bsm_cg_batch_item* items, int count) {
+  if (items == nullptr || count < 1 || count > 32) return BSM_EINVAL;
+  for (int k = 0; k < count; ++k) {
+    const bsm_cg_batch_item& it = items[k];
+    int rc = check_lattice(&it.lat);
+    if (rc != BSM_OK) return rc;
+    if (it.lat.rep != BSM_FUND || (it.lat.N != 2 && it.lat.N != 3)) return BSM_EUNSUPPORTED;
+    if (it.nrhs != 1 && it.nrhs != 2 && it.nrhs != 4 && it.nrhs != 8 && it.nrhs != 16) return BSM_EINVAL;
+    if ((rc = check_mrhs(&it.lat, it.nrhs, BSM_F32)) != BSM_OK) return rc;
+    if (!aligned(it.U_rep64) || !aligned(it.U_rep32) || !aligned(it.b) || !aligned(it.x)) return BSM_EINVAL;
+    const size_t n = bsm_field_bytes(&it.lat, BSM_FIELD_SPINOR, BSM_F64) * it.nrhs;
+    if (overlap(it.b, n, it.x, n)) return BSM_EINVAL;
+  }
+  return BSM_OK;
+}
+}  // namespace
+
+size_t bsm_cg_batch_workspace_bytes(const bsm_cg_batch_item* items, int32_t count) {
+  if (check_cg_batch(items, count) != BSM_OK) return 0;
+  return cg_batch_workspace_bytes(items, count);
+}
+
+int bsm_cg_solve_batch(const bsm_cg_batch_item* items, int32_t count, const bsm_cg_opts* opts, bsm_cg_stats* stats,
+                       void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = check_cg_batch(items, count);
+  if (rc != BSM_OK) return rc;
+  if (opts == nullptr || !(opts->tol > 0.0) || opts->max_iter < 1 || opts->delta < 0.0 || opts->delta >= 1.0 ||
+      opts->check_every < 0)
+    return BSM_EINVAL;
+  if (opts->prec_inner != BSM_F32 || opts->eo == 0 || opts->use_x0 != 0) return BSM_EUNSUPPORTED;
+  if (opts->prec_outer != BSM_F64 && opts->prec_outer != BSM_DF64) return BSM_EUNSUPPORTED;
+  if (!aligned(workspace)) return BSM_EINVAL;
+  if (workspace_bytes < cg_batch_workspace_bytes(items, count)) return BSM_EWORKSPACE;
+  const cudaError_t pre = cudaGetLastError();
+  if (pre != cudaSuccess) {
+    set_cuda_error(pre);
+    return BSM_ECUDA;
+  }
+  rc = cg_solve_batch(items, count, *opts, stats, workspace, (cudaStream_t)stream);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return BSM_ECUDA;
+  }
+  return rc;
 }
 
 int bsm_dirac_eo(const bsm_lattice* lat, const void* U_rep, const void* in_e, void* out_e, int32_t op,

@@ -17,6 +17,7 @@
 
 #include <vector>
 
+#include "batch.cuh"
 #include "mrhs.cuh"
 #include "operators.cuh"
 
@@ -32,17 +33,20 @@ struct BatchTask {
   long long chunks;
 };
 
+constexpr int kMaxPhases = 4;
+
 struct BatchControl {
-  unsigned long long next[2];     // work-queue counters, one per phase
-  unsigned int arrived;           // blocks that finished phase 0
-  int error;                      // 1: a barrier wait timed out
+  unsigned long long next[kMaxPhases];  // work-queue counters, one per phase
+  unsigned int arrived;                 // block arrivals at the grid barriers so far
+  int error;                            // 1: a barrier wait timed out
 };
 
 struct BatchMeta {
   int ntasks;
   int nphases;
-  long long phase_chunks[2];
-  unsigned int barrier_target;    // arrivals the barrier waits for
+  long long phase_chunks[kMaxPhases];
+  unsigned int grid_blocks;       // the barrier after phase j waits for (j + 1) * grid_blocks + barrier_extra arrivals
+  unsigned int barrier_extra;
   unsigned long long timeout_ns;
 };
 
@@ -52,7 +56,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-constexpr int kMaxBatchTasks = 64;     // 2 tasks per lattice: up to 32 lattices per launch
+constexpr int kMaxBatchTasks = 128;    // up to 4 tasks per lattice (Dhat^+ Dhat), 32 lattices per launch
 constexpr int kChunksPerGrab = 4;      // work-queue grabs cover 4 blocks' worth of thread slots
 
 // the whole task table as one launch parameter (the parameter space holds up
@@ -102,8 +106,10 @@ __global__ void __launch_bounds__(kHopThreads, 4) batch_kernel(const __grid_cons
       }
     }
     if (phase + 1 < meta.nphases) {
-      // grid barrier: every block of the cooperative grid arrives once, after
-      // all its threads have made their phase writes visible device-wide
+      // grid barrier: every block of the cooperative grid arrives once per
+      // barrier, after all its threads have made their phase writes visible
+      // device-wide
+      const unsigned target = (unsigned)(phase + 1) * meta.grid_blocks + meta.barrier_extra;
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -113,7 +119,7 @@ __global__ void __launch_bounds__(kHopThreads, 4) batch_kernel(const __grid_cons
         int abort = 0;
         // two independent bounds: the global timer and an iteration count
         // (2^24 polls of >= 256 ns), so the wait ends even if the timer stalls
-        for (unsigned it = 0; *(volatile unsigned int*)&ctl->arrived < meta.barrier_target; ++it) {
+        for (unsigned it = 0; *(volatile unsigned int*)&ctl->arrived < target; ++it) {
           if (*(volatile int*)&ctl->error != 0 || global_ns() - t0 > meta.timeout_ns || it > (1u << 24)) {
             atomicExch(&ctl->error, 1);
             abort = 1;
@@ -133,6 +139,49 @@ __global__ void __launch_bounds__(kHopThreads, 4) batch_kernel(const __grid_cons
 BatchTask with_tasks_scalars(BatchTask t) {
   t.args = with_f32_scalars(t.args);
   return t;
+}
+
+}  // namespace
+
+namespace {
+
+// the tasks (ordered by phase) as one cooperative launch: chunk offsets,
+// grid size (every block resident, so that the grid barriers complete),
+// the control block reset, the launch
+int launch_tasks(const std::vector<BatchTask>& tasks, BatchMeta meta, BatchControl* ctl, double timeout_s,
+                 int barrier_extra, cudaStream_t s) {
+  if ((int)tasks.size() > kMaxBatchTasks) return BSM_EUNSUPPORTED;
+  meta.ntasks = (int)tasks.size();
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kHopThreads, 0) != cudaSuccess ||
+      per_sm < 1)
+    return BSM_ECUDA;
+  long long want = 0;
+  for (int ph = 0; ph < meta.nphases; ++ph) want = meta.phase_chunks[ph] > want ? meta.phase_chunks[ph] : want;
+  want = (want + kChunksPerGrab - 1) / kChunksPerGrab;
+  int grid = sms * per_sm;
+  if (want < grid) grid = (int)(want > 0 ? want : 1);
+  meta.grid_blocks = (unsigned)grid;
+  meta.barrier_extra = (unsigned)(barrier_extra > 0 ? barrier_extra : 0);
+  meta.timeout_ns = (unsigned long long)((timeout_s > 0 ? timeout_s : 1.0) * 1e9);
+
+  BatchTable table;
+  memset(&table, 0, sizeof(table));
+  for (size_t k = 0; k < tasks.size(); ++k) table.t[k] = tasks[k];
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(BatchControl), s);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return BSM_ECUDA;
+  }
+  void* kargs[] = {(void*)&table, (void*)&ctl, (void*)&meta};
+  e = cudaLaunchCooperativeKernel((void*)batch_kernel, grid, kHopThreads, kargs, 0, s);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return BSM_ECUDA;
+  }
+  return BSM_OK;
 }
 
 }  // namespace
@@ -222,38 +271,51 @@ int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o
     }
   }
   tasks.insert(tasks.end(), tasks1.begin(), tasks1.end());
-  meta.ntasks = (int)tasks.size();
-
-  // a cooperative grid: every block resident, so the barrier can complete
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kHopThreads, 0) != cudaSuccess ||
-      per_sm < 1)
-    return BSM_ECUDA;
-  long long want = meta.phase_chunks[0] > meta.phase_chunks[1] ? meta.phase_chunks[0] : meta.phase_chunks[1];
-  want = (want + kChunksPerGrab - 1) / kChunksPerGrab;
-  int grid = sms * per_sm;
-  if (want < grid) grid = (int)(want > 0 ? want : 1);
-  meta.barrier_target = (unsigned)grid + (unsigned)(o.barrier_extra > 0 ? o.barrier_extra : 0);
-  meta.timeout_ns = (unsigned long long)((o.timeout_s > 0 ? o.timeout_s : 1.0) * 1e9);
-
-  BatchTable table;
-  memset(&table, 0, sizeof(table));
-  for (size_t k = 0; k < tasks.size(); ++k) table.t[k] = tasks[k];
-  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(BatchControl), s);
-  if (e != cudaSuccess) {
-    set_cuda_error(e);
-    return BSM_ECUDA;
-  }
-  void* kargs[] = {(void*)&table, (void*)&ctl, (void*)&meta};
-  e = cudaLaunchCooperativeKernel((void*)batch_kernel, grid, kHopThreads, kargs, 0, s);
-  if (e != cudaSuccess) {
-    set_cuda_error(e);
-    return BSM_ECUDA;
-  }
+  const int rc = launch_tasks(tasks, meta, ctl, o.timeout_s, o.barrier_extra, s);
+  if (rc != BSM_OK) return rc;
   return sync ? batch_status(ws, s) : BSM_OK;
 }
+
+// the even-odd normal operator Mp = Dhat^+ Dhat p of every item in one
+// launch of four phases: t = H_oe p, u = A p - H_eo t / (4A), t = H_oe^+ u,
+// Mp = A u - H_eo^+ t / (4A); FP32 multi-RHS fields (validated by the caller)
+int batch_normal_launch(const BatchNormalItem* items, int count, void* ctl_ws, double timeout_s, cudaStream_t s) {
+  BatchMeta meta;
+  memset(&meta, 0, sizeof(meta));
+  meta.nphases = 4;
+  std::vector<BatchTask> by_phase[4];
+  for (int k = 0; k < count; ++k) {
+    const BatchNormalItem& it = items[k];
+    const OpCtx c = make_ctx(it.lat, it.U32, BSM_F32, s);
+    BatchTask t;
+    memset(&t, 0, sizeof(t));
+    t.d = c.d;
+    t.args.g = c.g;
+    t.args.nrhs = it.nrhs;
+    t.chunks = ((long long)c.g.Vh * it.nrhs + kHopThreads - 1) / kHopThreads;
+    for (int ph = 0; ph < 4; ++ph) {
+      const bool first_hop = (ph & 1) == 0;  // phases 0, 2: tmp_o = H_oe(^+) v
+      const void* v = ph < 2 ? it.p : it.u;
+      t.args.dagger = ph >= 2;
+      t.args.p = first_hop ? 1 : 0;
+      t.args.links = c.links + (size_t)t.args.p * c.link_block;
+      t.args.in = first_hop ? v : it.t;
+      t.args.out = first_hop ? it.t : (ph == 1 ? it.u : it.Mp);
+      t.args.x = first_hop ? nullptr : v;
+      t.args.a = first_hop ? 0.0 : c.A;
+      t.args.b = first_hop ? 1.0 : -1.0 / (4.0 * c.A);
+      t.phase = ph;
+      t.chunk0 = meta.phase_chunks[ph];
+      meta.phase_chunks[ph] += t.chunks;
+      by_phase[ph].push_back(with_tasks_scalars(t));
+    }
+  }
+  std::vector<BatchTask> tasks;
+  for (int ph = 0; ph < 4; ++ph) tasks.insert(tasks.end(), by_phase[ph].begin(), by_phase[ph].end());
+  return launch_tasks(tasks, meta, reinterpret_cast<BatchControl*>(ctl_ws), timeout_s, 0, s);
+}
+
+size_t batch_control_bytes() { return (sizeof(BatchControl) + 255) / 256 * 256; }
 
 // waits for `s` and reads the error flag the last batch on this workspace left
 int batch_status(void* ws, cudaStream_t s) {

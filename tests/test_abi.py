@@ -256,3 +256,27 @@ def test_slab_arguments_are_checked(bsm):
     # one face: X Y Z / 2 sites x 2 spins x d colours, complex
     assert bsm.bsm_face_bytes(ok, bsm.F64) == 4 * 4 * 4 // 2 * 2 * 3 * 16
     assert bsm.bsm_face_bytes(ok, bsm.F32) == 4 * 4 * 4 // 2 * 2 * 3 * 8
+
+
+def test_cg_batch_arguments_are_checked(bsm):
+    lat = bsm.lattice((4, 4, 4, 4), 3, bsm.FUND, 0.1)
+    A = 1 << 24
+    fb = bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR, bsm.F64)
+
+    def items(nrhs=2, lat_=lat, x=8 * A):
+        return bsm.cg_batch_items([(lat_, A, 2 * A, 4 * A, x, nrhs)])
+
+    assert bsm.bsm_cg_batch_workspace_bytes(items()) > 0
+    assert bsm.bsm_cg_batch_workspace_bytes(items(nrhs=3)) == 0           # nrhs a power of two <= 16
+    assert bsm.bsm_cg_batch_workspace_bytes(items(nrhs=32)) == 0
+    assert bsm.bsm_cg_batch_workspace_bytes(items(lat_=bsm.lattice((4, 4, 4, 4), 3, bsm.ADJ, 0.1))) == 0
+    assert bsm.bsm_cg_batch_workspace_bytes(items(x=4 * A + fb)) == 0      # b and x overlap
+    ws = 16 * A
+    opts = bsm.cg_opts(prec_inner=bsm.F32)
+    for bad, want in ((bsm.cg_opts(prec_inner=bsm.F64), bsm.EUNSUPPORTED),
+                      (bsm.cg_opts(prec_inner=bsm.F32, eo=False), bsm.EUNSUPPORTED),
+                      (bsm.cg_opts(prec_inner=bsm.F32, tol=0.0), bsm.EINVAL),
+                      (bsm.cg_opts(prec_inner=bsm.F32, prec_outer=bsm.F32), bsm.EUNSUPPORTED)):
+        assert bsm._lib.bsm_cg_solve_batch(items(), 1, ctypes.byref(bad), None, ws, 1 << 40, None) == want
+    assert bsm._lib.bsm_cg_solve_batch(items(), 1, ctypes.byref(opts), None, ws, 1024, None) == bsm.EWORKSPACE
+    assert bsm._lib.bsm_cg_solve_batch(items(), 0, ctypes.byref(opts), None, ws, 1 << 40, None) == bsm.EINVAL

@@ -591,6 +591,7 @@ def run_ours(args):
         out["batch"] = run_batch(max(3, min(args.steps, 20)), flush)
         out["batch_small"] = run_batch(max(3, min(args.steps, 20)), flush, BATCH_SMALL)
         out["cg_small_graph"] = run_cg_graph(args.cg_max_iter)
+        out["cg_batch"] = run_cg_batch(max_iter=args.cg_max_iter)
     if rank == 0 and not args.no_precond:
         out["precond"] = run_precond(peak, peak_src, args.steps)
     if rank == 0 and not args.no_cg:
@@ -633,6 +634,12 @@ def run_ours(args):
                              "best_mixed_s": c[c["best_mixed"]]["seconds"],
                              "fp64_over_mixed_time": c.get("fp64_over_mixed_time"), "iters": cg_iters,
                              "true_res_normal": c[c["best_mixed"]]["true_res_normal"]}
+    if "cg_batch" in out:
+        c = out["cg_batch"]
+        out["cg_batch_summary"] = {"systems": c["systems"], "batched_s": c["batched"]["seconds"],
+                                   "per_system_mixed_s": c["per_system_mixed"]["seconds"],
+                                   "per_system_fp64_s": c["per_system_fp64"]["seconds"],
+                                   "true_res_normal_max": c["batched"]["true_res_normal_max"]}
     out["links_to_rep_ms_f32"] = round(links_ms, 3)
     barrier(world)
     if rank == 0:
@@ -771,6 +778,78 @@ def run_batch(steps, flush, shapes=BATCH_SHAPES):
         ms = total / steps
         res[name] = {"ms": round(ms, 4), "gflops": round(flop / (ms * 1e-3) / 1e9, 1)}
     res["status"] = bsm.bsm_strerror(bsm.bsm_dslash_batch_status(ws))
+    return res
+
+
+def run_cg_batch(shapes=None, nrhs=None, max_iter=20000):
+    """The uneven batch (16 lattices 8^4 .. 24^3 x 48, SU(2) and SU(3)
+    fundamental, smooth links eps = 0.3, m0 = 0.1, 8 Gaussian RHS each): all
+    128 systems to 1e-10 by the batched mixed-precision CG (one persistent
+    launch of Dhat^+ Dhat for the whole batch per iteration, graph-replayed
+    iterations, double-float reliable updates), against the same
+    mixed-precision solver called once per system, and against plain FP64 CG
+    once per system, on the same GPU."""
+    import torch
+    from paper_1401_3733_gb300 import bsm, fields
+
+    shapes = shapes or BATCH_SHAPES
+    nrhs = nrhs or BATCH_NRHS
+    entries = []
+    for k, (dims, N) in enumerate(shapes):
+        lat = bsm.lattice(dims, N, bsm.FUND, 0.1, (math.pi, 0, 0, 0))
+        Ud = torch.from_numpy(fields.gauge_field(dims, N, "smooth", seed=20 + k, eps=0.3)).cuda()
+        L = {p: bsm.empty_field(lat, bsm.FIELD_LINKS, p) for p in (bsm.F32, bsm.DF64, bsm.F64)}
+        for p, t in L.items():
+            bsm.bsm_links_to_rep(lat, Ud, t, p)
+        del Ud
+        fb = bsm.bsm_field_bytes(lat, bsm.FIELD_SPINOR, bsm.F64)
+        b = torch.empty(nrhs * fb, dtype=torch.uint8, device="cuda")
+        src = fields.device_gaussian_spinors(dims, N, nrhs, seed=40 + k)
+        for r in range(nrhs):
+            bsm.bsm_pack_spinor(lat, src[r], b[r * fb:(r + 1) * fb], bsm.F64)
+        del src
+        entries.append((lat, L, b, torch.zeros_like(b), fb))
+    stream = torch.cuda.Stream()
+    res = {"lattices": len(entries), "nrhs": nrhs, "systems": len(entries) * nrhs,
+           "sites": int(sum(np.prod(d) for d, _ in shapes))}
+    # batched
+    items = bsm.cg_batch_items([(lat, L[bsm.DF64], L[bsm.F32], b, x, nrhs) for lat, L, b, x, fb in entries])
+    ws = torch.empty(bsm.bsm_cg_batch_workspace_bytes(items), dtype=torch.uint8, device="cuda")
+    opts = bsm.cg_opts(tol=1e-10, max_iter=max_iter, prec_inner=bsm.F32, prec_outer=bsm.DF64, delta=CG_DELTA,
+                       check_every=CG_CHECK_EVERY, use_graph=True)
+    best = None
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, stats = bsm.bsm_cg_solve_batch(items, opts, ws, stream=stream, raise_on_error=False)
+        el = time.perf_counter() - t0
+        best = el if best is None or el < best else best
+    res["batched"] = {"status": bsm.bsm_strerror(st), "seconds": round(best, 4),
+                      "iters_max": max(s.iters for s in stats),
+                      "true_res_normal_max": max(s.true_res_normal for s in stats),
+                      "true_res_full_max": max(s.true_res_full for s in stats),
+                      "reliable_updates_total": sum(s.reliable_updates for s in stats)}
+    del ws
+    # one solve per system: the same mixed solver, and plain FP64 CG
+    for name, inner, outer in (("per_system_mixed", bsm.F32, bsm.DF64), ("per_system_fp64", bsm.F64, bsm.F64)):
+        total, iters, worst = 0.0, 0, 0.0
+        for lat, L, b, x, fb in entries:
+            ws1 = torch.empty(bsm.bsm_workspace_bytes(lat, bsm.CALL_CG, inner), dtype=torch.uint8, device="cuda")
+            for r in range(nrhs):
+                x1 = torch.zeros(fb, dtype=torch.uint8, device="cuda")
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, s1 = bsm.bsm_cg_solve(lat, L[outer], L[bsm.F32], b[r * fb:(r + 1) * fb], x1,
+                                          bsm.cg_opts(tol=1e-10, max_iter=max_iter, prec_inner=inner,
+                                                      prec_outer=outer, delta=CG_DELTA,
+                                                      check_every=CG_CHECK_EVERY), ws1, raise_on_error=False)
+                total += time.perf_counter() - t0
+                iters = max(iters, s1.iters)
+                worst = max(worst, s1.true_res_normal)
+            del ws1
+        res[name] = {"seconds": round(total, 4), "iters_max": iters, "true_res_normal_max": worst}
+    res["per_system_mixed_over_batched"] = round(res["per_system_mixed"]["seconds"] / res["batched"]["seconds"], 3)
+    res["fp64_over_batched"] = round(res["per_system_fp64"]["seconds"] / res["batched"]["seconds"], 3)
     return res
 
 

@@ -43,11 +43,15 @@ constexpr int kBtBlockElems = kBtThreads * 8;  // float4 elements per block of a
 
 struct SysState {
   double rr, rr_max, rr_prev, pAp, alpha, beta, stop2, rhs2;
+  double rr_true;   // |bp - M x|^2 of the last reliable update
+  double res_full;  // |b - D x|^2 at the end
   float alpha_f, beta_f;
   int active;       // 1: iterating; 0: stopped (zero steps)
   int want_update;  // the residual fell by delta or below the stop: reliable update at the next host check
   int nan;
-  int iters;
+  int iters;        // iterations taken while active
+  int updates;      // reliable updates
+  int stop_iter;    // iterations when it stopped
 };
 
 struct BtItem {
@@ -118,19 +122,50 @@ __global__ void __launch_bounds__(kBtThreads) bt_xr_kernel(const __grid_constant
   bt_block_partials(acc, I.nrhs, part + (size_t)blockIdx.x * kMaxRhs);
 }
 
+constexpr int kSumThreads = 128;  // threads that sum one system's block partials
+
+// sum over the item's blocks of one system's partials, in a fixed order:
+// thread t adds blocks t, t + 128, ..., then a fixed shuffle and warp tree;
+// the result is valid in thread 0
 __device__ double bt_sum(const BtTable& T, const double* part, int k, int r) {
   const BtItem& I = T.it[k];
   double s = 0.0;
-  for (int b = 0; b < I.nblk; ++b) s += part[(size_t)(I.blk0 + b) * kMaxRhs + r];
-  return s;
+  for (int b = threadIdx.x; b < I.nblk; b += kSumThreads) s += part[(size_t)(I.blk0 + b) * kMaxRhs + r];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double w[kSumThreads / 32];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int j = 0; j < kSumThreads / 32; ++j) t += w[j];
+  return t;
 }
 
-// one thread per system: alpha_s = |r|^2 / |Dhat p|^2 (zero for a stopped system)
-__global__ void bt_alpha_kernel(const __grid_constant__ BtTable T, SysState* st, const double* part) {
-  const int k = blockIdx.x, r = threadIdx.x;
+// fixed-order sum of part[0..n) by one block of kSumThreads threads; valid in thread 0
+__device__ double block_sum_fixed(const double* part, int n) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < n; b += kSumThreads) s += part[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double w[kSumThreads / 32];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int j = 0; j < kSumThreads / 32; ++j) t += w[j];
+  __syncthreads();
+  return t;
+}
+
+// one block per system (grid: items x 16): alpha_s = |r|^2 / |Dhat p|^2 (zero for a stopped system)
+__global__ void __launch_bounds__(kSumThreads) bt_alpha_kernel(const __grid_constant__ BtTable T, SysState* st,
+                                                               const double* part) {
+  const int k = blockIdx.x, r = blockIdx.y;
   if (r >= T.it[k].nrhs) return;
-  SysState& S = st[T.it[k].sys0 + r];
   const double pAp = bt_sum(T, part, k, r);
+  if (threadIdx.x != 0) return;
+  SysState& S = st[T.it[k].sys0 + r];
   S.pAp = pAp;
   double a = 0.0;
   if (!isfinite(pAp)) S.nan = 1;
@@ -139,12 +174,14 @@ __global__ void bt_alpha_kernel(const __grid_constant__ BtTable T, SysState* st,
   S.alpha_f = (float)a;
 }
 
-// one thread per system: the new |r|^2, beta_s, the reliable-update trigger
-__global__ void bt_beta_kernel(const __grid_constant__ BtTable T, SysState* st, const double* part, double delta2) {
-  const int k = blockIdx.x, r = threadIdx.x;
+// one block per system: the new |r|^2, beta_s, the reliable-update trigger
+__global__ void __launch_bounds__(kSumThreads) bt_beta_kernel(const __grid_constant__ BtTable T, SysState* st,
+                                                              const double* part, double delta2) {
+  const int k = blockIdx.x, r = blockIdx.y;
   if (r >= T.it[k].nrhs) return;
-  SysState& S = st[T.it[k].sys0 + r];
   const double rr = bt_sum(T, part, k, r);
+  if (threadIdx.x != 0) return;
+  SysState& S = st[T.it[k].sys0 + r];
   if (!S.active) {
     S.beta = 0.0;
     S.beta_f = 0.f;
@@ -208,14 +245,57 @@ __global__ void __launch_bounds__(kBtThreads) slot_dots_kernel(const float4* rv,
   block_sums_store_f32<kBtThreads, 2>(v, part, gridDim.x);
 }
 
-// p[slot] -= (<r, p> / <r, r>) r[slot] (sums of the partials in a fixed order, by every thread)
+// c = -<r, p> / <r, r> from the slot_dots partials (one thread, fixed order)
+__global__ void __launch_bounds__(kSumThreads) slot_coef_kernel(const double* part, int nb, float* c) {
+  const double rp = block_sum_fixed(part, nb);
+  const double rr = block_sum_fixed(part + nb, nb);
+  if (threadIdx.x == 0) *c = rr > 0.0 ? (float)(-rp / rr) : 0.f;
+}
+
+// p[slot] += c r[slot]
 __global__ void __launch_bounds__(kBtThreads) slot_project_kernel(float4* pv, const float4* rv, long long n32, int nrhs,
-                                                                  int r, const double* part, int nb) {
-  double rp = 0.0, rr = 0.0;
-  for (int b = 0; b < nb; ++b) rp += part[b], rr += part[nb + b];
-  const float c = rr > 0.0 ? (float)(-rp / rr) : 0.f;
+                                                                  int r, const float* cp) {
+  const float c = *cp;
   for (long long k = blockIdx.x * (long long)kBtThreads + threadIdx.x; k < n32; k += (long long)gridDim.x * kBtThreads)
     pv[k * nrhs + r] = axpy4(c, rv[k * nrhs + r], pv[k * nrhs + r]);
+}
+
+// the reliable update's outcome for one system, on the device: stop once the
+// recomputed residual (summed from the partials in a fixed order) is below
+// the bound, else continue from it (beta from the last iterated residual)
+__global__ void __launch_bounds__(kSumThreads) sys_update_kernel(SysState* st, int sys, const double* part, int nb) {
+  const double rr = block_sum_fixed(part, nb);
+  if (threadIdx.x != 0) return;
+  SysState& S = st[sys];
+  S.rr_true = rr;
+  ++S.updates;
+  S.want_update = 0;
+  if (!isfinite(rr)) {
+    S.nan = 1;
+    S.active = 0;
+    return;
+  }
+  if (rr <= S.stop2) {
+    S.active = 0;
+    S.rr = rr;
+    S.stop_iter = S.iters;
+    return;
+  }
+  S.beta = S.rr_prev > 0.0 ? rr / S.rr_prev : 0.0;
+  S.beta_f = (float)S.beta;
+  S.rr = S.rr_max = rr;
+}
+
+// the true residual of a system at the end (partials of |bp - M x|^2 and |b - D x|^2)
+__global__ void __launch_bounds__(kSumThreads) sys_final_kernel(SysState* st, int sys, const double* part_n, int nn,
+                                                                const double* part_f, int nf) {
+  const double a = block_sum_fixed(part_n, nn);
+  const double b = block_sum_fixed(part_f, nf);
+  if (threadIdx.x != 0) return;
+  SysState& S = st[sys];
+  S.rr_true = a;
+  S.res_full = b;
+  if (S.active) S.stop_iter = S.iters;
 }
 
 int slot_blocks(long long n) {
@@ -395,14 +475,13 @@ struct BatchSolver {
     return BSM_OK;
   }
 
-  // r64 (in thc) = bp - M x_e of system (k, r); |r64|^2 -> scal[0]
-  int true_residual(int k, int r) {
+  // r64 (in thc) = bp - M x_e of system (k, r); partials of |r64|^2 in
+  // part_out; returns their count (or < 0)
+  int true_residual(int k, int r, double* part_out) {
     const ItemPlan& P = plan[k];
     int rc = apply_normal_outer(k, x_of(k, r), thc);
     if (rc != BSM_OK) return rc;
-    const int n = axpby_launch(BSM_F64, 1.0, P.bp[r], -1.0, thc, P.half64 / 16, opart, s);
-    reduce_launch(opart, n, scal, s);
-    return BSM_OK;
+    return axpby_launch(BSM_F64, 1.0, P.bp[r], -1.0, thc, P.half64 / 16, part_out, s);
   }
 
   // restart the FP32 residual of (k, r) from r64 (thc) and re-project p against it
@@ -412,7 +491,9 @@ struct BatchSolver {
     const int nr = items[k].nrhs, nb = slot_blocks(n32);
     slot_conv_kernel<<<nb, kBtThreads, 0, s>>>(P.r32, reinterpret_cast<const double2*>(thc), n32, nr, r);
     slot_dots_kernel<<<nb, kBtThreads, 0, s>>>(P.r32, P.p32, n32, nr, r, opart);
-    slot_project_kernel<<<nb, kBtThreads, 0, s>>>(P.p32, P.r32, n32, nr, r, opart, nb);
+    float* c = reinterpret_cast<float*>(scal + 8);
+    slot_coef_kernel<<<1, kSumThreads, 0, s>>>(opart, nb, c);
+    slot_project_kernel<<<nb, kBtThreads, 0, s>>>(P.p32, P.r32, n32, nr, r, c);
   }
 
   // one iteration of every system
@@ -422,10 +503,10 @@ struct BatchSolver {
     int rc = batch_normal_launch(nitems.data(), count, w + y.ctl, 1.0, s);
     if (rc != BSM_OK) return rc;
     bt_norm_u_kernel<<<nb, kBtThreads, 0, s>>>(T, part);
-    bt_alpha_kernel<<<count, kMaxRhs, 0, s>>>(T, st, part);
+    bt_alpha_kernel<<<dim3(count, kMaxRhs), kSumThreads, 0, s>>>(T, st, part);
     bt_xr_kernel<<<nb, kBtThreads, 0, s>>>(T, st, part);
     const double delta = o.delta > 0 ? o.delta : 0.1;
-    bt_beta_kernel<<<count, kMaxRhs, 0, s>>>(T, st, part, delta * delta);
+    bt_beta_kernel<<<dim3(count, kMaxRhs), kSumThreads, 0, s>>>(T, st, part, delta * delta);
     return BSM_OK;
   }
 };
@@ -443,7 +524,6 @@ int cg_solve_batch(const bsm_cg_batch_item* items, int count, const bsm_cg_opts&
   const int nsys = B.y.nsys;
   const int check = o.check_every > 0 ? o.check_every : 8;
   std::vector<SysState> hs(nsys);
-  std::vector<int> updates(nsys, 0), stop_iter(nsys, 0);
   std::vector<double> b2(nsys, 0.0);
   int rc = BSM_OK;
 
@@ -490,6 +570,10 @@ int cg_solve_batch(const bsm_cg_batch_item* items, int count, const bsm_cg_opts&
   }
 
   int status = BSM_OK, iter = 0;
+  auto read_states = [&]() -> int {
+    cudaMemcpyAsync(hs.data(), B.st, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, s);
+    return cudaStreamSynchronize(s) == cudaSuccess ? BSM_OK : BSM_ECUDA;
+  };
   for (;;) {
     int running = 0;
     for (const SysState& S : hs) running += S.active;
@@ -508,50 +592,33 @@ int cg_solve_batch(const bsm_cg_batch_item* items, int count, const bsm_cg_opts&
         if ((rc = B.iterate()) != BSM_OK) return rc;
     }
     iter += check;
-    if ((rc = batch_status(B.w + B.y.ctl, s)) != BSM_OK) {
+    if ((rc = batch_status(B.w + B.y.ctl, s)) != BSM_OK || (rc = read_states()) != BSM_OK) {
       if (exec) cudaGraphExecDestroy(exec);
       return rc;
     }
-    cudaMemcpyAsync(hs.data(), B.st, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return BSM_ECUDA;
-    bool changed = false;
+    // reliable updates of the systems that asked for one, queued without a
+    // host round trip (the outcome is decided on the device)
+    int queued = 0;
     for (int k = 0, sys = 0; k < count; ++k)
       for (int r = 0; r < items[k].nrhs; ++r, ++sys) {
-        SysState& S = hs[sys];
-        if (S.nan) {
-          status = BSM_ENAN;
-          continue;
-        }
-        if (!S.active || !S.want_update) continue;
-        // reliable update at the outer precision
+        const SysState& S = hs[sys];
+        if (S.nan) status = BSM_ENAN;
+        if (!S.active || !S.want_update || S.nan) continue;
         const ItemPlan& P = B.plan[k];
         const long long n32 = (long long)(P.half32 / 16);
         slot_acc_kernel<<<slot_blocks(n32), kBtThreads, 0, s>>>(reinterpret_cast<double2*>(B.x_of(k, r)), P.x32, n32,
                                                                items[k].nrhs, r);
-        if ((rc = B.true_residual(k, r)) != BSM_OK) return rc;
-        double rr_true = 0.0;
-        if ((rc = B.host_scalar(B.scal, &rr_true)) != BSM_OK) return rc;
-        ++updates[sys];
-        changed = true;
-        if (!isfinite(rr_true)) {
-          status = BSM_ENAN;
-          S.active = 0;
-          continue;
-        }
-        if (rr_true <= S.stop2) {  // converged: zero steps from now on
-          S.active = 0;
-          S.rr = rr_true;
-          stop_iter[sys] = S.iters;
-        } else {
-          B.restart_slot(k, r);
-          S.beta = S.rr_prev > 0.0 ? rr_true / S.rr_prev : 0.0;
-          S.beta_f = (float)S.beta;
-          S.rr = S.rr_max = rr_true;
-        }
-        S.want_update = 0;
+        const int n = B.true_residual(k, r, B.opart + kBlasMaxBlocks);
+        if (n < 0) return n;
+        B.restart_slot(k, r);
+        sys_update_kernel<<<1, kSumThreads, 0, s>>>(B.st, sys, B.opart + kBlasMaxBlocks, n);
+        ++queued;
       }
     if (status == BSM_ENAN) break;
-    if (changed) cudaMemcpyAsync(B.st, hs.data(), sizeof(SysState) * nsys, cudaMemcpyHostToDevice, s);
+    if (queued && (rc = read_states()) != BSM_OK) {
+      if (exec) cudaGraphExecDestroy(exec);
+      return rc;
+    }
   }
   if (exec) cudaGraphExecDestroy(exec);
 
@@ -560,15 +627,13 @@ int cg_solve_batch(const bsm_cg_batch_item* items, int count, const bsm_cg_opts&
     const ItemPlan& P = B.plan[k];
     const size_t h = P.half64;
     for (int r = 0; r < items[k].nrhs; ++r, ++sys) {
-      if (hs[sys].active) {  // not converged: fold in the last FP32 steps
+      if (hs[sys].active) {  // not stopped: fold in the last FP32 steps
         const long long n32 = (long long)(P.half32 / 16);
         slot_acc_kernel<<<slot_blocks(n32), kBtThreads, 0, s>>>(reinterpret_cast<double2*>(B.x_of(k, r)), P.x32,
                                                                n32, items[k].nrhs, r);
-        stop_iter[sys] = hs[sys].iters;
       }
-      if ((rc = B.true_residual(k, r)) != BSM_OK) return rc;
-      double rr_true = 0.0;
-      if ((rc = B.host_scalar(B.scal, &rr_true)) != BSM_OK) return rc;
+      const int nn = B.true_residual(k, r, B.opart);
+      if (nn < 0) return nn;
       char* x = B.x_of(k, r);
       const char* b = B.b_of(k, r);
       if (B.po == BSM_DF64) {
@@ -586,19 +651,22 @@ int cg_solve_batch(const bsm_cg_batch_item* items, int count, const bsm_cg_opts&
           return rc;
         if ((rc = op_dirac(P.co, x, B.tfa, 0, nullptr, nullptr)) < 0) return rc;
       }
-      const int n = axpby_launch(BSM_F64, -1.0, b, 1.0, B.tfa, 2 * h / 16, B.opart, s);
-      reduce_launch(B.opart, n, B.scal + 1, s);
-      double res_full = 0.0;
-      if ((rc = B.host_scalar(B.scal + 1, &res_full)) != BSM_OK) return rc;
-      if (stats) {
-        bsm_cg_stats& Q = stats[sys];
-        Q.iters = stop_iter[sys];
-        Q.reliable_updates = updates[sys];
-        Q.true_res_normal = hs[sys].rhs2 > 0 ? sqrt(rr_true / hs[sys].rhs2) : 0.0;
-        Q.true_res_full = b2[sys] > 0 ? sqrt(res_full / b2[sys]) : 0.0;
-      }
-      if (status == BSM_OK && !(hs[sys].rhs2 == 0.0 || rr_true <= o.tol * o.tol * hs[sys].rhs2)) status = BSM_ENOCONV;
+      const int nf = axpby_launch(BSM_F64, -1.0, b, 1.0, B.tfa, 2 * h / 16, B.opart + kBlasMaxBlocks, s);
+      sys_final_kernel<<<1, kSumThreads, 0, s>>>(B.st, sys, B.opart, nn, B.opart + kBlasMaxBlocks, nf);
     }
+  }
+  cudaMemcpyAsync(hs.data(), B.st, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return BSM_ECUDA;
+  for (int sys = 0; sys < nsys; ++sys) {
+    const SysState& S = hs[sys];
+    if (stats) {
+      bsm_cg_stats& Q = stats[sys];
+      Q.iters = S.stop_iter;
+      Q.reliable_updates = S.updates;
+      Q.true_res_normal = S.rhs2 > 0 ? sqrt(S.rr_true / S.rhs2) : 0.0;
+      Q.true_res_full = b2[sys] > 0 ? sqrt(S.res_full / b2[sys]) : 0.0;
+    }
+    if (status == BSM_OK && !(S.rhs2 == 0.0 || S.rr_true <= o.tol * o.tol * S.rhs2)) status = BSM_ENOCONV;
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats)

@@ -12,14 +12,13 @@
 // channels x 4 spins complex FP32, so that one layer is a transport kernel
 // writing X (rows x 9 C 4 complex: the 9 transported copies of every channel)
 // followed by a dense GEMM Y = X W (K = 9 C 4, N = C_out 4) that every site
-// shares: a genuine dense contraction, run by cuBLAS (complex FP32 for
-// training; realified BF16 with FP32 accumulation for inference).  Training:
-// the complex gradients G_W = X^H G_Y, G_X = G_Y W^H (cuBLAS) and the adjoint
+// shares: a genuine dense contraction, run by the tall-skinny kernels of
+// ptc_gemm.cu (complex FP32 for training; realified BF16 with FP32
+// accumulation for inference).  Training: the complex gradients
+// G_W = X^H G_Y (split over the rows), G_X = G_Y W^H and the adjoint
 // transport G_phi(y) = G_0(y) + sum_mu [U_mu(y-mu)^+ G_{+mu}(y-mu) +
 // U_mu(y) G_{-mu}(y+mu)] (below), then Adam.
-#include <cublas_v2.h>
 #include <math.h>
-#include <mutex>
 
 #include "blas.cuh"
 #include "operators.cuh"
@@ -27,6 +26,11 @@
 namespace bsm {
 
 bool ptc_fused_supported(int C);
+int ptc_crow_gemm(const void* A, const void* B, void* C, long long rows, int K, int N, bool b_herm, cudaStream_t s);
+int ptc_cred_gemm(const void* A, const void* B, void* C, long long rows, int M, int N, void* scratch,
+                  cudaStream_t s);
+int ptc_brow_gemm(const void* A, const void* B, void* C, long long rows, int K, int N, bool out_bf16,
+                  cudaStream_t s);
 size_t ptc_fused_weight_bytes(int C);
 int ptc_fused_apply(const char* links, size_t link_block, int d, int C, const void* F, const void* W1,
                     const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, bool even_only,
@@ -35,20 +39,6 @@ int ptc_fused_apply(const char* links, size_t link_block, int d, int C, const vo
 namespace {
 
 constexpr int kPtcThreads = 128;
-
-// ---------------------------------------------------------------------------
-// cuBLAS handle per device (created once; cuBLAS's own workspace is set to a
-// slice of the caller's workspace on every call)
-// ---------------------------------------------------------------------------
-std::mutex g_blas_mu;
-cublasHandle_t g_blas[64] = {};
-
-cublasHandle_t blas_handle() {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  if (g_blas[dev] == nullptr && cublasCreate(&g_blas[dev]) != CUBLAS_STATUS_SUCCESS) g_blas[dev] = nullptr;
-  return g_blas[dev];
-}
 
 struct PtcGeom {
   Geom g;
@@ -327,34 +317,8 @@ void launch_permute(const void* src, void* dst, int Ci, int Co, bool back, cudaS
                                                       reinterpret_cast<float2*>(dst), Ci, Co, back ? 1 : 0);
 }
 
-constexpr size_t kBlasWs = size_t(32) << 20;
+constexpr size_t kGemmScratch = size_t(32) << 20;  // split-K partials of the weight gradients
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
-
-// row-major C(MxN) = op(A) op(B), op = identity or conjugate transpose, complex FP32
-bool cgemm_rm(cublasHandle_t h, bool ah, bool bh, int M, int N, int K, const void* A, int lda, const void* B,
-              int ldb, void* Cm, int ldc) {
-  // column-major view: C^T (N x M) = op(B)^T op(A)^T
-  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
-  return cublasCgemm(h, bh ? CUBLAS_OP_C : CUBLAS_OP_N, ah ? CUBLAS_OP_C : CUBLAS_OP_N, N, M, K, &one,
-                     reinterpret_cast<const cuComplex*>(B), ldb, reinterpret_cast<const cuComplex*>(A), lda, &zero,
-                     reinterpret_cast<cuComplex*>(Cm), ldc) == CUBLAS_STATUS_SUCCESS;
-}
-
-// row-major real C(M x N) = A(M x K) B(K x N), A and B BF16, FP32 accumulation, C in ctype
-bool bgemm_rm(cublasHandle_t h, int M, int N, int K, const void* A, const void* B, void* Cm, cudaDataType ctype) {
-  const float one = 1.f, zero = 0.f;
-  return cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, N, M, K, &one, B, CUDA_R_16BF, N, A, CUDA_R_16BF, K, &zero, Cm,
-                      ctype, N, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT) == CUBLAS_STATUS_SUCCESS;
-}
-
-// the handle of this device, bound to stream s and to the workspace slice; null on failure
-cublasHandle_t bind_blas(void* blas_ws, cudaStream_t s) {
-  cublasHandle_t h = blas_handle();
-  if (h == nullptr || cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS ||
-      cublasSetWorkspace(h, blas_ws, kBlasWs) != CUBLAS_STATUS_SUCCESS)
-    return nullptr;
-  return h;
-}
 
 }  // namespace
 
@@ -363,7 +327,7 @@ cublasHandle_t bind_blas(void* blas_ws, cudaStream_t s) {
 // 4C x 36); out = sum_k T_k Z2_k.  Both intermediates of width 9 x 4 are far
 // narrower than the 9 x 4C transports of a C-channel field.
 struct PtcLayout {
-  size_t X1, Y1, Z2, W2p, W1r, W2r, Wt, G, GZ2, GY1, GW2p, invn, part, blasws, total;
+  size_t X1, Y1, Z2, W2p, W1r, W2r, Wt, G, GZ2, GY1, GW2p, invn, part, scratch, total;
 };
 
 PtcLayout ptc_layout(const bsm_lattice& L, int C, int nb, bool train) {
@@ -388,7 +352,7 @@ PtcLayout ptc_layout(const bsm_lattice& L, int C, int nb, bool train) {
     y.invn = o; o = al(o + (size_t)(nb + 1) * 8);  // 1/|e_b|^2, then the loss
     y.part = o; o = al(o + (size_t)kBlasMaxBlocks * 8);
   }
-  y.blasws = o; o = al(o + kBlasWs);
+  y.scratch = o; o = al(o + kGemmScratch);
   y.total = o;
   return y;
 }
@@ -432,14 +396,12 @@ int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void*
   if (bf && ptc_fused_supported(C))
     return ptc_fused_apply(c.links, c.link_block, c.d, C, in, W1, w + y.W2p, w + y.Wt, w + y.Z2, out, c.g, nb,
                            even_only, s);
-  std::lock_guard<std::mutex> lock(g_blas_mu);
-  cublasHandle_t h = bind_blas(w + y.blasws, s);
-  if (h == nullptr) return BSM_ECUDA;
   launch_transport(c, in, w + y.X1, nb, 1, bf, false, s);
+  int rc;
   if (!bf) {
-    if (!cgemm_rm(h, false, false, rows, 4 * C, 36, w + y.X1, 36, W1, 4 * C, w + y.Y1, 4 * C) ||
-        !cgemm_rm(h, false, false, rows, 36, 4 * C, w + y.Y1, 4 * C, w + y.W2p, 36, w + y.Z2, 36))
-      return BSM_ECUDA;
+    if ((rc = ptc_crow_gemm(w + y.X1, W1, w + y.Y1, rows, 36, 4 * C, false, s)) != BSM_OK ||
+        (rc = ptc_crow_gemm(w + y.Y1, w + y.W2p, w + y.Z2, rows, 4 * C, 36, false, s)) != BSM_OK)
+      return rc;
   } else {
     __nv_bfloat16* w1r = reinterpret_cast<__nv_bfloat16*>(w + y.W1r);
     __nv_bfloat16* w2r = reinterpret_cast<__nv_bfloat16*>(w + y.W2r);
@@ -447,9 +409,9 @@ int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void*
     ptc_realify_kernel<<<(4 * C * 36 + 127) / 128, 128, 0, s>>>(reinterpret_cast<const float2*>(w + y.W2p), w2r,
                                                                 4 * C, 36);
     // Y1 in BF16 (it is only an operand of the second GEMM), Z2 in FP32
-    if (!bgemm_rm(h, rows, 2 * 4 * C, 2 * 36, w + y.X1, w1r, w + y.Y1, CUDA_R_16BF) ||
-        !bgemm_rm(h, rows, 2 * 36, 2 * 4 * C, w + y.Y1, w2r, w + y.Z2, CUDA_R_32F))
-      return BSM_ECUDA;
+    if ((rc = ptc_brow_gemm(w + y.X1, w1r, w + y.Y1, rows, 2 * 36, 2 * 4 * C, true, s)) != BSM_OK ||
+        (rc = ptc_brow_gemm(w + y.Y1, w2r, w + y.Z2, rows, 2 * 4 * C, 2 * 36, false, s)) != BSM_OK)
+      return rc;
   }
   launch_stencil(c, w + y.Z2, out, nb, 1, s);
   return BSM_OK;
@@ -463,16 +425,14 @@ int ptc_loss_grad(const bsm_lattice& L, const void* U32, const void* W1, const v
   char* w = reinterpret_cast<char*>(ws);
   const int rows = (int)((long long)nb * 2 * c.g.Vh * c.d);
   double l = 0.0;
+  int rc;
   {
-    std::lock_guard<std::mutex> lock(g_blas_mu);
-    cublasHandle_t h = bind_blas(w + y.blasws, s);
-    if (h == nullptr) return BSM_ECUDA;
     // forward, keeping X1, Y1 and Z2; the output goes to G's slot
     launch_permute(W2, w + y.W2p, C, 1, false, s);
     launch_transport(c, r, w + y.X1, nb, 1, false, false, s);
-    if (!cgemm_rm(h, false, false, rows, 4 * C, 36, w + y.X1, 36, W1, 4 * C, w + y.Y1, 4 * C) ||
-        !cgemm_rm(h, false, false, rows, 36, 4 * C, w + y.Y1, 4 * C, w + y.W2p, 36, w + y.Z2, 36))
-      return BSM_ECUDA;
+    if ((rc = ptc_crow_gemm(w + y.X1, W1, w + y.Y1, rows, 36, 4 * C, false, s)) != BSM_OK ||
+        (rc = ptc_crow_gemm(w + y.Y1, w + y.W2p, w + y.Z2, rows, 4 * C, 36, false, s)) != BSM_OK)
+      return rc;
     launch_stencil(c, w + y.Z2, w + y.G, nb, 1, s);
     // loss and G = dloss/dout (in place)
     const long long per = (long long)rows / nb * 4, n = (long long)rows * 4;
@@ -486,10 +446,10 @@ int ptc_loss_grad(const bsm_lattice& L, const void* U32, const void* W1, const v
     reduce_launch(part, lb, invn + nb, s);
     // backward: G_Z2 = T^+ G; G_W2p = Y1^H G_Z2; G_Y1 = G_Z2 W2p^H; G_W1 = X1^H G_Y1
     launch_transport(c, w + y.G, w + y.GZ2, nb, 1, false, true, s);
-    if (!cgemm_rm(h, true, false, 4 * C, 36, rows, w + y.Y1, 4 * C, w + y.GZ2, 36, w + y.GW2p, 36) ||
-        !cgemm_rm(h, false, true, rows, 4 * C, 36, w + y.GZ2, 36, w + y.W2p, 36, w + y.GY1, 4 * C) ||
-        !cgemm_rm(h, true, false, 36, 4 * C, rows, w + y.X1, 36, w + y.GY1, 4 * C, GW1, 4 * C))
-      return BSM_ECUDA;
+    if ((rc = ptc_cred_gemm(w + y.Y1, w + y.GZ2, w + y.GW2p, rows, 4 * C, 36, w + y.scratch, s)) != BSM_OK ||
+        (rc = ptc_crow_gemm(w + y.GZ2, w + y.W2p, w + y.GY1, rows, 36, 4 * C, true, s)) != BSM_OK ||
+        (rc = ptc_cred_gemm(w + y.X1, w + y.GY1, GW1, rows, 36, 4 * C, w + y.scratch, s)) != BSM_OK)
+      return rc;
     launch_permute(w + y.GW2p, GW2, C, 1, true, s);
     if (cudaMemcpyAsync(&l, invn + nb, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

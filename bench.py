@@ -974,30 +974,115 @@ def run_large(steps, peak, peak_kind, max_iter):
 
 # learned preconditioner workload: 16^3 x 32 SU(3), smooth links exp(i 0.5 H);
 # m0 = -0.62 is where the Lanczos estimate of cond(Dhat^+ Dhat) peaks on this
-# ensemble (about 1.4e3); training on four 8^3 x 16 configurations of the
-# same ensemble, evaluation on a held-out 16^3 x 32 one
+# ensemble (about 1.4e3).  Training pairs come from plain FP64 CG iterates on
+# 50 configurations of the ensemble at 8^3 x 16 (the network's two-hop
+# stencil is local, so a small volume carries its training signal), and the
+# solvers are evaluated on a held-out 16^3 x 32 configuration.
 PRECOND = dict(dims=(32, 16, 16, 16), train_dims=(16, 8, 8, 8), N=3, eps=0.5, m0=-0.62,
-               phase=(math.pi, 0.0, 0.0, 0.0), eval_seed=3, src_seed=4, train_seeds=(100, 101, 102, 103),
-               channels=12, steps=2500, batch=8, lr=3e-3, restart=32)
+               phase=(math.pi, 0.0, 0.0, 0.0), eval_seed=3, src_seed=4, train_seeds=tuple(range(100, 150)),
+               pair_sources=4, pair_iters=(2, 5, 10, 20, 40), channels=12, steps=2500, batch=8, lr=3e-3,
+               restart=32)
 
 
-def train_ptc(cfg, seed=7):
-    """Adam on loss = sum_b |M(D e_b) - e_b|^2 / |e_b|^2 with fresh Gaussian
-    e_b every step (cfg['steps'] x cfg['batch'] pairs), cycling over the
-    training configurations; D e by the library's FP64 operator."""
+def cg_pairs(cfg, seed=7):
+    """Residual/error pairs of D x = b from plain FP64 CG (bsm_cg_solve on the
+    even-odd normal equations): for each training configuration and Gaussian
+    source b, the converged x* (1e-12) and the iterates x_k after k
+    iterations (a solve stopped at max_iter = k); r_k = b - D x_k and
+    e_k = x* - x_k satisfy D e_k = r_k.  Returns, per configuration, its FP32
+    links and the pairs as one-channel PTC fields."""
     import torch
     from paper_1401_3733_gb300 import bsm, fields
 
-    dims, N, C, nb = cfg["train_dims"], cfg["N"], cfg["channels"], cfg["batch"]
+    dims, N = cfg["train_dims"], cfg["N"]
     lat = bsm.lattice(dims, N, bsm.FUND, cfg["m0"], cfg["phase"])
     V = int(np.prod(dims))
-    confs = []
+    fb = V * N * 4
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    ws = torch.empty(bsm.bsm_workspace_bytes(lat, bsm.CALL_CG, bsm.F64), dtype=torch.uint8, device="cuda")
+    b64, x64, xk, dx = (bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F64) for _ in range(4))
+    out, iters, t0 = [], [], time.perf_counter()
     for sd in cfg["train_seeds"]:
         Ud = torch.from_numpy(fields.gauge_field(dims, N, "smooth", seed=sd, eps=cfg["eps"])).cuda()
         l64, l32 = bsm.empty_field(lat, bsm.FIELD_LINKS, bsm.F64), bsm.empty_field(lat, bsm.FIELD_LINKS, bsm.F32)
         bsm.bsm_links_to_rep(lat, Ud, l64, bsm.F64)
         bsm.bsm_links_to_rep(lat, Ud, l32, bsm.F32)
-        confs.append((l64, l32))
+        npair = cfg["pair_sources"] * len(cfg["pair_iters"])
+        R = torch.empty(npair * fb, dtype=torch.complex64, device="cuda")
+        E = torch.empty_like(R)
+        j = 0
+        for _ in range(cfg["pair_sources"]):
+            bsm.bsm_pack_spinor(lat, torch.randn((V, 4, N), dtype=torch.complex128, device="cuda", generator=g),
+                                b64, bsm.F64)
+            x64.zero_()
+            _, st = bsm.bsm_cg_solve(lat, l64, None, b64, x64, bsm.cg_opts(tol=1e-12, max_iter=20000), ws)
+            iters.append(st.iters)
+            for k in cfg["pair_iters"]:
+                xk.zero_()
+                bsm.bsm_cg_solve(lat, l64, None, b64, xk, bsm.cg_opts(tol=1e-30, max_iter=k, check_every=1), ws,
+                                 raise_on_error=False)
+                bsm.bsm_dslash(lat, l64, xk, dx, bsm.FULL, 0, bsm.F64)
+                r = b64.view(torch.float64) - dx.view(torch.float64)           # r_k = b - D x_k
+                e = x64.view(torch.float64) - xk.view(torch.float64)           # e_k = x* - x_k
+                bsm.bsm_ptc_pack(lat, r.view(torch.uint8), R[j * fb:(j + 1) * fb])
+                bsm.bsm_ptc_pack(lat, e.view(torch.uint8), E[j * fb:(j + 1) * fb])
+                j += 1
+        out.append((l32, R, E, npair))
+    torch.cuda.synchronize()
+    return out, {"kind": "plain FP64 CG iterates: r_k = b - D x_k, e_k = x* - x_k", "pairs": len(out) * out[0][3],
+                 "configs": len(out), "sources_per_config": cfg["pair_sources"],
+                 "cg_iterates": list(cfg["pair_iters"]), "cg_iters_to_1e-12": [min(iters), max(iters)],
+                 "seconds": round(time.perf_counter() - t0, 2)}
+
+
+def synthetic_pairs(cfg, seed=7):
+    """Exact residual/error pairs of D x = b with a Gaussian error: e ~ N(0, 1)
+    per real component, r = D e (the library's FP64 operator), the same
+    number of pairs per training configuration as cg_pairs."""
+    import torch
+    from paper_1401_3733_gb300 import bsm, fields
+
+    dims, N = cfg["train_dims"], cfg["N"]
+    lat = bsm.lattice(dims, N, bsm.FUND, cfg["m0"], cfg["phase"])
+    V = int(np.prod(dims))
+    fb = V * N * 4
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    e64, r64 = bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F64), bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F64)
+    npair = cfg["pair_sources"] * len(cfg["pair_iters"])
+    out, t0 = [], time.perf_counter()
+    for sd in cfg["train_seeds"]:
+        Ud = torch.from_numpy(fields.gauge_field(dims, N, "smooth", seed=sd, eps=cfg["eps"])).cuda()
+        l64, l32 = bsm.empty_field(lat, bsm.FIELD_LINKS, bsm.F64), bsm.empty_field(lat, bsm.FIELD_LINKS, bsm.F32)
+        bsm.bsm_links_to_rep(lat, Ud, l64, bsm.F64)
+        bsm.bsm_links_to_rep(lat, Ud, l32, bsm.F32)
+        R = torch.empty(npair * fb, dtype=torch.complex64, device="cuda")
+        E = torch.empty_like(R)
+        for j in range(npair):
+            bsm.bsm_pack_spinor(lat, torch.randn((V, 4, N), dtype=torch.complex128, device="cuda", generator=g),
+                                e64, bsm.F64)
+            bsm.bsm_dslash(lat, l64, e64, r64, bsm.FULL, 0, bsm.F64)
+            bsm.bsm_ptc_pack(lat, e64, E[j * fb:(j + 1) * fb])
+            bsm.bsm_ptc_pack(lat, r64, R[j * fb:(j + 1) * fb])
+        out.append((l32, R, E, npair))
+    torch.cuda.synchronize()
+    return out, {"kind": "exact pairs r = D e, Gaussian e", "pairs": len(out) * npair, "configs": len(out),
+                 "seconds": round(time.perf_counter() - t0, 2)}
+
+
+def train_ptc(cfg, seed=7, pairs="synthetic"):
+    """Adam on loss = sum_b |M(r_b) - e_b|^2 / |e_b|^2 over a pool of
+    residual/error pairs (synthetic_pairs, or cg_pairs from plain FP64 CG):
+    each step takes a batch of pairs of one training configuration (cycling
+    over the configurations), cfg['steps'] x cfg['batch'] samples in all."""
+    import torch
+    from paper_1401_3733_gb300 import bsm
+
+    dims, N, C, nb = cfg["train_dims"], cfg["N"], cfg["channels"], cfg["batch"]
+    lat = bsm.lattice(dims, N, bsm.FUND, cfg["m0"], cfg["phase"])
+    V = int(np.prod(dims))
+    pool, pair_info = (cg_pairs if pairs == "cg" else synthetic_pairs)(cfg, seed)
     A = 4.0 + cfg["m0"]
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
@@ -1011,28 +1096,25 @@ def train_ptc(cfg, seed=7):
     v = [torch.zeros_like(t) for t in W]
     fb = V * N * 4
     R, E = (torch.empty(nb * fb, dtype=torch.complex64, device="cuda") for _ in range(2))
-    e64, r64 = bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F64), bsm.empty_field(lat, bsm.FIELD_SPINOR, bsm.F64)
     ws = torch.empty(bsm.bsm_ptc_workspace_bytes(lat, C, nb, 1), dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(seed)
     losses = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for step in range(1, cfg["steps"] + 1):
-        l64, l32 = confs[step % len(confs)]
-        e = torch.randn((nb, V, 4, N), dtype=torch.complex128, device="cuda", generator=g)
-        for b in range(nb):
-            bsm.bsm_pack_spinor(lat, e[b], e64, bsm.F64)
-            bsm.bsm_dslash(lat, l64, e64, r64, bsm.FULL, 0, bsm.F64)
-            bsm.bsm_ptc_pack(lat, e64, E[b * fb:(b + 1) * fb])
-            bsm.bsm_ptc_pack(lat, r64, R[b * fb:(b + 1) * fb])
+        l32, PR, PE, npair = pool[step % len(pool)]
+        for b, j in enumerate(rng.choice(npair, size=nb, replace=npair < nb)):
+            R[b * fb:(b + 1) * fb].copy_(PR[j * fb:(j + 1) * fb])
+            E[b * fb:(b + 1) * fb].copy_(PE[j * fb:(j + 1) * fb])
         losses.append(bsm.bsm_ptc_loss_grad(lat, l32, W[0], W[1], C, R, E, nb, G[0], G[1], ws) / nb)
         lr = cfg["lr"] if step <= 2 * cfg["steps"] // 3 else cfg["lr"] / 3
         for k in range(2):
             bsm.bsm_ptc_adam_step(W[k], G[k], m[k], v[k], lr, step)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
-    return W, {"train_lattice_TXYZ": list(dims), "configs": len(confs), "pairs": cfg["steps"] * nb,
-               "steps": cfg["steps"], "seconds": round(secs, 2), "loss_first": round(losses[0], 5),
-               "loss_last100": round(float(np.mean(losses[-100:])), 5)}
+    return W, {"train_lattice_TXYZ": list(dims), "training_pairs": pair_info,
+               "samples": cfg["steps"] * nb, "steps": cfg["steps"], "seconds": round(secs, 2),
+               "loss_first": round(losses[0], 5), "loss_last100": round(float(np.mean(losses[-100:])), 5)}
 
 
 def run_precond(peak, peak_kind, steps):
@@ -1105,6 +1187,19 @@ def run_precond(peak, peak_kind, steps):
     best = min((k for k in res if k.startswith("fgcr_eo_ptc")), key=lambda k: res[k]["seconds"])
     res["best_ptc"] = best
     res["cg_mixed_over_best_ptc_time"] = round(res["cg_mixed_df64"]["seconds"] / res[best]["seconds"], 3)
+    # the same network trained on residual/error pairs of plain FP64 CG
+    # iterates instead (their errors are dominated by the low modes, which a
+    # two-hop local network cannot invert: compare its loss and iterations)
+    Wcg, train_cg = train_ptc(cfg, pairs="cg")
+    o = cases["fgcr_eo_ptc_bf16_fp32cycles"]
+    ws = torch.empty(bsm.bsm_fgcr_workspace_bytes(lat, o), dtype=torch.uint8, device="cuda")
+    x = torch.empty_like(b)
+    st, stats = bsm.bsm_fgcr_solve(lat, L[o.prec_outer], L[bsm.F32], Wcg[0], Wcg[1], b, x, o, ws, raise_on_error=False)
+    res["cg_pair_network"] = {"training": train_cg, "fgcr_eo_ptc_bf16_fp32cycles": {
+        "status": bsm.bsm_strerror(st), "iters": stats.iters, "seconds": round(stats.seconds, 5),
+        "true_res": stats.true_res},
+        "iteration_reduction_eo": round(res["fgcr_eo_none_fp64"]["iters"] / max(1, stats.iters), 2)}
+    del ws
     res["ptc_apply"] = ptc_apply_roofline(W, C, peak, peak_kind, steps)
     return res
 

@@ -825,6 +825,7 @@ def run_cg_batch(shapes=None, nrhs=None, max_iter=20000):
         el = time.perf_counter() - t0
         best = el if best is None or el < best else best
     res["batched"] = {"status": bsm.bsm_strerror(st), "seconds": round(best, 4),
+                      "launch_config": dict(zip(("rhs_per_thread", "chunks_per_grab"), bsm.bsm_batch_last_config())),
                       "iters_max": max(s.iters for s in stats),
                       "true_res_normal_max": max(s.true_res_normal for s in stats),
                       "true_res_full_max": max(s.true_res_full for s in stats),

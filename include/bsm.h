@@ -460,6 +460,16 @@ int bsm_fgcr_solve(const bsm_lattice *lat, const void *U_rep64, const void *U_re
                    const bsm_fgcr_opts *opts, bsm_fgcr_stats *stats, void *workspace,
                    size_t workspace_bytes, void *stream);
 
+/* The launch configuration the last batch call on this thread used: RHS
+ * per thread (1 or 2) and chunks of 128 thread slots per work-queue grab
+ * (1, 2, 4 or 8).  bsm_dslash_batch, bsm_dslash_batch_async and
+ * bsm_cg_solve_batch pick it per batch shape (the lattices and their nrhs)
+ * on their first call by timing every candidate on `stream` (which
+ * synchronises it), unless the stream is capturing a graph or the
+ * environment sets BSM_BATCH_TUNE=0; then the tuned choice if one exists,
+ * else (1, 4).  The results do not depend on it.  Pure host. */
+int bsm_batch_last_config(int32_t *rhs_per_thread, int32_t *chunks_per_grab);
+
 /* A batch of systems solved together: mixed-precision CG (FP32 iterations,
  * reliable updates at opts->prec_outer) on the even-odd normal equations of
  * every right-hand side of several lattices of uneven size (Sec. II-B CG; the

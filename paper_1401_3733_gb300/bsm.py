@@ -150,6 +150,8 @@ _lib.bsm_cg_batch_workspace_bytes.restype = ctypes.c_size_t
 _lib.bsm_cg_solve_batch.argtypes = [ctypes.POINTER(CgBatchItem), ctypes.c_int32, ctypes.POINTER(CgOpts),
                                     ctypes.POINTER(CgStats), _P, ctypes.c_size_t, _P]
 _lib.bsm_cg_solve_batch.restype = ctypes.c_int
+_lib.bsm_batch_last_config.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+_lib.bsm_batch_last_config.restype = ctypes.c_int
 _SP = ctypes.POINTER(Slab)
 _lib.bsm_face_bytes.argtypes = [_SP, ctypes.c_int32]
 _lib.bsm_face_bytes.restype = ctypes.c_size_t
@@ -441,3 +443,10 @@ def bsm_cg_solve_batch(items, opts: CgOpts, workspace, stream=None, raise_on_err
     if raise_on_error:
         _check(st, "bsm_cg_solve_batch")
     return st, list(stats)
+
+
+def bsm_batch_last_config():
+    """(RHS per thread, chunks per work-queue grab) of the last batch call on this thread."""
+    rb, grab = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.bsm_batch_last_config(ctypes.byref(rb), ctypes.byref(grab)), "bsm_batch_last_config")
+    return rb.value, grab.value

@@ -24,6 +24,7 @@ size_t batch_workspace_bytes(const bsm_batch_item* items, int count, int op);
 int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o, void* ws, cudaStream_t s,
                  bool sync);
 int batch_status(void* ws, cudaStream_t s);
+void batch_last_config(int* rb, int* grab);
 bool mrhs_set_block(int prec, int d, bool real, int nrhs, int Vh, int block);
 size_t cg_workspace_bytes(const bsm_lattice& L, int prec_inner, int eo, int prec_outer);
 size_t cg_batch_workspace_bytes(const bsm_cg_batch_item* items, int count);
@@ -375,6 +376,15 @@ int bsm_dslash_batch(const bsm_batch_item* items, int32_t count, const bsm_batch
 int bsm_dslash_batch_async(const bsm_batch_item* items, int32_t count, const bsm_batch_opts* opts,
                            void* workspace, size_t workspace_bytes, void* stream) {
   return dslash_batch(items, count, opts, workspace, workspace_bytes, stream, false);
+}
+
+int bsm_batch_last_config(int32_t* rhs_per_thread, int32_t* chunks_per_grab) {
+  if (rhs_per_thread == nullptr || chunks_per_grab == nullptr) return BSM_EINVAL;
+  int rb = 1, grab = 4;
+  batch_last_config(&rb, &grab);
+  *rhs_per_thread = rb;
+  *chunks_per_grab = grab;
+  return BSM_OK;
 }
 
 int bsm_dslash_batch_status(void* workspace, void* stream) {

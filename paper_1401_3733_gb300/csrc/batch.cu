@@ -13,8 +13,13 @@
 // global timer: a block that waits longer than the limit raises an error flag
 // and returns, and the call reports BSM_ETIMEOUT instead of hanging.
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "batch.cuh"
@@ -44,6 +49,7 @@ struct BatchControl {
 struct BatchMeta {
   int ntasks;
   int nphases;
+  int grab;                       // chunks taken per work-queue grab
   long long phase_chunks[kMaxPhases];
   unsigned int grid_blocks;       // the barrier after phase j waits for (j + 1) * grid_blocks + barrier_extra arrivals
   unsigned int barrier_extra;
@@ -57,7 +63,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 constexpr int kMaxBatchTasks = 128;    // up to 4 tasks per lattice (Dhat^+ Dhat), 32 lattices per launch
-constexpr int kChunksPerGrab = 4;      // work-queue grabs cover 4 blocks' worth of thread slots
+// launch configuration: RHS per thread (RB) and chunks per work-queue grab;
+// picked per batch shape by timing (batch_tuned_config), or the default
+struct BatchConfig {
+  int rb = 1;
+  int grab = 4;
+};
 
 // the whole task table as one launch parameter (the parameter space holds up
 // to 32 KB from CUDA 12.1 on sm_70+)
@@ -66,10 +77,13 @@ struct BatchTable {
 };
 static_assert(sizeof(BatchTable) + sizeof(BatchMeta) + sizeof(void*) < 32000, "batch table exceeds the parameter space");
 
-// 128 registers, 4 blocks per SM (measured: 7 % faster than 168 / 3 on the
-// 16-lattice batch, as for the d = 3 multi-RHS kernel)
-__global__ void __launch_bounds__(kHopThreads, 4) batch_kernel(const __grid_constant__ BatchTable table,
-                                                                BatchControl* ctl, const BatchMeta meta) {
+// RB = 1: 128 registers, 4 blocks per SM (measured: 7 % faster than 168 / 3
+// on the 16-lattice batch, as for the d = 3 multi-RHS kernel); RB = 2: two
+// RHS per thread (each link element applied to both), 2 blocks per SM.  A
+// thread slot of a task is (site, block of RB RHS).
+template <int RB>
+__global__ void __launch_bounds__(kHopThreads, RB == 1 ? 4 : 2) batch_kernel(const __grid_constant__ BatchTable table,
+                                                                             BatchControl* ctl, const BatchMeta meta) {
   __shared__ BatchTask s_tasks[kMaxBatchTasks];
   __shared__ long long s_chunk;
   __shared__ int s_abort;
@@ -80,27 +94,28 @@ __global__ void __launch_bounds__(kHopThreads, 4) batch_kernel(const __grid_cons
     int first = 0;
     while (first < meta.ntasks && s_tasks[first].phase != phase) ++first;
     for (;;) {
-      if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(&ctl->next[phase], 1ull) * kChunksPerGrab;
+      if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(&ctl->next[phase], 1ull) * meta.grab;
       __syncthreads();
       const long long c0 = s_chunk;
       __syncthreads();
       if (c0 >= meta.phase_chunks[phase]) break;
       int k = first;
-      for (int sub = 0; sub < kChunksPerGrab; ++sub) {
+      for (int sub = 0; sub < meta.grab; ++sub) {
         const long long c = c0 + sub;
         if (c >= meta.phase_chunks[phase]) break;
         while (c >= s_tasks[k].chunk0 + s_tasks[k].chunks) ++k;  // chunks ascend with k
         const BatchTask& tk = s_tasks[k];
         const long long u = (c - tk.chunk0) * kHopThreads + threadIdx.x;
-        if (u < (long long)tk.args.g.Vh * tk.args.nrhs) {
-          const int i = (int)(u / tk.args.nrhs), r = (int)(u - (long long)i * tk.args.nrhs);
-          // phase 1 reads the odd temporaries written in phase 0: through L2 only
+        const int nblk = tk.args.nrhs / RB;
+        if (u < (long long)tk.args.g.Vh * nblk) {
+          const int i = (int)(u / nblk), r = (int)(u - (long long)i * nblk) * RB;
+          // later phases read what an earlier phase of this launch wrote: through L2 only
           if (phase == 0) {
-            if (tk.d == 2) mrhs_site<F32, 2, false, 1>(tk.args, i, r);
-            else mrhs_site<F32, 3, false, 1>(tk.args, i, r);
+            if (tk.d == 2) mrhs_site<F32, 2, false, RB>(tk.args, i, r);
+            else mrhs_site<F32, 3, false, RB>(tk.args, i, r);
           } else {
-            if (tk.d == 2) mrhs_site<F32, 2, false, 1, true>(tk.args, i, r);
-            else mrhs_site<F32, 3, false, 1, true>(tk.args, i, r);
+            if (tk.d == 2) mrhs_site<F32, 2, false, RB, true>(tk.args, i, r);
+            else mrhs_site<F32, 3, false, RB, true>(tk.args, i, r);
           }
         }
       }
@@ -149,18 +164,19 @@ namespace {
 // grid size (every block resident, so that the grid barriers complete),
 // the control block reset, the launch
 int launch_tasks(const std::vector<BatchTask>& tasks, BatchMeta meta, BatchControl* ctl, double timeout_s,
-                 int barrier_extra, cudaStream_t s) {
+                 int barrier_extra, const BatchConfig& cfg, cudaStream_t s) {
   if ((int)tasks.size() > kMaxBatchTasks) return BSM_EUNSUPPORTED;
   meta.ntasks = (int)tasks.size();
+  meta.grab = cfg.grab;
+  const void* kern = cfg.rb == 2 ? (const void*)batch_kernel<2> : (const void*)batch_kernel<1>;
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kHopThreads, 0) != cudaSuccess ||
-      per_sm < 1)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kHopThreads, 0) != cudaSuccess || per_sm < 1)
     return BSM_ECUDA;
   long long want = 0;
   for (int ph = 0; ph < meta.nphases; ++ph) want = meta.phase_chunks[ph] > want ? meta.phase_chunks[ph] : want;
-  want = (want + kChunksPerGrab - 1) / kChunksPerGrab;
+  want = (want + cfg.grab - 1) / cfg.grab;
   int grid = sms * per_sm;
   if (want < grid) grid = (int)(want > 0 ? want : 1);
   meta.grid_blocks = (unsigned)grid;
@@ -176,7 +192,7 @@ int launch_tasks(const std::vector<BatchTask>& tasks, BatchMeta meta, BatchContr
     return BSM_ECUDA;
   }
   void* kargs[] = {(void*)&table, (void*)&ctl, (void*)&meta};
-  e = cudaLaunchCooperativeKernel((void*)batch_kernel, grid, kHopThreads, kargs, 0, s);
+  e = cudaLaunchCooperativeKernel(kern, grid, kHopThreads, kargs, 0, s);
   if (e != cudaSuccess) {
     set_cuda_error(e);
     return BSM_ECUDA;
@@ -201,11 +217,9 @@ size_t batch_workspace_bytes(const bsm_batch_item* items, int count, int op) {
 
 int batch_status(void* ws, cudaStream_t s);
 
-// launches the batch on `s`; with sync, waits and reads the error flag
-// (BSM_ETIMEOUT), else returns at once (nothing but a memset and the
-// cooperative launch is enqueued, so the call can be captured in a graph)
-int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o, void* ws, cudaStream_t s,
-                 bool sync) {
+// builds the tasks of a D or Dhat batch for the configuration and enqueues the launch
+int batch_launch_cfg(const bsm_batch_item* items, int count, const bsm_batch_opts& o, void* ws, cudaStream_t s,
+                     const BatchConfig& cfg) {
   const auto align = [](size_t v) { return (v + 255) / 256 * 256; };
   char* w = reinterpret_cast<char*>(ws);
   BatchControl* ctl = reinterpret_cast<BatchControl*>(w);
@@ -221,7 +235,7 @@ int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o
     const size_t half = c.half_bytes * it.nrhs;
     const char* in = reinterpret_cast<const char*>(it.in);
     char* out = reinterpret_cast<char*>(it.out);
-    const long long chunks = ((long long)c.g.Vh * it.nrhs + kHopThreads - 1) / kHopThreads;
+    const long long chunks = ((long long)c.g.Vh * (it.nrhs / cfg.rb) + kHopThreads - 1) / kHopThreads;
     BatchTask t;
     memset(&t, 0, sizeof(t));
     t.d = c.d;
@@ -271,15 +285,14 @@ int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o
     }
   }
   tasks.insert(tasks.end(), tasks1.begin(), tasks1.end());
-  const int rc = launch_tasks(tasks, meta, ctl, o.timeout_s, o.barrier_extra, s);
-  if (rc != BSM_OK) return rc;
-  return sync ? batch_status(ws, s) : BSM_OK;
+  return launch_tasks(tasks, meta, ctl, o.timeout_s, o.barrier_extra, cfg, s);
 }
 
 // the even-odd normal operator Mp = Dhat^+ Dhat p of every item in one
 // launch of four phases: t = H_oe p, u = A p - H_eo t / (4A), t = H_oe^+ u,
 // Mp = A u - H_eo^+ t / (4A); FP32 multi-RHS fields (validated by the caller)
-int batch_normal_launch(const BatchNormalItem* items, int count, void* ctl_ws, double timeout_s, cudaStream_t s) {
+int batch_normal_launch_cfg(const BatchNormalItem* items, int count, void* ctl_ws, double timeout_s, cudaStream_t s,
+                            const BatchConfig& cfg) {
   BatchMeta meta;
   memset(&meta, 0, sizeof(meta));
   meta.nphases = 4;
@@ -292,7 +305,7 @@ int batch_normal_launch(const BatchNormalItem* items, int count, void* ctl_ws, d
     t.d = c.d;
     t.args.g = c.g;
     t.args.nrhs = it.nrhs;
-    t.chunks = ((long long)c.g.Vh * it.nrhs + kHopThreads - 1) / kHopThreads;
+    t.chunks = ((long long)c.g.Vh * (it.nrhs / cfg.rb) + kHopThreads - 1) / kHopThreads;
     for (int ph = 0; ph < 4; ++ph) {
       const bool first_hop = (ph & 1) == 0;  // phases 0, 2: tmp_o = H_oe(^+) v
       const void* v = ph < 2 ? it.p : it.u;
@@ -312,7 +325,121 @@ int batch_normal_launch(const BatchNormalItem* items, int count, void* ctl_ws, d
   }
   std::vector<BatchTask> tasks;
   for (int ph = 0; ph < 4; ++ph) tasks.insert(tasks.end(), by_phase[ph].begin(), by_phase[ph].end());
-  return launch_tasks(tasks, meta, reinterpret_cast<BatchControl*>(ctl_ws), timeout_s, 0, s);
+  return launch_tasks(tasks, meta, reinterpret_cast<BatchControl*>(ctl_ws), timeout_s, 0, cfg, s);
+}
+
+namespace {
+
+// --- launch-configuration tuner: per batch shape, the first call times every
+// (RB, grab) candidate on the caller's stream and keeps the fastest ---------
+std::mutex g_tune_mu;
+std::map<std::string, BatchConfig> g_tuned;
+thread_local BatchConfig g_last;
+
+bool tuning_allowed(cudaStream_t s) {
+  const char* env = getenv("BSM_BATCH_TUNE");
+  if (env != nullptr && env[0] == '0') return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+  return true;
+}
+
+template <typename Launch>
+int tuned_launch(const std::string& key, bool rb2_ok, cudaStream_t s, void* ctl_ws, Launch launch) {
+  BatchConfig cfg;
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      cfg = it->second;
+      have = true;
+    }
+  }
+  if (!have && tuning_allowed(s)) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return BSM_ECUDA;
+    float best = 1e30f;
+    BatchConfig win;
+    for (int rb = 1; rb <= (rb2_ok ? 2 : 1); ++rb)
+      for (int grab : {1, 2, 4, 8}) {
+        BatchConfig c;
+        c.rb = rb;
+        c.grab = grab;
+        int rc = launch(c);  // warm-up
+        float ms = 0.f, tot = 0.f;
+        for (int r = 0; r < 3 && rc == BSM_OK; ++r) {
+          cudaEventRecord(e0, s);
+          rc = launch(c);
+          cudaEventRecord(e1, s);
+          if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            rc = BSM_ECUDA;
+          tot += ms;
+        }
+        if (rc == BSM_OK) rc = batch_status(ctl_ws, s);
+        if (rc != BSM_OK) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return rc;
+        }
+        if (tot < best) {
+          best = tot;
+          win = c;
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cfg = win;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[key] = cfg;
+  }
+  g_last = cfg;
+  return launch(cfg);
+}
+
+std::string shape_key(const char* op, const bsm_lattice* lats, const int* nrhs, int count, size_t stride) {
+  std::string k(op);
+  for (int i = 0; i < count; ++i) {
+    const bsm_lattice& L = *reinterpret_cast<const bsm_lattice*>(reinterpret_cast<const char*>(lats) + i * stride);
+    const int n = *reinterpret_cast<const int*>(reinterpret_cast<const char*>(nrhs) + i * stride);
+    char buf[96];
+    snprintf(buf, sizeof(buf), "|%d,%d,%d,%d:%d:%d", L.dims[0], L.dims[1], L.dims[2], L.dims[3], L.N, n);
+    k += buf;
+  }
+  return k;
+}
+
+}  // namespace
+
+// launches the batch on `s`; with sync, waits and reads the error flag
+// (BSM_ETIMEOUT), else returns at once (nothing but a memset and the
+// cooperative launch is enqueued, so the call can be captured in a graph).
+// The first call per batch shape tunes the launch configuration (which
+// synchronises `s`) unless the stream is capturing or BSM_BATCH_TUNE=0.
+int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o, void* ws, cudaStream_t s,
+                 bool sync) {
+  bool even = true;
+  for (int k = 0; k < count; ++k) even = even && items[k].nrhs % 2 == 0;
+  const std::string key = shape_key(o.op == BSM_BATCH_DHAT ? "dhat" : "d", &items[0].lat, &items[0].nrhs, count,
+                                    sizeof(bsm_batch_item));
+  const int rc = tuned_launch(key, even, s, ws,
+                              [&](const BatchConfig& c) { return batch_launch_cfg(items, count, o, ws, s, c); });
+  if (rc != BSM_OK) return rc;
+  return sync ? batch_status(ws, s) : BSM_OK;
+}
+
+int batch_normal_launch(const BatchNormalItem* items, int count, void* ctl_ws, double timeout_s, cudaStream_t s) {
+  bool even = true;
+  for (int k = 0; k < count; ++k) even = even && items[k].nrhs % 2 == 0;
+  const std::string key = shape_key("normal", &items[0].lat, &items[0].nrhs, count, sizeof(BatchNormalItem));
+  return tuned_launch(key, even, s, ctl_ws, [&](const BatchConfig& c) {
+    return batch_normal_launch_cfg(items, count, ctl_ws, timeout_s, s, c);
+  });
+}
+
+void batch_last_config(int* rb, int* grab) {
+  *rb = g_last.rb;
+  *grab = g_last.grab;
 }
 
 size_t batch_control_bytes() { return (sizeof(BatchControl) + 255) / 256 * 256; }

@@ -553,6 +553,13 @@ int cg_solve_batch(const bsm_cg_batch_item* items, int count, const bsm_cg_opts&
   }
   cudaMemcpyAsync(B.st, hs.data(), sizeof(SysState) * nsys, cudaMemcpyHostToDevice, s);
 
+  // one application of the batch operator before any capture: its first
+  // call per batch shape tunes the launch configuration (p is zero here, and
+  // u, t, Mp are recomputed by the first iteration)
+  if ((rc = batch_normal_launch(B.nitems.data(), count, B.w + B.y.ctl, 1.0, s)) != BSM_OK ||
+      (rc = batch_status(B.w + B.y.ctl, s)) != BSM_OK)
+    return rc;
+
   // the iterations between host checks, captured once (not on the legacy default stream)
   cudaGraphExec_t exec = nullptr;
   const bool graph = o.use_graph != 0 && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;

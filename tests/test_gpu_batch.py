@@ -18,9 +18,9 @@ SHAPES = [((4, 4, 4, 4), 3, 2), ((2, 4, 6, 8), 2, 3), ((6, 6, 4, 4), 3, 1), ((8,
           ((4, 2, 2, 2), 3, 3)]   # (dims, N, nrhs)
 
 
-def make_batch(op, seed=900):
+def make_batch(op, seed=900, shapes=SHAPES):
     items, refs = [], []
-    for k, (dims, N, nrhs) in enumerate(SHAPES):
+    for k, (dims, N, nrhs) in enumerate(shapes):
         phase = (np.pi, 0, 0, 0)
         olat = orc.Lattice(dims, N, orc.FUND, 0.1 + 0.05 * k, phase)
         blat = bsm.lattice(dims, N, bsm.FUND, 0.1 + 0.05 * k, phase)
@@ -121,3 +121,31 @@ def test_async_batch_timeout_is_reported_by_the_status_query():
     assert bsm.bsm_dslash_batch_status(ws) == bsm.ETIMEOUT
     assert bsm.bsm_dslash_batch_async(arr, opts, ws) == bsm.OK
     assert bsm.bsm_dslash_batch_status(ws) == bsm.OK
+
+
+EVEN_SHAPES = [((4, 4, 4, 4), 3, 2), ((6, 4, 2, 4), 2, 4), ((8, 4, 4, 2), 3, 2)]
+
+
+@pytest.mark.parametrize("op", [bsm.BATCH_D, bsm.BATCH_DHAT], ids=["D", "Dhat"])
+def test_tuned_launch_configuration_changes_nothing(op, monkeypatch):
+    """The first call on a batch shape times every (RHS per thread, chunks
+    per grab) candidate and keeps the fastest; with BSM_BATCH_TUNE=0 an
+    untuned shape runs (1, 4).  Both give the same bits, and the oracle's."""
+    items, refs = make_batch(op, seed=970, shapes=EVEN_SHAPES)
+    arr = bsm.batch_items(items)
+    opts = bsm.BatchOpts(op, bsm.F32, 0.0, 0)
+    ws = torch.empty(bsm.bsm_batch_workspace_bytes(arr, opts), dtype=torch.uint8, device="cuda")
+    monkeypatch.setenv("BSM_BATCH_TUNE", "0")
+    assert bsm.bsm_dslash_batch(arr, opts, ws) == bsm.OK
+    assert bsm.bsm_batch_last_config() == (1, 4)
+    first = [ref[4].clone() for ref in refs]
+    monkeypatch.delenv("BSM_BATCH_TUNE")
+    assert bsm.bsm_dslash_batch(arr, opts, ws) == bsm.OK
+    rb, grab = bsm.bsm_batch_last_config()
+    assert rb in (1, 2) and grab in (1, 2, 4, 8)
+    for (olat, R, psis, blat, out, nrhs), f in zip(refs, first):
+        assert torch.equal(out, f)
+        got = unpack(blat, out, nrhs)
+        for r in range(nrhs):
+            want = orc.dirac(olat, R, psis[r]) if op == bsm.BATCH_D else orc.dhat(olat, R, psis[r], orc.DHAT)
+            assert rel(got[r], want) <= TOL[bsm.F32]

@@ -231,10 +231,12 @@ int bsm_dslash_mrhs(const bsm_lattice *lat, const void *U_rep, const void *in, v
 
 /* The RHS block (RHS per thread) that bsm_dslash_mrhs uses for this
  * (lattice, nrhs, prec): 0 before the first call has tuned it, 1..4 for the
- * SIMT kernel, 16 for the tensor-core kernel (BF16, complex d = 4, 6, 8,
- * nrhs = 4, 8, 12, 16: one warp per site, the link x spinor block products
- * as mma.sync m16n8k16 with FP32 accumulation); or a negative bsm_status.
- * Pure host. */
+ * SIMT kernel, 102 and 104 for the SIMT kernel with 2 or 4 RHS per thread
+ * held as lane pairs of packed FP32 instructions (one instruction serves two
+ * RHS; 104 for d <= 3), 16 for the tensor-core kernel (BF16, complex d = 4,
+ * 6, 8, nrhs = 4, 8, 12, 16: one warp per site, the link x spinor block
+ * products as mma.sync m16n8k16 with FP32 accumulation); or a negative
+ * bsm_status.  Pure host. */
 int bsm_dslash_mrhs_block(const bsm_lattice *lat, int32_t nrhs, int32_t prec);
 
 /* Pins the RHS block bsm_dslash_mrhs uses for (lattice, nrhs, prec) instead

@@ -1,8 +1,9 @@
 // mrhs.cu -- launch of the multi-RHS hopping block with an autotuned RHS
 // block: the first launch for a (precision, d, n_rhs, V_h) shape times every
-// compiled block size RB that divides n_rhs, and the tensor-core kernel where
-// it applies (BF16, d = 4, 6, 8), on the caller's stream and keeps the
-// fastest for the rest of the process.
+// compiled block size RB that divides n_rhs, the f32x2-paired kernels (2 or 4
+// RHS per thread as lane pairs) and the tensor-core kernel where it applies
+// (BF16, d = 4, 6, 8), on the caller's stream and keeps the fastest for the
+// rest of the process.
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -61,6 +62,8 @@ bool mrhs_set_block(int prec, int d, bool real, int nrhs, int Vh, int block) {
   }
   if (block == kTensorCoreBlock) {
     if (prec != BSM_BF16 || real || !(d == 4 || d == 6 || d == 8) || nrhs % 4 != 0 || nrhs > 16) return false;
+  } else if (block == kPairedBlock + 2 || block == kPairedBlock + 4) {
+    if (block - kPairedBlock > max_rb(d) || nrhs % (block - kPairedBlock) != 0) return false;
   } else if (block < 1 || block > max_rb(d) || nrhs % block != 0) {
     return false;
   }
@@ -95,9 +98,12 @@ int launch_mrhs(int prec, int d, bool real, const MrhsArgs& A, cudaStream_t s) {
         return BSM_ECUDA;
       }
       float best_ms = -1.f;
-      for (int c = 1; c <= kTensorCoreBlock; ++c) {
-        if (c > max_rb(d) && c != kTensorCoreBlock) continue;
-        if (c != kTensorCoreBlock && A.nrhs % c != 0) continue;
+      for (int c = 1; c <= kPairedBlock + 4; ++c) {
+        const bool paired = c == kPairedBlock + 2 || c == kPairedBlock + 4;
+        const int rhs = paired ? c - kPairedBlock : c;
+        if (!paired && c > max_rb(d) && c != kTensorCoreBlock) continue;
+        if (paired && rhs > max_rb(d)) continue;
+        if (c != kTensorCoreBlock && A.nrhs % rhs != 0) continue;
         const float ms = time_rb(prec, d, real, c, A, s, e0, e1);
         if (ms > 0.f && (best_ms < 0.f || ms < best_ms)) {
           best_ms = ms;

@@ -152,3 +152,40 @@ def test_mrhs_set_block_rejects_unavailable_blocks():
         bsm.bsm_dslash_mrhs_set_block(lat, 12, bsm.F32, bsm.MRHS_TENSOR_CORE_BLOCK)   # FP32, d = 3
     with pytest.raises(bsm.BsmError):
         bsm.bsm_dslash_mrhs_set_block(lat, 12, bsm.F32, 5)
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_dslash_mrhs_set_block(lat, 6, bsm.F32, 104)                          # 4 paired RHS, 6 RHS
+    six = bsm.lattice((4, 4, 4, 4), 6)
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_dslash_mrhs_set_block(six, 12, bsm.F32, 104)                         # 4 paired RHS, d = 6
+
+
+@pytest.mark.parametrize("prec", [bsm.F32, bsm.BF16], ids=["f32", "bf16"])
+@pytest.mark.parametrize("N,rep,block", [(2, bsm.FUND, 104), (3, bsm.FUND, 102), (3, bsm.FUND, 104),
+                                         (2, bsm.ADJ, 104), (6, bsm.FUND, 102), (4, bsm.ASYM, 102)],
+                         ids=["SU2-F-4pair", "SU3-F-2pair", "SU3-F-4pair", "SU2-ADJ-4pair", "SU6-F-2pair",
+                              "SU4-AS-2pair"])
+def test_mrhs_paired_kernel_is_bit_identical(N, rep, block, prec):
+    """The f32x2-paired kernel (two RHS per packed register) performs the
+    scalar kernel's operations lane by lane: pinned, it gives the same bits as
+    the one-RHS-per-thread kernel for both parity blocks, the adjoint and the
+    full operator, and the oracle's operator per RHS."""
+    dims, nrhs = (4, 4, 2, 6), 12
+    olat, blat, U, R, psis = setup(dims, N, rep, nrhs, 900 + N + block)
+    Ud = gpu_links(blat, U, prec)
+    inp = pack(blat, psis, prec)
+    half = bsm.bsm_field_bytes(blat, bsm.FIELD_HALF_SPINOR, prec) * nrhs
+    results = {}
+    for b in (block, 1):
+        bsm.bsm_dslash_mrhs_set_block(blat, nrhs, prec, b)
+        assert bsm.bsm_dslash_mrhs_block(blat, nrhs, prec) == b
+        full = mrhs_field(blat, nrhs, prec)
+        bsm.bsm_dslash_mrhs(blat, Ud, inp, full, nrhs, bsm.FULL, 0, prec)
+        odd = mrhs_field(blat, nrhs, prec)
+        bsm.bsm_dslash_mrhs(blat, Ud, inp[:half], odd[half:], nrhs, bsm.ODD, 1, prec)
+        results[b] = (full, odd)
+    bsm.bsm_dslash_mrhs_set_block(blat, nrhs, prec, 0)
+    assert torch.equal(results[block][0], results[1][0])
+    assert torch.equal(results[block][1], results[1][1])
+    got = unpack(blat, results[block][0], nrhs, prec)
+    for r in range(nrhs):
+        assert rel(got[r], orc.dirac(olat, R, psis[r])) <= TOL[prec]

@@ -3,41 +3,107 @@
 //
 // For one site and one of its 8 direction-senses the hop is a small dense
 // contraction: W = U h, with U the d x d link and h the d x (2 spins x n_rhs)
-// block of spin-projected neighbour spinors.  In real form
+// block of spin-projected neighbour spinors.  In real form, with the real
+// parts of the colours in K rows 0..7 and the imaginary parts in rows 8..15,
 //     [Wr; Wi] = [[Ur, -Ui], [Ui, Ur]] [hr; hi]
-// is an M = K = 2d (padded to 16), N = 2 n_rhs GEMM, i.e. one
-// mma.sync.m16n8k16 (bf16 x bf16 -> f32) per 8 columns.  The lower spin
-// components of the term are sg B_mu^+ (U h) = U (sg B_mu^+ h): a second
-// B operand h' built from the same spinors, so both halves of the spinor
-// accumulate inside the MMA accumulators across all 8 direction-senses.
-// Each site has its own link, so the contraction cannot share an A operand
-// across sites (tcgen05 needs M >= 64 rows with one A); one warp owns one
-// site and issues 2 * n_rhs / 4 MMAs per direction-sense.
+// is an M = K = 16, N = 2 n_rhs GEMM: one mma.sync.m16n8k16 (bf16 x bf16 ->
+// f32) per 8 columns.  The lower spin components of the term are
+// sg B_mu^+ (U h) = U (sg B_mu^+ h), a second B operand that is a sign flip
+// and re/im exchange of the first one's registers, so both spin halves
+// accumulate in the MMA accumulators across all 8 direction-senses and no
+// reconstruction runs per direction.  Each site has its own link, so no A
+// operand is shared across sites (tcgen05 needs M >= 64 rows with one A):
+// one warp owns one site at a time.
 //
-// Per warp and direction-sense: the link (d^2 bf16 pairs) is staged in
-// shared memory, each lane builds its A-fragment registers from it, the
-// lanes build h^T and h'^T (n x 16 bf16, K rows 2d..15 kept zero) from the
-// neighbour spinors, and the MMAs run.  The epilogue writes the FP32
-// accumulators to shared memory, reassembles complex spinor components per
-// (RHS, colour), applies the optional a*x + b*H form and stores BF16.
+// Operands are built in registers.  Lane (g, t) = (lane / 4, lane % 4) of
+// the warp holds, in the mma.sync fragment layouts,
+//   A: link elements U[g][t], U[g][t + d/2] (real and imaginary pairs);
+//   B: colours t and t + d/2 of column n = g of each 8-column tile,
+// i.e. the K index runs over the colours in the order (0, d/2, 1, d/2+1, ...);
+// this pairing puts the lanes t of one shared-memory read on different banks.
+// Columns are assigned so that one lane holds both spins of one RHS: tile
+// 2k has spin 0 and tile 2k+1 spin 1 of RHS r = 8k + g; for n_rhs = 4 or 12
+// the last tile holds RHS 8k + (g & 3), spin g >> 2.  A lane therefore reads
+// four (psi0, psi2) / (psi1, psi3) words per RHS, projects them with packed
+// bf16x2 FMAs (u + s l, s = +-1 or +-i: one rounding to BF16, as storing an
+// FP32 projection would give) and packs the real and imaginary pairs.
+//
+// Data movement: a block of 4 warps works on 4 consecutive sites at a time
+// (one per warp), whose links share the 32-byte sectors of the tiled link
+// layout; the block copies the next 4 sites' links into a double buffer of
+// per-site link blocks (cp.async, 8 bytes per element) while it computes the
+// current ones.  Every warp runs through its site's 8 direction-senses as a
+// stream of items and copies item j + S - 2 (the neighbour's multi-RHS spinor
+// block, 2d plane rows of n_rhs words, as 16-byte cp.async pieces of the
+// lanes) into an S-stage ring of its shared memory while it computes item j;
+// the same-site input of the a x + b H form is copied the same way during the
+// site.  The grid is persistent.  On 24^4 x 12 RHS at d = 6 the copies alone
+// take 0.48 ms per D and the arithmetic alone 0.40 ms; overlapped, 0.59 ms.
+// (Moving half or all of each item by TMA tile copies, completing on
+// mbarriers, measured slower: 0.73 and 0.66 ms.)
 #include "mrhs.cuh"
 
 namespace bsm {
 
 namespace {
 
-constexpr int kTcWarps = 4;  // warps (sites) per block
+constexpr int kTcWarps = 4;        // warps (sites) per block
+constexpr int kTcBlocksPerSm = 4;  // register budget: 128 per thread
+constexpr int kTcSmemPerSm = 216 * 1024;
+constexpr unsigned kSign2 = 0x80008000u;
 
-__device__ __forceinline__ unsigned short bf16_bits(float x) {
-  const __nv_bfloat16 b = __float2bfloat16_rn(x);
-  unsigned short u;
-  memcpy(&u, &b, 2);
-  return u;
+template <int D, int NR>
+struct TcLayout {
+  static constexpr int spin_bytes = 2 * D * NR * 8;  // a site's block: [2d planes][n_rhs words]
+  // per-site link block: 4 d^2 (fwd, bwd) pairs; the stride is 16 words mod
+  // 32 so that the copies of two sites (lanes 0-7, 8-15) use different banks
+  static constexpr int link_site = 4 * D * D * 8 + ((4 * D * D * 8 / 4) % 32 == 16 ? 0 : 64);
+  static constexpr int link_buf = kTcWarps * link_site;
+  static constexpr int block_for(int S) { return kTcWarps * (S + 1) * spin_bytes + 2 * link_buf; }
+  static constexpr int S = kTcBlocksPerSm * block_for(8) <= kTcSmemPerSm ? 8 : 4;  // ring depth
+  static constexpr int warp_bytes = (S + 1) * spin_bytes;  // S stages, then the x block
+  static constexpr int links_off = kTcWarps * warp_bytes;  // two link buffers
+  static constexpr int block_bytes = links_off + 2 * link_buf;
+  static constexpr int link_elems = kTcWarps * 4 * D * D;  // elements of a quad's links
+  static constexpr int row_chunks = NR / 2;                // 16-byte pieces of a plane row
+  static constexpr int chunks = 2 * D * row_chunks;        // pieces of a block
+  static constexpr int per_lane = (chunks + 31) / 32;
+  static constexpr int NT = NR / 4;                        // 8-column tiles
+  static constexpr int NGF = NR / 8;                       // RHS groups filling two tiles
+  static constexpr bool HALF = (NR % 8) != 0;              // a last tile of 4 RHS x 2 spins
+  static_assert(NR % 4 == 0 && NR <= 16, "n_rhs in {4, 8, 12, 16}");
+  static_assert(spin_bytes % 16 == 0 && link_site % 16 == 0, "aligned areas");
+  static_assert((4 * D * D) % 8 == 0 && D % 2 == 0 && S - 2 <= 7, "copy mappings");
+};
+
+__device__ __forceinline__ void cp_async8_ca(unsigned s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
 }
-__device__ __forceinline__ float bits_bf16(unsigned short u) {
-  __nv_bfloat16 b;
-  memcpy(&b, &u, 2);
-  return __bfloat162float(b);
+__device__ __forceinline__ void cp_async16_cg(unsigned s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ uint2 lds64(unsigned a) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];\n" : "=r"(v.x), "=r"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint4 lds128(unsigned a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+
+// d = a * b + c on bf16x2, rounded once
+__device__ __forceinline__ unsigned hfma2(unsigned a, unsigned b, unsigned c) {
+  unsigned d;
+  asm("fma.rn.bf16x2 %0, %1, %2, %3;\n" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
 }
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
@@ -48,210 +114,382 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-template <int D, int NT>
-struct TcShared {
-  unsigned link[D * D];                 // bf16 (re, im) pairs of the link
-  unsigned short h[2][8 * NT][16];      // h^T and h'^T: [column n][K row]
-  float c[2][16][8 * NT];               // accumulators for the epilogue
+// unsigned division n / d for n < 2^31 by a multiply and a shift:
+// m = ceil(2^(31 + l) / d), l = ceil(log2 d) (Granlund and Montgomery 1994)
+struct FastDiv {
+  unsigned m;
+  int sh;  // l - 1, or -1 for d = 1
+  __device__ __forceinline__ void init(unsigned dv) {
+    if (dv <= 1) {
+      m = 0;
+      sh = -1;
+      return;
+    }
+    const int l = 32 - __clz(dv - 1);
+    m = (unsigned)(((1ull << (31 + l)) + dv - 1) / dv);
+    sh = l - 1;
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const { return sh < 0 ? n : __umulhi(n, m) >> sh; }
 };
 
-// value of the realified, padded link at (row r, column k) for this lane's
-// fragment slot: 0 = zero, else 1 + element index * 4 + part * 2 + negate
-__device__ __forceinline__ int a_code(int D, int r, int k) {
-  if (r >= 2 * D || k >= 2 * D) return 0;
-  const int rb = r / D, kb = k / D, e = (r % D) * D + (k % D);
-  const int part = rb == kb ? 0 : 1;       // Ur on the diagonal blocks, Ui off it
-  const int neg = (rb == 0 && kb == 1) ? 1 : 0;  // -Ui in the upper right block
-  return 1 + e * 4 + part * 2 + neg;
+// the 8 neighbours (forward, backward per direction) of eo site i of parity
+// p, as eo_neighbours computes them, with the divisions by multiplications
+struct TcGeom {
+  FastDiv zh, y, x;
+  __device__ __forceinline__ void init(const Geom& g) {
+    zh.init((unsigned)g.Zh);
+    y.init((unsigned)g.Y);
+    x.init((unsigned)g.X);
+  }
+  __device__ __forceinline__ void neighbours(const Geom& g, int i, int p, int (&nb8)[8]) const {
+    const int row = (int)zh.div((unsigned)i), k = i - row * g.Zh;
+    const int r2 = (int)y.div((unsigned)row), yy = row - r2 * g.Y;
+    const int t = (int)x.div((unsigned)r2), xx = r2 - t * g.X;
+    const int z = 2 * k + ((t + xx + yy + p) & 1);
+    nb8[0] = (t == g.T - 1) ? i - (g.T - 1) * g.st : i + g.st;
+    nb8[1] = (t == 0) ? i + (g.T - 1) * g.st : i - g.st;
+    nb8[2] = (xx == g.X - 1) ? i - (g.X - 1) * g.sx : i + g.sx;
+    nb8[3] = (xx == 0) ? i + (g.X - 1) * g.sx : i - g.sx;
+    nb8[4] = (yy == g.Y - 1) ? i - (g.Y - 1) * g.sy : i + g.sy;
+    nb8[5] = (yy == 0) ? i + (g.Y - 1) * g.sy : i - g.sy;
+    const int Z = 2 * g.Zh;
+    const int zf = (z == Z - 1) ? 0 : z + 1;
+    const int zb = (z == 0) ? Z - 1 : z - 1;
+    nb8[6] = row * g.Zh + (zf >> 1);
+    nb8[7] = row * g.Zh + (zb >> 1);
+  }
+};
+
+// bf16x2 (re, im) factors: +1 = 0x3f80, -1 = 0xbf80 in each half
+constexpr unsigned kPP = 0x3f803f80u, kPM = 0xbf803f80u, kMM = 0xbf80bf80u, kMP = 0x3f80bf80u;
+
+// B-operand registers of one spin: (Re h[c], Re h[c']) and (Im h[c], Im h[c'])
+struct Bfrag {
+  unsigned re, im;
+};
+
+// The projected spins of one RHS for direction MU, colours c, c' of this
+// lane, from the staged words w[0..3] = planes c, c', D+c, D+c', each
+// (low word, high word) = (psi0, psi2) or (psi1, psi3) as bf16x2 (re, im):
+//   h0 = u0 + s b0, h1 = u1 + s b1, (b0, b1) = B_mu (l0, l1)   (u = psi0,1, l = psi2,3)
+// with MU = 0: (l0, l1); 1: (-i l1, -i l0); 2: (-l1, l0); 3: (-i l0, i l1);
+// SM is the sign bits of s = -+1.
+template <int MU, unsigned SM>
+__device__ __forceinline__ void tc_project(const uint2 (&w)[4], Bfrag& b0, Bfrag& b1) {
+  const unsigned l0c = w[0].y, l0d = w[1].y, l1c = w[2].y, l1d = w[3].y;
+  unsigned s0c, s0d, s1c, s1d;
+  constexpr unsigned f0 = (MU == 0 ? kPP : MU == 2 ? kMM : kPM) ^ SM;
+  constexpr unsigned f1 = (MU == 0 || MU == 2 ? kPP : MU == 1 ? kPM : kMP) ^ SM;
+  if constexpr (MU == 0) {
+    s0c = l0c, s0d = l0d, s1c = l1c, s1d = l1d;
+  } else if constexpr (MU == 1) {  // -i (x + iy) = y - ix: exchange re/im, then (1, -1)
+    s0c = __byte_perm(l1c, 0, 0x1032), s0d = __byte_perm(l1d, 0, 0x1032);
+    s1c = __byte_perm(l0c, 0, 0x1032), s1d = __byte_perm(l0d, 0, 0x1032);
+  } else if constexpr (MU == 2) {
+    s0c = l1c, s0d = l1d, s1c = l0c, s1d = l0d;
+  } else {  // -i l0 and i l1 = (-y, x)
+    s0c = __byte_perm(l0c, 0, 0x1032), s0d = __byte_perm(l0d, 0, 0x1032);
+    s1c = __byte_perm(l1c, 0, 0x1032), s1d = __byte_perm(l1d, 0, 0x1032);
+  }
+  const unsigned h0c = hfma2(f0, s0c, w[0].x), h0d = hfma2(f0, s0d, w[1].x);
+  const unsigned h1c = hfma2(f1, s1c, w[2].x), h1d = hfma2(f1, s1d, w[3].x);
+  b0.re = __byte_perm(h0c, h0d, 0x5410);
+  b0.im = __byte_perm(h0c, h0d, 0x7632);
+  b1.re = __byte_perm(h1c, h1d, 0x5410);
+  b1.im = __byte_perm(h1c, h1d, 0x7632);
 }
 
-__device__ __forceinline__ unsigned short a_value(const unsigned* link, int code) {
-  if (code == 0) return 0;
-  const int c = code - 1, e = c >> 2, part = (c >> 1) & 1, neg = c & 1;
-  const unsigned v = link[e];
-  const unsigned short u = part ? (unsigned short)(v >> 16) : (unsigned short)(v & 0xffffu);
-  return neg ? (unsigned short)(u ^ 0x8000u) : u;
+// The lower-spin operands s q, q = B_mu^+ h: MU = 0: (h0, h1); 1: (i h1, i h0);
+// 2: (h1, -h0); 3: (i h0, -i h1).  Multiplying by +-1 or +-i only flips signs
+// and exchanges the real and imaginary registers, so these are exact.
+template <int MU, unsigned M>
+__device__ __forceinline__ void tc_lower(const Bfrag& h0, const Bfrag& h1, Bfrag& q0, Bfrag& q1) {
+  constexpr unsigned N = kSign2;
+  if constexpr (MU == 0) {
+    q0 = {h0.re ^ M, h0.im ^ M};
+    q1 = {h1.re ^ M, h1.im ^ M};
+  } else if constexpr (MU == 1) {
+    q0 = {h1.im ^ (N ^ M), h1.re ^ M};
+    q1 = {h0.im ^ (N ^ M), h0.re ^ M};
+  } else if constexpr (MU == 2) {
+    q0 = {h1.re ^ M, h1.im ^ M};
+    q1 = {h0.re ^ (N ^ M), h0.im ^ (N ^ M)};
+  } else {
+    q0 = {h0.im ^ (N ^ M), h0.re ^ M};
+    q1 = {h1.im ^ M, h1.re ^ (N ^ M)};
+  }
 }
 
-template <int MU, int FB, int D, int NT>
-__device__ __forceinline__ void tc_sense(const MrhsArgs& A, TcShared<D, NT>& sh, const uint2* lt, int n, float sg,
-                                         const int (&acode)[8], float (&cu)[NT][4], float (&cl)[NT][4]) {
-  const int lane = threadIdx.x & 31;
-  const int nr = 4 * NT;
-  // stage the link
-  for (int e = lane; e < D * D; e += 32) {
-    const uint2 v = __ldg(lt + (MU * D * D + e) * kLinkTile);
-    sh.link[e] = FB == 0 ? v.x : v.y;
-  }
-  // h and h' columns n = 2 r + s, K rows (colour c: re at c, im at c + d)
-  const uint2* in = reinterpret_cast<const uint2*>(A.in);
-  const size_t Vn = (size_t)A.g.Vh * nr;
-  for (int idx = lane; idx < nr * D; idx += 32) {
-    const int r = idx / D, c = idx - r * D;
-    const size_t e = (size_t)n * nr + r;
-    const uint2 v0 = __ldg(in + (size_t)c * Vn + e);        // (psi0, psi2)
-    const uint2 v1 = __ldg(in + (size_t)(D + c) * Vn + e);  // (psi1, psi3)
-    const float2 p0 = bf2_to_f2(v0.x), p2 = bf2_to_f2(v0.y), p1 = bf2_to_f2(v1.x), p3 = bf2_to_f2(v1.y);
-    const cx<float> u0 = cmake(p0.x, p0.y), u1 = cmake(p1.x, p1.y), l0 = cmake(p2.x, p2.y), l1 = cmake(p3.x, p3.y);
-    cx<float> b0, b1;  // B_mu l
-    if (MU == 0) {
-      b0 = l0;
-      b1 = l1;
-    } else if (MU == 1) {
-      b0 = cmake(l1.im, -l1.re);
-      b1 = cmake(l0.im, -l0.re);
-    } else if (MU == 2) {
-      b0 = cmake(-l1.re, -l1.im);
-      b1 = l0;
-    } else {
-      b0 = cmake(l0.im, -l0.re);
-      b1 = cmake(-l1.im, l1.re);
+// A fragments of a link: lane (g, t) holds rows g, g + 8 and K columns 2t,
+// 2t+1, 2t+8, 2t+9 of [[Ur, -Ui], [Ui, Ur]], i.e. colours c = t and c' = t + d/2,
+// from elements e0 = U[g][c], e1 = U[g][c']; `mask` is zero for lanes whose
+// columns lie outside the d x d block
+__device__ __forceinline__ void tc_afrag(unsigned e0, unsigned e1, unsigned mask, unsigned (&a)[4]) {
+  a[0] = __byte_perm(e0, e1, 0x5410) & mask;  // Ur
+  a[1] = __byte_perm(e0, e1, 0x7632) & mask;  // Ui
+  a[2] = a[1] ^ kSign2;                       // -Ui
+  a[3] = a[0];                                // Ur
+}
+
+// per-lane constant offsets
+template <int D, int NR>
+struct TcLane {
+  using L = TcLayout<D, NR>;
+  unsigned rd[4];  // planes c, c', D+c, D+c' (c = t, c' = t + d/2) at RHS g; colours 0, d/2 for idle lanes
+  unsigned rdh;    // to RHS 8 NGF + (g & 3) instead of g
+  unsigned la;     // link element (g, c) within a site's link block; (g, c') is d/2 elements on
+  unsigned amask;
+  size_t src[L::per_lane];  // cp.async piece k of a block at site 0 (bytes from the field base)
+  unsigned dst[L::per_lane];
+  __device__ __forceinline__ void init(int lane, int Vh) {
+#pragma unroll
+    for (int k = 0; k < L::per_lane; ++k) {
+      const int cc = min(lane + 32 * k, L::chunks - 1);
+      const int plane = cc / L::row_chunks, w = cc % L::row_chunks;
+      src[k] = (size_t)plane * Vh * NR * 8 + (size_t)w * 16;
+      dst[k] = (unsigned)(plane * NR * 8 + w * 16);
     }
-    const cx<float> h0 = cmake(fmaf(sg, b0.re, u0.re), fmaf(sg, b0.im, u0.im));
-    const cx<float> h1 = cmake(fmaf(sg, b1.re, u1.re), fmaf(sg, b1.im, u1.im));
-    cx<float> q0, q1;  // B_mu^+ h
-    if (MU == 0) {
-      q0 = h0;
-      q1 = h1;
-    } else if (MU == 1) {
-      q0 = cmake(-h1.im, h1.re);
-      q1 = cmake(-h0.im, h0.re);
-    } else if (MU == 2) {
-      q0 = h1;
-      q1 = cmake(-h0.re, -h0.im);
-    } else {
-      q0 = cmake(-h0.im, h0.re);
-      q1 = cmake(h1.im, -h1.re);
-    }
-    sh.h[0][2 * r][c] = bf16_bits(h0.re);
-    sh.h[0][2 * r][D + c] = bf16_bits(h0.im);
-    sh.h[0][2 * r + 1][c] = bf16_bits(h1.re);
-    sh.h[0][2 * r + 1][D + c] = bf16_bits(h1.im);
-    sh.h[1][2 * r][c] = bf16_bits(sg * q0.re);
-    sh.h[1][2 * r][D + c] = bf16_bits(sg * q0.im);
-    sh.h[1][2 * r + 1][c] = bf16_bits(sg * q1.re);
-    sh.h[1][2 * r + 1][D + c] = bf16_bits(sg * q1.im);
+    const int g = lane >> 2, t = lane & 3;
+    const int c = t < D / 2 ? t : 0;
+    const int planes[4] = {c, c + D / 2, D + c, D + c + D / 2};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) rd[m] = (unsigned)((planes[m] * NR + g) * 8);
+    rdh = (unsigned)(8 * (8 * L::NGF + (g & 3)) - 8 * g);
+    la = (unsigned)((min(g, D - 1) * D + c) * 8);
+    amask = t < D / 2 ? ~0u : 0u;
   }
-  __syncwarp();
-  // A fragment of the realified link
+};
+
+// one direction-sense (MU, FB) of the warp's current site from its stage
+template <int MU, int FB, bool DAG, int D, int NR>
+__device__ __forceinline__ void tc_item(unsigned stage, unsigned lsite, const TcLane<D, NR>& ln, unsigned (&abwd)[4],
+                                        float (&cu)[NR / 4][4], float (&cl)[NR / 4][4], int g) {
+  using L = TcLayout<D, NR>;
+  // sg = -1 (+1 for the adjoint) on forward senses, -sg on backward ones
+  constexpr unsigned SM = ((DAG ? 0u : kSign2) ^ (FB ? kSign2 : 0u));
   unsigned a[4];
+  if constexpr (FB == 0) {
+    const uint2 v0 = lds64(lsite + ln.la + MU * D * D * 8);            // (fwd, bwd) of U[g][c]
+    const uint2 v1 = lds64(lsite + ln.la + (MU * D * D + D / 2) * 8);  // and of U[g][c + d/2]
+    tc_afrag(v0.x, v1.x, ln.amask, a);
+    tc_afrag(v0.y, v1.y, ln.amask, abwd);
+  } else {
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-    a[q] = (unsigned)a_value(sh.link, acode[2 * q]) | ((unsigned)a_value(sh.link, acode[2 * q + 1]) << 16);
-  const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int j = 0; j < NT; ++j) {
-    const unsigned* hu = reinterpret_cast<const unsigned*>(sh.h[0][8 * j + g]);
-    const unsigned* hl = reinterpret_cast<const unsigned*>(sh.h[1][8 * j + g]);
-    mma_bf16(cu[j], a, hu[t], hu[t + 4]);
-    mma_bf16(cl[j], a, hl[t], hl[t + 4]);
+    for (int q = 0; q < 4; ++q) a[q] = abwd[q];
   }
-  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < L::NGF; ++k) {
+    uint2 w[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) w[m] = lds64(stage + ln.rd[m] + 64 * k);
+    Bfrag h0, h1, q0, q1;
+    tc_project<MU, SM>(w, h0, h1);
+    tc_lower<MU, SM>(h0, h1, q0, q1);
+    mma_bf16(cu[2 * k], a, h0.re, h0.im);
+    mma_bf16(cu[2 * k + 1], a, h1.re, h1.im);
+    mma_bf16(cl[2 * k], a, q0.re, q0.im);
+    mma_bf16(cl[2 * k + 1], a, q1.re, q1.im);
+  }
+  if constexpr (L::HALF) {
+    uint2 w[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) w[m] = lds64(stage + ln.rd[m] + ln.rdh);
+    Bfrag h0, h1, q0, q1;
+    tc_project<MU, SM>(w, h0, h1);
+    tc_lower<MU, SM>(h0, h1, q0, q1);
+    const bool s1 = g >= 4;  // this lane's column holds spin 1
+    mma_bf16(cu[2 * L::NGF], a, s1 ? h1.re : h0.re, s1 ? h1.im : h0.im);
+    mma_bf16(cl[2 * L::NGF], a, s1 ? q1.re : q0.re, s1 ? q1.im : q0.im);
+  }
 }
 
-template <int MU, int D, int NT>
-__device__ __forceinline__ void tc_direction(const MrhsArgs& A, TcShared<D, NT>& sh, const uint2* lt, int nf, int nb,
-                                             float sg, const int (&acode)[8], float (&cu)[NT][4],
-                                             float (&cl)[NT][4]) {
-  tc_sense<MU, 0, D, NT>(A, sh, lt, nf, sg, acode, cu, cl);
-  tc_sense<MU, 1, D, NT>(A, sh, lt, nb, -sg, acode, cu, cl);
+// output words of one lane: plane, RHS r and r + 1, from upper (spin s) and
+// lower (spin s + 2) accumulators -> (psi_s, psi_s+2) pairs, optionally
+// a x + b W with x from the staged same-site block
+__device__ __forceinline__ void tc_store(const MrhsArgs& A, char* out, size_t off, bool with_x, unsigned xs,
+                                         const float (&u)[4], const float (&l)[4]) {
+  float v[8] = {u[0], u[2], l[0], l[2], u[1], u[3], l[1], l[3]};  // (re, im) of psi_s(r), psi_s+2(r), ... r + 1
+  if (with_x) {
+    const uint4 xv = lds128(xs);
+    const unsigned xw[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 f = bf2_to_f2(xw[q]);
+      v[2 * q] = fmaf(A.af, f.x, A.bf * v[2 * q]);
+      v[2 * q + 1] = fmaf(A.af, f.y, A.bf * v[2 * q + 1]);
+    }
+  } else if (!A.b_one) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] *= A.bf;
+  }
+  *reinterpret_cast<uint4*>(out + off) =
+      make_uint4(f2_to_bf2(v[0], v[1]), f2_to_bf2(v[2], v[3]), f2_to_bf2(v[4], v[5]), f2_to_bf2(v[6], v[7]));
 }
 
-template <int D, int NT>
-__global__ void __launch_bounds__(32 * kTcWarps) hop_mrhs_tc_kernel(const MrhsArgs A) {
-  __shared__ TcShared<D, NT> shared_all[kTcWarps];
+template <int D, int NR, bool DAG>
+__global__ void __launch_bounds__(32 * kTcWarps, kTcBlocksPerSm) hop_mrhs_tc_kernel(const MrhsArgs A) {
+  using L = TcLayout<D, NR>;
+  constexpr int S = L::S;
+  extern __shared__ __align__(128) unsigned char tc_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kTcWarps + warp;  // this warp's output site
-  if (i >= A.g.Vh) return;                     // uniform over the warp
-  TcShared<D, NT>& sh = shared_all[warp];
-  // K rows 2d..15 of h^T, h'^T stay zero
-  for (int e = lane; e < 2 * 8 * NT * 16; e += 32) (&sh.h[0][0][0])[e] = 0;
   const int g = lane >> 2, t = lane & 3;
-  int acode[8];  // fragment slots: (g, 2t..2t+1), (g+8, 2t..), (g, 2t+8..), (g+8, 2t+8..)
-  acode[0] = a_code(D, g, 2 * t);
-  acode[1] = a_code(D, g, 2 * t + 1);
-  acode[2] = a_code(D, g + 8, 2 * t);
-  acode[3] = a_code(D, g + 8, 2 * t + 1);
-  acode[4] = a_code(D, g, 2 * t + 8);
-  acode[5] = a_code(D, g, 2 * t + 9);
-  acode[6] = a_code(D, g + 8, 2 * t + 8);
-  acode[7] = a_code(D, g + 8, 2 * t + 9);
-  __syncwarp();
+  const int Vh = A.g.Vh;
+  const int nq = (Vh + kTcWarps - 1) / kTcWarps;  // quads of consecutive sites
+  int q = blockIdx.x;
+  if (q >= nq) return;  // uniform over the block, before any barrier
 
-  int nf[4], nb[4];
-  eo_neighbours(A.g, i, A.p, nf, nb);
-  const uint2* lt = LinkIO<BF16, D, false>::tile_ptr(A.links, i);
-  const float sg = A.dagger ? 1.f : -1.f;
-  float cu[NT][4], cl[NT][4];
-#pragma unroll
-  for (int j = 0; j < NT; ++j)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) cu[j][q] = cl[j][q] = 0.f;
-  tc_direction<0, D, NT>(A, sh, lt, nf[0], nb[0], sg, acode, cu, cl);
-  tc_direction<1, D, NT>(A, sh, lt, nf[1], nb[1], sg, acode, cu, cl);
-  tc_direction<2, D, NT>(A, sh, lt, nf[2], nb[2], sg, acode, cu, cl);
-  tc_direction<3, D, NT>(A, sh, lt, nf[3], nb[3], sg, acode, cu, cl);
+  const unsigned base = (unsigned)__cvta_generic_to_shared(tc_smem);
+  const unsigned ring = base + warp * L::warp_bytes;
+  const unsigned xbuf = ring + S * L::spin_bytes;
+  const unsigned links = base + L::links_off;
+  TcLane<D, NR> ln;
+  ln.init(lane, A.g.Vh);
+  TcGeom geo;
+  geo.init(A.g);
+  __syncthreads();
 
-  // epilogue: accumulators -> shared (rows = re/im of colours, columns = (rhs, spin))
+  const bool with_x = A.x != nullptr;
+  char* out = static_cast<char*>(A.out);
+  const char* in = static_cast<const char*>(A.in);
+  const char* xin = static_cast<const char*>(A.x);
+
+  // the links of quad qq (sites 4 qq .. 4 qq + 3, one link tile) into buffer b
+  auto fetch_links = [&](int qq, int b) {
+    const uint2* lt = LinkIO<BF16, D, false>::tile_ptr(A.links, kTcWarps * qq);
+    for (int idx = threadIdx.x; idx < L::link_elems; idx += 32 * kTcWarps) {
+      const int s = (idx >> 3) & 3, P = ((idx >> 5) << 3) | (idx & 7);
+      if (kTcWarps * qq + s < Vh)
+        cp_async8_ca(links + b * L::link_buf + s * L::link_site + P * 8, lt + (size_t)P * kLinkTile + s);
+    }
+  };
+
+  int site = kTcWarps * q + warp;
+  int nb8[8];
+  // Every step commits one cp.async group (its item's pieces; at step 0 also
+  // the next quad's links, at step 1 the site's x block), so the group of
+  // item j is complete once at most S - 2 newer groups are pending.
+  auto issue = [&](unsigned st, const char* field, int n) {  // site n's block of `field` into st
+    const char* src = field + (size_t)(unsigned)n * (NR * 8);
 #pragma unroll
-  for (int j = 0; j < NT; ++j) {
-    const int col = 8 * j + 2 * t;
-    sh.c[0][g][col] = cu[j][0];
-    sh.c[0][g][col + 1] = cu[j][1];
-    sh.c[0][g + 8][col] = cu[j][2];
-    sh.c[0][g + 8][col + 1] = cu[j][3];
-    sh.c[1][g][col] = cl[j][0];
-    sh.c[1][g][col + 1] = cl[j][1];
-    sh.c[1][g + 8][col] = cl[j][2];
-    sh.c[1][g + 8][col + 1] = cl[j][3];
+    for (int c = 0; c < L::per_lane; ++c)
+      if (L::chunks % 32 == 0 || lane + 32 * c < L::chunks) cp_async16_cg(st + ln.dst[c], src + ln.src[c]);
+  };
+  fetch_links(q, 0);
+  if (site < Vh) geo.neighbours(A.g, site, A.p, nb8);
+#pragma unroll
+  for (int j = 0; j < S - 2; ++j) {
+    if (site < Vh) issue(ring + j * L::spin_bytes, in, nb8[j]);
+    cp_commit();
   }
-  __syncwarp();
-  const int nr = 4 * NT;
-  const size_t Vn = (size_t)A.g.Vh * nr;
-  uint2* out = reinterpret_cast<uint2*>(A.out);
-  const uint2* xin = reinterpret_cast<const uint2*>(A.x);
-  const float a = A.af, b = A.bf;
-  for (int idx = lane; idx < nr * D; idx += 32) {
-    const int r = idx / D, c = idx - r * D;
-    float s[4][2];  // spin, re/im
-    for (int sp = 0; sp < 2; ++sp) {
-      s[sp][0] = sh.c[0][c][2 * r + sp];
-      s[sp][1] = sh.c[0][D + c][2 * r + sp];
-      s[sp + 2][0] = sh.c[1][c][2 * r + sp];
-      s[sp + 2][1] = sh.c[1][D + c][2 * r + sp];
-    }
-    const size_t e = (size_t)i * nr + r;
-    if (xin != nullptr) {
-      const uint2 x0 = __ldg(xin + (size_t)c * Vn + e), x1 = __ldg(xin + (size_t)(D + c) * Vn + e);
-      const float2 xs[4] = {bf2_to_f2(x0.x), bf2_to_f2(x1.x), bf2_to_f2(x0.y), bf2_to_f2(x1.y)};
-      for (int sp = 0; sp < 4; ++sp) {
-        s[sp][0] = fmaf(a, xs[sp].x, b * s[sp][0]);
-        s[sp][1] = fmaf(a, xs[sp].y, b * s[sp][1]);
+
+  for (int k = 0; q < nq; ++k) {
+    const int qn = q + gridDim.x;
+    const int next = kTcWarps * qn + warp;
+    const bool active = site < Vh, next_active = qn < nq && next < Vh;
+    // quad q's links: in the prologue's groups (k = 0) or in step 0's group of
+    // the previous iteration, seven groups back
+    if (k == 0) cp_wait<0>();
+    else cp_wait<7>();
+    __syncthreads();  // the links are in buffer k & 1 for every warp; buffer (k + 1) & 1 is free
+    const unsigned lsite = links + (k & 1) * L::link_buf + warp * L::link_site;
+
+    if (active) {
+      float cu[L::NT][4], cl[L::NT][4];
+#pragma unroll
+      for (int j = 0; j < L::NT; ++j)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cu[j][c] = cl[j][c] = 0.f;
+      unsigned abwd[4];
+      auto step = [&](auto ds_c) {
+        constexpr int ds = decltype(ds_c)::value;
+        constexpr int fj = ds + S - 2;  // item to copy: the next site's from fj = 8 on
+        constexpr int fds = fj % 8;
+        if constexpr (ds == 10 - S) {  // the current site's last copy went out in the step before
+          if (next_active) geo.neighbours(A.g, next, A.p, nb8);
+        }
+        if (fj < 8 || next_active) issue(ring + (fj % S) * L::spin_bytes, in, nb8[fds]);
+        if constexpr (ds == 0) {
+          if (qn < nq) fetch_links(qn, (k + 1) & 1);
+        }
+        if constexpr (ds == 1) {  // this site's own input for a x + b H, read in the epilogue
+          if (with_x) issue(xbuf, xin, site);
+        }
+        cp_commit();
+        cp_wait<S - 2>();  // this lane's pieces of item ds
+        __syncwarp();      // every lane's pieces of item ds are visible; the stage read two steps ago is free
+        tc_item<ds / 2, ds % 2, DAG, D, NR>(ring + (ds % S) * L::spin_bytes, lsite, ln, abwd, cu, cl, g);
+      };
+      step(std::integral_constant<int, 0>{});
+      step(std::integral_constant<int, 1>{});
+      step(std::integral_constant<int, 2>{});
+      step(std::integral_constant<int, 3>{});
+      step(std::integral_constant<int, 4>{});
+      step(std::integral_constant<int, 5>{});
+      step(std::integral_constant<int, 6>{});
+      step(std::integral_constant<int, 7>{});
+
+      // epilogue: lane (g, t) holds colour g (rows g, g + 8) of columns 2t, 2t+1 of every tile
+      if (g < D) {
+#pragma unroll
+        for (int kk = 0; kk < L::NGF; ++kk) {
+          const int r = 8 * kk + 2 * t;
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            const int plane = s * D + g;
+            const size_t off = (((size_t)plane * Vh + site) * NR + r) * 8;
+            const unsigned xs = xbuf + (unsigned)((plane * NR + r) * 8);
+            tc_store(A, out, off, with_x, xs, cu[2 * kk + s], cl[2 * kk + s]);
+          }
+        }
+        if constexpr (L::HALF) {
+          const int r = 8 * L::NGF + 2 * (t & 1), plane = (t >> 1) * D + g;
+          const size_t off = (((size_t)plane * Vh + site) * NR + r) * 8;
+          const unsigned xs = xbuf + (unsigned)((plane * NR + r) * 8);
+          tc_store(A, out, off, with_x, xs, cu[2 * L::NGF], cl[2 * L::NGF]);
+        }
       }
-    } else if (b != 1.f) {
-      for (int sp = 0; sp < 4; ++sp) {
-        s[sp][0] *= b;
-        s[sp][1] *= b;
-      }
+      __syncwarp();  // the x block and the stages are read before later copies refill them
     }
-    out[(size_t)c * Vn + e] = make_uint2(f2_to_bf2(s[0][0], s[0][1]), f2_to_bf2(s[2][0], s[2][1]));
-    out[(size_t)(D + c) * Vn + e] = make_uint2(f2_to_bf2(s[1][0], s[1][1]), f2_to_bf2(s[3][0], s[3][1]));
+    q = qn;
+    site = next;
   }
+  cp_wait<0>();
 }
 
-template <int D, int NT>
-void launch_tc_t(const MrhsArgs& A, cudaStream_t s) {
-  const int blocks = (A.g.Vh + kTcWarps - 1) / kTcWarps;
-  hop_mrhs_tc_kernel<D, NT><<<blocks, 32 * kTcWarps, 0, s>>>(with_f32_scalars(A));
+template <int D, int NR, bool DAG>
+bool launch_tc_dag(const MrhsArgs& A, cudaStream_t s) {
+  using L = TcLayout<D, NR>;
+  const size_t smem = (size_t)L::block_bytes;
+  static int blocks_per_sm = 0, sms = 0;
+  if (blocks_per_sm == 0) {
+    cudaFuncSetAttribute(hop_mrhs_tc_kernel<D, NR, DAG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, n = 0, b = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      sms = n;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, hop_mrhs_tc_kernel<D, NR, DAG>, 32 * kTcWarps, smem) !=
+        cudaSuccess)
+      b = 1;
+    if (sms <= 0) sms = 1;
+    blocks_per_sm = std::max(b, 1);
+  }
+  const int nq = (A.g.Vh + kTcWarps - 1) / kTcWarps;
+  const int blocks = std::min(nq, sms * blocks_per_sm);
+  hop_mrhs_tc_kernel<D, NR, DAG><<<blocks, 32 * kTcWarps, smem, s>>>(with_f32_scalars(A));
+  return true;
+}
+
+template <int D, int NR>
+bool launch_tc_t(const MrhsArgs& A, cudaStream_t s) {
+  return A.dagger ? launch_tc_dag<D, NR, true>(A, s) : launch_tc_dag<D, NR, false>(A, s);
 }
 
 template <int D>
 bool launch_tc_nt(const MrhsArgs& A, cudaStream_t s) {
   switch (A.nrhs) {
-    case 4: launch_tc_t<D, 1>(A, s); return true;
-    case 8: launch_tc_t<D, 2>(A, s); return true;
-    case 12: launch_tc_t<D, 3>(A, s); return true;
-    case 16: launch_tc_t<D, 4>(A, s); return true;
+    case 4: return launch_tc_t<D, 4>(A, s);
+    case 8: return launch_tc_t<D, 8>(A, s);
+    case 12: return launch_tc_t<D, 12>(A, s);
+    case 16: return launch_tc_t<D, 16>(A, s);
     default: return false;
   }
 }

@@ -116,7 +116,7 @@ def test_mrhs_matches_single_rhs_calls():
         assert rel(got[r], c.cpu().numpy()) < 1e-6
 
 
-@pytest.mark.parametrize("nrhs", [4, 12])
+@pytest.mark.parametrize("nrhs", [4, 8, 12, 16])
 @pytest.mark.parametrize("N,rep", [(4, bsm.FUND), (6, bsm.FUND), (4, bsm.ASYM), (3, bsm.SYM), (8, bsm.FUND)],
                          ids=["SU4-F", "SU6-F", "SU4-AS", "SU3-S", "SU8-F"])
 def test_mrhs_tensor_core_path(N, rep, nrhs):
@@ -144,6 +144,29 @@ def test_mrhs_tensor_core_path(N, rep, nrhs):
         assert rel(tc[0][r], orc.dirac(olat, R, psis[r])) <= TOL[prec]
         assert rel(tc[1][r], orc.hop(olat, R, psis[r], out_parity=orc.ODD, dagger=True)) <= TOL[prec]
         assert rel(tc[0][r], simt[0][r]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("nrhs", [12, 16])
+@pytest.mark.parametrize("dims", [(12, 8, 8, 8), (6, 6, 2, 10)], ids=["8^3x12", "ragged"])
+def test_mrhs_tensor_core_many_sites_per_block(dims, nrhs):
+    """8^3 x 12 (V_h = 3072) has more 4-site groups than the persistent
+    grid has blocks, so warps carry their copy pipeline from one site into
+    the next; 6 x 6 x 2 x 10 (V_h = 360) ends in a partly filled 32-site link
+    tile.  Every RHS against the oracle and against the SIMT kernel."""
+    N, prec = 6, bsm.BF16
+    olat, blat, U, R, psis = setup(dims, N, bsm.FUND, nrhs, 900 + nrhs)
+    Ud = gpu_links(blat, U, prec)
+    inp = pack(blat, psis, prec)
+    results = {}
+    for block in (bsm.MRHS_TENSOR_CORE_BLOCK, 1):
+        bsm.bsm_dslash_mrhs_set_block(blat, nrhs, prec, block)
+        full = mrhs_field(blat, nrhs, prec)
+        bsm.bsm_dslash_mrhs(blat, Ud, inp, full, nrhs, bsm.FULL, 0, prec)
+        results[block] = unpack(blat, full, nrhs, prec)
+    bsm.bsm_dslash_mrhs_set_block(blat, nrhs, prec, 0)
+    for r in range(nrhs):
+        assert rel(results[bsm.MRHS_TENSOR_CORE_BLOCK][r], orc.dirac(olat, R, psis[r])) <= TOL[prec]
+        assert rel(results[bsm.MRHS_TENSOR_CORE_BLOCK][r], results[1][r]) <= TOL[prec]
 
 
 def test_mrhs_set_block_rejects_unavailable_blocks():

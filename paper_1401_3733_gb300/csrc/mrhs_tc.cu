@@ -49,7 +49,6 @@ namespace {
 
 constexpr int kTcWarps = 4;        // warps (sites) per block
 constexpr int kTcBlocksPerSm = 4;  // register budget: 128 per thread
-constexpr int kTcSmemPerSm = 216 * 1024;
 constexpr unsigned kSign2 = 0x80008000u;
 
 template <int D, int NR>
@@ -59,8 +58,7 @@ struct TcLayout {
   // 32 so that the copies of two sites (lanes 0-7, 8-15) use different banks
   static constexpr int link_site = 4 * D * D * 8 + ((4 * D * D * 8 / 4) % 32 == 16 ? 0 : 64);
   static constexpr int link_buf = kTcWarps * link_site;
-  static constexpr int block_for(int S) { return kTcWarps * (S + 1) * spin_bytes + 2 * link_buf; }
-  static constexpr int S = kTcBlocksPerSm * block_for(8) <= kTcSmemPerSm ? 8 : 4;  // ring depth
+  static constexpr int S = 4;  // ring depth: two items in flight (8 stages measured no faster: the copies are bandwidth-bound)
   static constexpr int warp_bytes = (S + 1) * spin_bytes;  // S stages, then the x block
   static constexpr int links_off = kTcWarps * warp_bytes;  // two link buffers
   static constexpr int block_bytes = links_off + 2 * link_buf;

@@ -454,25 +454,31 @@ __global__ void __launch_bounds__(32 * kTcWarps, kTcBlocksPerSm) hop_mrhs_tc_ker
   cp_wait<0>();
 }
 
+// launch shape per device: the shared-memory opt-in and the occupancy are
+// per device, so they are set up once for each device the kernel runs on
+constexpr int kTcMaxDevices = 64;
+
 template <int D, int NR, bool DAG>
 bool launch_tc_dag(const MrhsArgs& A, cudaStream_t s) {
   using L = TcLayout<D, NR>;
   const size_t smem = (size_t)L::block_bytes;
-  static int blocks_per_sm = 0, sms = 0;
-  if (blocks_per_sm == 0) {
-    cudaFuncSetAttribute(hop_mrhs_tc_kernel<D, NR, DAG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int dev = 0, n = 0, b = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-      sms = n;
+  static int grid_cap[kTcMaxDevices];  // SMs x resident blocks, 0 until set up
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTcMaxDevices) return false;
+  if (grid_cap[dev] == 0) {
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(hop_mrhs_tc_kernel<D, NR, DAG>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return false;
+    int sms = 0, b = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return false;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, hop_mrhs_tc_kernel<D, NR, DAG>, 32 * kTcWarps, smem) !=
-        cudaSuccess)
-      b = 1;
-    if (sms <= 0) sms = 1;
-    blocks_per_sm = std::max(b, 1);
+            cudaSuccess ||
+        b <= 0)
+      return false;
+    grid_cap[dev] = sms * b;
   }
   const int nq = (A.g.Vh + kTcWarps - 1) / kTcWarps;
-  const int blocks = std::min(nq, sms * blocks_per_sm);
-  hop_mrhs_tc_kernel<D, NR, DAG><<<blocks, 32 * kTcWarps, smem, s>>>(with_f32_scalars(A));
+  hop_mrhs_tc_kernel<D, NR, DAG><<<std::min(nq, grid_cap[dev]), 32 * kTcWarps, smem, s>>>(with_f32_scalars(A));
   return true;
 }
 

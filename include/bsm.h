@@ -463,13 +463,17 @@ int bsm_fgcr_solve(const bsm_lattice *lat, const void *U_rep64, const void *U_re
                    size_t workspace_bytes, void *stream);
 
 /* The launch configuration the last batch call on this thread used: RHS
- * per thread (1 or 2) and chunks of 128 thread slots per work-queue grab
+ * per thread (1 or 2, or 102 / 104 for 2 / 4 RHS held as lane pairs of
+ * packed FP32 instructions, as in bsm_dslash_mrhs_block; every lattice's
+ * nrhs is a multiple of it) and chunks of 128 thread slots per work-queue grab
  * (1, 2, 4 or 8).  bsm_dslash_batch, bsm_dslash_batch_async and
  * bsm_cg_solve_batch pick it per batch shape (the lattices and their nrhs)
  * on their first call by timing every candidate on `stream` (which
  * synchronises it), unless the stream is capturing a graph or the
  * environment sets BSM_BATCH_TUNE=0; then the tuned choice if one exists,
- * else (1, 4).  The results do not depend on it.  Pure host. */
+ * else (1, 4).  BSM_BATCH_CONFIG="rb:grab" (e.g. "104:2") pins one
+ * configuration for every batch whose nrhs are multiples of rb.  The
+ * results do not depend on it.  Pure host. */
 int bsm_batch_last_config(int32_t *rhs_per_thread, int32_t *chunks_per_grab);
 
 /* A batch of systems solved together: mixed-precision CG (FP32 iterations,

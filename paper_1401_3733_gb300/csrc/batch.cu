@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <map>
+#include <numeric>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -66,8 +67,9 @@ constexpr int kMaxBatchTasks = 128;    // up to 4 tasks per lattice (Dhat^+ Dhat
 // launch configuration: RHS per thread (RB) and chunks per work-queue grab;
 // picked per batch shape by timing (batch_tuned_config), or the default
 struct BatchConfig {
-  int rb = 1;
+  int rb = 1;           // RHS per thread: 1 or 2, or 2 and 4 as packed pairs
   int grab = 4;
+  bool paired = false;  // RHS held two per f32x2 register pair (bit-identical results)
 };
 
 // the whole task table as one launch parameter (the parameter space holds up
@@ -79,9 +81,11 @@ static_assert(sizeof(BatchTable) + sizeof(BatchMeta) + sizeof(void*) < 32000, "b
 
 // RB = 1: 128 registers, 4 blocks per SM (measured: 7 % faster than 168 / 3
 // on the 16-lattice batch, as for the d = 3 multi-RHS kernel); RB = 2: two
-// RHS per thread (each link element applied to both), 2 blocks per SM.  A
-// thread slot of a task is (site, block of RB RHS).
-template <int RB>
+// RHS per thread (each link element applied to both), 2 blocks per SM;
+// PAIRED: RB = 2 or 4 RHS per thread as lane pairs of packed FP32
+// instructions (the multi-RHS paired kernel's site code).  A thread slot of
+// a task is (site, block of RB RHS).
+template <int RB, bool PAIRED>
 __global__ void __launch_bounds__(kHopThreads, RB == 1 ? 4 : 2) batch_kernel(const __grid_constant__ BatchTable table,
                                                                              BatchControl* ctl, const BatchMeta meta) {
   __shared__ BatchTask s_tasks[kMaxBatchTasks];
@@ -110,7 +114,15 @@ __global__ void __launch_bounds__(kHopThreads, RB == 1 ? 4 : 2) batch_kernel(con
         if (u < (long long)tk.args.g.Vh * nblk) {
           const int i = (int)(u / nblk), r = (int)(u - (long long)i * nblk) * RB;
           // later phases read what an earlier phase of this launch wrote: through L2 only
-          if (phase == 0) {
+          if constexpr (PAIRED) {
+            if (phase == 0) {
+              if (tk.d == 2) mrhs_site_paired<F32, 2, false, RB / 2>(tk.args, i, r);
+              else mrhs_site_paired<F32, 3, false, RB / 2>(tk.args, i, r);
+            } else {
+              if (tk.d == 2) mrhs_site_paired<F32, 2, false, RB / 2, true>(tk.args, i, r);
+              else mrhs_site_paired<F32, 3, false, RB / 2, true>(tk.args, i, r);
+            }
+          } else if (phase == 0) {
             if (tk.d == 2) mrhs_site<F32, 2, false, RB>(tk.args, i, r);
             else mrhs_site<F32, 3, false, RB>(tk.args, i, r);
           } else {
@@ -168,7 +180,8 @@ int launch_tasks(const std::vector<BatchTask>& tasks, BatchMeta meta, BatchContr
   if ((int)tasks.size() > kMaxBatchTasks) return BSM_EUNSUPPORTED;
   meta.ntasks = (int)tasks.size();
   meta.grab = cfg.grab;
-  const void* kern = cfg.rb == 2 ? (const void*)batch_kernel<2> : (const void*)batch_kernel<1>;
+  const void* kern = cfg.paired ? (cfg.rb == 4 ? (const void*)batch_kernel<4, true> : (const void*)batch_kernel<2, true>)
+                                : (cfg.rb == 2 ? (const void*)batch_kernel<2, false> : (const void*)batch_kernel<1, false>);
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -344,9 +357,32 @@ bool tuning_allowed(cudaStream_t s) {
   return true;
 }
 
+// candidates: RHS blocks 1 and 2, and packed pairs of 2 and 4 RHS, where
+// every lattice's nrhs is a multiple of the block; with every grab size
+// BSM_BATCH_CONFIG="rb:grab" (rb = 1, 2, 102 or 104) pins the configuration
+// for every shape whose nrhs allow it; false if it is unset or malformed
+bool pinned_config(int nrhs_gcd, BatchConfig& cfg) {
+  const char* env = getenv("BSM_BATCH_CONFIG");
+  int rb = 0, grab = 0;
+  if (env == nullptr || sscanf(env, "%d:%d", &rb, &grab) != 2) return false;
+  const bool paired = rb == kPairedBlock + 2 || rb == kPairedBlock + 4;
+  if (paired) rb -= kPairedBlock;
+  if (!(rb == 1 || rb == 2 || (paired && rb == 4)) || !(grab == 1 || grab == 2 || grab == 4 || grab == 8) ||
+      nrhs_gcd % rb != 0)
+    return false;
+  cfg.rb = rb;
+  cfg.grab = grab;
+  cfg.paired = paired;
+  return true;
+}
+
 template <typename Launch>
-int tuned_launch(const std::string& key, bool rb2_ok, cudaStream_t s, void* ctl_ws, Launch launch) {
+int tuned_launch(const std::string& key, int nrhs_gcd, cudaStream_t s, void* ctl_ws, Launch launch) {
   BatchConfig cfg;
+  if (pinned_config(nrhs_gcd, cfg)) {
+    g_last = cfg;
+    return launch(cfg);
+  }
   bool have = false;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -361,10 +397,11 @@ int tuned_launch(const std::string& key, bool rb2_ok, cudaStream_t s, void* ctl_
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return BSM_ECUDA;
     float best = 1e30f;
     BatchConfig win;
-    for (int rb = 1; rb <= (rb2_ok ? 2 : 1); ++rb)
+    const BatchConfig blocks[4] = {{1, 4, false}, {2, 4, false}, {2, 4, true}, {4, 4, true}};
+    for (const BatchConfig& blk : blocks) {
+      if (nrhs_gcd % blk.rb != 0) continue;
       for (int grab : {1, 2, 4, 8}) {
-        BatchConfig c;
-        c.rb = rb;
+        BatchConfig c = blk;
         c.grab = grab;
         int rc = launch(c);  // warm-up
         float ms = 0.f, tot = 0.f;
@@ -387,6 +424,7 @@ int tuned_launch(const std::string& key, bool rb2_ok, cudaStream_t s, void* ctl_
           win = c;
         }
       }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cfg = win;
@@ -418,27 +456,28 @@ std::string shape_key(const char* op, const bsm_lattice* lats, const int* nrhs, 
 // synchronises `s`) unless the stream is capturing or BSM_BATCH_TUNE=0.
 int batch_launch(const bsm_batch_item* items, int count, const bsm_batch_opts& o, void* ws, cudaStream_t s,
                  bool sync) {
-  bool even = true;
-  for (int k = 0; k < count; ++k) even = even && items[k].nrhs % 2 == 0;
+  int gcd = 0;
+  for (int k = 0; k < count; ++k) gcd = std::gcd(gcd, (int)items[k].nrhs);
   const std::string key = shape_key(o.op == BSM_BATCH_DHAT ? "dhat" : "d", &items[0].lat, &items[0].nrhs, count,
                                     sizeof(bsm_batch_item));
-  const int rc = tuned_launch(key, even, s, ws,
+  const int rc = tuned_launch(key, gcd, s, ws,
                               [&](const BatchConfig& c) { return batch_launch_cfg(items, count, o, ws, s, c); });
   if (rc != BSM_OK) return rc;
   return sync ? batch_status(ws, s) : BSM_OK;
 }
 
 int batch_normal_launch(const BatchNormalItem* items, int count, void* ctl_ws, double timeout_s, cudaStream_t s) {
-  bool even = true;
-  for (int k = 0; k < count; ++k) even = even && items[k].nrhs % 2 == 0;
+  int gcd = 0;
+  for (int k = 0; k < count; ++k) gcd = std::gcd(gcd, items[k].nrhs);
   const std::string key = shape_key("normal", &items[0].lat, &items[0].nrhs, count, sizeof(BatchNormalItem));
-  return tuned_launch(key, even, s, ctl_ws, [&](const BatchConfig& c) {
+  return tuned_launch(key, gcd, s, ctl_ws, [&](const BatchConfig& c) {
     return batch_normal_launch_cfg(items, count, ctl_ws, timeout_s, s, c);
   });
 }
 
+// RHS per thread as the multi-RHS block codes: 1, 2, or 102, 104 for packed pairs
 void batch_last_config(int* rb, int* grab) {
-  *rb = g_last.rb;
+  *rb = g_last.paired ? kPairedBlock + g_last.rb : g_last.rb;
   *grab = g_last.grab;
 }
 

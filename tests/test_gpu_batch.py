@@ -129,8 +129,9 @@ EVEN_SHAPES = [((4, 4, 4, 4), 3, 2), ((6, 4, 2, 4), 2, 4), ((8, 4, 4, 2), 3, 2)]
 @pytest.mark.parametrize("op", [bsm.BATCH_D, bsm.BATCH_DHAT], ids=["D", "Dhat"])
 def test_tuned_launch_configuration_changes_nothing(op, monkeypatch):
     """The first call on a batch shape times every (RHS per thread, chunks
-    per grab) candidate and keeps the fastest; with BSM_BATCH_TUNE=0 an
-    untuned shape runs (1, 4).  Both give the same bits, and the oracle's."""
+    per grab) candidate, packed-pair blocks included, and keeps the fastest;
+    with BSM_BATCH_TUNE=0 an untuned shape runs (1, 4).  Both give the same
+    bits, and the oracle's."""
     items, refs = make_batch(op, seed=970, shapes=EVEN_SHAPES)
     arr = bsm.batch_items(items)
     opts = bsm.BatchOpts(op, bsm.F32, 0.0, 0)
@@ -142,10 +143,38 @@ def test_tuned_launch_configuration_changes_nothing(op, monkeypatch):
     monkeypatch.delenv("BSM_BATCH_TUNE")
     assert bsm.bsm_dslash_batch(arr, opts, ws) == bsm.OK
     rb, grab = bsm.bsm_batch_last_config()
-    assert rb in (1, 2) and grab in (1, 2, 4, 8)
+    assert rb in (1, 2, 102, 104) and grab in (1, 2, 4, 8)
     for (olat, R, psis, blat, out, nrhs), f in zip(refs, first):
         assert torch.equal(out, f)
         got = unpack(blat, out, nrhs)
         for r in range(nrhs):
             want = orc.dirac(olat, R, psis[r]) if op == bsm.BATCH_D else orc.dhat(olat, R, psis[r], orc.DHAT)
             assert rel(got[r], want) <= TOL[bsm.F32]
+
+
+@pytest.mark.parametrize("op", [bsm.BATCH_D, bsm.BATCH_DHAT], ids=["D", "Dhat"])
+def test_every_launch_configuration_gives_the_same_bits(op, monkeypatch):
+    """Each RHS block (1 and 2 RHS per thread, 2 and 4 as packed pairs),
+    pinned with BSM_BATCH_CONFIG, against the default (1, 4): the same bits,
+    on lattices whose nrhs (4) admit every block."""
+    shapes = [((4, 4, 4, 4), 3, 4), ((6, 4, 2, 4), 2, 4), ((8, 4, 4, 2), 3, 4)]
+    items, refs = make_batch(op, seed=980, shapes=shapes)
+    arr = bsm.batch_items(items)
+    opts = bsm.BatchOpts(op, bsm.F32, 0.0, 0)
+    ws = torch.empty(bsm.bsm_batch_workspace_bytes(arr, opts), dtype=torch.uint8, device="cuda")
+    monkeypatch.setenv("BSM_BATCH_CONFIG", "1:4")
+    assert bsm.bsm_dslash_batch(arr, opts, ws) == bsm.OK
+    base = [ref[4].clone() for ref in refs]
+    for olat, R, psis, blat, out, nrhs in refs:
+        got = unpack(blat, out, nrhs)
+        for r in range(nrhs):
+            want = orc.dirac(olat, R, psis[r]) if op == bsm.BATCH_D else orc.dhat(olat, R, psis[r], orc.DHAT)
+            assert rel(got[r], want) <= TOL[bsm.F32]
+    for cfg in ("2:1", "102:2", "104:8", "104:1"):
+        monkeypatch.setenv("BSM_BATCH_CONFIG", cfg)
+        for ref in refs:
+            ref[4].zero_()
+        assert bsm.bsm_dslash_batch(arr, opts, ws) == bsm.OK
+        assert bsm.bsm_batch_last_config() == tuple(int(v) for v in cfg.split(":"))
+        for ref, b in zip(refs, base):
+            assert torch.equal(ref[4], b), cfg

@@ -53,6 +53,8 @@ TRAFFIC = {
                  "sources": ["hop_df64.cu", "f32x2.cuh", "hop.cuh", "bsm_internal.cuh", "df64.cuh"]},
     "hop_f32": {"bytes_per_site": 736.0, "sha": "eb66718d6a4215c0",
                 "sources": ["hop_f32.cu", "hop.cuh", "bsm_internal.cuh"]},
+    "hop_f32r12": {"bytes_per_site": 544.0, "sha": "ab237da849b7016d",
+                   "sources": ["hop_f32r12.cu", "hop.cuh", "bsm_internal.cuh"]},
 }
 
 
@@ -624,7 +626,7 @@ def run_ours(args):
         if prec == bsm.F64:
             entry.update(bound="alu (FP64 DFMA, 1.26 TFLOP/s nominal)", hbm_frac=round(ach / peak, 4))
         else:
-            t = traffic_per_site("hop_f32") if prec == bsm.F32 else None
+            t = traffic_per_site("hop_f32" if prec == bsm.F32 else "hop_f32r12")
             entry["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                                  "frac": round(ach / peak, 4), "peak_source": peak_src,
                                  "traffic": None if t is None else round(t * Vh)}

@@ -53,7 +53,12 @@ constexpr unsigned kSign2 = 0x80008000u;
 
 template <int D, int NR>
 struct TcLayout {
-  static constexpr int spin_bytes = 2 * D * NR * 8;  // a site's block: [2d planes][n_rhs words]
+  // a site's block in shared memory: 2d plane rows of n_rhs words; rows are
+  // padded by 32 bytes when n_rhs is a multiple of 8, so that the row pitch is
+  // 8 or 24 words mod 32 and the lanes t of one read (rows t, t + d/2, ...
+  // apart) fall on different banks
+  static constexpr int pitch = NR * 8 + (NR % 8 == 0 ? 32 : 0);
+  static constexpr int spin_bytes = 2 * D * pitch;
   // per-site link block: 4 d^2 (fwd, bwd) pairs; the stride is 16 words mod
   // 32 so that the copies of two sites (lanes 0-7, 8-15) use different banks
   static constexpr int link_site = 4 * D * D * 8 + ((4 * D * D * 8 / 4) % 32 == 16 ? 0 : 64);
@@ -245,13 +250,13 @@ struct TcLane {
       const int cc = min(lane + 32 * k, L::chunks - 1);
       const int plane = cc / L::row_chunks, w = cc % L::row_chunks;
       src[k] = (size_t)plane * Vh * NR * 8 + (size_t)w * 16;
-      dst[k] = (unsigned)(plane * NR * 8 + w * 16);
+      dst[k] = (unsigned)(plane * L::pitch + w * 16);
     }
     const int g = lane >> 2, t = lane & 3;
     const int c = t < D / 2 ? t : 0;
     const int planes[4] = {c, c + D / 2, D + c, D + c + D / 2};
 #pragma unroll
-    for (int m = 0; m < 4; ++m) rd[m] = (unsigned)((planes[m] * NR + g) * 8);
+    for (int m = 0; m < 4; ++m) rd[m] = (unsigned)(planes[m] * L::pitch + g * 8);
     rdh = (unsigned)(8 * (8 * L::NGF + (g & 3)) - 8 * g);
     la = (unsigned)((min(g, D - 1) * D + c) * 8);
     amask = t < D / 2 ? ~0u : 0u;
@@ -435,14 +440,14 @@ __global__ void __launch_bounds__(32 * kTcWarps, kTcBlocksPerSm) hop_mrhs_tc_ker
           for (int s = 0; s < 2; ++s) {
             const int plane = s * D + g;
             const size_t off = (((size_t)plane * Vh + site) * NR + r) * 8;
-            const unsigned xs = xbuf + (unsigned)((plane * NR + r) * 8);
+            const unsigned xs = xbuf + (unsigned)(plane * L::pitch + r * 8);
             tc_store(A, out, off, with_x, xs, cu[2 * kk + s], cl[2 * kk + s]);
           }
         }
         if constexpr (L::HALF) {
           const int r = 8 * L::NGF + 2 * (t & 1), plane = (t >> 1) * D + g;
           const size_t off = (((size_t)plane * Vh + site) * NR + r) * 8;
-          const unsigned xs = xbuf + (unsigned)((plane * NR + r) * 8);
+          const unsigned xs = xbuf + (unsigned)(plane * L::pitch + r * 8);
           tc_store(A, out, off, with_x, xs, cu[2 * L::NGF], cl[2 * L::NGF]);
         }
       }

@@ -38,9 +38,10 @@
 // lanes) into an S-stage ring of its shared memory while it computes item j;
 // the same-site input of the a x + b H form is copied the same way during the
 // site.  The grid is persistent.  On 24^4 x 12 RHS at d = 6 the copies alone
-// take 0.48 ms per D and the arithmetic alone 0.40 ms; overlapped, 0.59 ms.
-// (Moving half or all of each item by TMA tile copies, completing on
-// mbarriers, measured slower: 0.73 and 0.66 ms.)
+// take about 0.48 ms per D and the arithmetic alone 0.40 ms; overlapped,
+// 0.56 ms.  (Moving half or all of each item by TMA tile copies, completing
+// on mbarriers, measured slower: 0.73 and 0.66 ms; so did copying the 4
+// sites' neighbour blocks as one slab per block, 0.57 ms.)
 #include "mrhs.cuh"
 
 namespace bsm {

@@ -17,6 +17,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <numeric>
 #include <mutex>
@@ -175,9 +176,24 @@ namespace {
 // the tasks (ordered by phase) as one cooperative launch: chunk offsets,
 // grid size (every block resident, so that the grid barriers complete),
 // the control block reset, the launch
-int launch_tasks(const std::vector<BatchTask>& tasks, BatchMeta meta, BatchControl* ctl, double timeout_s,
+int launch_tasks(std::vector<BatchTask> tasks, BatchMeta meta, BatchControl* ctl, double timeout_s,
                  int barrier_extra, const BatchConfig& cfg, cudaStream_t s) {
   if ((int)tasks.size() > kMaxBatchTasks) return BSM_EUNSUPPORTED;
+  // The queue hands out chunks in table order: within a phase, the d = 3
+  // tasks before the d = 2 ones (so that the blocks run one site routine at a
+  // time, not both), and large tasks before small ones (the small ones fill
+  // the tail).  Each task writes only its own output, so the order changes
+  // no result.
+  std::stable_sort(tasks.begin(), tasks.end(), [](const BatchTask& a, const BatchTask& b) {
+    if (a.phase != b.phase) return a.phase < b.phase;
+    if (a.d != b.d) return a.d > b.d;
+    return a.chunks > b.chunks;
+  });
+  for (int ph = 0; ph < meta.nphases; ++ph) meta.phase_chunks[ph] = 0;
+  for (BatchTask& t : tasks) {
+    t.chunk0 = meta.phase_chunks[t.phase];
+    meta.phase_chunks[t.phase] += t.chunks;
+  }
   meta.ntasks = (int)tasks.size();
   meta.grab = cfg.grab;
   const void* kern = cfg.paired ? (cfg.rb == 4 ? (const void*)batch_kernel<4, true> : (const void*)batch_kernel<2, true>)

@@ -373,10 +373,22 @@ size_t bsm_ptc_workspace_bytes(const bsm_lattice *lat, int32_t channels, int32_t
 
 /* out = M(in) for nbatch one-channel PTC fields.  prec BSM_F32: complex FP32
  * GEMMs; BSM_BF16: transported fields and weights rounded to BF16, products
- * accumulated in FP32 (inference).  Asynchronous on `stream`. */
+ * accumulated in FP32 (inference).  Asynchronous on `stream`.  The BF16
+ * path with 2, 4, 8 or 12 channels runs one tensor-core kernel whose waits
+ * for MMA completion are bounded (2^20 polls; the environment variable
+ * BSM_PTC_WAIT_POLLS lowers the bound, 0 making every first wait give up,
+ * for tests of this path): a block whose wait gives up waits once more,
+ * bounded, for its MMAs in flight, issues no further MMAs, stores NaN for
+ * its remaining outputs and sets an error word in the workspace, which each
+ * call clears first and bsm_ptc_status reads. */
 int bsm_ptc_apply(const bsm_lattice *lat, const void *U_rep32, const void *W1, const void *W2,
                   int32_t channels, const void *in, void *out, int32_t nbatch, int32_t prec,
                   void *workspace, size_t workspace_bytes, void *stream);
+
+/* Waits for `stream` and returns BSM_ETIMEOUT if the last bsm_ptc_apply on
+ * this workspace had a bounded tensor-core wait give up, else BSM_OK
+ * (BSM_EINVAL for a NULL or misaligned workspace). */
+int bsm_ptc_status(void *workspace, void *stream);
 
 /* Training loss and gradients, FP32:
  *   loss = sum_b |M(r_b) - e_b|^2 / |e_b|^2
@@ -429,13 +441,13 @@ typedef struct {
                         BSM_DF64 (double-float, about 48 significand bits), in
                         which case U_rep64 is a BSM_DF64 link field; the
                         vectors stay FP64 either way */
-  int32_t fallback;  /* nonzero: when FGCR ends with BSM_ENOCONV or BSM_ENAN,
-                        solve the same system with CG on the normal equations
-                        (bsm_cg_solve: mixed precision with U_rep32 when it is
-                        given, else plain at prec_outer; eo as above; from the
-                        FGCR iterate after BSM_ENOCONV, from zero after
-                        BSM_ENAN) to the normal-equation residual tol, and
-                        return that solve's status */
+  int32_t fallback;  /* nonzero: when FGCR ends with BSM_ENOCONV, BSM_ENAN
+                        or BSM_ETIMEOUT, solve the same system with CG on the
+                        normal equations (bsm_cg_solve: mixed precision with
+                        U_rep32 when it is given, else plain at prec_outer; eo
+                        as above; from the FGCR iterate after BSM_ENOCONV,
+                        from zero otherwise) to the normal-equation residual
+                        tol, and return that solve's status */
   int32_t fallback_max_iter; /* CG iterations of the fallback (0 -> 20000) */
 } bsm_fgcr_opts;
 typedef struct {
@@ -453,8 +465,10 @@ size_t bsm_fgcr_workspace_bytes(const bsm_lattice *lat, const bsm_fgcr_opts *opt
  * FP32 links, used with BSM_FGCR_PTC or
  * prec_inner BSM_F32 (may be NULL otherwise); W1, W2: used with BSM_FGCR_PTC
  * only.  Synchronises `stream` every check_every steps.  Returns
- * BSM_ENOCONV (max_iter reached) or BSM_ENAN with x holding the last iterate,
- * unless opts->fallback is set: then plain CG, the library's reference solver,
+ * BSM_ENOCONV (max_iter reached), BSM_ENAN, or BSM_ETIMEOUT (a bounded
+ * tensor-core wait of the BF16 network gave up, see bsm_ptc_apply; checked
+ * after every restart cycle) with x holding the last iterate, unless
+ * opts->fallback is set: then plain CG, the library's reference solver,
  * takes over and its status is returned (stats->fgcr_status keeps FGCR's).
  * The workspace is then sized for both solvers. */
 int bsm_fgcr_solve(const bsm_lattice *lat, const void *U_rep64, const void *U_rep32,

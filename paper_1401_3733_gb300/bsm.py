@@ -138,6 +138,8 @@ _lib.bsm_ptc_workspace_bytes.argtypes = [_LP, ctypes.c_int32, ctypes.c_int32, ct
 _lib.bsm_ptc_workspace_bytes.restype = ctypes.c_size_t
 _lib.bsm_ptc_apply.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
                                ctypes.c_size_t, _P]
+_lib.bsm_ptc_status.argtypes = [_P, _P]
+_lib.bsm_ptc_status.restype = ctypes.c_int
 _lib.bsm_ptc_loss_grad.argtypes = [_LP, _P, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P,
                                    ctypes.POINTER(ctypes.c_double), _P, ctypes.c_size_t, _P]
 _lib.bsm_ptc_adam_step.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_int32, _P]
@@ -363,6 +365,10 @@ def bsm_ptc_apply(lat, U_rep32, W1, W2, channels, inp, out, nbatch, prec, worksp
     nbytes = workspace.numel() * workspace.element_size()
     _check(_lib.bsm_ptc_apply(ctypes.byref(lat), _ptr(U_rep32), _ptr(W1), _ptr(W2), channels, _ptr(inp), _ptr(out),
                               nbatch, prec, _ptr(workspace), nbytes, _stream(stream)), "bsm_ptc_apply")
+
+
+def bsm_ptc_status(workspace, stream=None) -> int:
+    return _lib.bsm_ptc_status(_ptr(workspace), _stream(stream))
 
 
 def bsm_ptc_loss_grad(lat, U_rep32, W1, W2, channels, r, e, nbatch, G_W1, G_W2, workspace, stream=None) -> float:

@@ -35,7 +35,7 @@ int cg_solve(const bsm_lattice& L, const void* U64, const void* U32, const void*
 size_t ptc_workspace_bytes(const bsm_lattice& L, int C, int nb, bool train);
 int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, bool even_only, cudaStream_t s);
 int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* in,
-              void* out, int nb, int prec, void* ws, cudaStream_t s, bool even_only = false);
+              void* out, int nb, int prec, void* ws, cudaStream_t s, bool even_only = false, bool reset_err = true);
 int ptc_loss_grad(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* r,
                   const void* e, int nb, void* GW1, void* GW2, double* loss, void* ws, cudaStream_t s);
 int ptc_adam(void* W, const void* G, void* m, void* v, long long nfloat, double lr, int step, cudaStream_t s);
@@ -527,6 +527,18 @@ int bsm_ptc_apply(const bsm_lattice* lat, const void* U_rep32, const void* W1, c
   return finish(ptc_apply(*lat, U_rep32, W1, W2, channels, in, out, nbatch, prec, workspace, (cudaStream_t)stream));
 }
 
+int bsm_ptc_status(void* workspace, void* stream) {
+  if (!aligned(workspace)) return BSM_EINVAL;
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, workspace, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return BSM_ECUDA;
+  }
+  return err ? BSM_ETIMEOUT : BSM_OK;
+}
+
 int bsm_ptc_loss_grad(const bsm_lattice* lat, const void* U_rep32, const void* W1, const void* W2, int32_t channels,
                       const void* r, const void* e, int32_t nbatch, void* G_W1, void* G_W2, double* loss,
                       void* workspace, size_t workspace_bytes, void* stream) {
@@ -590,7 +602,7 @@ int bsm_fgcr_solve(const bsm_lattice* lat, const void* U_rep64, const void* U_re
     set_cuda_error(e);
     return BSM_ECUDA;
   }
-  if (opts->fallback != 0 && (rc == BSM_ENOCONV || rc == BSM_ENAN)) {
+  if (opts->fallback != 0 && (rc == BSM_ENOCONV || rc == BSM_ENAN || rc == BSM_ETIMEOUT)) {
     // the plain solver of the paper's method on the same system: mixed
     // precision CG on the normal equations (reliable updates at prec_outer)
     bsm_cg_opts co{};

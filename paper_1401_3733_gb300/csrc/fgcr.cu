@@ -27,7 +27,7 @@ int ptc_pack(const bsm_lattice& L, const double* psi, void* F, bool unpack, bool
 int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, int even_only, cudaStream_t s);
 bool ptc_fused_supported(int C);
 int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* in,
-              void* out, int nb, int prec, void* ws, cudaStream_t s, bool even_only = false);
+              void* out, int nb, int prec, void* ws, cudaStream_t s, bool even_only = false, bool reset_err = true);
 
 namespace {
 
@@ -324,6 +324,17 @@ struct Fgcr {
     return cudaStreamSynchronize(s) == cudaSuccess ? BSM_OK : BSM_ECUDA;
   }
 
+  // the network's error word (the first word of its workspace: set when an
+  // MMA-completion wait of the fused kernel gave up): BSM_ETIMEOUT if set
+  int network_status() const {
+    if (o.precond != BSM_FGCR_PTC) return BSM_OK;
+    int err = 0;
+    if (cudaMemcpyAsync(&err, w + y.ptc, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return BSM_ECUDA;
+    return err ? BSM_ETIMEOUT : BSM_OK;
+  }
+
   // out = D in (full) or Dhat in (even half; odd temporary in tmp)
   int apply(const OpCtx& c, const void* in, void* out) const {
     const int rc = o.eo ? op_dhat(c, in, out, w + y.tmp, 0, nullptr, nullptr) : op_dirac(c, in, out, 0, nullptr, nullptr);
@@ -356,7 +367,7 @@ struct Fgcr {
              : ptc_pack(L, reinterpret_cast<const double*>(r), w + y.F_in, false, o.eo != 0, s);
     if (rc != BSM_OK) return rc;
     if ((rc = ptc_apply(L, U32, W1, W2, o.channels, w + y.F_in, w + y.F_out, 1, o.ptc_prec, w + y.ptc, s,
-                        o.eo != 0)) != BSM_OK)
+                        o.eo != 0, false)) != BSM_OK)
       return rc;
     return f32 ? ptc_pack32(L, reinterpret_cast<const float*>(z), w + y.F_out, true, o.eo ? 1 : 0, s)
                : ptc_pack(L, reinterpret_cast<const double*>(z), w + y.F_out, true, o.eo != 0, s);
@@ -487,6 +498,7 @@ int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const voi
   reduce_launch(F.part, F.G, F.scalar, s);
   if ((rc = F.host_read(F.scalar, &rr)) != BSM_OK) return rc;
   double2* xv = reinterpret_cast<double2*>(x);
+  if (o.precond == BSM_FGCR_PTC && cudaMemsetAsync(w + F.y.ptc, 0, sizeof(int), s) != cudaSuccess) return BSM_ECUDA;
   int it = 0, cycles = 0, status = BSM_OK;
   while (rr > stop2) {
     if (it >= o.max_iter) {
@@ -519,6 +531,10 @@ int fgcr_solve(const bsm_lattice& L, const void* U64, const void* U32, const voi
     if (k < 0) return k;
     it += k;
     ++cycles;
+    if ((rc = F.network_status()) != BSM_OK) {  // the network's tensor-core waits gave up
+      status = rc;
+      break;
+    }
     if (!isfinite(rr)) {
       status = BSM_ENAN;
       break;

@@ -33,7 +33,7 @@ int ptc_brow_gemm(const void* A, const void* B, void* C, long long rows, int K, 
                   cudaStream_t s);
 size_t ptc_fused_weight_bytes(int C);
 int ptc_fused_apply(const char* links, size_t link_block, int d, int C, const void* F, const void* W1,
-                    const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, bool even_only,
+                    const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, bool even_only, int* err,
                     cudaStream_t s);
 
 namespace {
@@ -327,7 +327,7 @@ size_t al(size_t v) { return (v + 255) / 256 * 256; }
 // 4C x 36); out = sum_k T_k Z2_k.  Both intermediates of width 9 x 4 are far
 // narrower than the 9 x 4C transports of a C-channel field.
 struct PtcLayout {
-  size_t X1, Y1, Z2, W2p, W1r, W2r, Wt, G, GZ2, GY1, GW2p, invn, part, scratch, total;
+  size_t err, X1, Y1, Z2, W2p, W1r, W2r, Wt, G, GZ2, GY1, GW2p, invn, part, scratch, total;
 };
 
 PtcLayout ptc_layout(const bsm_lattice& L, int C, int nb, bool train) {
@@ -337,6 +337,7 @@ PtcLayout ptc_layout(const bsm_lattice& L, int C, int nb, bool train) {
   const size_t c8 = sizeof(float2);
   PtcLayout y{};
   size_t o = 0;
+  y.err = o; o = al(o + sizeof(int));  // error word of the fused kernel (offset 0, read by bsm_ptc_status)
   y.X1 = o; o = al(o + rows * 36 * c8);
   y.Y1 = o; o = al(o + rows * 4 * C * c8);
   y.Z2 = o; o = al(o + rows * 36 * c8);
@@ -385,17 +386,18 @@ int ptc_pack32(const bsm_lattice& L, const float* psi, void* F, bool unpack, int
 // even rows of `out` are wanted (the even-even block of the network); the odd
 // rows of `out` are then left unwritten.
 int ptc_apply(const bsm_lattice& L, const void* U32, const void* W1, const void* W2, int C, const void* in,
-              void* out, int nb, int prec, void* ws, cudaStream_t s, bool even_only) {
+              void* out, int nb, int prec, void* ws, cudaStream_t s, bool even_only, bool reset_err) {
   const OpCtx c = make_ctx(L, U32, BSM_F32, s);
   const PtcLayout y = ptc_layout(L, C, nb, false);
   char* w = reinterpret_cast<char*>(ws);
+  if (reset_err && cudaMemsetAsync(w + y.err, 0, sizeof(int), s) != cudaSuccess) return BSM_ECUDA;
   const int rows = (int)((long long)nb * 2 * c.g.Vh * c.d);
   const bool bf = prec == BSM_BF16;
   launch_permute(W2, w + y.W2p, C, 1, false, s);
   // BF16 with a fused kernel for this C: transports and both GEMMs in one pass (no cuBLAS)
   if (bf && ptc_fused_supported(C))
     return ptc_fused_apply(c.links, c.link_block, c.d, C, in, W1, w + y.W2p, w + y.Wt, w + y.Z2, out, c.g, nb,
-                           even_only, s);
+                           even_only, reinterpret_cast<int*>(w + y.err), s);
   launch_transport(c, in, w + y.X1, nb, 1, bf, false, s);
   int rc;
   if (!bf) {

@@ -32,6 +32,7 @@
 // handed over through hardware named barriers, so that the gathers from HBM
 // overlap the tensor-core work.
 #include <cuda_bf16.h>
+#include <stdlib.h>
 
 #include "bsm_internal.cuh"
 
@@ -132,9 +133,9 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, ui
 __device__ __forceinline__ void umma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
-// bounded wait for the completion of phase `parity` of `mbar`; false after kWaitCap polls
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (unsigned n = 0; n < kWaitCap; ++n) {
+// bounded wait for the completion of phase `parity` of `mbar`; false after `polls` polls
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsigned polls = kWaitCap) {
+  for (unsigned n = 0; n < polls; ++n) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -299,21 +300,40 @@ __device__ __forceinline__ void prefetch_tile(const char* links, size_t link_blo
   }
 }
 
+// An MMA-completion wait that gives up (after `polls` polls) is followed by
+// a second wait of kWaitCap polls for the same MMAs, so that nothing the
+// tensor core may still write is read or reused; the thread then records the
+// failure in the block's `failed` flag and the launch's error word `err`.
+// From the next MMA on, the block issues no more MMAs and waits for none:
+// its remaining tiles keep the buffer hand-over with the producers and store
+// their Z2 rows as NaN.
+__device__ __forceinline__ bool mma_wait(uint32_t mbar, uint32_t parity, unsigned polls, int* failed,
+                                         int* __restrict__ err) {
+  if (mbar_wait(mbar, parity, polls)) return true;
+  mbar_wait(mbar, parity, kWaitCap);
+  *reinterpret_cast<volatile int*>(failed) = 1;
+  atomicExch(err, 1);
+  return false;
+}
+
 // stage 2 (consumer thread c in [0, 128) = TMEM lane c) for one tile:
 // GEMM1 for all D row blocks, then per row block the Y1 read-back, GEMM2 and
-// the Z2 read-back.  Returns false if an MMA-completion wait gave up (the
-// tile's Z2 rows are then stored as NaN).
+// the Z2 read-back.  Returns false if an MMA-completion wait gave up or the
+// block had already given up (the tile's Z2 rows are then stored as NaN).
 template <int D, int C, bool EO>
 __device__ __forceinline__ bool mix_tile(const unsigned char* sX, const unsigned char* sW1,
                                          const unsigned char* sW2, unsigned char* sY1, uint64_t* mbar,
                                          uint32_t tmem, uint4* __restrict__ Z, long long zrows, const Geom& g,
-                                         const FusedTile& f, int c, int it, bool more) {
+                                         const FusedTile& f, int c, int it, bool more, unsigned polls,
+                                         int* failed, int* __restrict__ err) {
   using S = FusedShape<C>;
   constexpr int kY1Batch = S::N1 % 48 == 0 ? 48 : S::N1 % 32 == 0 ? 32 : 16;  // Y1 columns per TMEM wait
   const bool self_only = EO && f.p == 0, no_self = EO && f.p == 1;
   const int buf = it & 1;
-  bool ok = true;
-  if (c == 0) {
+  // read after the FULL barrier, which every consumer passed after any earlier failure was recorded
+  const bool skip1 = *reinterpret_cast<volatile int*>(failed) != 0;
+  bool ok = !skip1;
+  if (c == 0 && !skip1) {
     const uint32_t xa = smem_u32(sX), wa = smem_u32(sW1);
     for (int rb = 0; rb < D; ++rb)
       for (int kk = 0; kk < (self_only ? 1 : kK1 / 16); ++kk)  // self_only: X1 beyond slot 1 is zero
@@ -321,7 +341,7 @@ __device__ __forceinline__ bool mix_tile(const unsigned char* sX, const unsigned
              umma_desc(wa + kk * 256, kK1 / 8 * 128), umma_idesc(S::N1), kk);
     umma_commit(smem_u32(mbar));
   }
-  ok &= mbar_wait(smem_u32(mbar), it & 1);
+  if (!skip1) ok &= mma_wait(smem_u32(mbar), it & 1, polls, failed, err);
   tc_fence_after();
   if (more) named_arrive(kBarEmpty + buf, kFusedThreads);  // X1[buf] has been read
   const uint32_t lane = tmem + ((uint32_t)((c >> 5) * 32) << 16);
@@ -343,14 +363,17 @@ __device__ __forceinline__ bool mix_tile(const unsigned char* sX, const unsigned
     tc_fence_before();
     named_sync(kBarConsumers, kConsumers);
     tc_fence_after();
-    if (c == 0) {
+    // every consumer's GEMM1 (or previous GEMM2) wait is recorded before this barrier
+    const bool skip2 = *reinterpret_cast<volatile int*>(failed) != 0;
+    if (skip2) ok = false;
+    if (c == 0 && !skip2) {
       const uint32_t ya = smem_u32(sY1), wb = smem_u32(sW2);
       for (int kk = 0; kk < C / 2; ++kk)
         umma(tmem + kD2Col, umma_desc(ya + kk * 256, C * 128), umma_desc(wb + kk * 256, C * 128), umma_idesc(kN2),
              kk);
       umma_commit(smem_u32(mbar + 1));
     }
-    ok &= mbar_wait(smem_u32(mbar + 1), (it * D + rb) & 1);
+    if (!skip2) ok &= mma_wait(smem_u32(mbar + 1), (it * D + rb) & 1, polls, failed, err);
     tc_fence_after();
     // Z2 rows of this block: TMEM -> BF16 -> global, one 16-byte group (4
     // spins) per slot; slots 0..3 and 4..8 in one wait each
@@ -405,7 +428,7 @@ template <int D, int C, bool EO>
 __global__ void __launch_bounds__(kFusedThreads, 1)
     fused_kernel(const char* __restrict__ links, size_t link_block, const float2* __restrict__ F,
                  const unsigned char* __restrict__ Wt, uint4* __restrict__ Z, long long zrows, Geom g, int bpp,
-                 int ntiles) {
+                 int ntiles, int* __restrict__ err, unsigned polls) {
   using S = FusedShape<C>;
   constexpr int kRows = kFusedSites * D;
   constexpr int kX1Bytes = kRows * kK1 * 2;
@@ -416,7 +439,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   unsigned char* sY1 = sW2 + S::W2Bytes;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sY1 + S::Y1Bytes);  // [0] GEMM1 done, [1] GEMM2 done
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  int* failed = reinterpret_cast<int*>(tslot + 1);  // an MMA-completion wait of this block gave up
   const int tid = threadIdx.x;
+  if (tid == 0) *failed = 0;
 
   // weights into shared memory once; zero core column 9 of both X1 buffers;
   // barriers; tensor memory
@@ -458,7 +483,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
       named_sync(kBarFull + buf, kFusedThreads);
       tc_fence_after();
       mix_tile<D, C, EO>(sX + buf * kX1Bytes, sW1, sW2, sY1, mbar, tmem, Z, zrows, g, fused_tile(g, t, bpp), c, it,
-                         t + 2 * (int)gridDim.x < ntiles);
+                         t + 2 * (int)gridDim.x < ntiles, polls, failed, err);
     }
   }
   tc_fence_before();
@@ -543,7 +568,7 @@ size_t fused_smem() {
 
 template <int D, int C>
 int fused_launch(const char* links, size_t link_block, const void* F, const void* W1, const void* W2p, void* Wt,
-                 void* Z, void* out, const Geom& g, int nb, bool even_only, cudaStream_t s) {
+                 void* Z, void* out, const Geom& g, int nb, bool even_only, int* err, unsigned polls, cudaStream_t s) {
   using S = FusedShape<C>;
   const int n = S::N1 * kK1 + kN2 * S::N1;
   fused_prep_kernel<C><<<(n + 255) / 256, 256, 0, s>>>(reinterpret_cast<const float2*>(W1),
@@ -562,7 +587,7 @@ int fused_launch(const char* links, size_t link_block, const void* F, const void
   const long long sites = (long long)nb * 2 * g.Vh, zrows = sites * D;
   kern<<<ntiles < sms ? ntiles : sms, kFusedThreads, smem, s>>>(
       links, link_block, reinterpret_cast<const float2*>(F), reinterpret_cast<const unsigned char*>(Wt),
-      reinterpret_cast<uint4*>(Z), zrows, g, bpp, ntiles);
+      reinterpret_cast<uint4*>(Z), zrows, g, bpp, ntiles, err, polls);
   const long long outs = even_only ? sites / 2 : sites;
   stencil_bf16_kernel<D><<<(int)((outs + 127) / 128), 128, 0, s>>>(
       links, link_block, reinterpret_cast<const uint4*>(Z), zrows, reinterpret_cast<float2*>(out), g, nb,
@@ -572,14 +597,25 @@ int fused_launch(const char* links, size_t link_block, const void* F, const void
 
 template <int D>
 int fused_dispatch_c(int C, const char* links, size_t lb, const void* F, const void* W1, const void* W2p, void* Wt,
-                     void* Z, void* out, const Geom& g, int nb, bool eo, cudaStream_t s) {
+                     void* Z, void* out, const Geom& g, int nb, bool eo, int* err, unsigned polls, cudaStream_t s) {
   switch (C) {
-    case 2: return fused_launch<D, 2>(links, lb, F, W1, W2p, Wt, Z, out, g, nb, eo, s);
-    case 4: return fused_launch<D, 4>(links, lb, F, W1, W2p, Wt, Z, out, g, nb, eo, s);
-    case 8: return fused_launch<D, 8>(links, lb, F, W1, W2p, Wt, Z, out, g, nb, eo, s);
-    case 12: return fused_launch<D, 12>(links, lb, F, W1, W2p, Wt, Z, out, g, nb, eo, s);
+    case 2: return fused_launch<D, 2>(links, lb, F, W1, W2p, Wt, Z, out, g, nb, eo, err, polls, s);
+    case 4: return fused_launch<D, 4>(links, lb, F, W1, W2p, Wt, Z, out, g, nb, eo, err, polls, s);
+    case 8: return fused_launch<D, 8>(links, lb, F, W1, W2p, Wt, Z, out, g, nb, eo, err, polls, s);
+    case 12: return fused_launch<D, 12>(links, lb, F, W1, W2p, Wt, Z, out, g, nb, eo, err, polls, s);
     default: return BSM_EUNSUPPORTED;
   }
+}
+
+// polls of an MMA-completion wait before it gives up: kWaitCap, or the value
+// of BSM_PTC_WAIT_POLLS (0 makes every first wait give up at once, which is
+// how the tests reach the error path)
+unsigned wait_polls() {
+  const char* env = getenv("BSM_PTC_WAIT_POLLS");
+  if (env == nullptr || *env == '\0') return kWaitCap;
+  char* end = nullptr;
+  const unsigned long v = strtoul(env, &end, 10);
+  return (end != nullptr && *end == '\0' && v <= kWaitCap) ? (unsigned)v : kWaitCap;
 }
 
 }  // namespace
@@ -590,12 +626,14 @@ bool ptc_fused_supported(int C) { return C == 2 || C == 4 || C == 8 || C == 12; 
 // bytes of the realified weights in the core-matrix layout (bf16): GEMM1's B (8C x 80) and GEMM2's B (80 x 8C)
 size_t ptc_fused_weight_bytes(int C) { return (size_t)2 * (8 * C) * 80 * 2; }
 
-// Z: 9 x rows x 4 BF16 complex (4 bytes each), slot-major; Wt: ptc_fused_weight_bytes(C), 16-byte aligned
+// Z: 9 x rows x 4 BF16 complex (4 bytes each), slot-major; Wt: ptc_fused_weight_bytes(C), 16-byte aligned;
+// err: a device word the kernel sets to 1 when an MMA-completion wait gives up (never cleared here)
 int ptc_fused_apply(const char* links, size_t link_block, int d, int C, const void* F, const void* W1,
-                    const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, bool even_only,
+                    const void* W2p, void* Wt, void* Z, void* out, const Geom& g, int nb, bool even_only, int* err,
                     cudaStream_t s) {
-  if (d == 2) return fused_dispatch_c<2>(C, links, link_block, F, W1, W2p, Wt, Z, out, g, nb, even_only, s);
-  if (d == 3) return fused_dispatch_c<3>(C, links, link_block, F, W1, W2p, Wt, Z, out, g, nb, even_only, s);
+  const unsigned polls = wait_polls();
+  if (d == 2) return fused_dispatch_c<2>(C, links, link_block, F, W1, W2p, Wt, Z, out, g, nb, even_only, err, polls, s);
+  if (d == 3) return fused_dispatch_c<3>(C, links, link_block, F, W1, W2p, Wt, Z, out, g, nb, even_only, err, polls, s);
   return BSM_EUNSUPPORTED;
 }
 

@@ -188,6 +188,9 @@ def test_ptc_and_fgcr_validation(bsm):
         assert bsm.bsm_ptc_workspace_bytes(lat, C, nb, 0) == 0
     apply = bsm._lib.bsm_ptc_apply
     assert apply(L(adj), A, 2 * A, 3 * A, 4, 4 * A, 5 * A, 1, bsm.F32, 6 * A, big, 0) == bsm.EUNSUPPORTED
+    # the status query rejects a missing or misaligned workspace before touching the GPU
+    assert bsm._lib.bsm_ptc_status(None, None) == bsm.EINVAL
+    assert bsm._lib.bsm_ptc_status(A + 4, None) == bsm.EINVAL
     assert apply(L(good), A, 2 * A, 3 * A, 4, 4 * A, 5 * A, 1, bsm.F64, 6 * A, big, 0) == bsm.EUNSUPPORTED
     assert apply(L(good), A, 2 * A, 3 * A, 0, 4 * A, 5 * A, 1, bsm.F32, 6 * A, big, 0) == bsm.EINVAL
     assert apply(L(good), A, 2 * A + 4, 3 * A, 4, 4 * A, 5 * A, 1, bsm.F32, 6 * A, big, 0) == bsm.EINVAL

@@ -369,6 +369,67 @@ def test_fgcr_falls_back_to_cg(cause, eo):
     assert rel(orc.dirac(olat, R, to_canon(blat, x, bsm.F64)), b) <= 1e-9
 
 
+def test_fused_kernel_wait_that_gives_up_is_reported(monkeypatch):
+    """BSM_PTC_WAIT_POLLS=0 makes the first MMA-completion wait of every
+    block of the fused BF16 kernel give up at once: the block waits (bounded)
+    for its MMAs in flight, issues no more, stores NaN and sets the
+    workspace's error word, which bsm_ptc_status reports as BSM_ETIMEOUT.
+    The next call, with the default bound, clears the word and matches the
+    oracle: the GPU context stays usable."""
+    dims, N, rep, phase = CASES[0]
+    olat, blat = lats(dims, N, rep, phase)
+    U = fields.gauge_field(dims, N, "haar", seed=71)
+    R = orc.links_to_rep(olat, U)
+    U32 = gpu_links(blat, U, bsm.F32)
+    rng = np.random.default_rng(72)
+    C, nb = 12, 2
+    W1, W2 = rand_c(rng, (36, 4 * C), 0.3), rand_c(rng, (36 * C, 4), 0.1)
+    psis = [fields.gaussian_spinor(dims, olat.d, 73 + b) for b in range(nb)]
+    F = ptc_field(blat, psis)
+    out = torch.zeros_like(F)
+    ws = torch.empty(bsm.bsm_ptc_workspace_bytes(blat, C, nb, 0), dtype=torch.uint8, device="cuda")
+    W1d, W2d = dev_c64(W1), dev_c64(W2)
+    monkeypatch.setenv("BSM_PTC_WAIT_POLLS", "0")
+    bsm.bsm_ptc_apply(blat, U32, W1d, W2d, C, F, out, nb, bsm.BF16, ws)
+    assert bsm.bsm_ptc_status(ws) == bsm.ETIMEOUT
+    assert not bool(torch.isfinite(out).all())
+    monkeypatch.delenv("BSM_PTC_WAIT_POLLS")
+    bsm.bsm_ptc_apply(blat, U32, W1d, W2d, C, F, out, nb, bsm.BF16, ws)
+    assert bsm.bsm_ptc_status(ws) == bsm.OK
+    got = from_ptc_field(blat, out, nb)
+    for b in range(nb):
+        assert rel(got[b], oracle_net(olat, R, psis[b], W1, W2, C)) < 2e-2
+
+
+@pytest.mark.parametrize("eo", [True, False], ids=["eo", "full"])
+def test_fgcr_falls_back_when_the_network_wait_gives_up(monkeypatch, eo):
+    """An FGCR solve whose BF16 network had a tensor-core wait give up
+    (BSM_PTC_WAIT_POLLS=0) ends with BSM_ETIMEOUT; with opts.fallback the
+    plain CG solver finishes it and x solves D x = b (the oracle's D)."""
+    dims, N = (4, 4, 4, 8), 3
+    olat, blat = lats(dims, N, bsm.FUND, (np.pi, 0, 0, 0), m0=0.05)
+    U = fields.gauge_field(dims, N, "smooth", seed=74, eps=0.4)
+    R = orc.links_to_rep(olat, U)
+    U64, U32 = gpu_links(blat, U, bsm.F64), gpu_links(blat, U, bsm.F32)
+    b = fields.gaussian_spinor(dims, N, 75)
+    bd = gpu_spinor(blat, b, bsm.F64)
+    W1, W2 = neumann_weights(olat.m0)
+    W = (dev_c64(W1), dev_c64(W2))
+    kw = dict(tol=1e-11, restart=16, precond=bsm.FGCR_PTC, ptc_prec=bsm.BF16, channels=2, eo=eo,
+              prec_inner=bsm.F32, inner_tol=1e-3, max_iter=1000)
+    monkeypatch.setenv("BSM_PTC_WAIT_POLLS", "0")
+    st, _, _ = fgcr(blat, U64, U32, bd, bsm.fgcr_opts(**kw), W)
+    assert st == bsm.ETIMEOUT
+    st, stats, x = fgcr(blat, U64, U32, bd, bsm.fgcr_opts(fallback=True, **kw), W)
+    monkeypatch.delenv("BSM_PTC_WAIT_POLLS")
+    assert st == bsm.OK, bsm.bsm_strerror(st)
+    assert stats.fgcr_status == bsm.ETIMEOUT and stats.fallback_iters > 0
+    assert stats.true_res <= 1e-9
+    assert rel(orc.dirac(olat, R, to_canon(blat, x, bsm.F64)), b) <= 1e-9
+    st, stats, _ = fgcr(blat, U64, U32, bd, bsm.fgcr_opts(**kw), W)
+    assert st == bsm.OK and stats.fgcr_status == bsm.OK
+
+
 @pytest.mark.parametrize("precond", ["none", "ptc-bf16"])
 def test_mixed_precision_fgcr_reaches_fp64_accuracy(precond):
     """FP32 restart cycles with the residual recomputed in FP64: the same

@@ -212,3 +212,44 @@ def test_mrhs_paired_kernel_is_bit_identical(N, rep, block, prec):
     got = unpack(blat, results[block][0], nrhs, prec)
     for r in range(nrhs):
         assert rel(got[r], orc.dirac(olat, R, psis[r])) <= TOL[prec]
+
+
+# ----------------------------------------------------------------------------
+# the benchmark's multi-RHS workload at full size: 24^4, SU(6) fundamental,
+# 12 RHS, in the launch shapes the benchmark times
+# ----------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def mrhs_full_case():
+    dims, N, nrhs = (24, 24, 24, 24), 6, 12
+    phase = (np.pi, 0, 0, 0)
+    olat = orc.Lattice(dims, N, orc.FUND, 0.1, phase)
+    blat = bsm.lattice(dims, N, bsm.FUND, 0.1, phase)
+    U = fields.gauge_field(dims, N, "smooth", seed=7, eps=0.4)
+    R = orc.links_to_rep(olat, U)
+    src = fields.device_gaussian_spinors(dims, N, nrhs, seed=9)
+    return olat, blat, U, R, src, nrhs
+
+
+@pytest.mark.parametrize("prec,block", [(bsm.BF16, 0), (bsm.BF16, bsm.MRHS_TENSOR_CORE_BLOCK), (bsm.BF16, 1),
+                                        (bsm.F32, 0)], ids=["bf16-tuned", "bf16-tc", "bf16-simt", "f32-tuned"])
+def test_full_size_24c4_mrhs(mrhs_full_case, prec, block):
+    """The full operator D on all 12 RHS of the 24^4 SU(6) workload, with the
+    RHS block the tuner picks (as the benchmark runs it) or pinned; RHS 0, 7
+    and 11 compared with the oracle element by element."""
+    olat, blat, U, R, src, nrhs = mrhs_full_case
+    Ud = gpu_links(blat, U, prec)
+    n = bsm.bsm_field_bytes(blat, bsm.FIELD_SPINOR, prec) * nrhs
+    inp = torch.empty(n, dtype=torch.uint8, device="cuda")
+    out = torch.zeros_like(inp)
+    bsm.bsm_pack_spinor_mrhs(blat, src, inp, nrhs, prec)
+    if block:
+        bsm.bsm_dslash_mrhs_set_block(blat, nrhs, prec, block)
+    bsm.bsm_dslash_mrhs(blat, Ud, inp, out, nrhs, bsm.FULL, 0, prec)
+    if block:
+        bsm.bsm_dslash_mrhs_set_block(blat, nrhs, prec, 0)
+    got = torch.empty_like(src)
+    bsm.bsm_unpack_spinor_mrhs(blat, out, got, nrhs, prec)
+    for r in (0, 7, 11):
+        want = orc.dirac(olat, R, src[r].cpu().numpy())
+        assert rel(got[r].cpu().numpy(), want) <= TOL[prec], r

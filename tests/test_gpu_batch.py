@@ -178,3 +178,48 @@ def test_every_launch_configuration_gives_the_same_bits(op, monkeypatch):
         assert bsm.bsm_batch_last_config() == tuple(int(v) for v in cfg.split(":"))
         for ref, b in zip(refs, base):
             assert torch.equal(ref[4], b), cfg
+
+
+# the benchmark's uneven batch: 16 lattices 8^4 .. 48 x 24^3, SU(2) and SU(3)
+FULL_SHAPES = [((8, 8, 8, 8), 2), ((16, 8, 8, 8), 3), ((12, 12, 12, 12), 2), ((24, 12, 12, 12), 3),
+               ((16, 16, 16, 16), 2), ((32, 16, 16, 16), 3), ((20, 20, 20, 20), 2), ((24, 16, 16, 16), 3),
+               ((12, 8, 8, 8), 3), ((8, 12, 12, 12), 2), ((16, 12, 12, 12), 3), ((24, 24, 24, 24), 2),
+               ((32, 24, 24, 24), 3), ((48, 24, 24, 24), 2), ((40, 24, 24, 24), 3), ((48, 24, 24, 24), 3)]
+
+
+def test_full_size_uneven_batch_of_the_benchmark():
+    """The 16-lattice batch at full size, 8 RHS each, the full operator in
+    one persistent launch in the tuned configuration (as the benchmark runs
+    it): on the two largest and two small lattices RHS 0 and 7 against the
+    oracle, and on every lattice all RHS against one multi-RHS launch per
+    lattice (the same site arithmetic, so to rounding order)."""
+    nrhs, phase = 8, (np.pi, 0, 0, 0)
+    entries, refs = [], []
+    for k, (dims, N) in enumerate(FULL_SHAPES):
+        blat = bsm.lattice(dims, N, bsm.FUND, 0.1, phase)
+        U = fields.gauge_field(dims, N, "smooth", seed=20 + k, eps=0.3)
+        Ud = gpu_links(blat, U, bsm.F32)
+        src = fields.device_gaussian_spinors(dims, N, nrhs, seed=40 + k)
+        n = bsm.bsm_field_bytes(blat, bsm.FIELD_SPINOR, bsm.F32) * nrhs
+        inp = torch.empty(n, dtype=torch.uint8, device="cuda")
+        out = torch.zeros_like(inp)
+        bsm.bsm_pack_spinor_mrhs(blat, src, inp, nrhs, bsm.F32)
+        entries.append((blat, Ud, inp, out, nrhs))
+        refs.append((dims, N, U, src))
+    arr = bsm.batch_items(entries)
+    opts = bsm.BatchOpts(bsm.BATCH_D, bsm.F32, 0.0, 0)
+    ws = torch.empty(bsm.bsm_batch_workspace_bytes(arr, opts), dtype=torch.uint8, device="cuda")
+    assert bsm.bsm_dslash_batch(arr, opts, ws) == bsm.OK
+    for k, ((blat, Ud, inp, out, _), (dims, N, U, src)) in enumerate(zip(entries, refs)):
+        got = torch.empty_like(src)
+        bsm.bsm_unpack_spinor_mrhs(blat, out, got, nrhs, bsm.F32)
+        one = torch.zeros_like(out)
+        bsm.bsm_dslash_mrhs(blat, Ud, inp, one, nrhs, bsm.FULL, 0, bsm.F32)
+        ref = torch.empty_like(src)
+        bsm.bsm_unpack_spinor_mrhs(blat, one, ref, nrhs, bsm.F32)
+        assert float((got - ref).norm() / ref.norm()) <= 1e-6, dims
+        if k in (0, 1, 13, 15):
+            olat = orc.Lattice(dims, N, orc.FUND, 0.1, phase)
+            R = orc.links_to_rep(olat, U)
+            for r in (0, 7):
+                assert rel(got[r].cpu().numpy(), orc.dirac(olat, R, src[r].cpu().numpy())) <= TOL[bsm.F32], (dims, r)

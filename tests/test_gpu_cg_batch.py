@@ -92,3 +92,48 @@ def test_batch_statuses():
     assert st == bsm.EUNSUPPORTED
     st, _ = bsm.bsm_cg_solve_batch(items, bsm.cg_opts(prec_inner=bsm.F32), ws[:1024], raise_on_error=False)
     assert st == bsm.EWORKSPACE
+
+
+# the benchmark's uneven batch: 16 lattices 8^4 .. 48 x 24^3, SU(2) and SU(3)
+FULL_SHAPES = [((8, 8, 8, 8), 2), ((16, 8, 8, 8), 3), ((12, 12, 12, 12), 2), ((24, 12, 12, 12), 3),
+               ((16, 16, 16, 16), 2), ((32, 16, 16, 16), 3), ((20, 20, 20, 20), 2), ((24, 16, 16, 16), 3),
+               ((12, 8, 8, 8), 3), ((8, 12, 12, 12), 2), ((16, 12, 12, 12), 3), ((24, 24, 24, 24), 2),
+               ((32, 24, 24, 24), 3), ((48, 24, 24, 24), 2), ((40, 24, 24, 24), 3), ((48, 24, 24, 24), 3)]
+
+
+def test_full_size_batch_of_the_benchmark():
+    """All 128 systems of the benchmark's batch (16 lattices, 8 Gaussian RHS
+    each, m0 = 0.1, antiperiodic time) in one batched solve as the benchmark
+    runs it (captured graph, double-float reliable updates, tol 1e-10):
+    every system's recomputed normal-equation residual <= 1e-10, and on the
+    two largest and two small lattices the oracle's D applied to the GPU
+    solution gives back b (RHS 0 and 7)."""
+    nrhs, phase, m0 = 8, (np.pi, 0.0, 0.0, 0.0), 0.1
+    entries, refs = [], []
+    for k, (dims, N) in enumerate(FULL_SHAPES):
+        blat = bsm.lattice(dims, N, bsm.FUND, m0, phase)
+        U = fields.gauge_field(dims, N, "smooth", seed=20 + k, eps=0.3)
+        U64, U32 = gpu_links(blat, U, bsm.DF64), gpu_links(blat, U, bsm.F32)
+        fb = bsm.bsm_field_bytes(blat, bsm.FIELD_SPINOR, bsm.F64)
+        src = fields.device_gaussian_spinors(dims, N, nrhs, seed=40 + k)
+        b = torch.empty(nrhs * fb, dtype=torch.uint8, device="cuda")
+        for r in range(nrhs):
+            bsm.bsm_pack_spinor(blat, src[r], b[r * fb:(r + 1) * fb], bsm.F64)
+        entries.append((blat, U64, U32, b, torch.zeros_like(b), nrhs))
+        refs.append((dims, N, U, src, fb))
+    items = bsm.cg_batch_items(entries)
+    ws = torch.empty(bsm.bsm_cg_batch_workspace_bytes(items), dtype=torch.uint8, device="cuda")
+    opts = bsm.cg_opts(tol=1e-10, max_iter=20000, prec_inner=bsm.F32, prec_outer=bsm.DF64, delta=0.01,
+                       check_every=16, use_graph=True)
+    st, stats = bsm.bsm_cg_solve_batch(items, opts, ws, stream=torch.cuda.Stream())
+    assert st == bsm.OK
+    assert len(stats) == 16 * nrhs
+    assert max(s.true_res_normal for s in stats) <= 1e-10
+    for k in (0, 1, 13, 15):
+        dims, N, U, src, fb = refs[k]
+        blat, _, _, _, x, _ = entries[k]
+        olat = orc.Lattice(dims, N, orc.FUND, m0, phase)
+        R = orc.links_to_rep(olat, U)
+        for r in (0, 7):
+            b = src[r].cpu().numpy()
+            assert rel(orc.dirac(olat, R, solution(blat, x, fb, r)), b) <= 1e-9, (dims, r)

@@ -549,3 +549,26 @@ def test_even_only_network_application_matches_the_full_one(dims):
         assert st == bsm.OK and s.true_res <= 1.5e-10
         its[prec] = s.iters
     assert abs(its[bsm.F32] - its[bsm.BF16]) <= 2, its
+
+
+def test_full_size_16c32_fgcr_with_the_network():
+    """The learned-preconditioner workload at full size (16^3 x 32 SU(3),
+    smooth links eps 0.5, m0 = -0.62, antiperiodic time), solved as the
+    benchmark's best configuration runs (even-odd FGCR(32), BF16 network on
+    the tensor cores, FP32 cycles, double-float outer operator) with the
+    degree-2 Neumann weights standing in for trained ones: the oracle's D
+    applied to the GPU solution gives back b."""
+    dims, N, m0 = (32, 16, 16, 16), 3, -0.62
+    olat, blat = lats(dims, N, bsm.FUND, (np.pi, 0, 0, 0), m0=m0)
+    U = fields.gauge_field(dims, N, "smooth", seed=3, eps=0.5)
+    R = orc.links_to_rep(olat, U)
+    Udf, U32 = gpu_links(blat, U, bsm.DF64), gpu_links(blat, U, bsm.F32)
+    b = fields.gaussian_spinor(dims, N, 4)
+    bd = gpu_spinor(blat, b, bsm.F64)
+    W1, W2 = neumann_weights(m0)
+    opts = bsm.fgcr_opts(tol=1e-10, restart=32, precond=bsm.FGCR_PTC, ptc_prec=bsm.BF16, channels=2, eo=True,
+                         prec_inner=bsm.F32, prec_outer=bsm.DF64, inner_tol=1e-3, max_iter=20000)
+    st, stats, x = fgcr(blat, Udf, U32, bd, opts, (dev_c64(W1), dev_c64(W2)))
+    assert st == bsm.OK, bsm.bsm_strerror(st)
+    assert stats.true_res <= 1e-10
+    assert rel(orc.dirac(olat, R, to_canon(blat, x, bsm.F64)), b) <= 2e-10

@@ -191,9 +191,10 @@ int bsm_unpack_spinor(const bsm_lattice *lat, const void *dev, double *canon,
                       int32_t prec, void *stream);
 
 /* Multi-RHS pack/unpack: canonical FP64 spinors [nrhs][V][4][d] (device) <->
- * the multi-RHS device layout at `prec` (BSM_F32 or BSM_BF16): the
- * single-RHS layout with the RHS index innermost, element (plane, site, rhs)
- * at (plane*V_h + site)*nrhs + rhs within each parity; nrhs times
+ * the multi-RHS device layout at `prec` (BSM_F32 or BSM_BF16): the 2d
+ * planes of the single-RHS layout, site-major with the RHS index innermost,
+ * element (plane, site, rhs) at (site*2d + plane)*nrhs + rhs within each
+ * parity, so that one site's spinors of all RHS are contiguous; nrhs times
  * bsm_field_bytes(lat, BSM_FIELD_SPINOR, prec) bytes.  V*nrhs <= 2^30. */
 int bsm_pack_spinor_mrhs(const bsm_lattice *lat, const double *canon, void *dev,
                          int32_t nrhs, int32_t prec, void *stream);

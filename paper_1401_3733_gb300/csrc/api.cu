@@ -17,7 +17,7 @@ namespace bsm {
 
 int links_to_rep_launch(const bsm_lattice& L, const double* U, void* out, int prec, cudaStream_t s);
 void pack_spinor_launch(const bsm_lattice& L, const double* canon, void* dev, int d, int prec, bool unpack,
-                        int nrhs, cudaStream_t s);
+                        int nrhs, bool site_major, cudaStream_t s);
 int launch_mrhs(int prec, int d, bool real, const MrhsArgs& A, cudaStream_t s);
 int mrhs_tuned_block(int prec, int d, bool real, int nrhs, int Vh);
 size_t batch_workspace_bytes(const bsm_batch_item* items, int count, int op);
@@ -234,7 +234,7 @@ int bsm_pack_spinor(const bsm_lattice* lat, const double* canon, void* dev, int3
   if (rc != BSM_OK) return rc;
   if (!prec_lat_ok(lat, prec)) return BSM_EUNSUPPORTED;
   if (!aligned(canon) || !aligned(dev)) return BSM_EINVAL;
-  pack_spinor_launch(*lat, canon, dev, rep_info(lat->N, lat->rep).d, prec, false, 1, (cudaStream_t)stream);
+  pack_spinor_launch(*lat, canon, dev, rep_info(lat->N, lat->rep).d, prec, false, 1, false, (cudaStream_t)stream);
   return finish(BSM_OK);
 }
 
@@ -243,7 +243,7 @@ int bsm_unpack_spinor(const bsm_lattice* lat, const void* dev, double* canon, in
   if (rc != BSM_OK) return rc;
   if (!prec_lat_ok(lat, prec)) return BSM_EUNSUPPORTED;
   if (!aligned(canon) || !aligned(dev)) return BSM_EINVAL;
-  pack_spinor_launch(*lat, canon, const_cast<void*>(dev), rep_info(lat->N, lat->rep).d, prec, true, 1,
+  pack_spinor_launch(*lat, canon, const_cast<void*>(dev), rep_info(lat->N, lat->rep).d, prec, true, 1, false,
                      (cudaStream_t)stream);
   return finish(BSM_OK);
 }
@@ -277,7 +277,7 @@ int bsm_pack_spinor_mrhs(const bsm_lattice* lat, const double* canon, void* dev,
   if (rc != BSM_OK) return rc;
   if ((rc = check_mrhs(lat, nrhs, prec)) != BSM_OK) return rc;
   if (!aligned(canon) || !aligned(dev)) return BSM_EINVAL;
-  pack_spinor_launch(*lat, canon, dev, rep_info(lat->N, lat->rep).d, prec, false, nrhs, (cudaStream_t)stream);
+  pack_spinor_launch(*lat, canon, dev, rep_info(lat->N, lat->rep).d, prec, false, nrhs, true, (cudaStream_t)stream);
   return finish(BSM_OK);
 }
 
@@ -287,7 +287,7 @@ int bsm_unpack_spinor_mrhs(const bsm_lattice* lat, const void* dev, double* cano
   if (rc != BSM_OK) return rc;
   if ((rc = check_mrhs(lat, nrhs, prec)) != BSM_OK) return rc;
   if (!aligned(canon) || !aligned(dev)) return BSM_EINVAL;
-  pack_spinor_launch(*lat, canon, const_cast<void*>(dev), rep_info(lat->N, lat->rep).d, prec, true, nrhs,
+  pack_spinor_launch(*lat, canon, const_cast<void*>(dev), rep_info(lat->N, lat->rep).d, prec, true, nrhs, true,
                      (cudaStream_t)stream);
   return finish(BSM_OK);
 }

@@ -207,12 +207,19 @@ __global__ void __launch_bounds__(kSumThreads) bt_beta_kernel(const __grid_const
 // --- one system's slot (RHS r of an item) against its FP64 outer vectors ---
 // FP32 element (plane q = s d + c, site i) of a half spinor holds spins s and
 // s + 2 of colour c; FP64 element k holds one complex number, spin s at
-// plane q and spin s + 2 at plane q + 2d (n32 = 2 d V_h elements apart)
+// plane q and spin s + 2 at plane q + 2d (n32 = 2 d V_h elements apart).
+// The FP32 vectors hold all RHS in the site-major multi-RHS layout: element
+// k = q V_h + i of a single-RHS half spinor is element (i 2d + q) n_rhs + r.
+__device__ __forceinline__ long long slot_at(long long k, unsigned vh, long long n32, int nrhs, int r) {
+  const unsigned q = (unsigned)k / vh, i = (unsigned)k - q * vh;
+  return ((long long)i * (n32 / vh) + q) * nrhs + r;
+}
 
 // y64 += x32[slot], x32[slot] = 0
-__global__ void __launch_bounds__(kBtThreads) slot_acc_kernel(double2* y, float4* x, long long n32, int nrhs, int r) {
+__global__ void __launch_bounds__(kBtThreads) slot_acc_kernel(double2* y, float4* x, long long n32, unsigned vh,
+                                                              int nrhs, int r) {
   for (long long k = blockIdx.x * (long long)kBtThreads + threadIdx.x; k < n32; k += (long long)gridDim.x * kBtThreads) {
-    float4* xp = x + k * nrhs + r;
+    float4* xp = x + slot_at(k, vh, n32, nrhs, r);
     const float4 v = *xp;
     double2 a = y[k], b = y[k + n32];
     a.x += v.x, a.y += v.y, b.x += v.z, b.y += v.w;
@@ -223,21 +230,22 @@ __global__ void __launch_bounds__(kBtThreads) slot_acc_kernel(double2* y, float4
 }
 
 // y32[slot] = nearest FP32 of x64
-__global__ void __launch_bounds__(kBtThreads) slot_conv_kernel(float4* y, const double2* x, long long n32, int nrhs,
-                                                               int r) {
+__global__ void __launch_bounds__(kBtThreads) slot_conv_kernel(float4* y, const double2* x, long long n32, unsigned vh,
+                                                               int nrhs, int r) {
   for (long long k = blockIdx.x * (long long)kBtThreads + threadIdx.x; k < n32; k += (long long)gridDim.x * kBtThreads) {
     const double2 a = x[k], b = x[k + n32];
-    y[k * nrhs + r] = make_float4(__double2float_rn(a.x), __double2float_rn(a.y), __double2float_rn(b.x),
+    y[slot_at(k, vh, n32, nrhs, r)] = make_float4(__double2float_rn(a.x), __double2float_rn(a.y), __double2float_rn(b.x),
                                   __double2float_rn(b.y));
   }
 }
 
 // partials of Re<r, p> and |r|^2 of one slot
 __global__ void __launch_bounds__(kBtThreads) slot_dots_kernel(const float4* rv, const float4* pv, long long n32,
-                                                               int nrhs, int r, double* part) {
+                                                               unsigned vh, int nrhs, int r, double* part) {
   float rp = 0.f, rr = 0.f;
   for (long long k = blockIdx.x * (long long)kBtThreads + threadIdx.x; k < n32; k += (long long)gridDim.x * kBtThreads) {
-    const float4 a = rv[k * nrhs + r], b = pv[k * nrhs + r];
+    const long long e = slot_at(k, vh, n32, nrhs, r);
+    const float4 a = rv[e], b = pv[e];
     rp = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, rp))));
     rr += sq4(a);
   }
@@ -253,11 +261,13 @@ __global__ void __launch_bounds__(kSumThreads) slot_coef_kernel(const double* pa
 }
 
 // p[slot] += c r[slot]
-__global__ void __launch_bounds__(kBtThreads) slot_project_kernel(float4* pv, const float4* rv, long long n32, int nrhs,
-                                                                  int r, const float* cp) {
+__global__ void __launch_bounds__(kBtThreads) slot_project_kernel(float4* pv, const float4* rv, long long n32, unsigned vh,
+                                                                  int nrhs, int r, const float* cp) {
   const float c = *cp;
-  for (long long k = blockIdx.x * (long long)kBtThreads + threadIdx.x; k < n32; k += (long long)gridDim.x * kBtThreads)
-    pv[k * nrhs + r] = axpy4(c, rv[k * nrhs + r], pv[k * nrhs + r]);
+  for (long long k = blockIdx.x * (long long)kBtThreads + threadIdx.x; k < n32; k += (long long)gridDim.x * kBtThreads) {
+    const long long e = slot_at(k, vh, n32, nrhs, r);
+    pv[e] = axpy4(c, rv[e], pv[e]);
+  }
 }
 
 // the reliable update's outcome for one system, on the device: stop once the
@@ -489,11 +499,12 @@ struct BatchSolver {
     const ItemPlan& P = plan[k];
     const long long n32 = (long long)(P.half32 / 16);
     const int nr = items[k].nrhs, nb = slot_blocks(n32);
-    slot_conv_kernel<<<nb, kBtThreads, 0, s>>>(P.r32, reinterpret_cast<const double2*>(thc), n32, nr, r);
-    slot_dots_kernel<<<nb, kBtThreads, 0, s>>>(P.r32, P.p32, n32, nr, r, opart);
+    const unsigned vh = (unsigned)P.c32.g.Vh;
+    slot_conv_kernel<<<nb, kBtThreads, 0, s>>>(P.r32, reinterpret_cast<const double2*>(thc), n32, vh, nr, r);
+    slot_dots_kernel<<<nb, kBtThreads, 0, s>>>(P.r32, P.p32, n32, vh, nr, r, opart);
     float* c = reinterpret_cast<float*>(scal + 8);
     slot_coef_kernel<<<1, kSumThreads, 0, s>>>(opart, nb, c);
-    slot_project_kernel<<<nb, kBtThreads, 0, s>>>(P.p32, P.r32, n32, nr, r, c);
+    slot_project_kernel<<<nb, kBtThreads, 0, s>>>(P.p32, P.r32, n32, vh, nr, r, c);
   }
 
   // one iteration of every system
@@ -548,7 +559,7 @@ int cg_solve_batch(const bsm_cg_batch_item* items, int count, const bsm_cg_opts&
       S.active = S.rhs2 > 0.0;
       cudaMemsetAsync(B.x_of(k, r), 0, 2 * P.half64, s);
       slot_conv_kernel<<<slot_blocks((long long)(P.half32 / 16)), kBtThreads, 0, s>>>(
-          P.r32, P.bp[r], (long long)(P.half32 / 16), items[k].nrhs, r);
+          P.r32, P.bp[r], (long long)(P.half32 / 16), (unsigned)P.c32.g.Vh, items[k].nrhs, r);
     }
   }
   cudaMemcpyAsync(B.st, hs.data(), sizeof(SysState) * nsys, cudaMemcpyHostToDevice, s);
@@ -614,7 +625,7 @@ int cg_solve_batch(const bsm_cg_batch_item* items, int count, const bsm_cg_opts&
         const ItemPlan& P = B.plan[k];
         const long long n32 = (long long)(P.half32 / 16);
         slot_acc_kernel<<<slot_blocks(n32), kBtThreads, 0, s>>>(reinterpret_cast<double2*>(B.x_of(k, r)), P.x32, n32,
-                                                               items[k].nrhs, r);
+                                                               (unsigned)P.c32.g.Vh, items[k].nrhs, r);
         const int n = B.true_residual(k, r, B.opart + kBlasMaxBlocks);
         if (n < 0) return n;
         B.restart_slot(k, r);
@@ -637,7 +648,7 @@ int cg_solve_batch(const bsm_cg_batch_item* items, int count, const bsm_cg_opts&
       if (hs[sys].active) {  // not stopped: fold in the last FP32 steps
         const long long n32 = (long long)(P.half32 / 16);
         slot_acc_kernel<<<slot_blocks(n32), kBtThreads, 0, s>>>(reinterpret_cast<double2*>(B.x_of(k, r)), P.x32,
-                                                               n32, items[k].nrhs, r);
+                                                               n32, (unsigned)P.c32.g.Vh, items[k].nrhs, r);
       }
       const int nn = B.true_residual(k, r, B.opart);
       if (nn < 0) return nn;

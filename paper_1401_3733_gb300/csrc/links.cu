@@ -240,9 +240,10 @@ __global__ void links_to_rep_kernel(const double2* __restrict__ Uc, void* __rest
 }
 
 // canonical [nrhs][V][4][d] FP64 <-> device layout (RHS index innermost), one
-// thread per (RHS, site)
+// thread per (RHS, site); plane-major (the single-RHS layout) or site-major
+// (the multi-RHS layout, a site's planes of all RHS contiguous)
 __global__ void pack_spinor_kernel(const double2* __restrict__ canon, void* __restrict__ dev, int4 dims, int d,
-                                   int prec, int unpack, int nrhs) {
+                                   int prec, int unpack, int nrhs, int site_major) {
   const int V = dims.x * dims.y * dims.z * dims.w;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (tid >= (long long)V * nrhs) return;
@@ -254,25 +255,29 @@ __global__ void pack_spinor_kernel(const double2* __restrict__ canon, void* __re
   const int x = r % dims.y;
   const int t = r / dims.y;
   const int p = (t + x + y + z) & 1;
-  // element (plane q, eo site, rhs) sits at q * Vh * nrhs + (eo site * nrhs + rhs)
+  // element (plane q of P, eo site, rhs) sits at q * Vh * nrhs + (eo site * nrhs + rhs),
+  // or site-major at (eo site * P + q) * nrhs + rhs
   const size_t i = (size_t)(s >> 1) * nrhs + rhs;
   const size_t Vh = (size_t)V / 2 * nrhs;
+  auto at = [&](int q, int P) -> size_t {
+    return site_major ? ((size_t)(s >> 1) * P + q) * nrhs + rhs : (size_t)q * Vh + i;
+  };
   double2* cs = const_cast<double2*>(canon) + ((size_t)rhs * V + s) * 4 * d;
   if (prec == BSM_F64) {
     double2* blk = reinterpret_cast<double2*>(dev) + (size_t)p * 4 * d * Vh;
     for (int q = 0; q < 4 * d; ++q) {
-      if (unpack) cs[q] = blk[q * Vh + i];
-      else blk[q * Vh + i] = cs[q];
+      if (unpack) cs[q] = blk[at(q, 4 * d)];
+      else blk[at(q, 4 * d)] = cs[q];
     }
   } else if (prec == BSM_DF64) {
     float4* blk = reinterpret_cast<float4*>(dev) + (size_t)p * 4 * d * Vh;
     for (int q = 0; q < 4 * d; ++q) {
       if (unpack) {
-        const float4 v = blk[q * Vh + i];
+        const float4 v = blk[at(q, 4 * d)];
         cs[q] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
       } else {
         const df re(cs[q].x), im(cs[q].y);
-        blk[q * Vh + i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        blk[at(q, 4 * d)] = make_float4(re.hi, re.lo, im.hi, im.lo);
       }
     }
   } else if (prec == BSM_BF16) {
@@ -281,13 +286,13 @@ __global__ void pack_spinor_kernel(const double2* __restrict__ canon, void* __re
       for (int a = 0; a < d; ++a) {
         const int q = sp * d + a;
         if (unpack) {
-          const uint2 v = blk[q * Vh + i];
+          const uint2 v = blk[at(q, 2 * d)];
           const float2 u = bf2_to_f2(v.x), l = bf2_to_f2(v.y);
           cs[sp * d + a] = make_double2(u.x, u.y);
           cs[(sp + 2) * d + a] = make_double2(l.x, l.y);
         } else {
           const double2 u = cs[sp * d + a], w = cs[(sp + 2) * d + a];
-          blk[q * Vh + i] = make_uint2(f2_to_bf2((float)u.x, (float)u.y), f2_to_bf2((float)w.x, (float)w.y));
+          blk[at(q, 2 * d)] = make_uint2(f2_to_bf2((float)u.x, (float)u.y), f2_to_bf2((float)w.x, (float)w.y));
         }
       }
   } else {
@@ -296,12 +301,12 @@ __global__ void pack_spinor_kernel(const double2* __restrict__ canon, void* __re
       for (int a = 0; a < d; ++a) {
         const int q = sp * d + a;
         if (unpack) {
-          const float4 v = blk[q * Vh + i];
+          const float4 v = blk[at(q, 2 * d)];
           cs[sp * d + a] = make_double2(v.x, v.y);
           cs[(sp + 2) * d + a] = make_double2(v.z, v.w);
         } else {
           const double2 u = cs[sp * d + a], w = cs[(sp + 2) * d + a];
-          blk[q * Vh + i] = make_float4(__double2float_rn(u.x), __double2float_rn(u.y), __double2float_rn(w.x),
+          blk[at(q, 2 * d)] = make_float4(__double2float_rn(u.x), __double2float_rn(u.y), __double2float_rn(w.x),
                                         __double2float_rn(w.y));
         }
       }
@@ -351,12 +356,13 @@ int links_to_rep_launch(const bsm_lattice& L, const double* U, void* out, int pr
 }
 
 void pack_spinor_launch(const bsm_lattice& L, const double* canon, void* dev, int d, int prec, bool unpack,
-                        int nrhs, cudaStream_t s) {
+                        int nrhs, bool site_major, cudaStream_t s) {
   const int4 dims = make_int4(L.dims[0], L.dims[1], L.dims[2], L.dims[3]);
   const long long n = (long long)L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3] * nrhs;
   const int threads = 128;
   pack_spinor_kernel<<<(int)((n + threads - 1) / threads), threads, 0, s>>>(reinterpret_cast<const double2*>(canon),
-                                                                            dev, dims, d, prec, unpack ? 1 : 0, nrhs);
+                                                                            dev, dims, d, prec, unpack ? 1 : 0, nrhs,
+                                                                            site_major ? 1 : 0);
 }
 
 }  // namespace bsm

@@ -3,13 +3,17 @@
 // from memory once per site and applied to all RHS, which raises the
 // arithmetic intensity from ~1 to ~n_rhs/2 flop per byte.
 //
-// Multi-RHS spinor layout: the single-RHS layout with the RHS index
-// innermost, element (plane, site, rhs) at (plane*V_h + site)*n_rhs + rhs, so
-// SpinorIO addresses it as a field of V_h*n_rhs "sites".  One thread owns one
-// output site and a block of RB consecutive RHS; the RB spinors live in
-// registers and each link element, loaded once through L1 (the other RHS
-// blocks of the same site reuse it from there), multiplies all of them.
+// Multi-RHS spinor layout (site-major): the 2d planes of the single-RHS
+// FP32/BF16 layout with the RHS index innermost, element (plane, site, rhs)
+// at (site*2d + plane)*n_rhs + rhs, so that a site's spinors of all RHS are
+// one contiguous block of 2d*n_rhs elements, which SpinorIO addresses as a
+// field of n_rhs "sites" (mrhs_block).  One thread owns one output site and
+// a block of RB consecutive RHS; the RB spinors live in registers and each
+// link element, loaded once through L1 (the other RHS blocks of the same site
+// reuse it from there), multiplies all of them.
 #pragma once
+
+#include <type_traits>
 
 #include "f32x2.cuh"
 #include "hop.cuh"
@@ -35,19 +39,31 @@ __device__ __forceinline__ float epi_a<float, MrhsArgs>(const MrhsArgs& A) { ret
 template <>
 __device__ __forceinline__ float epi_b<float, MrhsArgs>(const MrhsArgs& A) { return A.bf; }
 
+// site n's block of a multi-RHS FP32 (float4 elements) or BF16 (uint2)
+// half spinor: 2d planes of n_rhs elements
+template <typename P, int D>
+__device__ __forceinline__ const void* mrhs_block(const void* base, int n, size_t nr) {
+  constexpr size_t elem = std::is_same<P, BF16>::value ? sizeof(uint2) : sizeof(float4);
+  return static_cast<const char*>(base) + (size_t)(unsigned)n * (2 * D) * nr * elem;
+}
+template <typename P, int D>
+__device__ __forceinline__ void* mrhs_block(void* base, int n, size_t nr) {
+  return const_cast<void*>(mrhs_block<P, D>(static_cast<const void*>(base), n, nr));
+}
+
 template <int MU, int FB, typename P, int D, bool REAL, int RB, bool L2IN = false>
 __device__ __forceinline__ void mrhs_sense(const MrhsArgs& A, const typename LinkIO<P, D, REAL>::vec* lt, int n,
                                            int r0, typename P::R sg, cx<typename P::R> (&acc)[RB][4][D]) {
   using R = typename P::R;
   using L = LinkIO<P, D, REAL>;
   const size_t nr = (size_t)A.nrhs;
-  const size_t Vn = (size_t)A.g.Vh * nr;
+  const void* blk = mrhs_block<P, D>(A.in, n, nr);
   cx<R> h[RB][2][D];
 #pragma unroll
   for (int j = 0; j < RB; ++j) {
     cx<R> psi[4][D];
-    if constexpr (L2IN) SpinorIO<P, D>::template load<true>(A.in, Vn, (int)((size_t)n * nr + r0 + j), psi);
-    else SpinorIO<P, D>::load(A.in, Vn, (int)((size_t)n * nr + r0 + j), psi);
+    if constexpr (L2IN) SpinorIO<P, D>::template load<true>(blk, nr, r0 + j, psi);
+    else SpinorIO<P, D>::load(blk, nr, r0 + j, psi);
     spin_project<MU>(psi, sg, h[j]);
   }
 #pragma unroll
@@ -108,15 +124,14 @@ __device__ __forceinline__ void mrhs_site(const MrhsArgs& A, int i, int r0) {
   mrhs_direction<3, P, D, REAL, RB, L2IN>(A, lt, nf[3], nb[3], r0, sg, acc);
 
   const size_t nr = (size_t)A.nrhs;
-  const size_t Vn = (size_t)A.g.Vh * nr;
   const R b = epi_b<R>(A);
 #pragma unroll
   for (int j = 0; j < RB; ++j) {
-    const int e = (int)((size_t)i * nr + r0 + j);
+    const int e = r0 + j;
     if (A.x != nullptr) {
       const R a = epi_a<R>(A);
       cx<R> xs[4][D];
-      SpinorIO<P, D>::load(A.x, Vn, e, xs);
+      SpinorIO<P, D>::load(mrhs_block<P, D>(A.x, i, nr), nr, e, xs);
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -128,7 +143,7 @@ __device__ __forceinline__ void mrhs_site(const MrhsArgs& A, int i, int r0) {
 #pragma unroll
         for (int c = 0; c < D; ++c) acc[j][s][c] = cmake(b * acc[j][s][c].re, b * acc[j][s][c].im);
     }
-    SpinorIO<P, D>::store(A.out, Vn, e, acc[j]);
+    SpinorIO<P, D>::store(mrhs_block<P, D>(A.out, i, nr), nr, e, acc[j]);
   }
 }
 
@@ -193,7 +208,7 @@ __device__ __forceinline__ void mrhs_sense_paired(const MrhsArgs& A, const typen
                                                   int r0, float sg, cxp (&acc)[NP][4][D]) {
   using L = LinkIO<P, D, REAL>;
   const size_t nr = (size_t)A.nrhs;
-  const size_t Vn = (size_t)A.g.Vh * nr;
+  const void* blk = mrhs_block<P, D>(A.in, n, nr);
   cxp H[NP][2][D];
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
@@ -201,9 +216,9 @@ __device__ __forceinline__ void mrhs_sense_paired(const MrhsArgs& A, const typen
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
       cx<float> psi[4][D];
-      const int e = (int)((size_t)n * nr + r0 + 2 * j + l);
-      if constexpr (L2IN) SpinorIO<P, D>::template load<true>(A.in, Vn, e, psi);
-      else SpinorIO<P, D>::load(A.in, Vn, e, psi);
+      const int e = r0 + 2 * j + l;
+      if constexpr (L2IN) SpinorIO<P, D>::template load<true>(blk, nr, e, psi);
+      else SpinorIO<P, D>::load(blk, nr, e, psi);
       spin_project<MU>(psi, sg, h[l]);
     }
 #pragma unroll
@@ -274,7 +289,6 @@ __device__ __forceinline__ void mrhs_site_paired(const MrhsArgs& A, int i, int r
   mrhs_sense_paired<3, 1, P, D, REAL, NP, L2IN>(A, lt, nb[3], r0, -sg, acc);
 
   const size_t nr = (size_t)A.nrhs;
-  const size_t Vn = (size_t)A.g.Vh * nr;
   const float b = epi_b<float>(A);
 #pragma unroll
   for (int j = 0; j < NP; ++j)
@@ -290,11 +304,11 @@ __device__ __forceinline__ void mrhs_site_paired(const MrhsArgs& A, int i, int r
           up2(acc[j][sp][a].im, i0v, i1v);
           o[sp][a] = l == 0 ? cmake(r0v, i0v) : cmake(r1v, i1v);
         }
-      const int e = (int)((size_t)i * nr + r0 + 2 * j + l);
+      const int e = r0 + 2 * j + l;
       if (A.x != nullptr) {
         const float a = epi_a<float>(A);
         cx<float> xs[4][D];
-        SpinorIO<P, D>::load(A.x, Vn, e, xs);
+        SpinorIO<P, D>::load(mrhs_block<P, D>(A.x, i, nr), nr, e, xs);
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
@@ -306,7 +320,7 @@ __device__ __forceinline__ void mrhs_site_paired(const MrhsArgs& A, int i, int r
 #pragma unroll
           for (int c = 0; c < D; ++c) o[sp][c] = cmake(b * o[sp][c].re, b * o[sp][c].im);
       }
-      SpinorIO<P, D>::store(A.out, Vn, e, o);
+      SpinorIO<P, D>::store(mrhs_block<P, D>(A.out, i, nr), nr, e, o);
     }
 }
 

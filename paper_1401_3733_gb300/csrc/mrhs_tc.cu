@@ -34,15 +34,18 @@
 // per-site link blocks (cp.async, 8 bytes per element) while it computes the
 // current ones.  Every warp runs through its site's 8 direction-senses as a
 // stream of items and copies item j + S - 2 (the neighbour's multi-RHS spinor
-// block, 2d plane rows of n_rhs words, as 16-byte cp.async pieces of the
-// lanes) into an S-stage ring of its shared memory while it computes item j;
-// the same-site input of the a x + b H form is copied the same way during the
-// site.  The grid is persistent.  On 24^4 x 12 RHS at d = 6 the copies alone
-// take about 0.48 ms per D and the arithmetic alone 0.40 ms; overlapped,
-// 0.56 ms.  (Moving half or all of each item by TMA tile copies, completing
-// on mbarriers, measured slower: 0.73 and 0.66 ms; so did copying the 4
-// sites' neighbour blocks as one slab per block, 0.57 ms, and staging only
-// their z neighbours once per block, 5 blocks in place of 8, 0.561 ms.)
+// block, 2d plane rows of n_rhs words, one contiguous run in the site-major
+// multi-RHS layout, as 16-byte cp.async pieces of the lanes) into an S-stage
+// ring of its shared memory while it computes item j; the same-site input of
+// the a x + b H form is copied the same way during the site.  The grid is
+// persistent.  The copies bound the kernel: on 24^4 x 12 RHS at d = 6 it
+// takes 0.50 ms per D, against 0.56 ms when each block was 2d rows 16 MB
+// apart (plane-major), where the copies alone took 0.48 ms and the arithmetic
+// alone 0.40 ms.  (In that layout, moving half or all of each item by TMA
+// tile copies, completing on mbarriers, measured slower: 0.73 and 0.66 ms; so
+// did copying the 4 sites' neighbour blocks as one slab per block, 0.57 ms,
+// and staging only their z neighbours once per block, 5 blocks in place of
+// 8, 0.561 ms.)
 #include "mrhs.cuh"
 
 namespace bsm {
@@ -71,6 +74,7 @@ struct TcLayout {
   static constexpr int block_bytes = links_off + 2 * link_buf;
   static constexpr int link_elems = kTcWarps * 4 * D * D;  // elements of a quad's links
   static constexpr int row_chunks = NR / 2;                // 16-byte pieces of a plane row
+  static constexpr int block_src = 2 * D * NR * 8;         // a site's block in memory: 2d rows, unpadded
   static constexpr int chunks = 2 * D * row_chunks;        // pieces of a block
   static constexpr int per_lane = (chunks + 31) / 32;
   static constexpr int NT = NR / 4;                        // 8-column tiles
@@ -244,14 +248,14 @@ struct TcLane {
   unsigned rdh;    // to RHS 8 NGF + (g & 3) instead of g
   unsigned la;     // link element (g, c) within a site's link block; (g, c') is d/2 elements on
   unsigned amask;
-  size_t src[L::per_lane];  // cp.async piece k of a block at site 0 (bytes from the field base)
+  unsigned src[L::per_lane];  // cp.async piece k of a site's block (bytes from its start)
   unsigned dst[L::per_lane];
-  __device__ __forceinline__ void init(int lane, int Vh) {
+  __device__ __forceinline__ void init(int lane) {
 #pragma unroll
     for (int k = 0; k < L::per_lane; ++k) {
       const int cc = min(lane + 32 * k, L::chunks - 1);
       const int plane = cc / L::row_chunks, w = cc % L::row_chunks;
-      src[k] = (size_t)plane * Vh * NR * 8 + (size_t)w * 16;
+      src[k] = (unsigned)cc * 16;  // the site's block is contiguous
       dst[k] = (unsigned)(plane * L::pitch + w * 16);
     }
     const int g = lane >> 2, t = lane & 3;
@@ -348,7 +352,7 @@ __global__ void __launch_bounds__(32 * kTcWarps, kTcBlocksPerSm) hop_mrhs_tc_ker
   const unsigned xbuf = ring + S * L::spin_bytes;
   const unsigned links = base + L::links_off;
   TcLane<D, NR> ln;
-  ln.init(lane, A.g.Vh);
+  ln.init(lane);
   TcGeom geo;
   geo.init(A.g);
   __syncthreads();
@@ -374,7 +378,7 @@ __global__ void __launch_bounds__(32 * kTcWarps, kTcBlocksPerSm) hop_mrhs_tc_ker
   // the next quad's links, at step 1 the site's x block), so the group of
   // item j is complete once at most S - 2 newer groups are pending.
   auto issue = [&](unsigned st, const char* field, int n) {  // site n's block of `field` into st
-    const char* src = field + (size_t)(unsigned)n * (NR * 8);
+    const char* src = field + (size_t)(unsigned)n * L::block_src;
 #pragma unroll
     for (int c = 0; c < L::per_lane; ++c)
       if (L::chunks % 32 == 0 || lane + 32 * c < L::chunks) cp_async16_cg(st + ln.dst[c], src + ln.src[c]);
@@ -441,14 +445,14 @@ __global__ void __launch_bounds__(32 * kTcWarps, kTcBlocksPerSm) hop_mrhs_tc_ker
 #pragma unroll
           for (int s = 0; s < 2; ++s) {
             const int plane = s * D + g;
-            const size_t off = (((size_t)plane * Vh + site) * NR + r) * 8;
+            const size_t off = (size_t)(unsigned)site * L::block_src + (size_t)(plane * NR + r) * 8;
             const unsigned xs = xbuf + (unsigned)(plane * L::pitch + r * 8);
             tc_store(A, out, off, with_x, xs, cu[2 * kk + s], cl[2 * kk + s]);
           }
         }
         if constexpr (L::HALF) {
           const int r = 8 * L::NGF + 2 * (t & 1), plane = (t >> 1) * D + g;
-          const size_t off = (((size_t)plane * Vh + site) * NR + r) * 8;
+          const size_t off = (size_t)(unsigned)site * L::block_src + (size_t)(plane * NR + r) * 8;
           const unsigned xs = xbuf + (unsigned)(plane * L::pitch + r * 8);
           tc_store(A, out, off, with_x, xs, cu[2 * L::NGF], cl[2 * L::NGF]);
         }

@@ -56,6 +56,31 @@ def test_mrhs_pack_roundtrip(prec):
         assert (np.abs(part(back) - part(want)) <= bound * np.abs(part(want))).all()
 
 
+def test_mrhs_layout_is_site_major():
+    """The documented multi-RHS layout, read back byte for byte: FP32 element
+    (plane q = s d + c, eo site i, RHS r) of parity p sits at
+    (p V_h + i) 2d n_rhs + q n_rhs + r as the float4 (psi[s][c], psi[s+2][c])
+    of RHS r, with eo site i = canonical index >> 1 (z fastest)."""
+    dims = (4, 2, 2, 6)
+    d, nrhs = 3, 5
+    lat = bsm.lattice(dims, 3)
+    psis = np.stack([fields.gaussian_spinor(dims, d, 70 + r) for r in range(nrhs)])  # [r][V][4][d]
+    dev = pack(lat, list(psis), bsm.F32)
+    torch.cuda.synchronize()
+    V = int(np.prod(dims))
+    got = dev.cpu().numpy().view(np.float32).reshape(2, V // 2, 2 * d, nrhs, 4)
+    t, x, y, z = np.unravel_index(np.arange(V), dims)
+    par, i = (t + x + y + z) & 1, np.arange(V) >> 1
+    want = np.full_like(got, np.nan)
+    for r in range(nrhs):
+        for s in range(2):
+            for c in range(d):
+                up, lo = psis[r, :, s, c], psis[r, :, s + 2, c]
+                for k, v in enumerate((up.real, up.imag, lo.real, lo.imag)):
+                    want[par, i, s * d + c, r, k] = v.astype(np.float32)
+    assert np.array_equal(got, want)
+
+
 @pytest.mark.parametrize("prec", [bsm.F32, bsm.BF16], ids=["f32", "bf16"])
 @pytest.mark.parametrize("N,rep", REP_CASES, ids=REP_IDS)
 def test_mrhs_all_reps(N, rep, prec):

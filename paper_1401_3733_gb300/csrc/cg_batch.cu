@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(kBtThreads) slot_conv_kernel(float4* y, const 
                                                                int nrhs, int r) {
   for (long long k = blockIdx.x * (long long)kBtThreads + threadIdx.x; k < n32; k += (long long)gridDim.x * kBtThreads) {
     const double2 a = x[k], b = x[k + n32];
-    y[slot_at(k, vh, n32, nrhs, r)] = make_float4(__double2float_rn(a.x), __double2float_rn(a.y), __double2float_rn(b.x),
-                                  __double2float_rn(b.y));
+    y[slot_at(k, vh, n32, nrhs, r)] =
+        make_float4(__double2float_rn(a.x), __double2float_rn(a.y), __double2float_rn(b.x), __double2float_rn(b.y));
   }
 }
 

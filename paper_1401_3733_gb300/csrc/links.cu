@@ -307,7 +307,7 @@ __global__ void pack_spinor_kernel(const double2* __restrict__ canon, void* __re
         } else {
           const double2 u = cs[sp * d + a], w = cs[(sp + 2) * d + a];
           blk[at(q, 2 * d)] = make_float4(__double2float_rn(u.x), __double2float_rn(u.y), __double2float_rn(w.x),
-                                        __double2float_rn(w.y));
+                                          __double2float_rn(w.y));
         }
       }
   }
